@@ -1,0 +1,218 @@
+/*
+ * calclens.h - C ABI of the GB300 lens-plane library (libcalclens_gb300.so).
+ *
+ * The library computes the hot path of curved-sky multiple-plane weak-lensing
+ * ray tracing (Becker 2012, "CALCLENS"): particle binning to HEALPix pixels,
+ * the spherical-harmonic (SHT) Poisson solve of a lens plane, the SHT+MG
+ * multigrid refinement on bundle patches, the deflection / shear derivatives
+ * and the multiple-plane ray recursion.  Every step runs in hand-written CUDA
+ * kernels for sm_103a.
+ *
+ * Conventions shared by all calls
+ * -------------------------------
+ * - Pointers are DEVICE pointers (caller-owned, already allocated) unless the
+ *   argument name ends in _host.  The library never frees caller memory.
+ * - Maps are HEALPix RING-ordered FP64 arrays of 12 nside^2 values unless an
+ *   `ordering` argument says otherwise; nside must be a power of two in
+ *   [1, 8192].  Positions are (z = cos theta, phi) in FP64, phi in [0, 2 pi].
+ * - Spherical-harmonic coefficients a_lm (m >= 0, l <= lmax) are complex FP64
+ *   stored as interleaved (re, im) pairs, packed m-major:
+ *   index(l, m) = m (2 lmax + 1 - m) / 2 + l, (lmax + 1)(lmax + 2) / 2 pairs.
+ *   Y_lm are orthonormal with the Condon-Shortley phase.
+ * - Calls are asynchronous on the context's stream and return a status
+ *   code before completion; clc_sync() waits and reports device-side errors.
+ *   Argument errors are reported as CLC_EINVAL before anything is launched.
+ *   No exception crosses the ABI.  A context is not thread-safe.
+ * - Lens fields are given in the orthonormal (theta-hat, phi-hat) basis with
+ *   the conventions of the paper's Appendix A: alpha = -grad psi,
+ *   U_ab = covariant Hessian of psi, kappa = U_tt + U_pp (twice the standard
+ *   convergence, Eq. lenspoisson), gamma_1 = (U_tt - U_pp) / 2, gamma_2 = U_tp.
+ */
+#ifndef CALCLENS_H
+#define CALCLENS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+  CLC_OK = 0,
+  CLC_EINVAL = 1,        /* invalid argument; nothing was launched            */
+  CLC_ENOMEM = 2,        /* device allocation failed                          */
+  CLC_ECUDA = 3,         /* a CUDA runtime call or kernel failed              */
+  CLC_ENOTCONVERGED = 4, /* MG hit max_cycles above tol; outputs are written  */
+  CLC_ETIMEOUT = 5       /* a bounded device-side wait gave up                */
+};
+
+enum { CLC_RING = 0, CLC_NEST = 1 };             /* HEALPix ordering        */
+enum { CLC_FP64 = 0, CLC_FP32 = 1, CLC_MIXED = 2 }; /* arithmetic of a solve */
+enum { CLC_SOLVER_SHT = 0, CLC_SOLVER_SHTMG = 1 }; /* plane Poisson solver    */
+
+typedef struct clc_ctx clc_ctx;
+typedef struct clc_plane_solution clc_plane_solution;
+
+/* Output lens fields; any pointer may be NULL to skip that field.  Each is a
+ * device FP64 array with one value per point (pixel or ray). */
+typedef struct clc_derivs {
+  double* a_th; /* alpha_theta */
+  double* a_ph; /* alpha_phi   */
+  double* u_tt; /* U_theta-theta */
+  double* u_pp; /* U_phi-phi     */
+  double* u_tp; /* U_theta-phi   */
+} clc_derivs;
+
+/* Parameters of the SHT+MG plane solver (paper Sec. 3.2). */
+typedef struct clc_mg_params {
+  int nside_sht;    /* HEALPix Nside of the global SHT step                  */
+  int lmax;         /* SHT band limit, lmax <= 4 nside_sht                   */
+  int nside_bundle; /* Nside of the bundle cells; one MG patch per bundle    */
+  int ncell;        /* cells per patch side on the finest level (power of 2, >= 16) */
+  int nu1, nu2;     /* red-black Gauss-Seidel sweeps before / after the coarse step */
+  int max_cycles;   /* V-cycle cap when iterating to tol                     */
+  int fixed_cycles; /* > 0: run exactly this many V-cycles, ignore tol       */
+  double tol;       /* stop when max over patches ||f - L u||_2 / ||f||_2 < tol */
+  int precision;    /* CLC_FP64 (all FP64) or CLC_FP32 (FP32 fields, FP64 coarsest) */
+} clc_mg_params;
+
+/* Ray state, structure of arrays of n rays (device FP64):
+ * x[3][n] Cartesian position, beta[3][n] propagation direction,
+ * A[4][n] and Ap[4][n] the inverse magnification matrices A^(n) and A^(n-1)
+ * (row-major 2x2: A_tt, A_tp, A_pt, A_pp) in the (theta-hat, phi-hat) basis at
+ * x, and bundle[n] the NEST index of each ray's home bundle (only read by the
+ * SHT+MG solver; may be NULL for the pure-SHT solver). */
+typedef struct clc_rays {
+  int64_t n;
+  double* x;
+  double* beta;
+  double* A;
+  double* Ap;
+  int32_t* bundle;
+} clc_rays;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+
+/* Create a context on CUDA device `device` that enqueues all work on
+ * `cuda_stream` (a cudaStream_t; NULL = the legacy default stream).
+ * The context owns scratch memory, SHT plans and Legendre tables. */
+int clc_create(clc_ctx** ctx, int device, void* cuda_stream);
+int clc_destroy(clc_ctx* ctx);
+/* Wait for all enqueued work; returns CLC_ECUDA / CLC_ETIMEOUT if a kernel
+ * failed or recorded a device-side error since the last sync. */
+int clc_sync(clc_ctx* ctx);
+/* Message describing the last non-OK status of this context ("" if none). */
+const char* clc_last_error(const clc_ctx* ctx);
+/* Release cached plans and Legendre tables (they are rebuilt on demand). */
+int clc_release_caches(clc_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Step 1: binning (paper Sec. 3.2 source construction; Sec. 3.1 indexing)   */
+
+/* counts[ang2pix(nside, z[i], phi[i])] += 1 for i < n, RING or NEST ordering.
+ * The pixel index follows the HEALPix formulas of Gorski et al. (2005) with
+ * every FP64 operation correctly rounded and unfused, so indices are
+ * reproducible bit for bit.  counts (uint32[12 nside^2]) is accumulated, not
+ * cleared.  n == 0 is a no-op. */
+int clc_bin_particles(clc_ctx* ctx, const double* z, const double* phi, int64_t n,
+                      int nside, int ordering, uint32_t* counts);
+
+/* kappa[p] = scale * (counts[p] / nbar - 1) (Eq. lenspoisson for equal-mass
+ * particles, nbar = particles per pixel), each operation rounded separately. */
+int clc_counts_to_kappa(clc_ctx* ctx, const uint32_t* counts, int nside, double nbar,
+                        double scale, double* kappa);
+
+/* Coarse RING map = mean of the (nside_fine / nside_coarse)^2 NEST children of
+ * every coarse pixel (children summed in NEST order): equal to binning the
+ * same particles at nside_coarse. */
+int clc_degrade(clc_ctx* ctx, const double* map_fine, int nside_fine, double* map_coarse,
+                int nside_coarse);
+
+/* ------------------------------------------------------------------------ */
+/* Step 2: spherical-harmonic transforms and the SHT Poisson solve (Sec. 3.2) */
+
+/* a_lm = (4 pi / Npix) sum_p map[p] Y*_lm(p) (uniform quadrature). */
+int clc_sht_analysis(clc_ctx* ctx, const double* map, int nside, int lmax, double* alm);
+/* map[p] = sum_lm a_lm Y_lm(p) for a real field (m < 0 implied). */
+int clc_sht_synthesis(clc_ctx* ctx, const double* alm, int nside, int lmax, double* map);
+
+/* Pure-SHT plane solve (Sec. 3.2): analysis of kappa, psi_lm = -kappa_lm /
+ * (l (l + 1)) with psi_00 = 0, synthesis of psi (if psi != NULL) and, for the
+ * non-NULL fields of `out` (out may be NULL), the deflection and Hessian at
+ * every pixel centre synthesised directly from psi_lm.
+ * precision: CLC_FP64 (FP64 Legendre contraction) or CLC_MIXED (split
+ * hi + lo FP16 tensor-core contraction with FP32 accumulation). */
+int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int lmax, int precision,
+                    double* psi, const clc_derivs* out);
+
+/* ------------------------------------------------------------------------ */
+/* Step 3: SHT+MG plane solve (Sec. 3.2)                                      */
+
+/* Allocate the multigrid state of one plane (patches of all 12 nside_bundle^2
+ * bundles) for maps of nside_fine.  The handle is owned by the caller and
+ * freed with clc_solution_destroy. */
+int clc_solution_create(clc_ctx* ctx, int nside_fine, const clc_mg_params* params,
+                        clc_plane_solution** sol);
+int clc_solution_destroy(clc_plane_solution* sol);
+/* V-cycles run and final max residual ratio of the last solve into sol. */
+int clc_solution_info(const clc_plane_solution* sol, int* cycles_host, double* residual_host);
+
+/* SHT step at (nside_sht, lmax) on kappa_fine degraded to nside_sht, then
+ * FAS multigrid V-cycles on every bundle patch (Dirichlet values and starting
+ * guess from the SHT potential, source = kappa_fine, both by HEALPix
+ * ring-bilinear interpolation), leaving the finest-level potential in `sol`.
+ * If `out` is non-NULL, the fourth-order finite-difference lens fields are
+ * evaluated at every pixel centre of nside_fine (each pixel in its own
+ * bundle's patch).  Returns CLC_ENOTCONVERGED if max_cycles were used without
+ * reaching tol (the solution and outputs are still written). */
+int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nside_fine,
+                      const clc_mg_params* params, clc_plane_solution* sol,
+                      const clc_derivs* out);
+
+/* ------------------------------------------------------------------------ */
+/* Step 4: lens fields at arbitrary points (Sec. 3.2 derivatives)            */
+
+/* alpha and U at n points (z, phi), each evaluated in the patch of bundle[i]
+ * (NEST index at nside_bundle; NULL = the bundle containing the point):
+ * fourth-order finite differences on the finest patch level, bilinear
+ * interpolation to the point, Appendix A formulas, rotation to the global
+ * (theta-hat, phi-hat) basis. */
+int clc_lens_derivs(clc_ctx* ctx, const clc_plane_solution* sol, const double* z,
+                    const double* phi, const int32_t* bundle, int64_t n, const clc_derivs* out);
+
+/* ------------------------------------------------------------------------ */
+/* Step 5: multiple-plane ray recursion (Sec. 2.2, Appendix B)               */
+
+/* Initialise rays at unit vectors of (z, phi) on the sphere of radius chi0:
+ * x = chi0 n, beta = n, A = Ap = identity (Eq. betaprop, posprop, Atraj).
+ * If bundle is non-NULL and nside_bundle > 0, bundle[i] = NEST pixel of the
+ * ray's start at nside_bundle. */
+int clc_rays_init(clc_ctx* ctx, const double* z, const double* phi, double chi0,
+                  int nside_bundle, clc_rays* rays);
+
+/* Advance all rays from the plane at chi_n to the sphere at chi_next using
+ * the lens fields of that plane: either the SHT+MG solution `sol` (sol !=
+ * NULL; rays looked up in their home bundle's patch) or RING maps `maps` of
+ * nside_maps (sol == NULL; ring-bilinear interpolation of alpha as a tangent
+ * 3-vector and U as a tangent 3x3 tensor).  chi_prev is the previous plane
+ * (0 for the first plane).  Eq. Atraj, Eq. betaprop, Eq. posprop and the
+ * parallel transport of Appendix B. */
+int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const clc_derivs* maps,
+                 int nside_maps, double chi_prev, double chi_n, double chi_next, clc_rays* rays);
+
+/* Full driver of the paper's Sec. 3 steps 2-5 over nplanes planes: for plane m
+ * solve for its potential from kappa_planes[m] (device RING maps of nside)
+ * with the chosen solver, then advance the rays from chi_host[m] to
+ * chi_host[m + 1] (chi_host has nplanes + 1 entries; the last is the source
+ * sphere).  For CLC_SOLVER_SHT, `mg` supplies only nside_sht = nside of the
+ * maps and lmax.  The rays must have been initialised at chi_host[0]. */
+int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
+                        const double* const* kappa_planes_host, int nplanes, int nside,
+                        const double* chi_host, clc_rays* rays);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CALCLENS_H */

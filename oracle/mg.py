@@ -342,3 +342,32 @@ def home_bundle(nside_fine, nside_bundle, nest_pix):
     right shift by 2 log2(Nf / N_b) bits (Sec. 3.1)."""
     shift = 2 * (hp.nside_order(nside_fine) - hp.nside_order(nside_bundle))
     return torch.as_tensor(nest_pix) >> shift
+
+
+def solve_plane(kappa_fine, nside_fine, nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2,
+                tol=1e-10, max_cycles=60, fixed_cycles=None, bundles=None, coarsest=8):
+    """The whole SHT+MG plane solve of Sec. 3.2 for the given bundles (all by
+    default): degrade kappa to the SHT grid, SHT Poisson solve, patch set-up,
+    V-cycles.  Returns dict with R, h, u (interior [B, N, N]), partials,
+    bundles, cycles, residual and psi_sht."""
+    from . import binning, sht
+    if bundles is None:
+        bundles = torch.arange(12 * nside_bundle * nside_bundle)
+    bundles = torch.as_tensor(bundles)
+    ks = binning.degrade_ring(kappa_fine, nside_fine, nside_sht)
+    psi_sht = sht.poisson_sht(ks, nside_sht, lmax, derivatives=False)["psi"]
+    R, h, u, f, ghosts = setup_patches(kappa_fine, nside_fine, psi_sht, nside_sht, nside_bundle, bundles,
+                                       ncell=ncell, coarsest=coarsest)
+    S = PatchSolver(ncell, h, ghosts, nu1=nu1, nu2=nu2, coarsest=coarsest)
+    cycles, rr = S.solve(u, f, tol=tol, max_cycles=max_cycles, fixed_cycles=fixed_cycles)
+    ui = u[:, 1:-1, 1:-1].clone()
+    return {"R": R, "h": h, "u": ui, "partials": fd_partials(ui, h), "bundles": bundles, "cycles": cycles,
+            "residual": rr, "psi_sht": psi_sht}
+
+
+def fields_at(sol, nside_bundle, nvec, home):
+    """Lens fields at unit vectors nvec[M, 3] whose home bundles are home[M]
+    (NEST indices at nside_bundle) from a solve_plane result."""
+    lookup = {int(b): k for k, b in enumerate(sol["bundles"].tolist())}
+    idx = torch.tensor([lookup[int(b)] for b in home.tolist()], dtype=torch.long)
+    return derivs_at(sol["partials"], sol["R"], sol["h"], idx, nvec)

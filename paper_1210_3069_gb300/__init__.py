@@ -1,0 +1,285 @@
+"""Python binding of libcalclens_gb300.so (GB300 lens-plane library).
+
+Argument marshalling only: torch supplies device memory and the stream, and
+every step of the computation runs in the library's CUDA kernels.  Importing
+works without a GPU; calls need the built library (``build()``) and a CUDA
+device, and raise ``CalclensError`` otherwise - there is no CPU fallback.
+
+Names follow the C ABI in include/calclens.h (``clc_<name>`` -> ``<name>``).
+"""
+import ctypes
+import os
+
+import torch
+
+from . import builder as _build
+
+LIB_PATH = _build.LIB
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT = range(6)
+RING, NEST = 0, 1
+FP64, FP32, MIXED = 0, 1, 2
+SOLVER_SHT, SOLVER_SHTMG = 0, 1
+
+_p = ctypes.c_void_p
+_i = ctypes.c_int
+_i64 = ctypes.c_int64
+_d = ctypes.c_double
+
+
+class CalclensError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"calclens status {code}: {msg}")
+        self.code = code
+
+
+class Derivs(ctypes.Structure):
+    _fields_ = [("a_th", _p), ("a_ph", _p), ("u_tt", _p), ("u_pp", _p), ("u_tp", _p)]
+
+
+class MGParams(ctypes.Structure):
+    _fields_ = [("nside_sht", _i), ("lmax", _i), ("nside_bundle", _i), ("ncell", _i), ("nu1", _i), ("nu2", _i),
+                ("max_cycles", _i), ("fixed_cycles", _i), ("tol", _d), ("precision", _i)]
+
+
+class Rays(ctypes.Structure):
+    _fields_ = [("n", _i64), ("x", _p), ("beta", _p), ("A", _p), ("Ap", _p), ("bundle", _p)]
+
+
+_SIGS = {
+    "clc_create": (_i, [ctypes.POINTER(_p), _i, _p]),
+    "clc_destroy": (_i, [_p]),
+    "clc_sync": (_i, [_p]),
+    "clc_last_error": (ctypes.c_char_p, [_p]),
+    "clc_release_caches": (_i, [_p]),
+    "clc_bin_particles": (_i, [_p, _p, _p, _i64, _i, _i, _p]),
+    "clc_counts_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
+    "clc_degrade": (_i, [_p, _p, _i, _p, _i]),
+    "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
+    "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
+    "clc_poisson_sht": (_i, [_p, _p, _i, _i, _i, _p, ctypes.POINTER(Derivs)]),
+    "clc_solution_create": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p)]),
+    "clc_solution_destroy": (_i, [_p]),
+    "clc_solution_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
+    "clc_poisson_shtmg": (_i, [_p, _p, _i, ctypes.POINTER(MGParams), _p, ctypes.POINTER(Derivs)]),
+    "clc_lens_derivs": (_i, [_p, _p, _p, _p, _p, _i64, ctypes.POINTER(Derivs)]),
+    "clc_rays_init": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(Rays)]),
+    "clc_ray_step": (_i, [_p, _p, ctypes.POINTER(Derivs), _i, _d, _d, _d, ctypes.POINTER(Rays)]),
+    "clc_raytrace_planes": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p), _i, _i, ctypes.POINTER(_d),
+                                 ctypes.POINTER(Rays)]),
+}
+
+
+def exported_symbols():
+    """Names of the C entry points the binding expects in the library."""
+    return list(_SIGS)
+
+
+def lib():
+    """Load the shared library (it must have been built with ``build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise CalclensError(ECUDA, f"{LIB_PATH} is missing: run paper_1210_3069_gb300.build() first")
+        L = ctypes.CDLL(LIB_PATH, mode=ctypes.RTLD_GLOBAL)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def build(force=False):
+    """Compile the CUDA library in-tree (see builder.py)."""
+    global _lib
+    path = _build.build(force=force)
+    return path
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise CalclensError(EINVAL, "tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise CalclensError(EINVAL, "tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context bound to a CUDA device and (by default) torch's
+    current stream on it."""
+
+    def __init__(self, device=0, stream=None):
+        if not torch.cuda.is_available():
+            raise CalclensError(ECUDA, "no CUDA device: the library has no CPU path")
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = ctypes.c_void_p()
+        self._check(lib().clc_create(ctypes.byref(h), device, ctypes.c_void_p(stream.cuda_stream)), None)
+        self.h = h
+
+    def _check(self, rc, h=-1):
+        if rc != OK:
+            hh = self.h if h == -1 else h
+            msg = lib().clc_last_error(hh).decode() if hh else ""
+            raise CalclensError(rc, msg)
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().clc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self):
+        return self._check(lib().clc_sync(self.h))
+
+    def release_caches(self):
+        return self._check(lib().clc_release_caches(self.h))
+
+    # -- step 1 -----------------------------------------------------------
+    def bin_particles(self, z, phi, nside, ordering=RING, counts=None):
+        if counts is None:
+            counts = torch.zeros(12 * nside * nside, dtype=torch.int32, device=self.device)
+        self._check(lib().clc_bin_particles(self.h, _ptr(z), _ptr(phi), z.numel(), nside, ordering, _ptr(counts)))
+        return counts
+
+    def counts_to_kappa(self, counts, nside, nbar, scale, kappa=None):
+        if kappa is None:
+            kappa = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_counts_to_kappa(self.h, _ptr(counts), nside, float(nbar), float(scale), _ptr(kappa)))
+        return kappa
+
+    def degrade(self, fine, nside_fine, nside_coarse, out=None):
+        if out is None:
+            out = torch.empty(12 * nside_coarse ** 2, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_degrade(self.h, _ptr(fine), nside_fine, _ptr(out), nside_coarse))
+        return out
+
+    # -- step 2 -----------------------------------------------------------
+    def sht_analysis(self, m, nside, lmax):
+        alm = torch.empty((lmax + 1) * (lmax + 2) // 2, dtype=torch.complex128, device=self.device)
+        self._check(lib().clc_sht_analysis(self.h, _ptr(m), nside, lmax, _ptr(alm)))
+        return alm
+
+    def sht_synthesis(self, alm, nside, lmax):
+        out = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_sht_synthesis(self.h, _ptr(alm), nside, lmax, _ptr(out)))
+        return out
+
+    def _derivs(self, n, want):
+        t = {k: torch.empty(n, dtype=torch.float64, device=self.device) for k in want}
+        d = Derivs(*[(_ptr(t[k]) if k in t else None) for k in ("a_th", "a_ph", "u_tt", "u_pp", "u_tp")])
+        return t, d
+
+    def poisson_sht(self, kappa, nside, lmax, precision=FP64, derivatives=True, psi=True):
+        npx = 12 * nside * nside
+        out, d = self._derivs(npx, ("a_th", "a_ph", "u_tt", "u_pp", "u_tp") if derivatives else ())
+        p = torch.empty(npx, dtype=torch.float64, device=self.device) if psi else None
+        self._check(lib().clc_poisson_sht(self.h, _ptr(kappa), nside, lmax, precision, _ptr(p),
+                                          ctypes.byref(d) if derivatives else None))
+        if psi:
+            out["psi"] = p
+        return out
+
+    # -- step 3 / 4 ---------------------------------------------------------
+    def solution(self, nside_fine, params):
+        return Solution(self, nside_fine, params)
+
+    def poisson_shtmg(self, kappa_fine, nside_fine, sol, derivatives=False, check=True):
+        npx = 12 * nside_fine * nside_fine
+        out, d = self._derivs(npx, ("a_th", "a_ph", "u_tt", "u_pp", "u_tp") if derivatives else ())
+        rc = lib().clc_poisson_shtmg(self.h, _ptr(kappa_fine), nside_fine, ctypes.byref(sol.params), sol.h,
+                                     ctypes.byref(d) if derivatives else None)
+        if rc != OK and not (rc == ENOTCONVERGED and not check):
+            self._check(rc)
+        return out
+
+    def lens_derivs(self, sol, z, phi, bundle=None):
+        out, d = self._derivs(z.numel(), ("a_th", "a_ph", "u_tt", "u_pp", "u_tp"))
+        self._check(lib().clc_lens_derivs(self.h, sol.h, _ptr(z), _ptr(phi), _ptr(bundle), z.numel(), ctypes.byref(d)))
+        return out
+
+    # -- step 5 -------------------------------------------------------------
+    def rays(self, n):
+        return RayState(self, n)
+
+    def rays_init(self, rays, z, phi, chi0, nside_bundle=0):
+        self._check(lib().clc_rays_init(self.h, _ptr(z), _ptr(phi), float(chi0), int(nside_bundle),
+                                        ctypes.byref(rays.struct())))
+
+    def ray_step(self, rays, chi_prev, chi_n, chi_next, sol=None, maps=None, nside_maps=0):
+        d = None
+        if maps is not None:
+            d = Derivs(*[_ptr(maps[k]) for k in ("a_th", "a_ph", "u_tt", "u_pp", "u_tp")])
+        self._check(lib().clc_ray_step(self.h, sol.h if sol is not None else None,
+                                       ctypes.byref(d) if d is not None else None, int(nside_maps),
+                                       float(chi_prev), float(chi_n), float(chi_next), ctypes.byref(rays.struct())))
+
+    def raytrace_planes(self, solver, params, kappa_planes, nside, chi, rays):
+        n = len(kappa_planes)
+        arr = (ctypes.c_void_p * n)(*[k.data_ptr() for k in kappa_planes])
+        chis = (ctypes.c_double * len(chi))(*[float(c) for c in chi])
+        self._check(lib().clc_raytrace_planes(self.h, solver, ctypes.byref(params), arr, n, nside, chis,
+                                              ctypes.byref(rays.struct())))
+
+
+class Solution:
+    """Multigrid state of one plane (clc_plane_solution)."""
+
+    def __init__(self, ctx, nside_fine, params):
+        self.ctx = ctx
+        self.params = params
+        self.nside_fine = nside_fine
+        h = ctypes.c_void_p()
+        ctx._check(lib().clc_solution_create(ctx.h, nside_fine, ctypes.byref(params), ctypes.byref(h)))
+        self.h = h
+
+    def info(self):
+        c = ctypes.c_int()
+        r = ctypes.c_double()
+        lib().clc_solution_info(self.h, ctypes.byref(c), ctypes.byref(r))
+        return c.value, r.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.ctx.sync()
+            lib().clc_solution_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RayState:
+    """Device ray state in the library's SoA layout."""
+
+    def __init__(self, ctx, n):
+        dev = ctx.device
+        self.n = n
+        self.x = torch.empty(3, n, dtype=torch.float64, device=dev)
+        self.beta = torch.empty(3, n, dtype=torch.float64, device=dev)
+        self.A = torch.empty(4, n, dtype=torch.float64, device=dev)
+        self.Ap = torch.empty(4, n, dtype=torch.float64, device=dev)
+        self.bundle = torch.zeros(n, dtype=torch.int32, device=dev)
+
+    def struct(self):
+        return Rays(self.n, _ptr(self.x), _ptr(self.beta), _ptr(self.A), _ptr(self.Ap), _ptr(self.bundle))
+
+
+def mg_params(nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2, max_cycles=60, fixed_cycles=0, tol=1e-10,
+              precision=FP64):
+    return MGParams(nside_sht, lmax, nside_bundle, ncell, nu1, nu2, max_cycles, fixed_cycles, tol, precision)

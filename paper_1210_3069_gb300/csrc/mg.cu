@@ -1,0 +1,666 @@
+// SHT+MG plane solver (paper Sec. 3.2): the SHT potential at (nside_sht,
+// lmax) supplies Dirichlet values and the starting guess on one patch per
+// bundle cell; FAS multigrid V-cycles with red-black Gauss-Seidel relaxation
+// refine it to the fine resolution.
+//
+// Discretisation (the paper defers to Barros 1992; readings documented with
+// the oracle): patch centred on the bundle centre rotated to (pi/2, 0), side
+// 4 sqrt(pi/3) / nside_bundle, n x n cell-centred cells of spacing h,
+// (Lu)_ij = aS_i (u_{i+1,j} - u_ij) + aN_i (u_{i-1,j} - u_ij) + b_i (u_{i,j+1} + u_{i,j-1} - 2 u_ij)
+// with aS = sin t'_{i+1/2} / (h^2 sin t'_i), aN = sin t'_{i-1/2} / (h^2 sin t'_i),
+// b = 1 / (h^2 sin^2 t'_i); Dirichlet values g on the patch edge through
+// ghost cells holding 2 g - u_adjacent (the -u part folded into the
+// diagonal); area-weighted restriction; bilinear prolongation with injection
+// next to the edge; exact solve on the coarsest level.
+//
+// All patches of all levels are processed by one launch per operation; every
+// patch is an independent problem (the paper's "embarrassingly parallel"
+// MG step, Sec. 3.1), so the launches shard naturally over the SMs.
+#include <cmath>
+
+#include "mg.cuh"
+#include "patch_fd.cuh"
+
+
+namespace clc {
+
+MGView mg_view(const clc_plane_solution* sol) {
+  MGView v;
+  v.npatch = sol->npatch;
+  v.n = sol->sizes[0];
+  v.h = sol->h;
+  v.rot = (const double*)sol->rot.p;
+  v.u = sol->u[0].p;
+  v.fp32 = sol->p.precision == CLC_FP32;
+  return v;
+}
+
+__device__ __forceinline__ double edge_pos(int k, int n, double h) {
+  if (k == 0) return -0.5 * n * h;
+  if (k == n + 1) return 0.5 * n * h;
+  return ((double)k - 0.5 - 0.5 * n) * h;
+}
+
+__device__ __forceinline__ double interp_map(const double* map, int nside, double th, double ph) {
+  const Interp8 w = interp_weights(nside, th, ph);
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (w.w[k] != 0.0) v += w.w[k] * map[w.p[k]];
+  return v;
+}
+
+__global__ void k_mg_rotations(int nb, int npatch, double* rot) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= npatch) return;
+  const int64_t rp = nest2ring(nb, b);
+  int64_t j;
+  const int i = pix2ring(nb, rp, &j);
+  const Ring r = ring_geom(nb, i);
+  const double phi = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
+  const double z = r.z, s = sqrt((1.0 - z) * (1.0 + z));
+  const double cp = cos(phi), sp = sin(phi);
+  double* R = rot + 9 * (size_t)b;
+  R[0] = s * cp; R[1] = s * sp; R[2] = z;
+  R[3] = -sp;    R[4] = cp;     R[5] = 0.0;
+  R[6] = -z * cp; R[7] = -z * sp; R[8] = s;
+}
+
+// Ghost ring (2 psi_SHT at the edge faces) of one level; on the finest level
+// also the starting guess psi_SHT and the source kappa_fine at cell centres.
+template <typename T>
+__global__ void k_mg_setup(int npatch, int n, double h, const double* __restrict__ rot, const double* __restrict__ psi,
+                           int ns, const double* __restrict__ kappa, int nf, int finest, T* __restrict__ u,
+                           T* __restrict__ f) {
+  const size_t side = n + 2;
+  const size_t total = (size_t)npatch * side * side;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / (side * side));
+    const int k1 = (int)((idx / side) % side), k2 = (int)(idx % side);
+    const bool ring = k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1;
+    if (!ring && !finest) {
+      u[idx] = (T)0;
+      continue;
+    }
+    const double tp = 0.5 * kPi + edge_pos(k1, n, h), pp = edge_pos(k2, n, h);
+    const double st = sin(tp), ct = cos(tp), sp = sin(pp), cp = cos(pp);
+    const double v[3] = {st * cp, st * sp, ct};
+    const double* R = rot + 9 * (size_t)b;
+    double g[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) g[k] = R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2];
+    const double th = atan2(sqrt(g[0] * g[0] + g[1] * g[1]), g[2]);
+    double ph = atan2(g[1], g[0]);
+    if (ph < 0) ph += 2.0 * kPi;
+    const double ps = interp_map(psi, ns, th, ph);
+    if (ring) {
+      u[idx] = (T)(2.0 * ps);
+    } else {
+      u[idx] = (T)ps;
+      f[(size_t)b * n * n + (size_t)(k1 - 1) * n + (k2 - 1)] = (T)interp_map(kappa, nf, th, ph);
+    }
+  }
+}
+
+// One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == colour.
+template <typename T>
+__global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
+                         const double* __restrict__ invd, int n, int npatch, int colour) {
+  const size_t half = n / 2;
+  const size_t total = (size_t)npatch * n * half;
+  const size_t side = n + 2;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int jj = (int)(idx % half);
+    const int i = (int)((idx / half) % n);
+    const size_t b = idx / (half * n);
+    const int j = 2 * jj + ((i + colour) & 1);
+    const T aS = (T)coef[i], aN = (T)coef[n + i], bb = (T)coef[2 * n + i];
+    T* U = u + b * side * side;
+    const size_t c = (size_t)(i + 1) * side + (j + 1);
+    const T nb = aS * U[c + side] + aN * U[c - side] + bb * (U[c + 1] + U[c - 1]);
+    U[c] = (nb - f[b * n * n + (size_t)i * n + j]) * (T)invd[(size_t)i * n + j];
+  }
+}
+
+// FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
+// fine residual and of u over its 2 x 2 children.
+template <typename T>
+__global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
+                           const double* __restrict__ invd, int n, int npatch, T* __restrict__ uc,
+                           T* __restrict__ uc0, T* __restrict__ fc) {
+  const int nc = n / 2;
+  const size_t total = (size_t)npatch * nc * nc;
+  const size_t side = n + 2, sidec = nc + 2;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int J = (int)(idx % nc);
+    const int I = (int)((idx / nc) % nc);
+    const size_t b = idx / ((size_t)nc * nc);
+    const T* U = u + b * side * side;
+    const T* Fb = f + b * n * n;
+    double nr = 0.0, nu = 0.0;
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * I + di;
+      const double aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj;
+        const size_t c = (size_t)(i + 1) * side + (j + 1);
+        const double uc_ = (double)U[c];
+        const double nb = aS * (double)U[c + side] + aN * (double)U[c - side] + bb * ((double)U[c + 1] + (double)U[c - 1]);
+        const double r = (double)Fb[(size_t)i * n + j] - (nb - uc_ / invd[(size_t)i * n + j]);
+        nr += area * r;
+        nu += area * uc_;
+      }
+    }
+    const double den = 2.0 * (coef[3 * n + 2 * I] + coef[3 * n + 2 * I + 1]);
+    const T ur = (T)(nu / den);
+    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+    uc0[b * (size_t)nc * nc + (size_t)I * nc + J] = ur;
+    fc[b * (size_t)nc * nc + (size_t)I * nc + J] = (T)(nr / den);
+  }
+}
+
+// f_c += L_c(u_c) (the FAS coarse-grid source)
+template <typename T>
+__global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const double* __restrict__ coef,
+                             const double* __restrict__ invd, int n, int npatch) {
+  const size_t total = (size_t)npatch * n * n;
+  const size_t side = n + 2;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % n);
+    const int i = (int)((idx / n) % n);
+    const size_t b = idx / ((size_t)n * n);
+    const T* U = u + b * side * side;
+    const size_t c = (size_t)(i + 1) * side + (j + 1);
+    const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
+                      coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
+    f[idx] = (T)((double)f[idx] + (nb - (double)U[c] / invd[(size_t)i * n + j]));
+  }
+}
+
+// u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge
+template <typename T>
+__global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n, int npatch) {
+  const int nc = n / 2;
+  const size_t total = (size_t)npatch * n * n;
+  const size_t side = n + 2, sidec = nc + 2;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % n);
+    const int i = (int)((idx / n) % n);
+    const size_t b = idx / ((size_t)n * n);
+    const int I = i >> 1, J = j >> 1;
+    const T* C = uc + b * sidec * sidec;
+    const T* C0 = uc0 + b * (size_t)nc * nc;
+    auto e = [&](int a, int c) -> double {
+      return (double)C[(size_t)(a + 1) * sidec + (c + 1)] - (double)C0[(size_t)a * nc + c];
+    };
+    double corr;
+    if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
+      corr = e(I, J);
+    } else {
+      const int Ii = min(max(I + ((i & 1) ? 1 : -1), 0), nc - 1);
+      const int Jj = min(max(J + ((j & 1) ? 1 : -1), 0), nc - 1);
+      corr = (9.0 * e(I, J) + 3.0 * e(Ii, J) + 3.0 * e(I, Jj) + e(Ii, Jj)) / 16.0;
+    }
+    T* U = u + b * side * side;
+    const size_t c = (size_t)(i + 1) * side + (j + 1);
+    U[c] = (T)((double)U[c] + corr);
+  }
+}
+
+// Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
+// u = Minv (f - ghost contributions), in FP64.
+template <typename T>
+__global__ void k_coarse_solve(T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
+                               const double* __restrict__ minv, int nc) {
+  extern __shared__ double rhs[];
+  const size_t b = blockIdx.x;
+  const int nn = nc * nc;
+  const size_t side = nc + 2;
+  T* U = u + b * side * side;
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    const int i = t / nc, j = t % nc;
+    double g = 0.0;
+    if (i == nc - 1) g += coef[i] * (double)U[(size_t)(i + 2) * side + (j + 1)];
+    if (i == 0) g += coef[nc + i] * (double)U[(size_t)i * side + (j + 1)];
+    if (j == nc - 1) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + (j + 2)];
+    if (j == 0) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + j];
+    rhs[t] = (double)f[b * nn + t] - g;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+    double acc = 0.0;
+    for (int k = 0; k < nn; ++k) acc += minv[(size_t)t * nn + k] * rhs[k];
+    U[(size_t)(t / nc + 1) * side + (t % nc + 1)] = (T)acc;
+  }
+}
+
+// per patch: ||f - L u||^2 and ||f||^2 on the finest level
+template <typename T>
+__global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
+                          const double* __restrict__ invd, int n, double* __restrict__ norms) {
+  const size_t b = blockIdx.x;
+  const size_t side = n + 2;
+  const T* U = u + b * side * side;
+  const T* Fb = f + b * (size_t)n * n;
+  double rr = 0.0, ff = 0.0;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, j = t % n;
+    const size_t c = (size_t)(i + 1) * side + (j + 1);
+    const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
+                      coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
+    const double fv = (double)Fb[t];
+    const double r = fv - (nb - (double)U[c] / invd[t]);
+    rr += r * r;
+    ff += fv * fv;
+  }
+  __shared__ double s1[32], s2[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { s1[w] = rr; s2[w] = ff; }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    rr = l < nw ? s1[l] : 0.0;
+    ff = l < nw ? s2[l] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) {
+      rr += __shfl_xor_sync(0xffffffffu, rr, o);
+      ff += __shfl_xor_sync(0xffffffffu, ff, o);
+    }
+    if (l == 0) { norms[2 * b] = rr; norms[2 * b + 1] = ff; }
+  }
+}
+
+__global__ void k_max_ratio(const double* __restrict__ norms, int npatch, double* __restrict__ out) {
+  double mx = 0.0;
+  for (int b = threadIdx.x; b < npatch; b += blockDim.x) {
+    const double fn = sqrt(norms[2 * b + 1]);
+    const double r = sqrt(norms[2 * b]) / (fn > 0 ? fn : 1.0);
+    mx = fmax(mx, r);
+  }
+  __shared__ double s[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) out[0] = mx;
+  }
+}
+
+// lens fields at every pixel centre of nside_fine, each in its own bundle's patch
+__global__ void k_fields_at_pixels(MGView V, int nf, int nb, double* a_th, double* a_ph, double* u_tt,
+                                   double* u_pp, double* u_tp) {
+  const int64_t np = 12ll * nf * nf;
+  const int shift = 2 * (ilog2(nf) - ilog2(nb));
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j;
+    const int i = pix2ring(nf, p, &j);
+    const Ring r = ring_geom(nf, i);
+    const double phi = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
+    const int64_t pn = ang2pix_nest(nf, r.z, phi);
+    const int b = (int)(pn >> shift);
+    const double nv[3] = {r.s * cos(phi), r.s * sin(phi), r.z};
+    double o[5];
+    patch_lens_fields(V, b, nv, o);
+    if (a_th) a_th[p] = o[0];
+    if (a_ph) a_ph[p] = o[1];
+    if (u_tt) u_tt[p] = o[2];
+    if (u_pp) u_pp[p] = o[3];
+    if (u_tp) u_tp[p] = o[4];
+  }
+}
+
+__global__ void k_fields_at_points(MGView V, const double* z, const double* phi, const int32_t* bundle, int64_t n,
+                                   int nb, double* a_th, double* a_ph, double* u_tt, double* u_pp, double* u_tp) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double zz = z[k], pp = phi[k];
+    const double s = sqrt((1.0 - zz) * (1.0 + zz));
+    const double nv[3] = {s * cos(pp), s * sin(pp), zz};
+    const int b = bundle ? bundle[k] : (int)ang2pix_nest(nb, zz, pp);
+    double o[5];
+    patch_lens_fields(V, b, nv, o);
+    if (a_th) a_th[k] = o[0];
+    if (a_ph) a_ph[k] = o[1];
+    if (u_tt) u_tt[k] = o[2];
+    if (u_pp) u_pp[k] = o[3];
+    if (u_tp) u_tp[k] = o[4];
+  }
+}
+
+static int blocks_for(clc_ctx* ctx, size_t n, int threads) {
+  size_t b = (n + threads - 1) / threads;
+  const size_t cap = (size_t)num_sms(ctx) * 32;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// host: invert a dense matrix (Gauss-Jordan with partial pivoting)
+static bool invert(std::vector<double>& A, int n) {
+  std::vector<double> inv((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[(size_t)r * n + c]) > std::fabs(A[(size_t)piv * n + c])) piv = r;
+    if (A[(size_t)piv * n + c] == 0.0) return false;
+    if (piv != c)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+        std::swap(inv[(size_t)c * n + k], inv[(size_t)piv * n + k]);
+      }
+    const double d = 1.0 / A[(size_t)c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[(size_t)c * n + k] *= d;
+      inv[(size_t)c * n + k] *= d;
+    }
+    for (int r = 0; r < n; ++r)
+      if (r != c) {
+        const double fct = A[(size_t)r * n + c];
+        if (fct != 0.0)
+          for (int k = 0; k < n; ++k) {
+            A[(size_t)r * n + k] -= fct * A[(size_t)c * n + k];
+            inv[(size_t)r * n + k] -= fct * inv[(size_t)c * n + k];
+          }
+      }
+  }
+  A.swap(inv);
+  return true;
+}
+
+struct LevelCoef {
+  std::vector<double> coef;  // aS, aN, b, area
+  std::vector<double> invd;
+};
+
+static LevelCoef level_coef(int n, double h) {
+  LevelCoef L;
+  L.coef.resize(4 * (size_t)n);
+  L.invd.resize((size_t)n * n);
+  for (int i = 0; i < n; ++i) {
+    const double th = 0.5 * kPi + (i + 0.5 - 0.5 * n) * h;
+    const double s = std::sin(th), sp = std::sin(th + 0.5 * h), sm = std::sin(th - 0.5 * h);
+    L.coef[i] = sp / (h * h * s);
+    L.coef[n + i] = sm / (h * h * s);
+    L.coef[2 * n + i] = 1.0 / (h * h * s * s);
+    L.coef[3 * n + i] = std::cos(th - 0.5 * h) - std::cos(th + 0.5 * h);
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double aS = L.coef[i], aN = L.coef[n + i], b = L.coef[2 * n + i];
+      double d = aS + aN + 2.0 * b;
+      if (i == 0) d += aN;
+      if (i == n - 1) d += aS;
+      if (j == 0) d += b;
+      if (j == n - 1) d += b;
+      L.invd[(size_t)i * n + j] = 1.0 / d;
+    }
+  return L;
+}
+
+template <typename T>
+struct MG {
+  clc_plane_solution* s;
+  clc_ctx* ctx;
+  T* U(int l) { return (T*)s->u[l].p; }
+  T* F(int l) { return (T*)s->f[l].p; }
+  T* U0(int l) { return (T*)s->u0[l].p; }
+  const double* C(int l) { return (const double*)s->coef[l].p; }
+  const double* D(int l) { return (const double*)s->invd[l].p; }
+
+  void smooth(int l) {
+    const int n = s->sizes[l];
+    const size_t work = (size_t)s->npatch * n * (n / 2);
+    const int nb = blocks_for(ctx, work, 256);
+    for (int colour = 0; colour < 2; ++colour)
+      k_smooth<T><<<nb, 256, 0, ctx->stream>>>(U(l), F(l), C(l), D(l), n, s->npatch, colour);
+  }
+
+  void vcycle(int l) {
+    const int n = s->sizes[l];
+    if (l == s->nlev - 1) {
+      k_coarse_solve<T><<<s->npatch, 64, n * n * sizeof(double), ctx->stream>>>(U(l), F(l), C(l),
+                                                                                 (const double*)s->coarse_inv.p, n);
+      return;
+    }
+    for (int k = 0; k < s->p.nu1; ++k) smooth(l);
+    const int nc = n / 2;
+    k_restrict<T><<<blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, ctx->stream>>>(
+        U(l), F(l), C(l), D(l), n, s->npatch, U(l + 1), U0(l + 1), F(l + 1));
+    k_coarse_rhs<T><<<blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, ctx->stream>>>(
+        U(l + 1), F(l + 1), C(l + 1), D(l + 1), nc, s->npatch);
+    vcycle(l + 1);
+    k_prolong<T><<<blocks_for(ctx, (size_t)s->npatch * n * n, 256), 256, 0, ctx->stream>>>(U(l), U(l + 1), U0(l + 1),
+                                                                                          n, s->npatch);
+    for (int k = 0; k < s->p.nu2; ++k) smooth(l);
+  }
+
+  int residual(double* ratio_host) {
+    const int n = s->sizes[0];
+    k_resnorm<T><<<s->npatch, 256, 0, ctx->stream>>>(U(0), F(0), C(0), D(0), n, (double*)s->norms.p);
+    k_max_ratio<<<1, 1024, 0, ctx->stream>>>((const double*)s->norms.p, s->npatch, (double*)s->ratio.p);
+    int rc = launch_check(ctx, "MG residual");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                    "residual copy");
+    if (rc) return rc;
+    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "residual sync");
+  }
+
+  int setup(const double* kappa_fine) {
+    for (int l = 0; l < s->nlev; ++l) {
+      const int n = s->sizes[l];
+      const double hl = s->h * (s->sizes[0] / n);
+      const size_t work = (size_t)s->npatch * (n + 2) * (n + 2);
+      k_mg_setup<T><<<blocks_for(ctx, work, 256), 256, 0, ctx->stream>>>(
+          s->npatch, n, hl, (const double*)s->rot.p, (const double*)s->psi_sht.p, s->p.nside_sht, kappa_fine,
+          s->nside_fine, l == 0, U(l), F(l));
+    }
+    return launch_check(ctx, "MG setup");
+  }
+
+  int solve() {
+    int rc;
+    double rr = 0.0;
+    s->cycles = 0;
+    if (s->p.fixed_cycles > 0) {
+      for (int k = 0; k < s->p.fixed_cycles; ++k) {
+        vcycle(0);
+        if ((rc = launch_check(ctx, "V-cycle"))) return rc;
+      }
+      s->cycles = s->p.fixed_cycles;
+      rc = residual(&rr);
+      s->residual = rr;
+      return rc;
+    }
+    if ((rc = residual(&rr))) return rc;
+    while (rr >= s->p.tol && s->cycles < s->p.max_cycles) {
+      vcycle(0);
+      if ((rc = launch_check(ctx, "V-cycle"))) return rc;
+      ++s->cycles;
+      if ((rc = residual(&rr))) return rc;
+    }
+    s->residual = rr;
+    if (rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
+    return CLC_OK;
+  }
+};
+
+static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
+  if (!p) return set_err(ctx, CLC_EINVAL, "null MG parameters");
+  if (!valid_nside(nf) || !valid_nside(p->nside_sht) || !valid_nside(p->nside_bundle) || p->nside_bundle > nf ||
+      p->nside_sht > 4096)
+    return set_err(ctx, CLC_EINVAL, "MG: bad nside");
+  if (p->lmax < 1 || p->lmax > 4 * p->nside_sht) return set_err(ctx, CLC_EINVAL, "MG: lmax must be in [1, 4 nside_sht]");
+  if (p->ncell < 16 || p->ncell > 4096 || (p->ncell & (p->ncell - 1)))
+    return set_err(ctx, CLC_EINVAL, "MG: ncell must be a power of two in [16, 4096]");
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1 || p->max_cycles < 0 || p->fixed_cycles < 0)
+    return set_err(ctx, CLC_EINVAL, "MG: bad sweep / cycle counts");
+  if (p->precision != CLC_FP64 && p->precision != CLC_FP32) return set_err(ctx, CLC_EINVAL, "MG: bad precision");
+  return CLC_OK;
+}
+
+}  // namespace clc
+
+using namespace clc;
+
+extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, clc_plane_solution** out) {
+  if (!ctx || !out) return CLC_EINVAL;
+  *out = nullptr;
+  int rc = check_params(ctx, nf, p);
+  if (rc) return rc;
+  cudaSetDevice(ctx->device);
+  auto* s = new clc_plane_solution();
+  s->ctx = ctx;
+  s->nside_fine = nf;
+  s->p = *p;
+  s->npatch = 12 * p->nside_bundle * p->nside_bundle;
+  s->h = 4.0 * std::sqrt(kPi / 3.0) / p->nside_bundle / p->ncell;
+  for (int n = p->ncell;; n /= 2) {
+    s->sizes.push_back(n);
+    if (n <= 8) break;
+  }
+  s->nlev = (int)s->sizes.size();
+  const size_t es = p->precision == CLC_FP32 ? sizeof(float) : sizeof(double);
+  size_t need = 0;
+  for (int l = 0; l < s->nlev; ++l) {
+    const size_t n = s->sizes[l];
+    need += s->npatch * ((n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
+  }
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  if (need + (size_t)(1ull << 30) > freeb) {
+    delete s;
+    return set_err(ctx, CLC_ENOMEM, "MG state of " + std::to_string(need >> 20) + " MiB does not fit");
+  }
+  auto alloc = [&](Buffer& b, size_t bytes) -> bool {
+    b.bytes = bytes;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      b.p = nullptr;
+      return false;
+    }
+    return true;
+  };
+  bool ok = true;
+  for (int l = 0; l < s->nlev && ok; ++l) {
+    const size_t n = s->sizes[l];
+    const double hl = s->h * (p->ncell / (int)n);
+    ok = alloc(s->u[l], s->npatch * (n + 2) * (n + 2) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
+         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) && alloc(s->coef[l], 4 * n * sizeof(double)) &&
+         alloc(s->invd[l], n * n * sizeof(double));
+    if (!ok) break;
+    LevelCoef lc = level_coef((int)n, hl);
+    cudaMemcpy(s->coef[l].p, lc.coef.data(), lc.coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->invd[l].p, lc.invd.data(), lc.invd.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  const int nc = s->sizes.back();
+  const size_t ns2 = 12ull * p->nside_sht * p->nside_sht;
+  ok = ok && alloc(s->rot, 9 * sizeof(double) * s->npatch) && alloc(s->coarse_inv, sizeof(double) * nc * nc * nc * nc) &&
+       alloc(s->psi_sht, sizeof(double) * ns2) && alloc(s->kappa_sht, sizeof(double) * ns2) &&
+       alloc(s->norms, 2 * sizeof(double) * s->npatch) && alloc(s->ratio, sizeof(double));
+  if (!ok) {
+    delete s;
+    return set_err(ctx, CLC_ENOMEM, "MG allocation failed");
+  }
+  // dense coarsest operator (interior unknowns; boundary terms excluded)
+  {
+    const double hc = s->h * (p->ncell / nc);
+    LevelCoef lc = level_coef(nc, hc);
+    const int nn = nc * nc;
+    std::vector<double> A((size_t)nn * nn, 0.0);
+    for (int i = 0; i < nc; ++i)
+      for (int j = 0; j < nc; ++j) {
+        const int r = i * nc + j;
+        A[(size_t)r * nn + r] = -1.0 / lc.invd[(size_t)i * nc + j];
+        if (i + 1 < nc) A[(size_t)r * nn + r + nc] += lc.coef[i];
+        if (i > 0) A[(size_t)r * nn + r - nc] += lc.coef[nc + i];
+        if (j + 1 < nc) A[(size_t)r * nn + r + 1] += lc.coef[2 * nc + i];
+        if (j > 0) A[(size_t)r * nn + r - 1] += lc.coef[2 * nc + i];
+      }
+    if (!invert(A, nn)) {
+      delete s;
+      return set_err(ctx, CLC_ECUDA, "coarsest MG operator is singular");
+    }
+    cudaMemcpy(s->coarse_inv.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  k_mg_rotations<<<(s->npatch + 127) / 128, 128, 0, ctx->stream>>>(p->nside_bundle, s->npatch, (double*)s->rot.p);
+  rc = launch_check(ctx, "k_mg_rotations");
+  if (rc) {
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return CLC_OK;
+}
+
+extern "C" int clc_solution_destroy(clc_plane_solution* s) {
+  if (!s) return CLC_EINVAL;
+  if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
+  delete s;
+  return CLC_OK;
+}
+
+extern "C" int clc_solution_info(const clc_plane_solution* s, int* cycles, double* residual) {
+  if (!s) return CLC_EINVAL;
+  if (cycles) *cycles = s->cycles;
+  if (residual) *residual = s->residual;
+  return CLC_OK;
+}
+
+extern "C" int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nf, const clc_mg_params* p,
+                                 clc_plane_solution* s, const clc_derivs* out) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = check_params(ctx, nf, p);
+  if (rc) return rc;
+  if (!s || !kappa_fine) return set_err(ctx, CLC_EINVAL, "clc_poisson_shtmg: null pointer");
+  if (s->nside_fine != nf || s->p.nside_bundle != p->nside_bundle || s->p.ncell != p->ncell ||
+      s->p.precision != p->precision || s->p.nside_sht != p->nside_sht)
+    return set_err(ctx, CLC_EINVAL, "clc_poisson_shtmg: solution was created for other parameters");
+  cudaSetDevice(ctx->device);
+  s->p = *p;
+  // global SHT step on kappa binned at the SHT resolution
+  if ((rc = clc_degrade(ctx, kappa_fine, nf, (double*)s->kappa_sht.p, p->nside_sht))) return rc;
+  if ((rc = clc_poisson_sht(ctx, (const double*)s->kappa_sht.p, p->nside_sht, p->lmax, CLC_FP64,
+                            (double*)s->psi_sht.p, nullptr)))
+    return rc;
+  int st;
+  if (p->precision == CLC_FP32) {
+    MG<float> mg{s, ctx};
+    if ((rc = mg.setup(kappa_fine))) return rc;
+    st = mg.solve();
+  } else {
+    MG<double> mg{s, ctx};
+    if ((rc = mg.setup(kappa_fine))) return rc;
+    st = mg.solve();
+  }
+  if (st != CLC_OK && st != CLC_ENOTCONVERGED) return st;
+  if (out && (out->a_th || out->a_ph || out->u_tt || out->u_pp || out->u_tp)) {
+    const int64_t np = 12ll * nf * nf;
+    k_fields_at_pixels<<<blocks_for(ctx, np, 128), 128, 0, ctx->stream>>>(mg_view(s), nf, p->nside_bundle, out->a_th,
+                                                                         out->a_ph, out->u_tt, out->u_pp, out->u_tp);
+    if ((rc = launch_check(ctx, "k_fields_at_pixels"))) return rc;
+  }
+  return st;
+}
+
+extern "C" int clc_lens_derivs(clc_ctx* ctx, const clc_plane_solution* s, const double* z, const double* phi,
+                               const int32_t* bundle, int64_t n, const clc_derivs* out) {
+  if (!ctx) return CLC_EINVAL;
+  if (!s || n < 0 || !out) return set_err(ctx, CLC_EINVAL, "clc_lens_derivs: bad arguments");
+  if (n == 0) return CLC_OK;
+  if (!z || !phi) return set_err(ctx, CLC_EINVAL, "clc_lens_derivs: null positions");
+  cudaSetDevice(ctx->device);
+  k_fields_at_points<<<blocks_for(ctx, n, 128), 128, 0, ctx->stream>>>(mg_view(s), z, phi, bundle, n,
+                                                                      s->p.nside_bundle, out->a_th, out->a_ph,
+                                                                      out->u_tt, out->u_pp, out->u_tp);
+  return launch_check(ctx, "k_fields_at_points");
+}

@@ -1,0 +1,304 @@
+// Multiple-plane ray recursion on the sphere (paper Sec. 2.2, Appendix B):
+// per ray and plane, the lens fields at the ray, the Jacobian recursion
+// A^(n+1) = (1 - c) A^(n-1) + c A^(n) - d U^(n) A^(n) (Eq. Atraj), the rotation
+// of the propagation direction about n x alpha by |alpha| (Eq. betaprop), the
+// advance to the next sphere (Eq. posprop, positive root) and the parallel
+// transport of A^(n+1) and A^(n) to the tangent basis at the new position
+// (Appendix B).  One thread per ray; the state is FP64 structure-of-arrays so
+// that each component is a coalesced stream.
+#include "mg.cuh"
+#include "patch_fd.cuh"
+
+int clc_poisson_sht(clc_ctx*, const double*, int, int, int, double*, const clc_derivs*);
+
+namespace clc {
+
+struct RayPtrs {
+  double* x;
+  double* beta;
+  double* A;
+  double* Ap;
+  const int32_t* bundle;
+  int64_t n;
+};
+
+__global__ void k_rays_init(const double* __restrict__ z, const double* __restrict__ phi, double chi0, int nb,
+                            RayPtrs R) {
+  const int64_t n = R.n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const double zz = z[k], pp = phi[k];
+    const double s = sqrt((1.0 - zz) * (1.0 + zz));
+    const double v[3] = {s * cos(pp), s * sin(pp), zz};
+    for (int c = 0; c < 3; ++c) {
+      R.x[c * n + k] = chi0 * v[c];
+      R.beta[c * n + k] = v[c];
+    }
+    R.A[k] = 1.0; R.A[n + k] = 0.0; R.A[2 * n + k] = 0.0; R.A[3 * n + k] = 1.0;
+    R.Ap[k] = 1.0; R.Ap[n + k] = 0.0; R.Ap[2 * n + k] = 0.0; R.Ap[3 * n + k] = 1.0;
+    if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)ang2pix_nest(nb, zz, pp);
+  }
+}
+
+__device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
+  const double rho = sqrt(n[0] * n[0] + n[1] * n[1]);
+  t[0] = n[2] * n[0] / rho; t[1] = n[2] * n[1] / rho; t[2] = -rho;
+  p[0] = -n[1] / rho; p[1] = n[0] / rho; p[2] = 0.0;
+}
+
+__device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ __forceinline__ double dot3(const double a[3], const double b[3]) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// rotate v about unit axis k by the angle with cosine c, sine s
+__device__ __forceinline__ void rodrigues(const double v[3], const double k[3], double c, double s, double o[3]) {
+  double kv[3];
+  cross3(k, v, kv);
+  const double kd = dot3(k, v) * (1.0 - c);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) o[i] = v[i] * c + kv[i] * s + k[i] * kd;
+}
+
+// Lens fields at the ray from RING maps: alpha as a tangent 3-vector and U as
+// a tangent 3x3 tensor, ring-bilinear interpolation, projection on the basis
+// at the ray.
+__device__ void map_lens_fields(const clc_derivs& M, int nside, const double nv[3], double out[5]) {
+  const double th = atan2(sqrt(nv[0] * nv[0] + nv[1] * nv[1]), nv[2]);
+  double ph = atan2(nv[1], nv[0]);
+  if (ph < 0) ph += 2.0 * kPi;
+  const Interp8 w = interp_weights(nside, th, ph);
+  double a3[3] = {0, 0, 0}, U3[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int k = 0; k < 8; ++k) {
+    if (w.w[k] == 0.0) continue;
+    const int64_t p = w.p[k];
+    int64_t j;
+    const int i = pix2ring(nside, p, &j);
+    const Ring r = ring_geom(nside, i);
+    const double phi = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
+    const double cp = cos(phi), sp = sin(phi);
+    const double t[3] = {r.z * cp, r.z * sp, -r.s};
+    const double q[3] = {-sp, cp, 0.0};
+    const double at = M.a_th[p], ap = M.a_ph[p], utt = M.u_tt[p], upp = M.u_pp[p], utp = M.u_tp[p];
+    const double ww = w.w[k];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      a3[a] += ww * (at * t[a] + ap * q[a]);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        U3[a][b] += ww * (utt * t[a] * t[b] + upp * q[a] * q[b] + utp * (t[a] * q[b] + q[a] * t[b]));
+    }
+  }
+  double t[3], q[3];
+  tangent_basis(nv, t, q);
+  out[0] = dot3(a3, t);
+  out[1] = dot3(a3, q);
+  double Ut[3], Uq[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    Ut[a] = U3[a][0] * t[0] + U3[a][1] * t[1] + U3[a][2] * t[2];
+    Uq[a] = U3[a][0] * q[0] + U3[a][1] * q[1] + U3[a][2] * q[2];
+  }
+  out[2] = dot3(t, Ut);
+  out[3] = dot3(q, Uq);
+  out[4] = dot3(t, Uq);
+}
+
+struct StepCoef {
+  double c, d, dchi2;
+};
+
+// transport matrix Q (2x2) from the basis at n0 to the basis at n1
+__device__ __forceinline__ void transport_q(const double n0[3], const double n1[3], double Q[4]) {
+  double cr[3];
+  cross3(n0, n1, cr);
+  const double s = sqrt(dot3(cr, cr));
+  const double c = dot3(n0, n1);
+  double t0[3], p0[3], t1[3], p1[3];
+  tangent_basis(n0, t0, p0);
+  tangent_basis(n1, t1, p1);
+  double tr[3], pr[3];
+  if (s > 0.0) {
+    const double k[3] = {cr[0] / s, cr[1] / s, cr[2] / s};
+    rodrigues(t0, k, c, s, tr);
+    rodrigues(p0, k, c, s, pr);
+  } else {
+    for (int i = 0; i < 3; ++i) { tr[i] = t0[i]; pr[i] = p0[i]; }
+  }
+  Q[0] = dot3(t1, tr); Q[1] = dot3(t1, pr);
+  Q[2] = dot3(p1, tr); Q[3] = dot3(p1, pr);
+}
+
+__device__ __forceinline__ void qaqt(const double Q[4], const double A[4], double o[4]) {
+  const double m0 = Q[0] * A[0] + Q[1] * A[2], m1 = Q[0] * A[1] + Q[1] * A[3];
+  const double m2 = Q[2] * A[0] + Q[3] * A[2], m3 = Q[2] * A[1] + Q[3] * A[3];
+  o[0] = m0 * Q[0] + m1 * Q[1];
+  o[1] = m0 * Q[2] + m1 * Q[3];
+  o[2] = m2 * Q[0] + m3 * Q[1];
+  o[3] = m2 * Q[2] + m3 * Q[3];
+}
+
+template <bool kMG>
+__global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, StepCoef sc) {
+  const int64_t n = R.n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double x[3], be[3], A[4], Ap[4];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { x[c] = R.x[c * n + k]; be[c] = R.beta[c * n + k]; }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { A[c] = R.A[c * n + k]; Ap[c] = R.Ap[c * n + k]; }
+    const double xn = sqrt(dot3(x, x));
+    const double nv[3] = {x[0] / xn, x[1] / xn, x[2] / xn};
+    double L[5];
+    if (kMG) patch_lens_fields(V, R.bundle[k], nv, L);
+    else map_lens_fields(M, nside_maps, nv, L);
+    // Eq. Atraj in the basis at n
+    const double U[4] = {L[2], L[4], L[4], L[3]};
+    double An[4];
+    An[0] = (1.0 - sc.c) * Ap[0] + sc.c * A[0] - sc.d * (U[0] * A[0] + U[1] * A[2]);
+    An[1] = (1.0 - sc.c) * Ap[1] + sc.c * A[1] - sc.d * (U[0] * A[1] + U[1] * A[3]);
+    An[2] = (1.0 - sc.c) * Ap[2] + sc.c * A[2] - sc.d * (U[2] * A[0] + U[3] * A[2]);
+    An[3] = (1.0 - sc.c) * Ap[3] + sc.c * A[3] - sc.d * (U[2] * A[1] + U[3] * A[3]);
+    // Eq. betaprop: rotate beta about n x alpha by |alpha|
+    double t[3], q[3];
+    tangent_basis(nv, t, q);
+    const double av[3] = {L[0] * t[0] + L[1] * q[0], L[0] * t[1] + L[1] * q[1], L[0] * t[2] + L[1] * q[2]};
+    const double am = sqrt(dot3(av, av));
+    double bn[3] = {be[0], be[1], be[2]};
+    if (am > 0.0) {
+      double kx[3];
+      cross3(nv, av, kx);
+      const double kk[3] = {kx[0] / am, kx[1] / am, kx[2] / am};
+      double sn, cs;
+      sincos(am, &sn, &cs);
+      rodrigues(be, kk, cs, sn, bn);
+    }
+    // Eq. posprop: lambda > 0 root, rationalised
+    const double xb = dot3(x, bn);
+    const double lam = sc.dchi2 / (xb + sqrt(xb * xb + sc.dchi2));
+    double x1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) x1[c] = x[c] + lam * bn[c];
+    const double x1n = sqrt(dot3(x1, x1));
+    const double n1[3] = {x1[0] / x1n, x1[1] / x1n, x1[2] / x1n};
+    // Appendix B: transport A^(n+1) and A^(n) to the basis at the new point
+    double Q[4], Ao[4], Apo[4];
+    transport_q(nv, n1, Q);
+    qaqt(Q, An, Ao);
+    qaqt(Q, A, Apo);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { R.x[c * n + k] = x1[c]; R.beta[c * n + k] = bn[c]; }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { R.A[c * n + k] = Ao[c]; R.Ap[c * n + k] = Apo[c]; }
+  }
+}
+
+static RayPtrs ray_ptrs(const clc_rays* r) {
+  RayPtrs p;
+  p.x = r->x; p.beta = r->beta; p.A = r->A; p.Ap = r->Ap; p.bundle = r->bundle; p.n = r->n;
+  return p;
+}
+
+static int rays_ok(clc_ctx* ctx, const clc_rays* r) {
+  if (!r || r->n < 0) return set_err(ctx, CLC_EINVAL, "bad ray state");
+  if (r->n > 0 && (!r->x || !r->beta || !r->A || !r->Ap)) return set_err(ctx, CLC_EINVAL, "null ray arrays");
+  return CLC_OK;
+}
+
+static int blocks(clc_ctx* ctx, int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)num_sms(ctx) * 16;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace clc
+
+using namespace clc;
+
+extern "C" int clc_rays_init(clc_ctx* ctx, const double* z, const double* phi, double chi0, int nb, clc_rays* r) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = rays_ok(ctx, r);
+  if (rc) return rc;
+  if (!(chi0 > 0) || (nb > 0 && !valid_nside(nb))) return set_err(ctx, CLC_EINVAL, "clc_rays_init: bad chi0 / nside");
+  if (r->n == 0) return CLC_OK;
+  if (!z || !phi) return set_err(ctx, CLC_EINVAL, "clc_rays_init: null positions");
+  cudaSetDevice(ctx->device);
+  k_rays_init<<<blocks(ctx, r->n, 256), 256, 0, ctx->stream>>>(z, phi, chi0, nb, ray_ptrs(r));
+  return launch_check(ctx, "k_rays_init");
+}
+
+extern "C" int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const clc_derivs* maps, int nside_maps,
+                            double chi_prev, double chi_n, double chi_next, clc_rays* r) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = rays_ok(ctx, r);
+  if (rc) return rc;
+  if (!(chi_prev >= 0 && chi_n > chi_prev && chi_next > chi_n))
+    return set_err(ctx, CLC_EINVAL, "clc_ray_step: need 0 <= chi_prev < chi_n < chi_next");
+  if (!sol && (!maps || !maps->a_th || !maps->a_ph || !maps->u_tt || !maps->u_pp || !maps->u_tp || !valid_nside(nside_maps)))
+    return set_err(ctx, CLC_EINVAL, "clc_ray_step: need a solution or five lens maps");
+  if (sol && !r->bundle && r->n > 0) return set_err(ctx, CLC_EINVAL, "clc_ray_step: SHT+MG lookup needs ray bundles");
+  if (r->n == 0) return CLC_OK;
+  cudaSetDevice(ctx->device);
+  StepCoef sc;
+  sc.c = (chi_n / chi_next) * ((chi_next - chi_prev) / (chi_n - chi_prev));
+  sc.d = (chi_next - chi_n) / chi_next;
+  sc.dchi2 = chi_next * chi_next - chi_n * chi_n;
+  clc_derivs M{};
+  if (maps) M = *maps;
+  if (sol) {
+    k_ray_step<true><<<blocks(ctx, r->n, 128), 128, 0, ctx->stream>>>(ray_ptrs(r), mg_view(sol), M, 0, sc);
+  } else {
+    MGView V{};
+    k_ray_step<false><<<blocks(ctx, r->n, 128), 128, 0, ctx->stream>>>(ray_ptrs(r), V, M, nside_maps, sc);
+  }
+  return launch_check(ctx, "k_ray_step");
+}
+
+extern "C" int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
+                                   const double* const* kappa_planes, int nplanes, int nside, const double* chi,
+                                   clc_rays* r) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = rays_ok(ctx, r);
+  if (rc) return rc;
+  if (!mg || !kappa_planes || !chi || nplanes < 1 || !valid_nside(nside) ||
+      (solver != CLC_SOLVER_SHT && solver != CLC_SOLVER_SHTMG))
+    return set_err(ctx, CLC_EINVAL, "clc_raytrace_planes: bad arguments");
+  for (int m = 0; m < nplanes; ++m)
+    if (!kappa_planes[m] || !(chi[m + 1] > chi[m]) || !(chi[m] > 0))
+      return set_err(ctx, CLC_EINVAL, "clc_raytrace_planes: null plane or non-increasing chi");
+  cudaSetDevice(ctx->device);
+  if (solver == CLC_SOLVER_SHT) {
+    const size_t np = 12ull * nside * nside;
+    double* maps = (double*)scratch(ctx, 4, 5 * np * sizeof(double));
+    if (!maps) return CLC_ENOMEM;
+    clc_derivs d{maps, maps + np, maps + 2 * np, maps + 3 * np, maps + 4 * np};
+    for (int m = 0; m < nplanes; ++m) {
+      if ((rc = clc_poisson_sht(ctx, kappa_planes[m], nside, mg->lmax, CLC_FP64, nullptr, &d))) return rc;
+      if ((rc = clc_ray_step(ctx, nullptr, &d, nside, m > 0 ? chi[m - 1] : 0.0, chi[m], chi[m + 1], r))) return rc;
+    }
+    return CLC_OK;
+  }
+  clc_plane_solution* sol = nullptr;
+  if ((rc = clc_solution_create(ctx, nside, mg, &sol))) return rc;
+  int status = CLC_OK;
+  for (int m = 0; m < nplanes && (status == CLC_OK || status == CLC_ENOTCONVERGED); ++m) {
+    rc = clc_poisson_shtmg(ctx, kappa_planes[m], nside, mg, sol, nullptr);
+    if (rc != CLC_OK && rc != CLC_ENOTCONVERGED) {
+      status = rc;
+      break;
+    }
+    if (rc == CLC_ENOTCONVERGED) status = rc;
+    rc = clc_ray_step(ctx, sol, nullptr, 0, m > 0 ? chi[m - 1] : 0.0, chi[m], chi[m + 1], r);
+    if (rc) {
+      status = rc;
+      break;
+    }
+  }
+  clc_solution_destroy(sol);
+  return status;
+}
