@@ -38,13 +38,22 @@ def alm_index(lmax, l, m):
     return m * (2 * lmax + 1 - m) // 2 + l
 
 
-def legendre_columns(lmax, z, sin_theta, mmax=None):
+def _times_pow2(p, e):
+    """p * 2^e for int64 exponents e, with one final rounding: 2^e alone
+    underflows FP64 for e < -1074 although p * 2^e may not."""
+    lo = e < -1000
+    e1 = torch.where(lo, e + 600, e).to(F64)
+    return torch.where(lo, torch.ldexp(p, e1) * 2.0 ** -600, torch.ldexp(p, e1))
+
+
+def legendre_columns(lmax, z, sin_theta, mmax=None, mmin=0):
     """Yield (m, lam) with lam[l - m, r] = lambda_lm(z_r) for l = m .. lmax.
 
     lambda_mm is carried as mantissa * 2^exponent so that sin^m theta never
     underflows; the l-recurrence runs on the mantissas (it is linear), which
     are renormalised by 2^-400 when they grow, and the result is converted
-    with ldexp (values below the FP64 range become 0 there).
+    with one final rounding (values below the FP64 range become 0 there).
+    Columns m < mmin are skipped.
     """
     if mmax is None:
         mmax = lmax
@@ -58,25 +67,27 @@ def legendre_columns(lmax, z, sin_theta, mmax=None):
             fr = torch.frexp(mant)
             mant = fr.mantissa
             expo = expo + fr.exponent.to(torch.int64)
+        if m < mmin:
+            continue
         nl = lmax - m + 1
         out = torch.empty((nl, z.numel()), dtype=F64)
         e = expo.clone()
         p2 = mant.clone()                      # lambda_{l-2}
-        out[0] = torch.ldexp(p2, e.to(F64))
+        out[0] = _times_pow2(p2, e)
         if nl > 1:
             p1 = math.sqrt(2.0 * m + 3.0) * z * p2   # lambda_{m+1, m}
-            out[1] = torch.ldexp(p1, e.to(F64))
+            out[1] = _times_pow2(p1, e)
             for l in range(m + 2, lmax + 1):
                 a = math.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
                 b = math.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
                 p0 = a * (z * p1 - b * p2)
                 big = torch.abs(p0) > 2.0 ** 400
                 if bool(big.any()):
-                    sc = torch.where(big, 2.0 ** -400, 1.0)
+                    sc = torch.where(big, torch.tensor(2.0 ** -400, dtype=F64), torch.tensor(1.0, dtype=F64))
                     p0 = p0 * sc
                     p1 = p1 * sc
                     e = e + torch.where(big, 400, 0)
-                out[l - m] = torch.ldexp(p0, e.to(F64))
+                out[l - m] = _times_pow2(p0, e)
                 p2, p1 = p1, p0
         yield m, out
 

@@ -16,6 +16,14 @@
 
 namespace clc {
 
+// p * 2^e, exact unless the result is subnormal or zero (one final rounding);
+// |p| < 2^410 and e <= 64 here.
+__device__ __forceinline__ double scale_pow2(double p, int e) {
+  if (e >= -1022) return p * __longlong_as_double((long long)(e + 1023) << 52);
+  if (e < -1600) return 0.0;
+  return (p * __longlong_as_double((long long)(e + 600 + 1023) << 52)) * 0x1p-600;
+}
+
 __global__ void k_legendre_build(int nside, int lmax, int R, const long long* __restrict__ off,
                                  const double* __restrict__ lognorm, const double2* __restrict__ ab,
                                  double* __restrict__ tab) {
@@ -30,10 +38,10 @@ __global__ void k_legendre_build(int nside, int lmax, int R, const long long* __
   int e = (int)floor(l2);
   double p2 = exp2(l2 - (double)e);
   if (m & 1) p2 = -p2;
-  col[r] = ldexp(p2, e);
+  col[r] = scale_pow2(p2, e);
   if (lt < m + 1) return;
   double p1 = sqrt(2.0 * m + 3.0) * z * p2;
-  col[(size_t)R + r] = ldexp(p1, e);
+  col[(size_t)R + r] = scale_pow2(p1, e);
   const double big = 0x1p400, small = 0x1p-400;
   for (int l = m + 2; l <= lt; ++l) {
     const double2 c = ab[alm_idx(lt, l, m)];
@@ -43,7 +51,7 @@ __global__ void k_legendre_build(int nside, int lmax, int R, const long long* __
       p1 *= small;
       e += 400;
     }
-    col[(size_t)(l - m) * R + r] = ldexp(p0, e);
+    col[(size_t)(l - m) * R + r] = scale_pow2(p0, e);
     p2 = p1;
     p1 = p0;
   }

@@ -17,10 +17,12 @@ def ctx():
 
 
 def rel_l2(a, b):
-    a = a.detach().cpu().double()
-    b = b.detach().cpu().double()
+    a = a.detach().cpu()
+    b = b.detach().cpu()
     if a.is_complex() or b.is_complex():
         a = torch.view_as_real(a.to(torch.complex128))
         b = torch.view_as_real(b.to(torch.complex128))
+    a = a.double()
+    b = b.double()
     den = float(torch.linalg.vector_norm(b))
     return float(torch.linalg.vector_norm(a - b)) / (den if den > 0 else 1.0)

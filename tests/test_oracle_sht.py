@@ -36,6 +36,21 @@ def test_legendre_high_degree_matches_scipy():
                 assert np.allclose(lam[l - m].numpy(), ref, rtol=1e-9, atol=1e-12), (l, m)
 
 
+def test_legendre_through_underflowed_start():
+    """sin^m theta underflows FP64 (lambda_mm ~ 1e-317) but lambda_lm grows
+    back to order one near the turning point l ~ m / sin theta: the scaled
+    recurrence must carry it (checked against mpmath)."""
+    import mpmath
+    mpmath.mp.dps = 40
+    th = torch.tensor([0.3], dtype=F64)
+    m, L = 600, 2100
+    for mm, lam in sht.legendre_columns(L, torch.cos(th), torch.sin(th), mmax=m, mmin=m):
+        for l in (600, 1200, 1800, 2000, 2100):
+            ref = float(mpmath.re(mpmath.spherharm(l, m, 0.3, 0)))
+            assert abs(float(lam[l - m, 0]) - ref) <= 1e-10 * abs(ref) + 1e-300, (l, ref)
+    assert abs(float(lam[2100 - m, 0])) > 1e-3
+
+
 def test_legendre_no_underflow_garbage():
     # near the pole sin^m theta underflows FP64 for large m; values must be 0
     # or tiny, never NaN / inf, and columns m <= 2 must stay accurate
