@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Throughput of the lens-plane hot path on GB300: lens planes per second.
+
+One step = one lens plane through the whole path of the paper's Sec. 3:
+bin the plane's particles to HEALPix pixels (Sec. 3.2), build its source
+kappa^(m) (Eq. lenspoisson), solve for the potential with the SHT+MG solver
+(SHT at nside_sht / lmax, FAS multigrid V-cycles on all bundle patches to
+the residual tolerance, Sec. 3.2), then put every ray of the Nside-2048 grid
+on the plane and advance it to the next one (lens-field lookup, Eq. Atraj,
+Eq. betaprop, Eq. posprop, Appendix B transport).
+
+Default workload (single plane, SHT+MG, Nside 2048): a seeded lognormal
+light-cone shell Poisson-sampled to 5e7 particles, nside_sht 512, lmax 1024,
+bundle Nside 32 (12288 patches of 256^2 cells), tolerance 1e-10, FP64, and
+50,331,648 rays.  All inputs are larger than L2, so no flush is needed.
+
+  python bench.py [--gpus N --steps K --warmup W] [--precision fp64|fp32]
+  python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Under torchrun every rank solves its own plane (independent seeds; weak
+scaling) and rank 0 prints one JSON line with the whole-job planes/s.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import cosmology, synthetic  # noqa: E402
+
+METRIC = "lens planes/s (SHT+MG, Nside=2048)"
+UNIT = "planes/s"
+
+WORKLOADS = {
+    # the single-plane SHT+MG configuration the metric is quoted on
+    "shtmg_plane_nside2048": dict(nside=2048, particles=50_000_000, nside_sht=512, lmax=1024, nside_bundle=32,
+                                  ncell=256, tol=1e-10, nu1=2, nu2=2, max_cycles=60, seed=1210002),
+    # a small case of the same kernels (profiling)
+    "shtmg_plane_nside512": dict(nside=512, particles=3_000_000, nside_sht=128, lmax=256, nside_bundle=8,
+                                 ncell=256, tol=1e-10, nu1=2, nu2=2, max_cycles=60, seed=1210002),
+}
+
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi SM clocks and throttle reasons while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[0]) for r in self.rows if len(r) >= 8 and r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 8:
+                for k, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(k)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def plane_geometry():
+    """Plane 20 of 40 shells of 50 Mpc/h (flat LCDM, Om = 0.25)."""
+    pl = cosmology.lens_planes(40, 50.0)
+    m = 20
+    return pl["chi"][m - 1], pl["chi"][m], pl["chi"][m + 1], pl["scale"][m] * pl["growth"][m]
+
+
+def smg_flops_per_cycle(cfg, npatch):
+    """Algorithmic FP64 flops of the red-black smoother per V-cycle: 8 per
+    updated cell (4-neighbour stencil, source, reciprocal diagonal)."""
+    n, tot = cfg["ncell"], 0
+    while n > 8:
+        tot += (cfg["nu1"] + cfg["nu2"]) * npatch * n * n * 8
+        n //= 2
+    return tot
+
+
+def run_gpu(args, cfg, rank, world):
+    import paper_1210_3069_gb300 as clc
+    clc.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(dev.index)
+    nf = cfg["nside"]
+    npix = 12 * nf * nf
+    chi_prev, chi_n, chi_next, scale = plane_geometry()
+    prec = clc.FP32 if args.precision == "fp32" else clc.FP64
+    P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
+                      nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=prec)
+    # seeded synthetic plane (a different shell per rank)
+    z, phi = synthetic.lognormal_particles(cfg["particles"], cfg["seed"] + rank, device=dev)
+    nbar = z.numel() / npix
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    kappa = torch.empty(npix, dtype=torch.float64, device=dev)
+    sol = ctx.solution(nf, P)
+    rays = ctx.rays(npix)
+    host_z = z.cpu().pin_memory()
+    host_phi = phi.cpu().pin_memory()
+    host_A = torch.empty(4, npix, dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    cycles = []
+
+    def step():
+        counts.zero_()
+        ctx.bin_particles(z, phi, nf, counts=counts)
+        ctx.counts_to_kappa(counts, nf, nbar, scale, kappa=kappa)
+        ctx.poisson_shtmg(kappa, nf, sol, check=False)
+        cycles.append(sol.info()[0])
+        ctx.rays_init_pixels(rays, nf, chi_n, cfg["nside_bundle"])
+        ctx.ray_step(rays, chi_prev, chi_n, chi_next, sol=sol)
+
+    def e2e_step():
+        z.copy_(host_z, non_blocking=True)
+        phi.copy_(host_phi, non_blocking=True)
+        step()
+        host_A.copy_(rays.A, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    prof = {k: ctx.profile_query(k) for k in ("k_smooth", "k_restrict", "k_coarse_rhs", "k_prolong", "k_coarse_solve",
+                                              "k_resnorm", "k_mg_setup", "k_ray_step", "k_bin", "k_legendre_analysis",
+                                              "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis",
+                                              "k_degrade", "k_rays_init", "k_counts_to_kappa")}
+    ctx.profile(False)
+    timed_cycles = cycles[-args.steps:]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t)
+    # end to end through the public API with host buffers
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    e2e_steps = max(1, min(args.steps, 3))
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t)
+    sol.close()
+    npatch = 12 * cfg["nside_bundle"] ** 2
+    flops = smg_flops_per_cycle(cfg, npatch) * sum(timed_cycles)
+    sm_n, sm_ms = prof["k_smooth"]
+    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, cycles=timed_cycles, smooth_flops=flops,
+                smooth_launches=sm_n, smooth_ms=sm_ms, clocks=clocks.summary(), npix=npix,
+                h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
+
+
+# ---------------------------------------------------------------------------
+# the FP64 oracle on a bounded sample of the same workload
+
+def oracle_plane_estimate(cfg, sample_patches=4, sample_rays=20_000, sample_particles=2_000_000, sht_mcols=16,
+                          cycles=None, seed=0):
+    """Seconds the oracle would take for one plane of `cfg`, from timed
+    samples: binning of sample_particles (scaled to all particles), the SHT
+    with the Legendre sums restricted to m < sht_mcols (scaled by the number
+    of (l, m) pairs) plus all ring FFTs, the MG set-up and V-cycles on
+    sample_patches patches (scaled to all patches) and one ray step of
+    sample_rays rays (scaled to all rays)."""
+    from oracle import binning, healpix as hp, mg as omg, rays as orays, sht
+    nf, ns, L, nb, ncell = cfg["nside"], cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], cfg["ncell"]
+    npix = 12 * nf * nf
+    parts = {}
+    z, phi = synthetic.lognormal_particles(sample_particles, cfg["seed"] + seed)
+    t = time.perf_counter()
+    counts = binning.bin_counts(nf, z, phi)
+    kap = binning.kappa_from_counts(counts, z.numel() / npix, 1.0)
+    parts["bin"] = (time.perf_counter() - t) * cfg["particles"] / z.numel()
+    # SHT (analysis + synthesis of psi) on the SHT grid
+    ks = torch.randn(12 * ns * ns, dtype=torch.float64, generator=torch.Generator().manual_seed(seed))
+    rt = hp.ring_table(ns)
+    t = time.perf_counter()
+    F = sht.ring_fourier(ns, ks, L)
+    G = torch.zeros_like(F)
+    for m, lam in sht.legendre_columns(L, rt["z"], rt["sin_theta"], mmax=sht_mcols - 1):
+        a = lam.to(torch.complex128) @ F[:, m]
+        G[:, m] = lam.T.to(torch.complex128) @ a
+    t_leg = time.perf_counter()
+    sht.ring_inverse_fourier(ns, G, L)
+    t_fft = time.perf_counter() - t_leg
+    pairs_all = (L + 1) * (L + 2) / 2
+    pairs_s = sum(L - m + 1 for m in range(sht_mcols))
+    parts["sht"] = (t_leg - t) * pairs_all / pairs_s + 2 * t_fft
+    # MG on a sample of patches
+    psi_s = sht.ring_inverse_fourier(ns, G, L)
+    bundles = torch.arange(sample_patches) * (12 * nb * nb // sample_patches)
+    t = time.perf_counter()
+    R, h, u, f, ghosts = omg.setup_patches(kap, nf, psi_s, ns, nb, bundles, ncell=ncell)
+    S = omg.PatchSolver(ncell, h, ghosts, nu1=cfg["nu1"], nu2=cfg["nu2"])
+    ncyc = cycles if cycles else 10
+    S.solve(u, f, fixed_cycles=ncyc)
+    parts["mg"] = (time.perf_counter() - t) * (12 * nb * nb) / sample_patches
+    # one ray step
+    sol = {"R": R, "h": h, "partials": omg.fd_partials(u[:, 1:-1, 1:-1], h), "bundles": bundles}
+    pix = torch.randint(0, npix, (sample_rays,), generator=torch.Generator().manual_seed(seed + 1))
+    n0 = hp.pix2vec_ring(nf, pix)
+    home = bundles[torch.randint(0, sample_patches, (sample_rays,), generator=torch.Generator().manual_seed(2))]
+    # rays placed at their patch centres so every lookup is valid
+    cen = torch.einsum("bji,j->bi", R, torch.tensor([1.0, 0.0, 0.0], dtype=torch.float64))
+    lookup = {int(b): k for k, b in enumerate(bundles.tolist())}
+    n0 = cen[torch.tensor([lookup[int(b)] for b in home.tolist()])] + 1e-4 * n0
+    n0 = n0 / torch.linalg.vector_norm(n0, dim=-1, keepdim=True)
+    t = time.perf_counter()
+    st = orays.init_rays(n0, 1000.0)
+    orays.step(st, lambda n: omg.fields_at(sol, nb, n, home), 950.0, 1000.0, 1050.0)
+    parts["rays"] = (time.perf_counter() - t) * npix / sample_rays
+    return sum(parts.values()), parts
+
+
+def cpu_baseline(cfg, cycles, seed=0, small=False):
+    kw = dict(sample_patches=2, sample_rays=5_000, sample_particles=500_000, sht_mcols=8) if small else {}
+    t0 = time.perf_counter()
+    secs, parts = oracle_plane_estimate(cfg, cycles=cycles, seed=seed, **kw)
+    wall = time.perf_counter() - t0
+    s = dict(sample_patches=2, sample_rays=5000, sample_particles=500000, sht_mcols=8) if small else \
+        dict(sample_patches=4, sample_rays=20000, sample_particles=2000000, sht_mcols=16)
+    sample = (f"oracle timed on {s['sample_particles']} particles (binning), Legendre columns m<{s['sht_mcols']} "
+              f"of the SHT plus all ring FFTs, {s['sample_patches']} MG patches x {cycles} V-cycles, "
+              f"{s['sample_rays']} ray steps; each part scaled to the full plane")
+    return {"value": 1.0 / secs, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": sample, "seconds_per_plane": secs, "parts_s": {k: round(v, 3) for k, v in parts.items()},
+            "wall_s": round(wall, 2)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="shtmg_plane_nside2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    cfg = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    config = {"workload": args.workload, **{k: v for k, v in cfg.items() if k != "seed"},
+              "rays": 12 * cfg["nside"] ** 2, "precision": args.precision,
+              "l2": "inputs larger than L2 (no flush)", "planes_per_rank_per_step": 1}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        steps = []
+        for s in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            cpu_baseline(cfg, cycles=12, seed=s, small=True)
+            steps.append(time.perf_counter() - t)
+        est = cpu_baseline(cfg, cycles=12, small=True)
+        line = {"metric": METRIC, "value": est["value"], "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 / est["value"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "impl": "reference", "cpu_baseline": {k: est[k] for k in ("kind", "cores", "sample", "value", "unit")},
+                "e2e": {"value": est["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    r = run_gpu(args, cfg, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_kind = load_peaks()
+    planes = world * args.steps
+    value = planes / (r["ms"] / 1000.0)
+    achieved = r["smooth_flops"] / (r["smooth_ms"] / 1000.0) / 1e12 if r["smooth_ms"] > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic", "config": config,
+        "rays_per_s": world * r["npix"] * args.steps / (r["ms"] / 1000.0),
+        "mg_cycles": r["cycles"],
+        "roofline": {"kernel": "k_smooth (red-black Gauss-Seidel, all levels)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
+                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; an FMA microbenchmark "
+                                    "measured 1.20 TFLOP/s)",
+                     "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_kind},
+        "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in r["prof"].items()},
+        "e2e": {"value": world / (r["e2e_ms"] / 1000.0), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(cfg, cycles=max(r["cycles"]) if r["cycles"] else 10)
+        line["cpu_baseline"].pop("parts_s", None)
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -192,6 +192,12 @@ int clc_lens_derivs(clc_ctx* ctx, const clc_plane_solution* sol, const double* z
 int clc_rays_init(clc_ctx* ctx, const double* z, const double* phi, double chi0,
                   int nside_bundle, clc_rays* rays);
 
+/* Rays on every RING pixel centre of nside (the paper's ray layout, Sec. 3.1):
+ * ray k starts at pixel k; rays->n must equal 12 nside^2.  bundle[k] (if
+ * nside_bundle > 0) = the pixel's NEST index shifted right by
+ * 2 log2(nside / nside_bundle). */
+int clc_rays_init_pixels(clc_ctx* ctx, int nside, double chi0, int nside_bundle, clc_rays* rays);
+
 /* Advance all rays from the plane at chi_n to the sphere at chi_next using
  * the lens fields of that plane: either the SHT+MG solution `sol` (sol !=
  * NULL; rays looked up in their home bundle's patch) or RING maps `maps` of
@@ -211,6 +217,19 @@ int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const clc_derivs* 
 int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
                         const double* const* kappa_planes_host, int nplanes, int nside,
                         const double* chi_host, clc_rays* rays);
+
+/* ------------------------------------------------------------------------ */
+/* Diagnostics (no counterpart in the paper beyond its per-step wall timers) */
+
+/* enable != 0: start recording a CUDA-event pair around every kernel launch
+ * of this context (previous records are dropped); 0: stop recording. */
+int clc_profile(clc_ctx* ctx, int enable);
+/* Launches recorded for the kernel `name` (e.g. "k_smooth") since profiling
+ * was enabled and their summed device time in milliseconds (waits for the
+ * stream). */
+int clc_profile_query(clc_ctx* ctx, const char* name, int64_t* launches_host, double* total_ms_host);
+/* Number of kernels this context has launched since it was created. */
+int64_t clc_launch_count(const clc_ctx* ctx);
 
 #ifdef __cplusplus
 }

@@ -314,11 +314,8 @@ def derivs_at(partials, R, h, b_index, nvec):
     fy = y - j0
     i0 = i0.long()
     j0 = j0.long()
-    P = partials[b_index]                                    # [M, 5, N, N]
-    ar = torch.arange(P.shape[0])
-
     def at(ii, jj):
-        return P[ar, :, ii, jj]
+        return partials[b_index, :, ii, jj]                  # [M, 5]
 
     val = ((1 - fx)[:, None] * (1 - fy)[:, None] * at(i0, j0) + fx[:, None] * (1 - fy)[:, None] * at(i0 + 1, j0)
            + (1 - fx)[:, None] * fy[:, None] * at(i0, j0 + 1) + fx[:, None] * fy[:, None] * at(i0 + 1, j0 + 1))

@@ -65,9 +65,13 @@ _SIGS = {
     "clc_poisson_shtmg": (_i, [_p, _p, _i, ctypes.POINTER(MGParams), _p, ctypes.POINTER(Derivs)]),
     "clc_lens_derivs": (_i, [_p, _p, _p, _p, _p, _i64, ctypes.POINTER(Derivs)]),
     "clc_rays_init": (_i, [_p, _p, _p, _d, _i, ctypes.POINTER(Rays)]),
+    "clc_rays_init_pixels": (_i, [_p, _i, _d, _i, ctypes.POINTER(Rays)]),
     "clc_ray_step": (_i, [_p, _p, ctypes.POINTER(Derivs), _i, _d, _d, _d, ctypes.POINTER(Rays)]),
     "clc_raytrace_planes": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p), _i, _i, ctypes.POINTER(_d),
                                  ctypes.POINTER(Rays)]),
+    "clc_profile": (_i, [_p, _i]),
+    "clc_profile_query": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(_d)]),
+    "clc_launch_count": (_i64, [_p]),
 }
 
 
@@ -147,6 +151,19 @@ class Context:
     def release_caches(self):
         return self._check(lib().clc_release_caches(self.h))
 
+    def profile(self, enable=True):
+        return self._check(lib().clc_profile(self.h, 1 if enable else 0))
+
+    def profile_query(self, name):
+        """(launches, total device ms) recorded for kernel `name`."""
+        n = _i64()
+        ms = _d()
+        self._check(lib().clc_profile_query(self.h, name.encode(), ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def launch_count(self):
+        return int(lib().clc_launch_count(self.h))
+
     # -- step 1 -----------------------------------------------------------
     def bin_particles(self, z, phi, nside, ordering=RING, counts=None):
         if counts is None:
@@ -217,6 +234,10 @@ class Context:
     def rays_init(self, rays, z, phi, chi0, nside_bundle=0):
         self._check(lib().clc_rays_init(self.h, _ptr(z), _ptr(phi), float(chi0), int(nside_bundle),
                                         ctypes.byref(rays.struct())))
+
+    def rays_init_pixels(self, rays, nside, chi0, nside_bundle=0):
+        self._check(lib().clc_rays_init_pixels(self.h, int(nside), float(chi0), int(nside_bundle),
+                                               ctypes.byref(rays.struct())))
 
     def ray_step(self, rays, chi_prev, chi_n, chi_next, sol=None, maps=None, nside_maps=0):
         d = None

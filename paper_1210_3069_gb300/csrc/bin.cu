@@ -65,7 +65,7 @@ extern "C" int clc_bin_particles(clc_ctx* ctx, const double* z, const double* ph
   if (n == 0) return CLC_OK;
   if (!z || !phi || !counts) return set_err(ctx, CLC_EINVAL, "clc_bin_particles: null pointer");
   cudaSetDevice(ctx->device);
-  k_bin<<<grid_for(ctx, n, 256), 256, 0, ctx->stream>>>(z, phi, n, nside, ordering == CLC_NEST, counts);
+  CLC_LAUNCH(ctx, "k_bin", k_bin, grid_for(ctx, n, 256), 256, 0, z, phi, n, nside, ordering == CLC_NEST, counts);
   return launch_check(ctx, "k_bin");
 }
 
@@ -76,7 +76,7 @@ extern "C" int clc_counts_to_kappa(clc_ctx* ctx, const uint32_t* counts, int nsi
   if (!counts || !kappa) return set_err(ctx, CLC_EINVAL, "clc_counts_to_kappa: null pointer");
   cudaSetDevice(ctx->device);
   const int64_t npix = 12ll * nside * nside;
-  k_counts_to_kappa<<<grid_for(ctx, npix, 256), 256, 0, ctx->stream>>>(counts, npix, nbar, scale, kappa);
+  CLC_LAUNCH(ctx, "k_counts_to_kappa", k_counts_to_kappa, grid_for(ctx, npix, 256), 256, 0, counts, npix, nbar, scale, kappa);
   return launch_check(ctx, "k_counts_to_kappa");
 }
 
@@ -88,6 +88,6 @@ extern "C" int clc_degrade(clc_ctx* ctx, const double* fine, int nf, double* coa
   int shift = 0;
   while ((ns << (shift / 2)) < nf) shift += 2;
   const int64_t npc = 12ll * ns * ns;
-  k_degrade<<<grid_for(ctx, npc, 256), 256, 0, ctx->stream>>>(fine, nf, coarse, ns, shift);
+  CLC_LAUNCH(ctx, "k_degrade", k_degrade, grid_for(ctx, npc, 256), 256, 0, fine, nf, coarse, ns, shift);
   return launch_check(ctx, "k_degrade");
 }

@@ -38,6 +38,11 @@ struct clc_ctx {
   cudaStream_t stream = nullptr;
   std::string err;
   int* d_err = nullptr;  // device error word
+  // launch accounting and optional per-kernel CUDA-event timing
+  long long launches = 0;
+  bool prof = false;
+  std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
+  std::vector<cudaEvent_t> ev_pool;
   std::map<int, std::shared_ptr<clc::FftPlan>> fft_plans;
   std::map<std::tuple<int, int, int>, std::shared_ptr<clc::LegendreTable>> leg_tables;
   // growable scratch buffers, reused across calls on this context's stream
@@ -47,6 +52,37 @@ struct clc_ctx {
 namespace clc {
 
 int set_err(clc_ctx* ctx, int code, const std::string& msg);
+cudaEvent_t pool_event(clc_ctx* ctx);
+
+// Counts every kernel launch of a context and, while profiling is enabled,
+// brackets it with CUDA events on the context's stream.
+struct LaunchScope {
+  clc_ctx* ctx;
+  const char* name;
+  cudaEvent_t start = nullptr;
+  LaunchScope(clc_ctx* c, const char* n) : ctx(c), name(n) {
+    ++ctx->launches;
+    if (ctx->prof) {
+      start = pool_event(ctx);
+      if (start) cudaEventRecord(start, ctx->stream);
+    }
+  }
+  ~LaunchScope() {
+    if (start) {
+      cudaEvent_t stop = pool_event(ctx);
+      if (stop) {
+        cudaEventRecord(stop, ctx->stream);
+        ctx->prof_ev[name].push_back({start, stop});
+      }
+    }
+  }
+};
+
+#define CLC_LAUNCH(ctx, name, kern, g, b, s, ...)                    \
+  do {                                                               \
+    ::clc::LaunchScope _clc_ls((ctx), (name));                       \
+    kern<<<(g), (b), (s), (ctx)->stream>>>(__VA_ARGS__);             \
+  } while (0)
 int cuda_check(clc_ctx* ctx, cudaError_t e, const char* what);
 // Grow scratch buffer `slot` to at least `bytes`; returns nullptr on failure
 // (the context's error is set).

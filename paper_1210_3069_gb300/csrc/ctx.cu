@@ -19,6 +19,29 @@ int cuda_check(clc_ctx* ctx, cudaError_t e, const char* what) {
 
 int launch_check(clc_ctx* ctx, const char* what) { return cuda_check(ctx, cudaGetLastError(), what); }
 
+cudaEvent_t pool_event(clc_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return e;
+}
+
+static void prof_reset(clc_ctx* ctx) {
+  for (auto& kv : ctx->prof_ev)
+    for (auto& pr : kv.second) {
+      ctx->ev_pool.push_back(pr.first);
+      ctx->ev_pool.push_back(pr.second);
+    }
+  ctx->prof_ev.clear();
+}
+
 void* scratch(clc_ctx* ctx, int slot, size_t bytes) {
   Buffer& b = ctx->scratch[slot];
   if (b.bytes >= bytes && b.p) return b.p;
@@ -78,6 +101,8 @@ extern "C" int clc_destroy(clc_ctx* ctx) {
   if (!ctx) return CLC_EINVAL;
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  prof_reset(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   ctx->fft_plans.clear();
   ctx->leg_tables.clear();
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -113,3 +138,33 @@ extern "C" const char* clc_last_error(const clc_ctx* ctx) {
   if (!ctx) return "null context";
   return ctx->err.c_str();
 }
+
+extern "C" int clc_profile(clc_ctx* ctx, int enable) {
+  if (!ctx) return CLC_EINVAL;
+  cudaStreamSynchronize(ctx->stream);
+  if (enable) prof_reset(ctx);
+  ctx->prof = enable != 0;
+  return CLC_OK;
+}
+
+extern "C" int clc_profile_query(clc_ctx* ctx, const char* name, int64_t* launches, double* total_ms) {
+  if (!ctx || !name) return CLC_EINVAL;
+  int rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "profile sync");
+  if (rc) return rc;
+  int64_t n = 0;
+  double ms = 0.0;
+  auto it = ctx->prof_ev.find(name);
+  if (it != ctx->prof_ev.end())
+    for (auto& pr : it->second) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pr.first, pr.second) == cudaSuccess) {
+        ms += t;
+        ++n;
+      }
+    }
+  if (launches) *launches = n;
+  if (total_ms) *total_ms = ms;
+  return CLC_OK;
+}
+
+extern "C" int64_t clc_launch_count(const clc_ctx* ctx) { return ctx ? ctx->launches : -1; }

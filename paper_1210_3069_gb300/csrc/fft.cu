@@ -295,12 +295,12 @@ std::shared_ptr<FftPlan> get_fft_plan(clc_ctx* ctx, int nside, int* rc) {
   *rc = cuda_check(ctx, cudaMemcpyAsync(p->cls.p, cls.data(), sizeof(int4) * cls.size(), cudaMemcpyHostToDevice,
                                         ctx->stream), "plan upload");
   if (*rc) return nullptr;
-  k_twiddle<<<64, 256, 0, ctx->stream>>>((double2*)p->twiddle.p, mmax);
+  CLC_LAUNCH(ctx, "k_twiddle", k_twiddle, 64, 256, 0, (double2*)p->twiddle.p, mmax);
   PlanDev d = plan_dev(*p);
   if (nside > 1 && chirp_n > 0) {
     const int smem = mmax * (int)sizeof(double2);
     cudaFuncSetAttribute(k_bluestein_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    k_bluestein_tables<<<nside - 1, 256, smem, ctx->stream>>>(nside, d, (double2*)p->chirp.p, (double2*)p->filter.p);
+    CLC_LAUNCH(ctx, "k_bluestein_tables", k_bluestein_tables, nside - 1, 256, smem, nside, d, (double2*)p->chirp.p, (double2*)p->filter.p);
   }
   *rc = launch_check(ctx, "FFT plan build");
   if (*rc) return nullptr;
@@ -313,7 +313,7 @@ int ring_analysis(clc_ctx* ctx, const FftPlan& plan, const double* map, int lmax
   const int nside = plan.nside;
   const int smem = plan.mmax_fft * (int)sizeof(double2);
   cudaFuncSetAttribute(k_ring_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_ring_analysis<<<4 * nside - 1, 256, smem, ctx->stream>>>(map, nside, lmax, weight, F, ldf, plan_dev(plan));
+  CLC_LAUNCH(ctx, "k_ring_analysis", k_ring_analysis, 4 * nside - 1, 256, smem, map, nside, lmax, weight, F, ldf, plan_dev(plan));
   return launch_check(ctx, "k_ring_analysis");
 }
 
@@ -329,7 +329,7 @@ int ring_synthesis(clc_ctx* ctx, const FftPlan& plan, const double2* G, int ld, 
   for (int f = 0; f < 6; ++f) a.out[f] = out[f];
   const int smem = plan.smem_bytes;
   cudaFuncSetAttribute(k_ring_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_ring_synthesis<<<4 * nside - 1, 256, smem, ctx->stream>>>(a, nside, lmax, mode, plan.mmax_fft, plan_dev(plan));
+  CLC_LAUNCH(ctx, "k_ring_synthesis", k_ring_synthesis, 4 * nside - 1, 256, smem, a, nside, lmax, mode, plan.mmax_fft, plan_dev(plan));
   return launch_check(ctx, "k_ring_synthesis");
 }
 

@@ -121,7 +121,7 @@ std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int l
   cudaMemcpyAsync(d_ab.p, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, ctx->stream);
   cudaMemcpyAsync(d_ln.p, lognorm.data(), sizeof(double) * lognorm.size(), cudaMemcpyHostToDevice, ctx->stream);
   dim3 grid((T->R + 127) / 128, lmax + 1);
-  k_legendre_build<<<grid, 128, 0, ctx->stream>>>(nside, lmax, T->R, (const long long*)T->offsets.p,
+  CLC_LAUNCH(ctx, "k_legendre_build", k_legendre_build, grid, 128, 0, nside, lmax, T->R, (const long long*)T->offsets.p,
                                                   (const double*)d_ln.p, (const double2*)d_ab.p, (double*)T->data.p);
   *rc = launch_check(ctx, "k_legendre_build");
   // the coefficient buffers are freed when this function returns: wait for the build
@@ -174,7 +174,7 @@ int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, in
   dim3 grid((L + 1 + 63) / 64, L + 1);
   const int smem = 2 * T.R * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_legendre_analysis<<<grid, 256, smem, ctx->stream>>>(T.nside, L, T.R, (const long long*)T.offsets.p,
+  CLC_LAUNCH(ctx, "k_legendre_analysis", k_legendre_analysis, grid, 256, smem, T.nside, L, T.R, (const long long*)T.offsets.p,
                                                         (const double*)T.data.p, F, ldf, alm);
   return launch_check(ctx, "k_legendre_analysis");
 }
@@ -245,7 +245,7 @@ int legendre_synthesis(clc_ctx* ctx, const LegendreTable& T, const double2* rhs,
   dim3 grid((T.R + 127) / 128, L + 1);
   const int smem = nq * (L + 2) * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  k_legendre_synthesis<<<grid, 128, smem, ctx->stream>>>(T.nside, L, T.R, (const long long*)T.offsets.p,
+  CLC_LAUNCH(ctx, "k_legendre_synthesis", k_legendre_synthesis, grid, 128, smem, T.nside, L, T.R, (const long long*)T.offsets.p,
                                                          (const double*)T.data.p, s, G, ld);
   return launch_check(ctx, "k_legendre_synthesis");
 }

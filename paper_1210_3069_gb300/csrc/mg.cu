@@ -124,6 +124,18 @@ __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const doubl
   }
 }
 
+// diagonal of the operator at cell (i, j): aS + aN + 2b, plus the ghost
+// extrapolation terms of edge cells
+__device__ __forceinline__ double diag_at(const double* coef, int n, int i, int j) {
+  const double aS = coef[i], aN = coef[n + i], b = coef[2 * n + i];
+  double d = aS + aN + 2.0 * b;
+  if (i == 0) d += aN;
+  if (i == n - 1) d += aS;
+  if (j == 0) d += b;
+  if (j == n - 1) d += b;
+  return d;
+}
+
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
 // fine residual and of u over its 2 x 2 children.
 template <typename T>
@@ -149,7 +161,7 @@ __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, con
         const size_t c = (size_t)(i + 1) * side + (j + 1);
         const double uc_ = (double)U[c];
         const double nb = aS * (double)U[c + side] + aN * (double)U[c - side] + bb * ((double)U[c + 1] + (double)U[c - 1]);
-        const double r = (double)Fb[(size_t)i * n + j] - (nb - uc_ / invd[(size_t)i * n + j]);
+        const double r = (double)Fb[(size_t)i * n + j] - (nb - uc_ * diag_at(coef, n, i, j));
         nr += area * r;
         nu += area * uc_;
       }
@@ -177,7 +189,7 @@ __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const d
     const size_t c = (size_t)(i + 1) * side + (j + 1);
     const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
                       coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
-    f[idx] = (T)((double)f[idx] + (nb - (double)U[c] / invd[(size_t)i * n + j]));
+    f[idx] = (T)((double)f[idx] + (nb - (double)U[c] * diag_at(coef, n, i, j)));
   }
 }
 
@@ -254,7 +266,7 @@ __global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, cons
     const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
                       coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
     const double fv = (double)Fb[t];
-    const double r = fv - (nb - (double)U[c] / invd[t]);
+    const double r = fv - (nb - (double)U[c] * diag_at(coef, n, i, j));
     rr += r * r;
     ff += fv * fv;
   }
@@ -421,32 +433,30 @@ struct MG {
     const size_t work = (size_t)s->npatch * n * (n / 2);
     const int nb = blocks_for(ctx, work, 256);
     for (int colour = 0; colour < 2; ++colour)
-      k_smooth<T><<<nb, 256, 0, ctx->stream>>>(U(l), F(l), C(l), D(l), n, s->npatch, colour);
+      CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, nb, 256, 0, U(l), F(l), C(l), D(l), n, s->npatch, colour);
   }
 
   void vcycle(int l) {
     const int n = s->sizes[l];
     if (l == s->nlev - 1) {
-      k_coarse_solve<T><<<s->npatch, 64, n * n * sizeof(double), ctx->stream>>>(U(l), F(l), C(l),
+      CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C(l),
                                                                                  (const double*)s->coarse_inv.p, n);
       return;
     }
     for (int k = 0; k < s->p.nu1; ++k) smooth(l);
     const int nc = n / 2;
-    k_restrict<T><<<blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, ctx->stream>>>(
-        U(l), F(l), C(l), D(l), n, s->npatch, U(l + 1), U0(l + 1), F(l + 1));
-    k_coarse_rhs<T><<<blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, ctx->stream>>>(
-        U(l + 1), F(l + 1), C(l + 1), D(l + 1), nc, s->npatch);
+    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, U(l), F(l), C(l), D(l), n, s->npatch, U(l + 1), U0(l + 1), F(l + 1));
+    CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, U(l + 1), F(l + 1), C(l + 1), D(l + 1), nc, s->npatch);
     vcycle(l + 1);
-    k_prolong<T><<<blocks_for(ctx, (size_t)s->npatch * n * n, 256), 256, 0, ctx->stream>>>(U(l), U(l + 1), U0(l + 1),
+    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, blocks_for(ctx, (size_t)s->npatch * n * n, 256), 256, 0, U(l), U(l + 1), U0(l + 1),
                                                                                           n, s->npatch);
     for (int k = 0; k < s->p.nu2; ++k) smooth(l);
   }
 
   int residual(double* ratio_host) {
     const int n = s->sizes[0];
-    k_resnorm<T><<<s->npatch, 256, 0, ctx->stream>>>(U(0), F(0), C(0), D(0), n, (double*)s->norms.p);
-    k_max_ratio<<<1, 1024, 0, ctx->stream>>>((const double*)s->norms.p, s->npatch, (double*)s->ratio.p);
+    CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, s->npatch, 256, 0, U(0), F(0), C(0), D(0), n, (double*)s->norms.p);
+    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, s->npatch, (double*)s->ratio.p);
     int rc = launch_check(ctx, "MG residual");
     if (rc) return rc;
     rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -460,8 +470,7 @@ struct MG {
       const int n = s->sizes[l];
       const double hl = s->h * (s->sizes[0] / n);
       const size_t work = (size_t)s->npatch * (n + 2) * (n + 2);
-      k_mg_setup<T><<<blocks_for(ctx, work, 256), 256, 0, ctx->stream>>>(
-          s->npatch, n, hl, (const double*)s->rot.p, (const double*)s->psi_sht.p, s->p.nside_sht, kappa_fine,
+      CLC_LAUNCH(ctx, "k_mg_setup", k_mg_setup<T>, blocks_for(ctx, work, 256), 256, 0, s->npatch, n, hl, (const double*)s->rot.p, (const double*)s->psi_sht.p, s->p.nside_sht, kappa_fine,
           s->nside_fine, l == 0, U(l), F(l));
     }
     return launch_check(ctx, "MG setup");
@@ -592,7 +601,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     }
     cudaMemcpy(s->coarse_inv.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
-  k_mg_rotations<<<(s->npatch + 127) / 128, 128, 0, ctx->stream>>>(p->nside_bundle, s->npatch, (double*)s->rot.p);
+  CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch, (double*)s->rot.p);
   rc = launch_check(ctx, "k_mg_rotations");
   if (rc) {
     delete s;
@@ -645,7 +654,7 @@ extern "C" int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nf,
   if (st != CLC_OK && st != CLC_ENOTCONVERGED) return st;
   if (out && (out->a_th || out->a_ph || out->u_tt || out->u_pp || out->u_tp)) {
     const int64_t np = 12ll * nf * nf;
-    k_fields_at_pixels<<<blocks_for(ctx, np, 128), 128, 0, ctx->stream>>>(mg_view(s), nf, p->nside_bundle, out->a_th,
+    CLC_LAUNCH(ctx, "k_fields_at_pixels", k_fields_at_pixels, blocks_for(ctx, np, 128), 128, 0, mg_view(s), nf, p->nside_bundle, out->a_th,
                                                                          out->a_ph, out->u_tt, out->u_pp, out->u_tp);
     if ((rc = launch_check(ctx, "k_fields_at_pixels"))) return rc;
   }
@@ -659,7 +668,7 @@ extern "C" int clc_lens_derivs(clc_ctx* ctx, const clc_plane_solution* s, const 
   if (n == 0) return CLC_OK;
   if (!z || !phi) return set_err(ctx, CLC_EINVAL, "clc_lens_derivs: null positions");
   cudaSetDevice(ctx->device);
-  k_fields_at_points<<<blocks_for(ctx, n, 128), 128, 0, ctx->stream>>>(mg_view(s), z, phi, bundle, n,
+  CLC_LAUNCH(ctx, "k_fields_at_points", k_fields_at_points, blocks_for(ctx, n, 128), 128, 0, mg_view(s), z, phi, bundle, n,
                                                                       s->p.nside_bundle, out->a_th, out->a_ph,
                                                                       out->u_tt, out->u_pp, out->u_tp);
   return launch_check(ctx, "k_fields_at_points");

@@ -39,6 +39,25 @@ __global__ void k_rays_init(const double* __restrict__ z, const double* __restri
   }
 }
 
+// rays at every RING pixel centre of nside
+__global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
+  const int64_t n = R.n;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j;
+    const int i = pix2ring(nside, k, &j);
+    const Ring r = ring_geom(nside, i);
+    const double pp = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
+    const double v[3] = {r.s * cos(pp), r.s * sin(pp), r.z};
+    for (int c = 0; c < 3; ++c) {
+      R.x[c * n + k] = chi0 * v[c];
+      R.beta[c * n + k] = v[c];
+    }
+    R.A[k] = 1.0; R.A[n + k] = 0.0; R.A[2 * n + k] = 0.0; R.A[3 * n + k] = 1.0;
+    R.Ap[k] = 1.0; R.Ap[n + k] = 0.0; R.Ap[2 * n + k] = 0.0; R.Ap[3 * n + k] = 1.0;
+    if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)(ang2pix_nest(nside, r.z, pp) >> (2 * (ilog2(nside) - ilog2(nb))));
+  }
+}
+
 __device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
   const double rho = sqrt(n[0] * n[0] + n[1] * n[1]);
   t[0] = n[2] * n[0] / rho; t[1] = n[2] * n[1] / rho; t[2] = -rho;
@@ -228,8 +247,20 @@ extern "C" int clc_rays_init(clc_ctx* ctx, const double* z, const double* phi, d
   if (r->n == 0) return CLC_OK;
   if (!z || !phi) return set_err(ctx, CLC_EINVAL, "clc_rays_init: null positions");
   cudaSetDevice(ctx->device);
-  k_rays_init<<<blocks(ctx, r->n, 256), 256, 0, ctx->stream>>>(z, phi, chi0, nb, ray_ptrs(r));
+  CLC_LAUNCH(ctx, "k_rays_init", k_rays_init, blocks(ctx, r->n, 256), 256, 0, z, phi, chi0, nb, ray_ptrs(r));
   return launch_check(ctx, "k_rays_init");
+}
+
+extern "C" int clc_rays_init_pixels(clc_ctx* ctx, int nside, double chi0, int nb, clc_rays* r) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = rays_ok(ctx, r);
+  if (rc) return rc;
+  if (!valid_nside(nside) || !(chi0 > 0) || (nb > 0 && (!valid_nside(nb) || nb > nside)) ||
+      r->n != 12ll * nside * nside)
+    return set_err(ctx, CLC_EINVAL, "clc_rays_init_pixels: need n = 12 nside^2, chi0 > 0, nside_bundle <= nside");
+  cudaSetDevice(ctx->device);
+  CLC_LAUNCH(ctx, "k_rays_init", k_rays_init_pixels, blocks(ctx, r->n, 256), 256, 0, nside, chi0, nb, ray_ptrs(r));
+  return launch_check(ctx, "k_rays_init_pixels");
 }
 
 extern "C" int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const clc_derivs* maps, int nside_maps,
@@ -251,10 +282,10 @@ extern "C" int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const c
   clc_derivs M{};
   if (maps) M = *maps;
   if (sol) {
-    k_ray_step<true><<<blocks(ctx, r->n, 128), 128, 0, ctx->stream>>>(ray_ptrs(r), mg_view(sol), M, 0, sc);
+    CLC_LAUNCH(ctx, "k_ray_step", k_ray_step<true>, blocks(ctx, r->n, 128), 128, 0, ray_ptrs(r), mg_view(sol), M, 0, sc);
   } else {
     MGView V{};
-    k_ray_step<false><<<blocks(ctx, r->n, 128), 128, 0, ctx->stream>>>(ray_ptrs(r), V, M, nside_maps, sc);
+    CLC_LAUNCH(ctx, "k_ray_step", k_ray_step<false>, blocks(ctx, r->n, 128), 128, 0, ray_ptrs(r), V, M, nside_maps, sc);
   }
   return launch_check(ctx, "k_ray_step");
 }

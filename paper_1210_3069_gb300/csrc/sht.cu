@@ -110,7 +110,7 @@ extern "C" int clc_sht_synthesis(clc_ctx* ctx, const double* alm, int nside, int
   double2* rhs = (double2*)scratch(ctx, 2, sizeof(double2) * Q);
   if (!rhs) return CLC_ENOMEM;
   dim3 grid((lmax + 2 + 127) / 128, lmax + 1);
-  k_alm_expand<<<grid, 128, 0, ctx->stream>>>((const double2*)alm, lmax, rhs);
+  CLC_LAUNCH(ctx, "k_alm_expand", k_alm_expand, grid, 128, 0, (const double2*)alm, lmax, rhs);
   if ((rc = launch_check(ctx, "k_alm_expand"))) return rc;
   const int lq[1] = {lmax};
   double* out[6] = {map, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -136,7 +136,7 @@ extern "C" int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int
   double2* rhs = (double2*)scratch(ctx, 2, sizeof(double2) * Q * 3);
   if (!rhs) return CLC_ENOMEM;
   dim3 grid((lmax + 2 + 127) / 128, lmax + 1);
-  k_poisson_rhs<<<grid, 128, 0, ctx->stream>>>(klm, lmax, rhs, Q);
+  CLC_LAUNCH(ctx, "k_poisson_rhs", k_poisson_rhs, grid, 128, 0, klm, lmax, rhs, Q);
   if ((rc = launch_check(ctx, "k_poisson_rhs"))) return rc;
   if (!derivs) {
     const int lq[1] = {lmax};
