@@ -343,6 +343,54 @@ __device__ __forceinline__ Interp8 interp_weights(int nside, double theta, doubl
   return o;
 }
 
+// Same interpolation with the ring colatitudes taken from a table
+// (ring_th[i - 1] = theta of ring i).
+__device__ __forceinline__ Interp8 interp_weights_tab(int nside, const double* __restrict__ ring_th, double theta,
+                                                     double phi) {
+  Interp8 o;
+  const int nr = 4 * nside - 1;
+  int i1 = ring_above(nside, cos(theta), 0.0);
+  while (i1 >= 1 && ring_th[i1 - 1] > theta) --i1;
+  while (i1 + 1 <= nr && ring_th[i1] <= theta) ++i1;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) { o.p[k] = 0; o.w[k] = 0.0; }
+  if (i1 == 0 || i1 == nr) {
+    const int ir = (i1 == 0) ? 1 : nr;
+    const double tr = ring_th[ir - 1];
+    const double w = (i1 == 0) ? theta / tr : (kPi - theta) / (kPi - tr);
+    int64_t a0, a1;
+    double fa;
+    ring_pair(nside, ir, phi, &a0, &a1, &fa);
+    o.p[0] = a0; o.w[0] = w * (1.0 - fa);
+    o.p[1] = a1; o.w[1] = w * fa;
+    const Ring r = ring_geom(nside, ir);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { o.p[4 + k] = r.first + k; o.w[4 + k] = (1.0 - w) * 0.25; }
+    return o;
+  }
+  const double ta = ring_th[i1 - 1], tb = ring_th[i1];
+  const double w = (theta - ta) / (tb - ta);
+  int64_t a0, a1, b0, b1;
+  double fa, fb;
+  ring_pair(nside, i1, phi, &a0, &a1, &fa);
+  ring_pair(nside, i1 + 1, phi, &b0, &b1, &fb);
+  o.p[0] = a0; o.w[0] = (1.0 - w) * (1.0 - fa);
+  o.p[1] = a1; o.w[1] = (1.0 - w) * fa;
+  o.p[2] = b0; o.w[2] = w * (1.0 - fb);
+  o.p[3] = b1; o.w[3] = w * fb;
+  return o;
+}
+
+__device__ __forceinline__ double interp_map_tab(const double* __restrict__ map, int nside,
+                                                 const double* __restrict__ ring_th, double th, double ph) {
+  const Interp8 w = interp_weights_tab(nside, ring_th, th, ph);
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (w.w[k] != 0.0) v += w.w[k] * map[w.p[k]];
+  return v;
+}
+
 __device__ __forceinline__ void record_error(int* d_err, int code) {
   atomicCAS(d_err, 0, code);
 }

@@ -30,25 +30,13 @@ MGView mg_view(const clc_plane_solution* sol) {
   v.n = sol->sizes[0];
   v.h = sol->h;
   v.rot = (const double*)sol->rot.p;
-  v.u = sol->u[0].p;
-  v.fp32 = sol->p.precision == CLC_FP32;
+  v.u = (const double*)sol->base.p;
   return v;
 }
 
-__device__ __forceinline__ double edge_pos(int k, int n, double h) {
-  if (k == 0) return -0.5 * n * h;
-  if (k == n + 1) return 0.5 * n * h;
-  return ((double)k - 0.5 - 0.5 * n) * h;
-}
-
-__device__ __forceinline__ double interp_map(const double* map, int nside, double th, double ph) {
-  const Interp8 w = interp_weights(nside, th, ph);
-  double v = 0.0;
-#pragma unroll
-  for (int k = 0; k < 8; ++k)
-    if (w.w[k] != 0.0) v += w.w[k] * map[w.p[k]];
-  return v;
-}
+// Launch shape of the MG kernels: blocks of 32 x 8 threads over the cells of
+// one patch, blockIdx.z = patch (no 64-bit index division anywhere).
+constexpr int kBX = 32, kBY = 8;
 
 __global__ void k_mg_rotations(int nb, int npatch, double* rot) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
@@ -66,162 +54,150 @@ __global__ void k_mg_rotations(int nb, int npatch, double* rot) {
   R[6] = -z * cp; R[7] = -z * sp; R[8] = s;
 }
 
-// Ghost ring (2 psi_SHT at the edge faces) of one level; on the finest level
-// also the starting guess psi_SHT and the source kappa_fine at cell centres.
-template <typename T>
-__global__ void k_mg_setup(int npatch, int n, double h, const double* __restrict__ rot, const double* __restrict__ psi,
-                           int ns, const double* __restrict__ kappa, int nf, int finest, T* __restrict__ u,
-                           T* __restrict__ f) {
-  const size_t side = n + 2;
-  const size_t total = (size_t)npatch * side * side;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int b = (int)(idx / (side * side));
-    const int k1 = (int)((idx / side) % side), k2 = (int)(idx % side);
-    const bool ring = k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1;
-    if (!ring && !finest) {
-      u[idx] = (T)0;
-      continue;
-    }
-    const double tp = 0.5 * kPi + edge_pos(k1, n, h), pp = edge_pos(k2, n, h);
-    const double st = sin(tp), ct = cos(tp), sp = sin(pp), cp = cos(pp);
-    const double v[3] = {st * cp, st * sp, ct};
-    const double* R = rot + 9 * (size_t)b;
-    double g[3];
+// global colatitude / longitude of patch-frame vector v in patch b
+__device__ __forceinline__ void cell_angles(const double* R, const double* v, double* th, double* ph) {
+  double g[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) g[k] = R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2];
-    const double th = atan2(sqrt(g[0] * g[0] + g[1] * g[1]), g[2]);
-    double ph = atan2(g[1], g[0]);
-    if (ph < 0) ph += 2.0 * kPi;
-    const double ps = interp_map(psi, ns, th, ph);
-    if (ring) {
-      u[idx] = (T)(2.0 * ps);
-    } else {
-      u[idx] = (T)ps;
-      f[(size_t)b * n * n + (size_t)(k1 - 1) * n + (k2 - 1)] = (T)interp_map(kappa, nf, th, ph);
-    }
+  for (int k = 0; k < 3; ++k) g[k] = R[k] * v[0] + R[3 + k] * v[1] + R[6 + k] * v[2];
+  *th = atan2(sqrt(g[0] * g[0] + g[1] * g[1]), g[2]);
+  double p = atan2(g[1], g[0]);
+  if (p < 0) p += 2.0 * kPi;
+  *ph = p;
+}
+
+// base = psi_SHT at the cell centres, 2 psi_SHT at the edge faces (ghost ring)
+__global__ void k_mg_setup_base(int n, const double* __restrict__ rot, const double* __restrict__ pvec,
+                                const double* __restrict__ psi, int ns, const double* __restrict__ ring_th,
+                                double* __restrict__ base) {
+  const int b = blockIdx.z;
+  const int k1 = blockIdx.y * kBY + threadIdx.y, k2 = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  if (k1 >= side || k2 >= side) return;
+  const int cell = k1 * side + k2;
+  double th, ph;
+  cell_angles(rot + 9 * (size_t)b, pvec + 3 * (size_t)cell, &th, &ph);
+  const double v = interp_map_tab(psi, ns, ring_th, th, ph);
+  const bool ring = k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1;
+  base[(size_t)b * side * side + cell] = ring ? 2.0 * v : v;
+}
+
+// defect f' = kappa(cell) - L(base) and ||kappa||^2 per patch
+template <typename T>
+__global__ void k_mg_setup_defect(int n, const double* __restrict__ rot, const double* __restrict__ pvec,
+                                  const double* __restrict__ kappa, int nf, const double* __restrict__ ring_th,
+                                  const double* __restrict__ base, const double* __restrict__ coef,
+                                  const double* __restrict__ diag, T* __restrict__ f, double* __restrict__ fnorm) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  double ff = 0.0;
+  if (i < n && j < n) {
+    const int cell = (i + 1) * side + (j + 1);
+    double th, ph;
+    cell_angles(rot + 9 * (size_t)b, pvec + 3 * (size_t)cell, &th, &ph);
+    const double src = interp_map_tab(kappa, nf, ring_th, th, ph);
+    const double* U = base + (size_t)b * side * side;
+    const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
+    f[(size_t)b * n * n + (size_t)i * n + j] = (T)(src - (nb - diag[i * n + j] * U[cell]));
+    ff = src * src;
   }
+  for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
 }
 
 // One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == colour.
 template <typename T>
 __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
-                         const double* __restrict__ invd, int n, int npatch, int colour) {
-  const size_t half = n / 2;
-  const size_t total = (size_t)npatch * n * half;
+                         const double* __restrict__ invd, int n, int colour) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y;
+  const int j = 2 * (blockIdx.x * kBX + threadIdx.x) + ((i + colour) & 1);
+  if (i >= n || j >= n) return;
   const size_t side = n + 2;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int jj = (int)(idx % half);
-    const int i = (int)((idx / half) % n);
-    const size_t b = idx / (half * n);
-    const int j = 2 * jj + ((i + colour) & 1);
-    const T aS = (T)coef[i], aN = (T)coef[n + i], bb = (T)coef[2 * n + i];
-    T* U = u + b * side * side;
-    const size_t c = (size_t)(i + 1) * side + (j + 1);
-    const T nb = aS * U[c + side] + aN * U[c - side] + bb * (U[c + 1] + U[c - 1]);
-    U[c] = (nb - f[b * n * n + (size_t)i * n + j]) * (T)invd[(size_t)i * n + j];
-  }
-}
-
-// diagonal of the operator at cell (i, j): aS + aN + 2b, plus the ghost
-// extrapolation terms of edge cells
-__device__ __forceinline__ double diag_at(const double* coef, int n, int i, int j) {
-  const double aS = coef[i], aN = coef[n + i], b = coef[2 * n + i];
-  double d = aS + aN + 2.0 * b;
-  if (i == 0) d += aN;
-  if (i == n - 1) d += aS;
-  if (j == 0) d += b;
-  if (j == n - 1) d += b;
-  return d;
+  T* U = u + (size_t)b * side * side;
+  const size_t c = (size_t)(i + 1) * side + (j + 1);
+  const T aS = (T)coef[i], aN = (T)coef[n + i], bb = (T)coef[2 * n + i];
+  const T nb = aS * U[c + side] + aN * U[c - side] + bb * (U[c + 1] + U[c - 1]);
+  U[c] = (nb - f[(size_t)b * n * n + (size_t)i * n + j]) * (T)invd[i * n + j];
 }
 
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
-// fine residual and of u over its 2 x 2 children.
+// fine residual and of the correction over its 2 x 2 children.
 template <typename T>
 __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
-                           const double* __restrict__ invd, int n, int npatch, T* __restrict__ uc,
-                           T* __restrict__ uc0, T* __restrict__ fc) {
+                           const double* __restrict__ diag, int n, T* __restrict__ uc, T* __restrict__ uc0,
+                           T* __restrict__ fc) {
   const int nc = n / 2;
-  const size_t total = (size_t)npatch * nc * nc;
+  const int b = blockIdx.z;
+  const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
+  if (I >= nc || J >= nc) return;
   const size_t side = n + 2, sidec = nc + 2;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int J = (int)(idx % nc);
-    const int I = (int)((idx / nc) % nc);
-    const size_t b = idx / ((size_t)nc * nc);
-    const T* U = u + b * side * side;
-    const T* Fb = f + b * n * n;
-    double nr = 0.0, nu = 0.0;
-    for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di;
-      const double aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
-      for (int dj = 0; dj < 2; ++dj) {
-        const int j = 2 * J + dj;
-        const size_t c = (size_t)(i + 1) * side + (j + 1);
-        const double uc_ = (double)U[c];
-        const double nb = aS * (double)U[c + side] + aN * (double)U[c - side] + bb * ((double)U[c + 1] + (double)U[c - 1]);
-        const double r = (double)Fb[(size_t)i * n + j] - (nb - uc_ * diag_at(coef, n, i, j));
-        nr += area * r;
-        nu += area * uc_;
-      }
+  const T* U = u + (size_t)b * side * side;
+  const T* Fb = f + (size_t)b * n * n;
+  double nr = 0.0, nu = 0.0;
+#pragma unroll
+  for (int di = 0; di < 2; ++di) {
+    const int i = 2 * I + di;
+    const double aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj) {
+      const int j = 2 * J + dj;
+      const size_t c = (size_t)(i + 1) * side + (j + 1);
+      const double ucv = (double)U[c];
+      const double nb = aS * (double)U[c + side] + aN * (double)U[c - side] + bb * ((double)U[c + 1] + (double)U[c - 1]);
+      const double r = (double)Fb[(size_t)i * n + j] - (nb - ucv * diag[i * n + j]);
+      nr += area * r;
+      nu += area * ucv;
     }
-    const double den = 2.0 * (coef[3 * n + 2 * I] + coef[3 * n + 2 * I + 1]);
-    const T ur = (T)(nu / den);
-    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
-    uc0[b * (size_t)nc * nc + (size_t)I * nc + J] = ur;
-    fc[b * (size_t)nc * nc + (size_t)I * nc + J] = (T)(nr / den);
   }
+  const double den = 2.0 * (coef[3 * n + 2 * I] + coef[3 * n + 2 * I + 1]);
+  const T ur = (T)(nu / den);
+  uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+  uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
+  fc[(size_t)b * nc * nc + (size_t)I * nc + J] = (T)(nr / den);
 }
 
 // f_c += L_c(u_c) (the FAS coarse-grid source)
 template <typename T>
 __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const double* __restrict__ coef,
-                             const double* __restrict__ invd, int n, int npatch) {
-  const size_t total = (size_t)npatch * n * n;
+                             const double* __restrict__ diag, int n) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
   const size_t side = n + 2;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx % n);
-    const int i = (int)((idx / n) % n);
-    const size_t b = idx / ((size_t)n * n);
-    const T* U = u + b * side * side;
-    const size_t c = (size_t)(i + 1) * side + (j + 1);
-    const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
-                      coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
-    f[idx] = (T)((double)f[idx] + (nb - (double)U[c] * diag_at(coef, n, i, j)));
-  }
+  const T* U = u + (size_t)b * side * side;
+  const size_t c = (size_t)(i + 1) * side + (j + 1);
+  const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
+                    coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
+  T* Fp = f + (size_t)b * n * n + (size_t)i * n + j;
+  *Fp = (T)((double)*Fp + (nb - (double)U[c] * diag[i * n + j]));
 }
 
 // u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge
 template <typename T>
-__global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n, int npatch) {
+__global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n) {
   const int nc = n / 2;
-  const size_t total = (size_t)npatch * n * n;
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
   const size_t side = n + 2, sidec = nc + 2;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int j = (int)(idx % n);
-    const int i = (int)((idx / n) % n);
-    const size_t b = idx / ((size_t)n * n);
-    const int I = i >> 1, J = j >> 1;
-    const T* C = uc + b * sidec * sidec;
-    const T* C0 = uc0 + b * (size_t)nc * nc;
-    auto e = [&](int a, int c) -> double {
-      return (double)C[(size_t)(a + 1) * sidec + (c + 1)] - (double)C0[(size_t)a * nc + c];
-    };
-    double corr;
-    if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
-      corr = e(I, J);
-    } else {
-      const int Ii = min(max(I + ((i & 1) ? 1 : -1), 0), nc - 1);
-      const int Jj = min(max(J + ((j & 1) ? 1 : -1), 0), nc - 1);
-      corr = (9.0 * e(I, J) + 3.0 * e(Ii, J) + 3.0 * e(I, Jj) + e(Ii, Jj)) / 16.0;
-    }
-    T* U = u + b * side * side;
-    const size_t c = (size_t)(i + 1) * side + (j + 1);
-    U[c] = (T)((double)U[c] + corr);
+  const int I = i >> 1, J = j >> 1;
+  const T* C = uc + (size_t)b * sidec * sidec;
+  const T* C0 = uc0 + (size_t)b * nc * nc;
+  auto e = [&](int a, int c) -> double {
+    return (double)C[(size_t)(a + 1) * sidec + (c + 1)] - (double)C0[(size_t)a * nc + c];
+  };
+  double corr;
+  if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
+    corr = e(I, J);
+  } else {
+    const int Ii = I + ((i & 1) ? 1 : -1);
+    const int Jj = J + ((j & 1) ? 1 : -1);
+    corr = (9.0 * e(I, J) + 3.0 * e(Ii, J) + 3.0 * e(I, Jj) + e(Ii, Jj)) * 0.0625;
   }
+  T* U = u + (size_t)b * side * side;
+  const size_t c = (size_t)(i + 1) * side + (j + 1);
+  U[c] = (T)((double)U[c] + corr);
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -251,51 +227,32 @@ __global__ void k_coarse_solve(T* __restrict__ u, const T* __restrict__ f, const
   }
 }
 
-// per patch: ||f - L u||^2 and ||f||^2 on the finest level
+// ||f' - L e||^2 per patch (f' the defect source, e the correction)
 template <typename T>
 __global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
-                          const double* __restrict__ invd, int n, double* __restrict__ norms) {
-  const size_t b = blockIdx.x;
-  const size_t side = n + 2;
-  const T* U = u + b * side * side;
-  const T* Fb = f + b * (size_t)n * n;
-  double rr = 0.0, ff = 0.0;
-  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-    const int i = t / n, j = t % n;
+                          const double* __restrict__ diag, int n, double* __restrict__ norms) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  double rr = 0.0;
+  if (i < n && j < n) {
+    const size_t side = n + 2;
+    const T* U = u + (size_t)b * side * side;
     const size_t c = (size_t)(i + 1) * side + (j + 1);
     const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
                       coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
-    const double fv = (double)Fb[t];
-    const double r = fv - (nb - (double)U[c] * diag_at(coef, n, i, j));
-    rr += r * r;
-    ff += fv * fv;
+    const double r = (double)f[(size_t)b * n * n + (size_t)i * n + j] - (nb - (double)U[c] * diag[i * n + j]);
+    rr = r * r;
   }
-  __shared__ double s1[32], s2[32];
-  for (int o = 16; o > 0; o >>= 1) {
-    rr += __shfl_xor_sync(0xffffffffu, rr, o);
-    ff += __shfl_xor_sync(0xffffffffu, ff, o);
-  }
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) { s1[w] = rr; s2[w] = ff; }
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    rr = l < nw ? s1[l] : 0.0;
-    ff = l < nw ? s2[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) {
-      rr += __shfl_xor_sync(0xffffffffu, rr, o);
-      ff += __shfl_xor_sync(0xffffffffu, ff, o);
-    }
-    if (l == 0) { norms[2 * b] = rr; norms[2 * b + 1] = ff; }
-  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  if (threadIdx.x == 0 && rr != 0.0) atomicAdd(norms + b, rr);
 }
 
-__global__ void k_max_ratio(const double* __restrict__ norms, int npatch, double* __restrict__ out) {
+__global__ void k_max_ratio(const double* __restrict__ rr, const double* __restrict__ ff, int npatch,
+                            double* __restrict__ out) {
   double mx = 0.0;
   for (int b = threadIdx.x; b < npatch; b += blockDim.x) {
-    const double fn = sqrt(norms[2 * b + 1]);
-    const double r = sqrt(norms[2 * b]) / (fn > 0 ? fn : 1.0);
-    mx = fmax(mx, r);
+    const double fn = sqrt(ff[b]);
+    mx = fmax(mx, sqrt(rr[b]) / (fn > 0 ? fn : 1.0));
   }
   __shared__ double s[32];
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -306,6 +263,17 @@ __global__ void k_max_ratio(const double* __restrict__ norms, int npatch, double
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (threadIdx.x == 0) out[0] = mx;
   }
+}
+
+// final potential u = base + e (interior cells)
+template <typename T>
+__global__ void k_combine(double* __restrict__ base, const T* __restrict__ e, int n) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
+  const size_t side = n + 2;
+  const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
+  base[c] += (double)e[c];
 }
 
 // lens fields at every pixel centre of nside_fine, each in its own bundle's patch
@@ -390,13 +358,15 @@ static bool invert(std::vector<double>& A, int n) {
 
 struct LevelCoef {
   std::vector<double> coef;  // aS, aN, b, area
-  std::vector<double> invd;
+  std::vector<double> invd;  // 1 / diagonal
+  std::vector<double> diag;  // diagonal (ghost extrapolation terms included)
 };
 
 static LevelCoef level_coef(int n, double h) {
   LevelCoef L;
   L.coef.resize(4 * (size_t)n);
   L.invd.resize((size_t)n * n);
+  L.diag.resize((size_t)n * n);
   for (int i = 0; i < n; ++i) {
     const double th = 0.5 * kPi + (i + 0.5 - 0.5 * n) * h;
     const double s = std::sin(th), sp = std::sin(th + 0.5 * h), sm = std::sin(th - 0.5 * h);
@@ -413,10 +383,13 @@ static LevelCoef level_coef(int n, double h) {
       if (i == n - 1) d += aS;
       if (j == 0) d += b;
       if (j == n - 1) d += b;
+      L.diag[(size_t)i * n + j] = d;
       L.invd[(size_t)i * n + j] = 1.0 / d;
     }
   return L;
 }
+
+static dim3 grid3(int nx, int ny, int npatch) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, npatch); }
 
 template <typename T>
 struct MG {
@@ -427,36 +400,41 @@ struct MG {
   T* U0(int l) { return (T*)s->u0[l].p; }
   const double* C(int l) { return (const double*)s->coef[l].p; }
   const double* D(int l) { return (const double*)s->invd[l].p; }
+  const double* G(int l) { return (const double*)s->diag[l].p; }
 
   void smooth(int l) {
     const int n = s->sizes[l];
-    const size_t work = (size_t)s->npatch * n * (n / 2);
-    const int nb = blocks_for(ctx, work, 256);
+    const dim3 blk(kBX, kBY);
     for (int colour = 0; colour < 2; ++colour)
-      CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, nb, 256, 0, U(l), F(l), C(l), D(l), n, s->npatch, colour);
+      CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), blk, 0, U(l), F(l), C(l), D(l), n, colour);
   }
 
   void vcycle(int l) {
     const int n = s->sizes[l];
+    const dim3 blk(kBX, kBY);
     if (l == s->nlev - 1) {
       CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C(l),
-                                                                                 (const double*)s->coarse_inv.p, n);
+                 (const double*)s->coarse_inv.p, n);
       return;
     }
     for (int k = 0; k < s->p.nu1; ++k) smooth(l);
     const int nc = n / 2;
-    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, U(l), F(l), C(l), D(l), n, s->npatch, U(l + 1), U0(l + 1), F(l + 1));
-    CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, blocks_for(ctx, (size_t)s->npatch * nc * nc, 256), 256, 0, U(l + 1), F(l + 1), C(l + 1), D(l + 1), nc, s->npatch);
+    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), F(l), C(l), G(l), n, U(l + 1),
+               U0(l + 1), F(l + 1));
+    CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
+               G(l + 1), nc);
     vcycle(l + 1);
-    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, blocks_for(ctx, (size_t)s->npatch * n * n, 256), 256, 0, U(l), U(l + 1), U0(l + 1),
-                                                                                          n, s->npatch);
+    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, grid3(n, n, s->npatch), blk, 0, U(l), U(l + 1), U0(l + 1), n);
     for (int k = 0; k < s->p.nu2; ++k) smooth(l);
   }
 
   int residual(double* ratio_host) {
     const int n = s->sizes[0];
-    CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, s->npatch, 256, 0, U(0), F(0), C(0), D(0), n, (double*)s->norms.p);
-    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, s->npatch, (double*)s->ratio.p);
+    cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, U(0), F(0), C(0), G(0), n,
+               (double*)s->norms.p);
+    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
+               s->npatch, (double*)s->ratio.p);
     int rc = launch_check(ctx, "MG residual");
     if (rc) return rc;
     rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -465,41 +443,53 @@ struct MG {
     return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "residual sync");
   }
 
+  // base (SHT solution + edge values), defect source f' = kappa - L base,
+  // ||kappa||^2 per patch, and a zero starting correction
   int setup(const double* kappa_fine) {
-    for (int l = 0; l < s->nlev; ++l) {
-      const int n = s->sizes[l];
-      const double hl = s->h * (s->sizes[0] / n);
-      const size_t work = (size_t)s->npatch * (n + 2) * (n + 2);
-      CLC_LAUNCH(ctx, "k_mg_setup", k_mg_setup<T>, blocks_for(ctx, work, 256), 256, 0, s->npatch, n, hl, (const double*)s->rot.p, (const double*)s->psi_sht.p, s->p.nside_sht, kappa_fine,
-          s->nside_fine, l == 0, U(l), F(l));
-    }
+    const int n = s->sizes[0];
+    const dim3 blk(kBX, kBY);
+    CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
+               (const double*)s->rot.p, (const double*)s->pvec.p, (const double*)s->psi_sht.p, s->p.nside_sht,
+               (const double*)s->ring_th_sht.p, (double*)s->base.p);
+    cudaMemsetAsync(s->fnorm.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect<T>, grid3(n, n, s->npatch), blk, 0, n,
+               (const double*)s->rot.p, (const double*)s->pvec.p, kappa_fine, s->nside_fine,
+               (const double*)s->ring_th_fine.p, (const double*)s->base.p, C(0), G(0), F(0), (double*)s->fnorm.p);
+    cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
     return launch_check(ctx, "MG setup");
+  }
+
+  int finish() {
+    const int n = s->sizes[0];
+    CLC_LAUNCH(ctx, "k_combine", k_combine<T>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p, U(0), n);
+    return launch_check(ctx, "MG combine");
   }
 
   int solve() {
     int rc;
     double rr = 0.0;
     s->cycles = 0;
+    int st = CLC_OK;
     if (s->p.fixed_cycles > 0) {
       for (int k = 0; k < s->p.fixed_cycles; ++k) {
         vcycle(0);
         if ((rc = launch_check(ctx, "V-cycle"))) return rc;
       }
       s->cycles = s->p.fixed_cycles;
-      rc = residual(&rr);
-      s->residual = rr;
-      return rc;
-    }
-    if ((rc = residual(&rr))) return rc;
-    while (rr >= s->p.tol && s->cycles < s->p.max_cycles) {
-      vcycle(0);
-      if ((rc = launch_check(ctx, "V-cycle"))) return rc;
-      ++s->cycles;
       if ((rc = residual(&rr))) return rc;
+    } else {
+      if ((rc = residual(&rr))) return rc;
+      while (rr >= s->p.tol && s->cycles < s->p.max_cycles) {
+        vcycle(0);
+        if ((rc = launch_check(ctx, "V-cycle"))) return rc;
+        ++s->cycles;
+        if ((rc = residual(&rr))) return rc;
+      }
+      if (rr >= s->p.tol) st = set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
     }
     s->residual = rr;
-    if (rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
-    return CLC_OK;
+    if ((rc = finish())) return rc;
+    return st;
   }
 };
 
@@ -544,6 +534,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const size_t n = s->sizes[l];
     need += s->npatch * ((n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
   }
+  need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   if (need + (size_t)(1ull << 30) > freeb) {
@@ -565,17 +556,53 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const double hl = s->h * (p->ncell / (int)n);
     ok = alloc(s->u[l], s->npatch * (n + 2) * (n + 2) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
          (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) && alloc(s->coef[l], 4 * n * sizeof(double)) &&
-         alloc(s->invd[l], n * n * sizeof(double));
+         alloc(s->invd[l], n * n * sizeof(double)) && alloc(s->diag[l], n * n * sizeof(double));
     if (!ok) break;
+    // the ghost rings of the correction stay zero (homogeneous Dirichlet data)
+    cudaMemset(s->u[l].p, 0, s->u[l].bytes);
     LevelCoef lc = level_coef((int)n, hl);
     cudaMemcpy(s->coef[l].p, lc.coef.data(), lc.coef.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(s->invd[l].p, lc.invd.data(), lc.invd.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(s->diag[l].p, lc.diag.data(), lc.diag.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  const size_t n0 = s->sizes[0];
+  ok = ok && alloc(s->base, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
+       alloc(s->pvec, (n0 + 2) * (n0 + 2) * 3 * sizeof(double)) &&
+       alloc(s->ring_th_sht, (4 * p->nside_sht - 1) * sizeof(double)) &&
+       alloc(s->ring_th_fine, (4 * nf - 1) * sizeof(double)) && alloc(s->fnorm, s->npatch * sizeof(double));
+  if (ok) {
+    // patch-frame unit vectors: cell centres inside, edge-face centres on the ring
+    std::vector<double> pv((n0 + 2) * (n0 + 2) * 3);
+    auto pos = [&](size_t k) {
+      if (k == 0) return -0.5 * n0 * s->h;
+      if (k == n0 + 1) return 0.5 * n0 * s->h;
+      return ((double)k - 0.5 - 0.5 * n0) * s->h;
+    };
+    for (size_t k1 = 0; k1 < n0 + 2; ++k1)
+      for (size_t k2 = 0; k2 < n0 + 2; ++k2) {
+        const double tp = 0.5 * kPi + pos(k1), pp = pos(k2);
+        double* v = &pv[3 * (k1 * (n0 + 2) + k2)];
+        v[0] = std::sin(tp) * std::cos(pp);
+        v[1] = std::sin(tp) * std::sin(pp);
+        v[2] = std::cos(tp);
+      }
+    cudaMemcpy(s->pvec.p, pv.data(), pv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    for (int which = 0; which < 2; ++which) {
+      const int ns = which ? nf : p->nside_sht;
+      std::vector<double> th(4 * ns - 1);
+      for (int i = 1; i <= 4 * ns - 1; ++i) {
+        const Ring r = ring_geom(ns, i);
+        th[i - 1] = std::atan2(r.s, r.z);
+      }
+      cudaMemcpy(which ? s->ring_th_fine.p : s->ring_th_sht.p, th.data(), th.size() * sizeof(double),
+                 cudaMemcpyHostToDevice);
+    }
   }
   const int nc = s->sizes.back();
   const size_t ns2 = 12ull * p->nside_sht * p->nside_sht;
   ok = ok && alloc(s->rot, 9 * sizeof(double) * s->npatch) && alloc(s->coarse_inv, sizeof(double) * nc * nc * nc * nc) &&
        alloc(s->psi_sht, sizeof(double) * ns2) && alloc(s->kappa_sht, sizeof(double) * ns2) &&
-       alloc(s->norms, 2 * sizeof(double) * s->npatch) && alloc(s->ratio, sizeof(double));
+       alloc(s->norms, sizeof(double) * s->npatch) && alloc(s->ratio, sizeof(double));
   if (!ok) {
     delete s;
     return set_err(ctx, CLC_ENOMEM, "MG allocation failed");
@@ -601,7 +628,8 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     }
     cudaMemcpy(s->coarse_inv.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
-  CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch, (double*)s->rot.p);
+  CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch,
+             (double*)s->rot.p);
   rc = launch_check(ctx, "k_mg_rotations");
   if (rc) {
     delete s;
@@ -654,8 +682,8 @@ extern "C" int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nf,
   if (st != CLC_OK && st != CLC_ENOTCONVERGED) return st;
   if (out && (out->a_th || out->a_ph || out->u_tt || out->u_pp || out->u_tp)) {
     const int64_t np = 12ll * nf * nf;
-    CLC_LAUNCH(ctx, "k_fields_at_pixels", k_fields_at_pixels, blocks_for(ctx, np, 128), 128, 0, mg_view(s), nf, p->nside_bundle, out->a_th,
-                                                                         out->a_ph, out->u_tt, out->u_pp, out->u_tp);
+    CLC_LAUNCH(ctx, "k_fields_at_pixels", k_fields_at_pixels, blocks_for(ctx, np, 128), 128, 0, mg_view(s), nf,
+               p->nside_bundle, out->a_th, out->a_ph, out->u_tt, out->u_pp, out->u_tp);
     if ((rc = launch_check(ctx, "k_fields_at_pixels"))) return rc;
   }
   return st;
@@ -668,8 +696,7 @@ extern "C" int clc_lens_derivs(clc_ctx* ctx, const clc_plane_solution* s, const 
   if (n == 0) return CLC_OK;
   if (!z || !phi) return set_err(ctx, CLC_EINVAL, "clc_lens_derivs: null positions");
   cudaSetDevice(ctx->device);
-  CLC_LAUNCH(ctx, "k_fields_at_points", k_fields_at_points, blocks_for(ctx, n, 128), 128, 0, mg_view(s), z, phi, bundle, n,
-                                                                      s->p.nside_bundle, out->a_th, out->a_ph,
-                                                                      out->u_tt, out->u_pp, out->u_tp);
+  CLC_LAUNCH(ctx, "k_fields_at_points", k_fields_at_points, blocks_for(ctx, n, 128), 128, 0, mg_view(s), z, phi,
+             bundle, n, s->p.nside_bundle, out->a_th, out->a_ph, out->u_tt, out->u_pp, out->u_tp);
   return launch_check(ctx, "k_fields_at_points");
 }

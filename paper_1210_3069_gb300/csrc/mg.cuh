@@ -10,9 +10,14 @@ struct clc_plane_solution {
   int npatch = 0, nlev = 0;
   double h = 0;                 // finest cell size (radians)
   std::vector<int> sizes;       // cells per side per level
-  clc::Buffer u[16], f[16], u0[16];  // per level: u with ghost ring, source, restricted u
+  clc::Buffer u[16], f[16], u0[16];  // per level: correction e (zero ghost ring), source, restricted e
+  clc::Buffer base;             // double[npatch][(n+2)^2]: SHT solution inside, 2 g on the ring; final u
+  clc::Buffer pvec;             // double[(n+2)^2][3]: patch-frame unit vectors of the finest level
+  clc::Buffer ring_th_sht, ring_th_fine;  // ring colatitude tables
+  clc::Buffer fnorm;            // double[npatch]: ||f||^2 of the source
   clc::Buffer coef[16];         // double[4][n] per level: aS, aN, b, area
   clc::Buffer invd[16];         // double[n][n] per level: 1 / diagonal
+  clc::Buffer diag[16];         // double[n][n] per level: diagonal
   clc::Buffer rot;              // double[npatch][9]: R_b (global -> patch frame)
   clc::Buffer coarse_inv;       // double[nc^2][nc^2]
   clc::Buffer psi_sht;          // double[12 nside_sht^2]
@@ -30,8 +35,7 @@ struct MGView {
   int n;           // finest cells per side
   double h;        // finest cell size
   const double* rot;
-  const void* u;   // finest level potential with ghost ring
-  int fp32;
+  const double* u; // finest level potential u = u_SHT + e (ghost-ring layout)
 };
 
 MGView mg_view(const clc_plane_solution* sol);

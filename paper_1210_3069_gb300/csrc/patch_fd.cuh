@@ -130,11 +130,7 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
 
 __device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], double out[5]) {
   const size_t stride = (size_t)(V.n + 2) * (V.n + 2);
-  const double* R = V.rot + 9 * (size_t)b;
-  if (V.fp32)
-    patch_lens_fields_t((const float*)V.u + stride * b, V.n, V.h, R, nv, out);
-  else
-    patch_lens_fields_t((const double*)V.u + stride * b, V.n, V.h, R, nv, out);
+  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.rot + 9 * (size_t)b, nv, out);
 }
 
 }  // namespace clc
