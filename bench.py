@@ -50,6 +50,10 @@ WORKLOADS = {
 }
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+KERNELS = ("k_smooth", "k_restrict", "k_coarse_rhs", "k_prolong", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
+           "k_add_mixed", "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
+           "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",
+           "k_degrade", "k_rays_init", "k_counts_to_kappa", "k_max_ratio")
 
 
 def load_peaks():
@@ -116,14 +120,54 @@ def plane_geometry():
     return pl["chi"][m - 1], pl["chi"][m], pl["chi"][m + 1], pl["scale"][m] * pl["growth"][m]
 
 
-def smg_flops_per_cycle(cfg, npatch):
-    """Algorithmic FP64 flops of the red-black smoother per V-cycle: 8 per
-    updated cell (4-neighbour stencil, source, reciprocal diagonal)."""
-    n, tot = cfg["ncell"], 0
+def kernel_models(cfg, precision, cycles, nsteps):
+    """Algorithmic work of the modelled kernels over the timed steps:
+    {name: (bound, amount, unit)}.  FP64 flops count a fused multiply-add
+    as 2.  Red-black smoothing per updated cell: 3 FMA + 1 add + 1 multiply
+    (8 flops) in FP64; in FP32 it streams the level once per colour:
+    8 bytes per cell per launch (u read, f and u of that colour).  The FP64
+    residual of the mixed path: 11 flops per fine cell."""
+    npatch = 12 * cfg["nside_bundle"] ** 2
+    sweeps = cfg["nu1"] + cfg["nu2"]
+    cells_cycle = 0
+    n = cfg["ncell"]
     while n > 8:
-        tot += (cfg["nu1"] + cfg["nu2"]) * npatch * n * n * 8
+        cells_cycle += npatch * n * n
         n //= 2
-    return tot
+    ncyc = sum(cycles)
+    out = {}
+    if precision == "fp64":
+        out["k_smooth"] = ("alu", 8.0 * sweeps * cells_cycle * ncyc, "flop")
+    else:
+        out["k_smooth"] = ("hbm", 8.0 * 2 * sweeps * cells_cycle * ncyc, "byte")
+    if precision == "mixed":
+        n0 = cfg["ncell"]
+        out["k_resid_mixed"] = ("alu", 11.0 * npatch * n0 * n0 * (ncyc + nsteps), "flop")
+    return out
+
+
+def roofline(prof, models, peaks, peak_kind):
+    """Roofline entries of the modelled kernels, largest total time first."""
+    ents = []
+    for name, (bound, amount, unit) in models.items():
+        n, ms = prof.get(name, (0, 0.0))
+        if ms <= 0:
+            continue
+        if bound == "alu":
+            ach = amount / (ms / 1e3) / 1e12
+            ents.append({"kernel": name, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "launches": n,
+                         "avg_launch_ms": ms / n,
+                         "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (derived; an FMA "
+                                        "microbenchmark measured 1.20 TFLOP/s)"})
+        else:
+            ach = amount / (ms / 1e3) / 1e9
+            pk = peaks.get("hbm_gbs", 6800.0)
+            ents.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                         "frac": ach / pk, "traffic": None, "launches": n, "avg_launch_ms": ms / n,
+                         "peak_source": f"HBM copy, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"})
+    ents.sort(key=lambda e: -e["avg_launch_ms"] * e["launches"])
+    return ents
 
 
 def run_gpu(args, cfg, rank, world):
@@ -135,7 +179,7 @@ def run_gpu(args, cfg, rank, world):
     nf = cfg["nside"]
     npix = 12 * nf * nf
     chi_prev, chi_n, chi_next, scale = plane_geometry()
-    prec = clc.FP32 if args.precision == "fp32" else clc.FP64
+    prec = {"fp32": clc.FP32, "fp64": clc.FP64, "mixed": clc.MIXED}[args.precision]
     P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
                       nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=prec)
     # seeded synthetic plane (a different shell per rank)
@@ -185,10 +229,7 @@ def run_gpu(args, cfg, rank, world):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     launches = ctx.launch_count() - launches0
-    prof = {k: ctx.profile_query(k) for k in ("k_smooth", "k_restrict", "k_coarse_rhs", "k_prolong", "k_coarse_solve",
-                                              "k_resnorm", "k_mg_setup", "k_ray_step", "k_bin", "k_legendre_analysis",
-                                              "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis",
-                                              "k_degrade", "k_rays_init", "k_counts_to_kappa")}
+    prof = {k: ctx.profile_query(k) for k in KERNELS}
     ctx.profile(False)
     timed_cycles = cycles[-args.steps:]
     if world > 1:
@@ -210,12 +251,8 @@ def run_gpu(args, cfg, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         e2e_ms = float(t)
     sol.close()
-    npatch = 12 * cfg["nside_bundle"] ** 2
-    flops = smg_flops_per_cycle(cfg, npatch) * sum(timed_cycles)
-    sm_n, sm_ms = prof["k_smooth"]
-    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, cycles=timed_cycles, smooth_flops=flops,
-                smooth_launches=sm_n, smooth_ms=sm_ms, clocks=clocks.summary(), npix=npix,
-                h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
+    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, cycles=timed_cycles, clocks=clocks.summary(),
+                npix=npix, h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
 
 
 # ---------------------------------------------------------------------------
@@ -300,7 +337,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
+                    help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
     ap.add_argument("--workload", default="shtmg_plane_nside2048", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -338,19 +376,18 @@ def main():
     peaks, peak_kind = load_peaks()
     planes = world * args.steps
     value = planes / (r["ms"] / 1000.0)
-    achieved = r["smooth_flops"] / (r["smooth_ms"] / 1000.0) / 1e12 if r["smooth_ms"] > 0 else None
+    roof = roofline(r["prof"], kernel_models(cfg, args.precision, r["cycles"], args.steps), peaks, peak_kind)
+    top = max(r["prof"].items(), key=lambda kv: kv[1][1])[0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic", "config": config,
+        "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}[args.precision], "data": "synthetic",
+        "config": config,
         "rays_per_s": world * r["npix"] * args.steps / (r["ms"] / 1000.0),
         "mg_cycles": r["cycles"],
-        "roofline": {"kernel": "k_smooth (red-black Gauss-Seidel, all levels)", "bound": "alu",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS if achieved else None, "traffic": None,
-                     "peak_source": "FP64: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; an FMA microbenchmark "
-                                    "measured 1.20 TFLOP/s)",
-                     "hbm_peak_gbs": peaks.get("hbm_gbs"), "hbm_peak_source": peak_kind},
+        "top_kernel": top,
+        "roofline": roof[0] if roof else None,
+        "roofline_all": roof,
         "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in r["prof"].items()},
         "e2e": {"value": world / (r["e2e_ms"] / 1000.0), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},

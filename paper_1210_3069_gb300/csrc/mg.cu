@@ -105,10 +105,74 @@ __global__ void k_mg_setup_defect(int n, const double* __restrict__ rot, const d
   if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
 }
 
+// Interpolation plan of one map for the positions of a patch level: either
+// all (n+2)^2 positions (ring = 1) or the n^2 interior cells (ring = 0).
+__global__ void k_mg_plan(int n, int ring, const double* __restrict__ rot, const double* __restrict__ pvec, int nside,
+                          const double* __restrict__ ring_th, int4* __restrict__ idx, double4_32a* __restrict__ w) {
+  const int b = blockIdx.z;
+  const int side = n + 2;
+  const int m = ring ? side : n;
+  const int k1 = blockIdx.y * kBY + threadIdx.y, k2 = blockIdx.x * kBX + threadIdx.x;
+  if (k1 >= m || k2 >= m) return;
+  const int cell = ring ? k1 * side + k2 : (k1 + 1) * side + (k2 + 1);
+  double th, ph;
+  cell_angles(rot + 9 * (size_t)b, pvec + 3 * (size_t)cell, &th, &ph);
+  const Interp8 o = interp_weights_tab(nside, ring_th, th, ph);
+  const size_t pos = (size_t)b * m * m + (size_t)k1 * m + k2;
+  if (o.w[4] != 0.0 || o.w[5] != 0.0) {
+    idx[pos] = make_int4(-1, 0, 0, 0);
+    w[pos] = double4_32a{th, ph, 0.0, 0.0};
+    return;
+  }
+  idx[pos] = make_int4((int)o.p[0], (int)o.p[1], (int)o.p[2], (int)o.p[3]);
+  w[pos] = double4_32a{o.w[0], o.w[1], o.w[2], o.w[3]};
+}
+
+__device__ __forceinline__ double apply_plan(const double* __restrict__ map, int nside, const double* __restrict__ ring_th,
+                                             int4 ix, double4_32a w) {
+  if (ix.x < 0) return interp_map_tab(map, nside, ring_th, w.x, w.y);
+  return w.x * map[ix.x] + w.y * map[ix.y] + w.z * map[ix.z] + w.w * map[ix.w];
+}
+
+__global__ void k_mg_setup_base_plan(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
+                                     const double* __restrict__ psi, int ns, const double* __restrict__ ring_th,
+                                     double* __restrict__ base) {
+  const int b = blockIdx.z;
+  const int k1 = blockIdx.y * kBY + threadIdx.y, k2 = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  if (k1 >= side || k2 >= side) return;
+  const size_t pos = (size_t)b * side * side + (size_t)k1 * side + k2;
+  const double v = apply_plan(psi, ns, ring_th, idx[pos], w[pos]);
+  const bool ring = k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1;
+  base[pos] = ring ? 2.0 * v : v;
+}
+
+template <typename T>
+__global__ void k_mg_setup_defect_plan(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
+                                       const double* __restrict__ kappa, int nf, const double* __restrict__ ring_th,
+                                       const double* __restrict__ base, const double* __restrict__ coef,
+                                       const double* __restrict__ diag, T* __restrict__ f, double* __restrict__ fnorm) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  double ff = 0.0;
+  if (i < n && j < n) {
+    const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
+    const double src = apply_plan(kappa, nf, ring_th, idx[pos], w[pos]);
+    const int cell = (i + 1) * side + (j + 1);
+    const double* U = base + (size_t)b * side * side;
+    const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
+    f[pos] = (T)(src - (nb - diag[i * n + j] * U[cell]));
+    ff = src * src;
+  }
+  for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
+}
+
 // One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == colour.
 template <typename T>
-__global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
-                         const double* __restrict__ invd, int n, int colour) {
+__global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ coef,
+                         const T* __restrict__ invd, int n, int colour) {
   const int b = blockIdx.z;
   const int i = blockIdx.y * kBY + threadIdx.y;
   const int j = 2 * (blockIdx.x * kBX + threadIdx.x) + ((i + colour) & 1);
@@ -116,17 +180,18 @@ __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const doubl
   const size_t side = n + 2;
   T* U = u + (size_t)b * side * side;
   const size_t c = (size_t)(i + 1) * side + (j + 1);
-  const T aS = (T)coef[i], aN = (T)coef[n + i], bb = (T)coef[2 * n + i];
-  const T nb = aS * U[c + side] + aN * U[c - side] + bb * (U[c + 1] + U[c - 1]);
-  U[c] = (nb - f[(size_t)b * n * n + (size_t)i * n + j]) * (T)invd[i * n + j];
+  const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
+  // (aS uS + aN uN + b (uE + uW) - f) / diag as three fused multiply-adds
+  const T t = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -f[(size_t)b * n * n + (size_t)i * n + j])));
+  U[c] = t * invd[i * n + j];
 }
 
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
 // fine residual and of the correction over its 2 x 2 children.
 template <typename T>
-__global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, const double* __restrict__ coef,
-                           const double* __restrict__ diag, int n, T* __restrict__ uc, T* __restrict__ uc0,
-                           T* __restrict__ fc) {
+__global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ coef,
+                           const T* __restrict__ diag, const T* __restrict__ rden, int n, T* __restrict__ uc,
+                           T* __restrict__ uc0, T* __restrict__ fc) {
   const int nc = n / 2;
   const int b = blockIdx.z;
   const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
@@ -134,43 +199,45 @@ __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, con
   const size_t side = n + 2, sidec = nc + 2;
   const T* U = u + (size_t)b * side * side;
   const T* Fb = f + (size_t)b * n * n;
-  double nr = 0.0, nu = 0.0;
+  T nr = 0, nu = 0;
 #pragma unroll
   for (int di = 0; di < 2; ++di) {
     const int i = 2 * I + di;
-    const double aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+    const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+    T rs = 0, us = 0;
 #pragma unroll
     for (int dj = 0; dj < 2; ++dj) {
       const int j = 2 * J + dj;
       const size_t c = (size_t)(i + 1) * side + (j + 1);
-      const double ucv = (double)U[c];
-      const double nb = aS * (double)U[c + side] + aN * (double)U[c - side] + bb * ((double)U[c + 1] + (double)U[c - 1]);
-      const double r = (double)Fb[(size_t)i * n + j] - (nb - ucv * diag[i * n + j]);
-      nr += area * r;
-      nu += area * ucv;
+      const T ucv = U[c];
+      // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
+      const T nb = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -diag[i * n + j] * ucv)));
+      rs += Fb[(size_t)i * n + j] - nb;
+      us += ucv;
     }
+    nr = fma(area, rs, nr);
+    nu = fma(area, us, nu);
   }
-  const double den = 2.0 * (coef[3 * n + 2 * I] + coef[3 * n + 2 * I + 1]);
-  const T ur = (T)(nu / den);
+  const T rd = rden[I];   // 1 / (2 (area_{2I} + area_{2I+1}))
+  const T ur = nu * rd;
   uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
   uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
-  fc[(size_t)b * nc * nc + (size_t)I * nc + J] = (T)(nr / den);
+  fc[(size_t)b * nc * nc + (size_t)I * nc + J] = nr * rd;
 }
 
 // f_c += L_c(u_c) (the FAS coarse-grid source)
 template <typename T>
-__global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const double* __restrict__ coef,
-                             const double* __restrict__ diag, int n) {
+__global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T* __restrict__ coef,
+                             const T* __restrict__ diag, int n) {
   const int b = blockIdx.z;
   const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
   if (i >= n || j >= n) return;
   const size_t side = n + 2;
   const T* U = u + (size_t)b * side * side;
   const size_t c = (size_t)(i + 1) * side + (j + 1);
-  const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
-                    coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
+  const T nb = fma(coef[2 * n + i], U[c + 1] + U[c - 1], fma(coef[n + i], U[c - side], fma(coef[i], U[c + side], -diag[i * n + j] * U[c])));
   T* Fp = f + (size_t)b * n * n + (size_t)i * n + j;
-  *Fp = (T)((double)*Fp + (nb - (double)U[c] * diag[i * n + j]));
+  *Fp = *Fp + nb;
 }
 
 // u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge
@@ -184,20 +251,18 @@ __global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* 
   const int I = i >> 1, J = j >> 1;
   const T* C = uc + (size_t)b * sidec * sidec;
   const T* C0 = uc0 + (size_t)b * nc * nc;
-  auto e = [&](int a, int c) -> double {
-    return (double)C[(size_t)(a + 1) * sidec + (c + 1)] - (double)C0[(size_t)a * nc + c];
-  };
-  double corr;
+  auto e = [&](int a, int c) -> T { return C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c]; };
+  T corr;
   if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
     corr = e(I, J);
   } else {
     const int Ii = I + ((i & 1) ? 1 : -1);
     const int Jj = J + ((j & 1) ? 1 : -1);
-    corr = (9.0 * e(I, J) + 3.0 * e(Ii, J) + 3.0 * e(I, Jj) + e(Ii, Jj)) * 0.0625;
+    corr = fma((T)9, e(I, J), fma((T)3, e(Ii, J) + e(I, Jj), e(Ii, Jj))) * (T)0.0625;
   }
   T* U = u + (size_t)b * side * side;
   const size_t c = (size_t)(i + 1) * side + (j + 1);
-  U[c] = (T)((double)U[c] + corr);
+  U[c] += corr;
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -263,6 +328,39 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (threadIdx.x == 0) out[0] = mx;
   }
+}
+
+// FP64 residual of the correction equation r = f' - L e64; its FP32 copy is
+// the source of the next FP32 V-cycle; ||r||^2 accumulated per patch
+__global__ void k_resid_mixed(const double* __restrict__ e, const double* __restrict__ fd,
+                              const double* __restrict__ coef, const double* __restrict__ diag, int n,
+                              float* __restrict__ r32, double* __restrict__ norms) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  double rr = 0.0;
+  if (i < n && j < n) {
+    const size_t side = n + 2;
+    const double* U = e + (size_t)b * side * side;
+    const size_t c = (size_t)(i + 1) * side + (j + 1);
+    const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
+    const double nb = fma(coef[2 * n + i], U[c + 1] + U[c - 1],
+                          fma(coef[n + i], U[c - side], fma(coef[i], U[c + side], -diag[i * n + j] * U[c])));
+    const double r = fd[pos] - nb;
+    r32[pos] = (float)r;
+    rr = r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  if (threadIdx.x == 0 && rr != 0.0) atomicAdd(norms + b, rr);
+}
+
+// e64 += delta32 on the interior cells
+__global__ void k_add_mixed(double* __restrict__ e, const float* __restrict__ d, int n) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
+  const size_t side = n + 2;
+  const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
+  e[c] += (double)d[c];
 }
 
 // final potential u = base + e (interior cells)
@@ -360,6 +458,7 @@ struct LevelCoef {
   std::vector<double> coef;  // aS, aN, b, area
   std::vector<double> invd;  // 1 / diagonal
   std::vector<double> diag;  // diagonal (ghost extrapolation terms included)
+  std::vector<double> rden;  // 1 / (2 (area_2I + area_2I+1)) for the coarse rows
 };
 
 static LevelCoef level_coef(int n, double h) {
@@ -386,6 +485,8 @@ static LevelCoef level_coef(int n, double h) {
       L.diag[(size_t)i * n + j] = d;
       L.invd[(size_t)i * n + j] = 1.0 / d;
     }
+  L.rden.resize(n / 2 > 0 ? n / 2 : 1);
+  for (int I = 0; I < n / 2; ++I) L.rden[I] = 1.0 / (2.0 * (L.coef[3 * n + 2 * I] + L.coef[3 * n + 2 * I + 1]));
   return L;
 }
 
@@ -395,12 +496,17 @@ template <typename T>
 struct MG {
   clc_plane_solution* s;
   clc_ctx* ctx;
+  bool mixed = false;  // FP32 V-cycles on an FP64 residual equation
   T* U(int l) { return (T*)s->u[l].p; }
   T* F(int l) { return (T*)s->f[l].p; }
   T* U0(int l) { return (T*)s->u0[l].p; }
-  const double* C(int l) { return (const double*)s->coef[l].p; }
-  const double* D(int l) { return (const double*)s->invd[l].p; }
-  const double* G(int l) { return (const double*)s->diag[l].p; }
+  static constexpr bool kF32 = sizeof(T) == 4;
+  const T* C(int l) { return (const T*)(kF32 ? s->coef32[l].p : s->coef[l].p); }
+  const T* D(int l) { return (const T*)(kF32 ? s->invd32[l].p : s->invd[l].p); }
+  const T* G(int l) { return (const T*)(kF32 ? s->diag32[l].p : s->diag[l].p); }
+  const T* RD(int l) { return (const T*)(kF32 ? s->rden32[l].p : s->rden[l].p); }
+  const double* C64(int l) { return (const double*)s->coef[l].p; }
+  const double* G64(int l) { return (const double*)s->diag[l].p; }
 
   void smooth(int l) {
     const int n = s->sizes[l];
@@ -413,14 +519,14 @@ struct MG {
     const int n = s->sizes[l];
     const dim3 blk(kBX, kBY);
     if (l == s->nlev - 1) {
-      CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C(l),
+      CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C64(l),
                  (const double*)s->coarse_inv.p, n);
       return;
     }
     for (int k = 0; k < s->p.nu1; ++k) smooth(l);
     const int nc = n / 2;
-    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), F(l), C(l), G(l), n, U(l + 1),
-               U0(l + 1), F(l + 1));
+    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), F(l), C(l), G(l), RD(l), n,
+               U(l + 1), U0(l + 1), F(l + 1));
     CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
                G(l + 1), nc);
     vcycle(l + 1);
@@ -431,7 +537,7 @@ struct MG {
   int residual(double* ratio_host) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
-    CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, U(0), F(0), C(0), G(0), n,
+    CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, U(0), F(0), C64(0), G64(0), n,
                (double*)s->norms.p);
     CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
                s->npatch, (double*)s->ratio.p);
@@ -446,17 +552,76 @@ struct MG {
   // base (SHT solution + edge values), defect source f' = kappa - L base,
   // ||kappa||^2 per patch, and a zero starting correction
   int setup(const double* kappa_fine) {
+    if (mixed) return setup_t<double>(kappa_fine, (double*)s->fd64.p);
+    return setup_t<T>(kappa_fine, F(0));
+  }
+
+  template <typename S>
+  int setup_t(const double* kappa_fine, S* fdst) {
     const int n = s->sizes[0];
     const dim3 blk(kBX, kBY);
-    CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
-               (const double*)s->rot.p, (const double*)s->pvec.p, (const double*)s->psi_sht.p, s->p.nside_sht,
-               (const double*)s->ring_th_sht.p, (double*)s->base.p);
     cudaMemsetAsync(s->fnorm.p, 0, sizeof(double) * s->npatch, ctx->stream);
-    CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect<T>, grid3(n, n, s->npatch), blk, 0, n,
-               (const double*)s->rot.p, (const double*)s->pvec.p, kappa_fine, s->nside_fine,
-               (const double*)s->ring_th_fine.p, (const double*)s->base.p, C(0), G(0), F(0), (double*)s->fnorm.p);
-    cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
+    if (s->plan) {
+      CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base_plan, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
+                 (const int4*)s->plan_psi_idx.p, (const double4_32a*)s->plan_psi_w.p, (const double*)s->psi_sht.p,
+                 s->p.nside_sht, (const double*)s->ring_th_sht.p, (double*)s->base.p);
+      CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect_plan<S>, grid3(n, n, s->npatch), blk, 0, n,
+                 (const int4*)s->plan_kap_idx.p, (const double4_32a*)s->plan_kap_w.p, kappa_fine, s->nside_fine,
+                 (const double*)s->ring_th_fine.p, (const double*)s->base.p, C64(0), G64(0), fdst,
+                 (double*)s->fnorm.p);
+    } else {
+      CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
+                 (const double*)s->rot.p, (const double*)s->pvec.p, (const double*)s->psi_sht.p, s->p.nside_sht,
+                 (const double*)s->ring_th_sht.p, (double*)s->base.p);
+      CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect<S>, grid3(n, n, s->npatch), blk, 0, n,
+                 (const double*)s->rot.p, (const double*)s->pvec.p, kappa_fine, s->nside_fine,
+                 (const double*)s->ring_th_fine.p, (const double*)s->base.p, C64(0), G64(0), fdst,
+                 (double*)s->fnorm.p);
+    }
+    cudaMemsetAsync(mixed ? s->e64.p : s->u[0].p, 0, mixed ? s->e64.bytes : s->u[0].bytes, ctx->stream);
     return launch_check(ctx, "MG setup");
+  }
+
+  // CLC_MIXED: r = f' - L e64 in FP64 (also the next FP32 source), FP32
+  // V-cycle on L d = r from d = 0, e64 += d; u = base + e64 at the end
+  int residual_mixed(double* ratio_host) {
+    const int n = s->sizes[0];
+    cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_mixed, grid3(n, n, s->npatch), dim3(kBX, kBY), 0,
+               (const double*)s->e64.p, (const double*)s->fd64.p, C64(0), G64(0), n, (float*)s->f[0].p,
+               (double*)s->norms.p);
+    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
+               s->npatch, (double*)s->ratio.p);
+    int rc = launch_check(ctx, "MG mixed residual");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                    "residual copy");
+    if (rc) return rc;
+    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "residual sync");
+  }
+
+  int solve_mixed() {
+    int rc;
+    double rr = 0.0;
+    s->cycles = 0;
+    const int n = s->sizes[0];
+    const bool fixed = s->p.fixed_cycles > 0;
+    while (true) {
+      if ((rc = residual_mixed(&rr))) return rc;
+      if (fixed ? s->cycles >= s->p.fixed_cycles : (rr < s->p.tol || s->cycles >= s->p.max_cycles)) break;
+      cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
+      vcycle(0);
+      CLC_LAUNCH(ctx, "k_add_mixed", k_add_mixed, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->e64.p,
+                 (const float*)s->u[0].p, n);
+      if ((rc = launch_check(ctx, "mixed V-cycle"))) return rc;
+      ++s->cycles;
+    }
+    s->residual = rr;
+    CLC_LAUNCH(ctx, "k_combine", k_combine<double>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p,
+               (const double*)s->e64.p, n);
+    if ((rc = launch_check(ctx, "MG combine"))) return rc;
+    if (!fixed && rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
+    return CLC_OK;
   }
 
   int finish() {
@@ -503,7 +668,8 @@ static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
     return set_err(ctx, CLC_EINVAL, "MG: ncell must be a power of two in [16, 4096]");
   if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1 || p->max_cycles < 0 || p->fixed_cycles < 0)
     return set_err(ctx, CLC_EINVAL, "MG: bad sweep / cycle counts");
-  if (p->precision != CLC_FP64 && p->precision != CLC_FP32) return set_err(ctx, CLC_EINVAL, "MG: bad precision");
+  if (p->precision != CLC_FP64 && p->precision != CLC_FP32 && p->precision != CLC_MIXED)
+    return set_err(ctx, CLC_EINVAL, "MG: bad precision");
   return CLC_OK;
 }
 
@@ -528,13 +694,14 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     if (n <= 8) break;
   }
   s->nlev = (int)s->sizes.size();
-  const size_t es = p->precision == CLC_FP32 ? sizeof(float) : sizeof(double);
+  const size_t es = p->precision == CLC_FP64 ? sizeof(double) : sizeof(float);
   size_t need = 0;
   for (int l = 0; l < s->nlev; ++l) {
     const size_t n = s->sizes[l];
     need += s->npatch * ((n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
   }
-  need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double);
+  need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double) *
+          (p->precision == CLC_MIXED ? 3 : 1);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   if (need + (size_t)(1ull << 30) > freeb) {
@@ -555,21 +722,28 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const size_t n = s->sizes[l];
     const double hl = s->h * (p->ncell / (int)n);
     ok = alloc(s->u[l], s->npatch * (n + 2) * (n + 2) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
-         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) && alloc(s->coef[l], 4 * n * sizeof(double)) &&
-         alloc(s->invd[l], n * n * sizeof(double)) && alloc(s->diag[l], n * n * sizeof(double));
+         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es));
     if (!ok) break;
     // the ghost rings of the correction stay zero (homogeneous Dirichlet data)
     cudaMemset(s->u[l].p, 0, s->u[l].bytes);
     LevelCoef lc = level_coef((int)n, hl);
-    cudaMemcpy(s->coef[l].p, lc.coef.data(), lc.coef.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(s->invd[l].p, lc.invd.data(), lc.invd.size() * sizeof(double), cudaMemcpyHostToDevice);
-    cudaMemcpy(s->diag[l].p, lc.diag.data(), lc.diag.size() * sizeof(double), cudaMemcpyHostToDevice);
+    auto put = [&](Buffer& b64, Buffer& b32, const std::vector<double>& v) -> bool {
+      if (!alloc(b64, v.size() * sizeof(double)) || !alloc(b32, v.size() * sizeof(float))) return false;
+      std::vector<float> v32(v.begin(), v.end());
+      cudaMemcpy(b64.p, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+      cudaMemcpy(b32.p, v32.data(), v32.size() * sizeof(float), cudaMemcpyHostToDevice);
+      return true;
+    };
+    ok = put(s->coef[l], s->coef32[l], lc.coef) && put(s->invd[l], s->invd32[l], lc.invd) &&
+         put(s->diag[l], s->diag32[l], lc.diag) && put(s->rden[l], s->rden32[l], lc.rden);
   }
   const size_t n0 = s->sizes[0];
   ok = ok && alloc(s->base, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
        alloc(s->pvec, (n0 + 2) * (n0 + 2) * 3 * sizeof(double)) &&
        alloc(s->ring_th_sht, (4 * p->nside_sht - 1) * sizeof(double)) &&
-       alloc(s->ring_th_fine, (4 * nf - 1) * sizeof(double)) && alloc(s->fnorm, s->npatch * sizeof(double));
+       alloc(s->ring_th_fine, (4 * nf - 1) * sizeof(double)) && alloc(s->fnorm, s->npatch * sizeof(double)) &&
+       (p->precision != CLC_MIXED || (alloc(s->e64, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
+                                     alloc(s->fd64, s->npatch * n0 * n0 * sizeof(double))));
   if (ok) {
     // patch-frame unit vectors: cell centres inside, edge-face centres on the ring
     std::vector<double> pv((n0 + 2) * (n0 + 2) * 3);
@@ -630,7 +804,26 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   }
   CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch,
              (double*)s->rot.p);
-  rc = launch_check(ctx, "k_mg_rotations");
+  // interpolation plans, if they fit with 4 GiB to spare
+  {
+    const size_t pr = (size_t)s->npatch * (n0 + 2) * (n0 + 2), pk = (size_t)s->npatch * n0 * n0;
+    const size_t bytes = (pr + pk) * (sizeof(int4) + 4 * sizeof(double));
+    size_t fb = 0, tb = 0;
+    cudaMemGetInfo(&fb, &tb);
+    if (bytes + (4ull << 30) < fb && alloc(s->plan_psi_idx, pr * sizeof(int4)) &&
+        alloc(s->plan_psi_w, pr * 4 * sizeof(double)) && alloc(s->plan_kap_idx, pk * sizeof(int4)) &&
+        alloc(s->plan_kap_w, pk * 4 * sizeof(double))) {
+      const dim3 blk(kBX, kBY);
+      CLC_LAUNCH(ctx, "k_mg_plan", k_mg_plan, grid3(n0 + 2, n0 + 2, s->npatch), blk, 0, (int)n0, 1,
+                 (const double*)s->rot.p, (const double*)s->pvec.p, p->nside_sht, (const double*)s->ring_th_sht.p,
+                 (int4*)s->plan_psi_idx.p, (double4_32a*)s->plan_psi_w.p);
+      CLC_LAUNCH(ctx, "k_mg_plan", k_mg_plan, grid3(n0, n0, s->npatch), blk, 0, (int)n0, 0, (const double*)s->rot.p,
+                 (const double*)s->pvec.p, nf, (const double*)s->ring_th_fine.p, (int4*)s->plan_kap_idx.p,
+                 (double4_32a*)s->plan_kap_w.p);
+      s->plan = true;
+    }
+  }
+  rc = launch_check(ctx, "k_mg_rotations / k_mg_plan");
   if (rc) {
     delete s;
     return rc;
@@ -670,7 +863,11 @@ extern "C" int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nf,
                             (double*)s->psi_sht.p, nullptr)))
     return rc;
   int st;
-  if (p->precision == CLC_FP32) {
+  if (p->precision == CLC_MIXED) {
+    MG<float> mg{s, ctx, true};
+    if ((rc = mg.setup(kappa_fine))) return rc;
+    st = mg.solve_mixed();
+  } else if (p->precision == CLC_FP32) {
     MG<float> mg{s, ctx};
     if ((rc = mg.setup(kappa_fine))) return rc;
     st = mg.solve();

@@ -15,9 +15,17 @@ struct clc_plane_solution {
   clc::Buffer pvec;             // double[(n+2)^2][3]: patch-frame unit vectors of the finest level
   clc::Buffer ring_th_sht, ring_th_fine;  // ring colatitude tables
   clc::Buffer fnorm;            // double[npatch]: ||f||^2 of the source
+  // interpolation plans (fixed by the patch geometry): 4 pixel indices and
+  // weights per position, index -1 = position needs the 8-pixel pole stencil
+  bool plan = false;
+  clc::Buffer plan_psi_idx, plan_psi_w;   // [npatch][(n+2)^2]: int4, double[4]
+  clc::Buffer plan_kap_idx, plan_kap_w;   // [npatch][n^2]
   clc::Buffer coef[16];         // double[4][n] per level: aS, aN, b, area
   clc::Buffer invd[16];         // double[n][n] per level: 1 / diagonal
   clc::Buffer diag[16];         // double[n][n] per level: diagonal
+  clc::Buffer rden[16];         // double[n/2] per level: 1 / (2 (area_2I + area_2I+1))
+  clc::Buffer coef32[16], invd32[16], diag32[16], rden32[16];  // float copies
+  clc::Buffer e64, fd64;        // CLC_MIXED: FP64 correction (ghost-ring layout) and defect source
   clc::Buffer rot;              // double[npatch][9]: R_b (global -> patch frame)
   clc::Buffer coarse_inv;       // double[nc^2][nc^2]
   clc::Buffer psi_sht;          // double[12 nside_sht^2]

@@ -82,6 +82,27 @@ def geometry_vec(z, phi):
     return torch.stack([s * torch.cos(phi), s * torch.sin(phi), z], -1)
 
 
+def test_shtmg_mixed_precision_converges_to_fp64_solution():
+    """CLC_MIXED: FP32 V-cycles on the FP64 residual equation reach the same
+    1e-10 relative residual and the same solution as the FP64 oracle."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, ns, lmax, nb, ncell = 64, 16, 32, 4, 32
+    kappa = _kappa(nf, 24)
+    P = _params(clc, ns, lmax, nb, ncell, tol=1e-10, prec=clc.MIXED)
+    sol = c.solution(nf, P)
+    got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
+    c.sync()
+    cyc, res = sol.info()
+    assert res < 1e-10
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, tol=1e-12)
+    home, nv = _pixel_home(nf, nb)
+    want = omg.fields_at(ref, nb, nv, home)
+    for k in KEYS:
+        assert rel_l2(got[k], want[k]) < 1e-7, k
+    sol.close()
+
+
 def test_shtmg_fp32_path():
     import paper_1210_3069_gb300 as clc
     c = ctx()
