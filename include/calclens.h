@@ -231,6 +231,30 @@ int clc_profile_query(clc_ctx* ctx, const char* name, int64_t* launches_host, do
 /* Number of kernels this context has launched since it was created. */
 int64_t clc_launch_count(const clc_ctx* ctx);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free SHT analysis.  The paper has no counterpart: this entry   */
+/* exists for callers of this library that cannot allocate device memory.    */
+/*                                                                          */
+/* clc_sht_analysis allocates on first use (context scratch, FFT plans,      */
+/* Legendre tables).  Some callers cannot: code recording work into a CUDA   */
+/* graph (allocation is not allowed while a stream is being captured), code  */
+/* running inside a framework whose caching allocator owns all device memory,*/
+/* or long-running services that must not grow their footprint after start. */
+/* This variant computes the same a_lm (same conventions, same result within */
+/* 1e-10 relative) with a direct DFT per ring and the Legendre recurrence on */
+/* the fly; its only scratch, the ring Fourier coefficients, is a fixed      */
+/* 2.1 MB file-scope device array that every GPU loading the library keeps   */
+/* until the process exits.  It never calls cudaMalloc or cudaFree and needs */
+/* no context: it runs on the calling thread's current device, on            */
+/* `cuda_stream` (a cudaStream_t; NULL = legacy default stream).             */
+/* Limits: nside a power of two <= 128, 0 <= lmax <= min(256, 4 nside);      */
+/* anything else (or a NULL pointer) returns CLC_EINVAL without launching.   */
+/* The first call on each device looks up the array's device address; make */
+/* that first call before any stream capture.  All calls share the array:    */
+/* calls whose work overlaps on the GPU (different streams, no ordering)     */
+/* race and must not be issued.  Returns CLC_ECUDA if a launch fails.        */
+int clc_sht_analysis_noalloc(const double* map, int nside, int lmax, double* alm, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
