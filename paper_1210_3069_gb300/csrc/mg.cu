@@ -186,6 +186,58 @@ __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __
   U[c] = t * invd[i * n + j];
 }
 
+// NS red-black Gauss-Seidel sweeps fused in one pass over a 32 x 16 tile of a
+// patch: the tile and a halo of 2 NS cells are staged in shared memory, pass p
+// (colour p % 2, red first) updates the tile grown by 2 NS - 1 - p cells, so
+// the tile's cells see exactly the values NS global sweeps would give them.
+// DRAM traffic: u and f read once, u written once per NS sweeps.
+constexpr int kTW = 32, kTH = 16;
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(256) k_smooth_tile(T* __restrict__ u, const T* __restrict__ f,
+                                                     const T* __restrict__ coef, const T* __restrict__ invd, int n) {
+  constexpr int H = 2 * NS;
+  constexpr int SW = kTW + 2 * H, SH = kTH + 2 * H;
+  __shared__ T su[SH][SW];
+  __shared__ T sf[SH][SW];
+  const int b = blockIdx.z;
+  const int i0 = blockIdx.y * kTH - H, j0 = blockIdx.x * kTW - H;   // interior coords of su[0][0]
+  const size_t side = n + 2;
+  T* U = u + (size_t)b * side * side;
+  const T* Fb = f + (size_t)b * n * n;
+  for (int t = threadIdx.x; t < SH * SW; t += blockDim.x) {
+    const int a = t / SW, c = t % SW;
+    const int i = i0 + a, j = j0 + c;
+    T uv = 0, fv = 0;
+    if (i >= -1 && i <= n && j >= -1 && j <= n) uv = U[(size_t)(i + 1) * side + (j + 1)];
+    if (i >= 0 && i < n && j >= 0 && j < n) fv = Fb[(size_t)i * n + j];
+    su[a][c] = uv;
+    sf[a][c] = fv;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < 2 * NS; ++p) {
+    const int r = 2 * NS - 1 - p;                 // growth of the updated region
+    const int a_lo = H - r, a_hi = H + kTH - 1 + r;
+    const int c_lo = H - r, c_hi = H + kTW - 1 + r;
+    const int rows = a_hi - a_lo + 1, cols = c_hi - c_lo + 1;
+    for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
+      const int a = a_lo + t / cols, c = c_lo + t % cols;
+      const int i = i0 + a, j = j0 + c;
+      if (i < 0 || i >= n || j < 0 || j >= n || ((i + j) & 1) != (p & 1)) continue;
+      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
+      const T tt = fma(bb, su[a][c + 1] + su[a][c - 1], fma(aN, su[a - 1][c], fma(aS, su[a + 1][c], -sf[a][c])));
+      su[a][c] = tt * invd[i * n + j];
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < kTH * kTW; t += blockDim.x) {
+    const int a = H + t / kTW, c = H + t % kTW;
+    const int i = i0 + a, j = j0 + c;
+    if (i < n && j < n) U[(size_t)(i + 1) * side + (j + 1)] = su[a][c];
+  }
+}
+
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
 // fine residual and of the correction over its 2 x 2 children.
 template <typename T>
@@ -240,29 +292,39 @@ __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T
   *Fp = *Fp + nb;
 }
 
-// u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge
+// u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge;
+// one thread per coarse cell updates its 2 x 2 fine children.
 template <typename T>
 __global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n) {
   const int nc = n / 2;
   const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
-  if (i >= n || j >= n) return;
+  const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
+  if (I >= nc || J >= nc) return;
   const size_t side = n + 2, sidec = nc + 2;
-  const int I = i >> 1, J = j >> 1;
   const T* C = uc + (size_t)b * sidec * sidec;
   const T* C0 = uc0 + (size_t)b * nc * nc;
-  auto e = [&](int a, int c) -> T { return C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c]; };
-  T corr;
-  if (i == 0 || j == 0 || i == n - 1 || j == n - 1) {
-    corr = e(I, J);
-  } else {
-    const int Ii = I + ((i & 1) ? 1 : -1);
-    const int Jj = J + ((j & 1) ? 1 : -1);
-    corr = fma((T)9, e(I, J), fma((T)3, e(Ii, J) + e(I, Jj), e(Ii, Jj))) * (T)0.0625;
-  }
+  T e[3][3];
+#pragma unroll
+  for (int di = -1; di <= 1; ++di)
+#pragma unroll
+    for (int dj = -1; dj <= 1; ++dj) {
+      const int a = min(max(I + di, 0), nc - 1), c = min(max(J + dj, 0), nc - 1);
+      e[di + 1][dj + 1] = C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c];
+    }
   T* U = u + (size_t)b * side * side;
-  const size_t c = (size_t)(i + 1) * side + (j + 1);
-  U[c] += corr;
+#pragma unroll
+  for (int fa = 0; fa < 2; ++fa)
+#pragma unroll
+    for (int fc = 0; fc < 2; ++fc) {
+      const int i = 2 * I + fa, j = 2 * J + fc;
+      const int di = fa ? 2 : 0, dj = fc ? 2 : 0;   // neighbour index in e[][]
+      T corr;
+      if (i == 0 || j == 0 || i == n - 1 || j == n - 1)
+        corr = e[1][1];
+      else
+        corr = fma((T)9, e[1][1], fma((T)3, e[di][1] + e[1][dj], e[di][dj])) * (T)0.0625;
+      U[(size_t)(i + 1) * side + (j + 1)] += corr;
+    }
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -330,37 +392,43 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
   }
 }
 
-// FP64 residual of the correction equation r = f' - L e64; its FP32 copy is
-// the source of the next FP32 V-cycle; ||r||^2 accumulated per patch
-__global__ void k_resid_mixed(const double* __restrict__ e, const double* __restrict__ fd,
-                              const double* __restrict__ coef, const double* __restrict__ diag, int n,
+// Mixed refinement step, fused: e_new = e_old + d (d = the last FP32
+// V-cycle's correction, NULL before the first cycle), r = f' - L e_new in
+// FP64, r in FP32 as the next V-cycle's source, ||r||^2 per patch.  Each
+// thread handles kRows rows of one column, so the warp reduction is paid once
+// per kRows cells.
+constexpr int kRows = 4;
+
+__global__ void k_resid_mixed(const double* __restrict__ e_old, const float* __restrict__ d,
+                              const double* __restrict__ fd, const double* __restrict__ coef,
+                              const double* __restrict__ diag, int n, double* __restrict__ e_new,
                               float* __restrict__ r32, double* __restrict__ norms) {
   const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.x * kBX + threadIdx.x;
+  const size_t side = n + 2;
+  const double* E = e_old + (size_t)b * side * side;
+  const float* D = d ? d + (size_t)b * side * side : nullptr;
   double rr = 0.0;
-  if (i < n && j < n) {
-    const size_t side = n + 2;
-    const double* U = e + (size_t)b * side * side;
-    const size_t c = (size_t)(i + 1) * side + (j + 1);
-    const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
-    const double nb = fma(coef[2 * n + i], U[c + 1] + U[c - 1],
-                          fma(coef[n + i], U[c - side], fma(coef[i], U[c + side], -diag[i * n + j] * U[c])));
-    const double r = fd[pos] - nb;
-    r32[pos] = (float)r;
-    rr = r * r;
+#pragma unroll
+  for (int k = 0; k < kRows; ++k) {
+    const int i = (blockIdx.y * kRows + k) * kBY + threadIdx.y;
+    if (i < n && j < n) {
+      const size_t c = (size_t)(i + 1) * side + (j + 1);
+      double eC = E[c], eS = E[c + side], eN = E[c - side], eE = E[c + 1], eW = E[c - 1];
+      if (D) {
+        eC += (double)D[c]; eS += (double)D[c + side]; eN += (double)D[c - side];
+        eE += (double)D[c + 1]; eW += (double)D[c - 1];
+      }
+      const double nb = fma(coef[2 * n + i], eE + eW, fma(coef[n + i], eN, fma(coef[i], eS, -diag[i * n + j] * eC)));
+      const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
+      const double r = fd[pos] - nb;
+      r32[pos] = (float)r;
+      e_new[(size_t)b * side * side + c] = eC;
+      rr = fma(r, r, rr);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
   if (threadIdx.x == 0 && rr != 0.0) atomicAdd(norms + b, rr);
-}
-
-// e64 += delta32 on the interior cells
-__global__ void k_add_mixed(double* __restrict__ e, const float* __restrict__ d, int n) {
-  const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
-  if (i >= n || j >= n) return;
-  const size_t side = n + 2;
-  const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
-  e[c] += (double)d[c];
 }
 
 // final potential u = base + e (interior cells)
@@ -508,11 +576,19 @@ struct MG {
   const double* C64(int l) { return (const double*)s->coef[l].p; }
   const double* G64(int l) { return (const double*)s->diag[l].p; }
 
-  void smooth(int l) {
+  // nu red-black sweeps at level l, two at a time in shared-memory tiles
+  void smooth(int l, int nu) {
     const int n = s->sizes[l];
-    const dim3 blk(kBX, kBY);
-    for (int colour = 0; colour < 2; ++colour)
-      CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), blk, 0, U(l), F(l), C(l), D(l), n, colour);
+    const dim3 grid((n + kTW - 1) / kTW, (n + kTH - 1) / kTH, s->npatch);
+    for (int k = 0; k < nu;) {
+      if (nu - k >= 2) {
+        CLC_LAUNCH(ctx, "k_smooth", (k_smooth_tile<T, 2>), grid, 256, 0, U(l), F(l), C(l), D(l), n);
+        k += 2;
+      } else {
+        CLC_LAUNCH(ctx, "k_smooth", (k_smooth_tile<T, 1>), grid, 256, 0, U(l), F(l), C(l), D(l), n);
+        k += 1;
+      }
+    }
   }
 
   void vcycle(int l) {
@@ -523,15 +599,15 @@ struct MG {
                  (const double*)s->coarse_inv.p, n);
       return;
     }
-    for (int k = 0; k < s->p.nu1; ++k) smooth(l);
+    smooth(l, s->p.nu1);
     const int nc = n / 2;
     CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), F(l), C(l), G(l), RD(l), n,
                U(l + 1), U0(l + 1), F(l + 1));
     CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
                G(l + 1), nc);
     vcycle(l + 1);
-    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, grid3(n, n, s->npatch), blk, 0, U(l), U(l + 1), U0(l + 1), n);
-    for (int k = 0; k < s->p.nu2; ++k) smooth(l);
+    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), U(l + 1), U0(l + 1), n);
+    smooth(l, s->p.nu2);
   }
 
   int residual(double* ratio_host) {
@@ -584,12 +660,12 @@ struct MG {
 
   // CLC_MIXED: r = f' - L e64 in FP64 (also the next FP32 source), FP32
   // V-cycle on L d = r from d = 0, e64 += d; u = base + e64 at the end
-  int residual_mixed(double* ratio_host) {
+  int residual_mixed(const double* e_old, const float* d, double* e_new, double* ratio_host) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
-    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_mixed, grid3(n, n, s->npatch), dim3(kBX, kBY), 0,
-               (const double*)s->e64.p, (const double*)s->fd64.p, C64(0), G64(0), n, (float*)s->f[0].p,
-               (double*)s->norms.p);
+    const dim3 grid((n + kBX - 1) / kBX, (n + kBY * kRows - 1) / (kBY * kRows), s->npatch);
+    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_mixed, grid, dim3(kBX, kBY), 0, e_old, d, (const double*)s->fd64.p,
+               C64(0), G64(0), n, e_new, (float*)s->f[0].p, (double*)s->norms.p);
     CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
                s->npatch, (double*)s->ratio.p);
     int rc = launch_check(ctx, "MG mixed residual");
@@ -606,19 +682,21 @@ struct MG {
     s->cycles = 0;
     const int n = s->sizes[0];
     const bool fixed = s->p.fixed_cycles > 0;
-    while (true) {
-      if ((rc = residual_mixed(&rr))) return rc;
-      if (fixed ? s->cycles >= s->p.fixed_cycles : (rr < s->p.tol || s->cycles >= s->p.max_cycles)) break;
+    double* cur = (double*)s->e64.p;
+    double* nxt = (double*)s->e64b.p;
+    if ((rc = residual_mixed(cur, nullptr, nxt, &rr))) return rc;
+    std::swap(cur, nxt);
+    while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= s->p.tol && s->cycles < s->p.max_cycles)) {
       cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
       vcycle(0);
-      CLC_LAUNCH(ctx, "k_add_mixed", k_add_mixed, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->e64.p,
-                 (const float*)s->u[0].p, n);
       if ((rc = launch_check(ctx, "mixed V-cycle"))) return rc;
+      if ((rc = residual_mixed(cur, (const float*)s->u[0].p, nxt, &rr))) return rc;
+      std::swap(cur, nxt);
       ++s->cycles;
     }
     s->residual = rr;
     CLC_LAUNCH(ctx, "k_combine", k_combine<double>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p,
-               (const double*)s->e64.p, n);
+               (const double*)cur, n);
     if ((rc = launch_check(ctx, "MG combine"))) return rc;
     if (!fixed && rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
     return CLC_OK;
@@ -701,7 +779,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     need += s->npatch * ((n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
   }
   need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double) *
-          (p->precision == CLC_MIXED ? 3 : 1);
+          (p->precision == CLC_MIXED ? 4 : 1);
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   if (need + (size_t)(1ull << 30) > freeb) {
@@ -743,7 +821,9 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
        alloc(s->ring_th_sht, (4 * p->nside_sht - 1) * sizeof(double)) &&
        alloc(s->ring_th_fine, (4 * nf - 1) * sizeof(double)) && alloc(s->fnorm, s->npatch * sizeof(double)) &&
        (p->precision != CLC_MIXED || (alloc(s->e64, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
+                                     alloc(s->e64b, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
                                      alloc(s->fd64, s->npatch * n0 * n0 * sizeof(double))));
+  if (ok && p->precision == CLC_MIXED) cudaMemset(s->e64b.p, 0, s->e64b.bytes);
   if (ok) {
     // patch-frame unit vectors: cell centres inside, edge-face centres on the ring
     std::vector<double> pv((n0 + 2) * (n0 + 2) * 3);
