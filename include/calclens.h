@@ -219,6 +219,27 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
                         const double* chi_host, clc_rays* rays);
 
 /* ------------------------------------------------------------------------ */
+/* Spectra of the final lensing fields (paper Sec. 5)                        */
+
+/* E and B coefficients (packed like clc_sht_analysis, l < 2 zero) of the
+ * spin-2 shear gamma_1 + i gamma_2 given as RING maps in the (theta-hat,
+ * phi-hat) basis.  Convention: a potential's shear gamma = eth^2 psi / 2
+ * (gamma_1 = (U_tt - U_pp)/2, gamma_2 = U_tp) has E_lm = N_l psi_lm / 2,
+ * N_l = sqrt((l+2)!/(l-2)!), and B_lm = 0; uniform quadrature as in
+ * clc_sht_analysis. */
+int clc_eb_analysis(clc_ctx* ctx, const double* gamma1, const double* gamma2, int nside, int lmax,
+                    double* E_alm, double* B_alm);
+/* cl[l] = (a_l0 b_l0* + 2 sum_{m>0} Re a_lm b_lm*) / (2l+1), l <= lmax
+ * (b = a if alm2 is NULL). */
+int clc_power_spectrum(clc_ctx* ctx, const double* alm, const double* alm2, int lmax, double* cl);
+/* From inverse magnification matrices A (SoA A[4][12 nside^2]: A_tt, A_tp,
+ * A_pt, A_pp at the RING pixel centres where the rays started), the spectra
+ * of kappa = 1 - (A_tt + A_pp)/2, of the E and B modes of
+ * gamma = (-(A_tt - A_pp)/2, -(A_tp + A_pt)/2) and of omega = (A_tp - A_pt)/2
+ * (Eq. invmagmat): cl_out[4][lmax + 1] in the order kappa, E, B, omega. */
+int clc_lensing_spectra(clc_ctx* ctx, const double* A, int nside, int lmax, double* cl_out);
+
+/* ------------------------------------------------------------------------ */
 /* Diagnostics (no counterpart in the paper beyond its per-step wall timers) */
 
 /* enable != 0: start recording a CUDA-event pair around every kernel launch

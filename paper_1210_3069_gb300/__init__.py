@@ -69,6 +69,9 @@ _SIGS = {
     "clc_ray_step": (_i, [_p, _p, ctypes.POINTER(Derivs), _i, _d, _d, _d, ctypes.POINTER(Rays)]),
     "clc_raytrace_planes": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p), _i, _i, ctypes.POINTER(_d),
                                  ctypes.POINTER(Rays)]),
+    "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
+    "clc_power_spectrum": (_i, [_p, _p, _p, _i, _p]),
+    "clc_lensing_spectra": (_i, [_p, _p, _i, _i, _p]),
     "clc_profile": (_i, [_p, _i]),
     "clc_profile_query": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(_d)]),
     "clc_launch_count": (_i64, [_p]),
@@ -208,6 +211,24 @@ class Context:
         if psi:
             out["psi"] = p
         return out
+
+    def eb_analysis(self, g1, g2, nside, lmax):
+        n = (lmax + 1) * (lmax + 2) // 2
+        E = torch.empty(n, dtype=torch.complex128, device=self.device)
+        B = torch.empty(n, dtype=torch.complex128, device=self.device)
+        self._check(lib().clc_eb_analysis(self.h, _ptr(g1), _ptr(g2), nside, lmax, _ptr(E), _ptr(B)))
+        return E, B
+
+    def power_spectrum(self, alm, lmax, alm2=None):
+        cl = torch.empty(lmax + 1, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_power_spectrum(self.h, _ptr(alm), _ptr(alm2), lmax, _ptr(cl)))
+        return cl
+
+    def lensing_spectra(self, A, nside, lmax):
+        """dict of C_l for kappa, E, B, omega from A[4, 12 nside^2]."""
+        cl = torch.empty(4, lmax + 1, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_lensing_spectra(self.h, _ptr(A), nside, lmax, _ptr(cl)))
+        return dict(zip(("kappa", "E", "B", "omega"), cl))
 
     # -- step 3 / 4 ---------------------------------------------------------
     def solution(self, nside_fine, params):

@@ -197,7 +197,7 @@ template <typename T, int NS>
 __global__ void __launch_bounds__(256) k_smooth_tile(T* __restrict__ u, const T* __restrict__ f,
                                                      const T* __restrict__ coef, const T* __restrict__ invd, int n) {
   constexpr int H = 2 * NS;
-  constexpr int SW = kTW + 2 * H, SH = kTH + 2 * H;
+  constexpr int SW = kTW + 2 * H, SH = kTH + 2 * H, HW = SW / 2;
   __shared__ T su[SH][SW];
   __shared__ T sf[SH][SW];
   const int b = blockIdx.z;
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(256) k_smooth_tile(T* __restrict__ u, const T*
   T* U = u + (size_t)b * side * side;
   const T* Fb = f + (size_t)b * n * n;
   for (int t = threadIdx.x; t < SH * SW; t += blockDim.x) {
-    const int a = t / SW, c = t % SW;
+    const int a = t / SW, c = t - a * SW;
     const int i = i0 + a, j = j0 + c;
     T uv = 0, fv = 0;
     if (i >= -1 && i <= n && j >= -1 && j <= n) uv = U[(size_t)(i + 1) * side + (j + 1)];
@@ -218,13 +218,13 @@ __global__ void __launch_bounds__(256) k_smooth_tile(T* __restrict__ u, const T*
 #pragma unroll
   for (int p = 0; p < 2 * NS; ++p) {
     const int r = 2 * NS - 1 - p;                 // growth of the updated region
-    const int a_lo = H - r, a_hi = H + kTH - 1 + r;
-    const int c_lo = H - r, c_hi = H + kTW - 1 + r;
-    const int rows = a_hi - a_lo + 1, cols = c_hi - c_lo + 1;
-    for (int t = threadIdx.x; t < rows * cols; t += blockDim.x) {
-      const int a = a_lo + t / cols, c = c_lo + t % cols;
+    // slots: every row, every other column (the cells of colour p % 2)
+    for (int t = threadIdx.x; t < SH * HW; t += blockDim.x) {
+      const int a = t / HW;
+      const int c = 2 * (t - a * HW) + ((p + i0 + j0 + a) & 1);
       const int i = i0 + a, j = j0 + c;
-      if (i < 0 || i >= n || j < 0 || j >= n || ((i + j) & 1) != (p & 1)) continue;
+      if (a < H - r || a > H + kTH - 1 + r || c < H - r || c > H + kTW - 1 + r) continue;
+      if (i < 0 || i >= n || j < 0 || j >= n) continue;
       const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
       const T tt = fma(bb, su[a][c + 1] + su[a][c - 1], fma(aN, su[a - 1][c], fma(aS, su[a + 1][c], -sf[a][c])));
       su[a][c] = tt * invd[i * n + j];
@@ -576,9 +576,17 @@ struct MG {
   const double* C64(int l) { return (const double*)s->coef[l].p; }
   const double* G64(int l) { return (const double*)s->diag[l].p; }
 
-  // nu red-black sweeps at level l, two at a time in shared-memory tiles
+  // nu red-black sweeps at level l: FP64 (ALU-bound) one colour per launch;
+  // FP32 (bandwidth-bound) two sweeps per launch in shared-memory tiles
   void smooth(int l, int nu) {
     const int n = s->sizes[l];
+    if (!kF32) {
+      for (int k = 0; k < nu; ++k)
+        for (int colour = 0; colour < 2; ++colour)
+          CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l),
+                     n, colour);
+      return;
+    }
     const dim3 grid((n + kTW - 1) / kTW, (n + kTH - 1) / kTH, s->npatch);
     for (int k = 0; k < nu;) {
       if (nu - k >= 2) {
@@ -687,8 +695,12 @@ struct MG {
     if ((rc = residual_mixed(cur, nullptr, nxt, &rr))) return rc;
     std::swap(cur, nxt);
     while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= s->p.tol && s->cycles < s->p.max_cycles)) {
+      // two FP32 V-cycles on L d = r (the second continues from the first)
+      // per FP64 refinement: the FP64 residual is the ALU-bound part
       cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
-      vcycle(0);
+      const int inner = (fixed ? s->p.fixed_cycles - s->cycles : s->p.max_cycles - s->cycles) >= 2 ? 2 : 1;
+      for (int k = 0; k < inner; ++k) vcycle(0);
+      s->cycles += inner - 1;
       if ((rc = launch_check(ctx, "mixed V-cycle"))) return rc;
       if ((rc = residual_mixed(cur, (const float*)s->u[0].p, nxt, &rr))) return rc;
       std::swap(cur, nxt);
