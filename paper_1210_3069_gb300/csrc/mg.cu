@@ -186,58 +186,6 @@ __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __
   U[c] = t * invd[i * n + j];
 }
 
-// NS red-black Gauss-Seidel sweeps fused in one pass over a 32 x 16 tile of a
-// patch: the tile and a halo of 2 NS cells are staged in shared memory, pass p
-// (colour p % 2, red first) updates the tile grown by 2 NS - 1 - p cells, so
-// the tile's cells see exactly the values NS global sweeps would give them.
-// DRAM traffic: u and f read once, u written once per NS sweeps.
-constexpr int kTW = 32, kTH = 16;
-
-template <typename T, int NS>
-__global__ void __launch_bounds__(256) k_smooth_tile(T* __restrict__ u, const T* __restrict__ f,
-                                                     const T* __restrict__ coef, const T* __restrict__ invd, int n) {
-  constexpr int H = 2 * NS;
-  constexpr int SW = kTW + 2 * H, SH = kTH + 2 * H, HW = SW / 2;
-  __shared__ T su[SH][SW];
-  __shared__ T sf[SH][SW];
-  const int b = blockIdx.z;
-  const int i0 = blockIdx.y * kTH - H, j0 = blockIdx.x * kTW - H;   // interior coords of su[0][0]
-  const size_t side = n + 2;
-  T* U = u + (size_t)b * side * side;
-  const T* Fb = f + (size_t)b * n * n;
-  for (int t = threadIdx.x; t < SH * SW; t += blockDim.x) {
-    const int a = t / SW, c = t - a * SW;
-    const int i = i0 + a, j = j0 + c;
-    T uv = 0, fv = 0;
-    if (i >= -1 && i <= n && j >= -1 && j <= n) uv = U[(size_t)(i + 1) * side + (j + 1)];
-    if (i >= 0 && i < n && j >= 0 && j < n) fv = Fb[(size_t)i * n + j];
-    su[a][c] = uv;
-    sf[a][c] = fv;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int p = 0; p < 2 * NS; ++p) {
-    const int r = 2 * NS - 1 - p;                 // growth of the updated region
-    // slots: every row, every other column (the cells of colour p % 2)
-    for (int t = threadIdx.x; t < SH * HW; t += blockDim.x) {
-      const int a = t / HW;
-      const int c = 2 * (t - a * HW) + ((p + i0 + j0 + a) & 1);
-      const int i = i0 + a, j = j0 + c;
-      if (a < H - r || a > H + kTH - 1 + r || c < H - r || c > H + kTW - 1 + r) continue;
-      if (i < 0 || i >= n || j < 0 || j >= n) continue;
-      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
-      const T tt = fma(bb, su[a][c + 1] + su[a][c - 1], fma(aN, su[a - 1][c], fma(aS, su[a + 1][c], -sf[a][c])));
-      su[a][c] = tt * invd[i * n + j];
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < kTH * kTW; t += blockDim.x) {
-    const int a = H + t / kTW, c = H + t % kTW;
-    const int i = i0 + a, j = j0 + c;
-    if (i < n && j < n) U[(size_t)(i + 1) * side + (j + 1)] = su[a][c];
-  }
-}
-
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
 // fine residual and of the correction over its 2 x 2 children.
 template <typename T>
@@ -576,27 +524,13 @@ struct MG {
   const double* C64(int l) { return (const double*)s->coef[l].p; }
   const double* G64(int l) { return (const double*)s->diag[l].p; }
 
-  // nu red-black sweeps at level l: FP64 (ALU-bound) one colour per launch;
-  // FP32 (bandwidth-bound) two sweeps per launch in shared-memory tiles
+  // nu red-black sweeps at level l, one colour per launch
   void smooth(int l, int nu) {
     const int n = s->sizes[l];
-    if (!kF32) {
-      for (int k = 0; k < nu; ++k)
-        for (int colour = 0; colour < 2; ++colour)
-          CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l),
-                     n, colour);
-      return;
-    }
-    const dim3 grid((n + kTW - 1) / kTW, (n + kTH - 1) / kTH, s->npatch);
-    for (int k = 0; k < nu;) {
-      if (nu - k >= 2) {
-        CLC_LAUNCH(ctx, "k_smooth", (k_smooth_tile<T, 2>), grid, 256, 0, U(l), F(l), C(l), D(l), n);
-        k += 2;
-      } else {
-        CLC_LAUNCH(ctx, "k_smooth", (k_smooth_tile<T, 1>), grid, 256, 0, U(l), F(l), C(l), D(l), n);
-        k += 1;
-      }
-    }
+    for (int k = 0; k < nu; ++k)
+      for (int colour = 0; colour < 2; ++colour)
+        CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l),
+                   n, colour);
   }
 
   void vcycle(int l) {
