@@ -219,6 +219,19 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
                         const double* chi_host, clc_rays* rays);
 
 /* ------------------------------------------------------------------------ */
+/* Split-precision tensor-core contraction (the building block of the        */
+/* mixed-precision Legendre transforms; the paper is all FP64)               */
+
+/* d[b] = a_hi[b] b_hi[b]^T + a_hi[b] b_lo[b]^T + a_lo[b] b_hi[b]^T for b < batch,
+ * on the tcgen05 tensor cores with FP32 accumulation.  a_* are FP16
+ * [batch][M][K], b_* FP16 [batch][N][K] (row-major, K contiguous), d FP32
+ * [batch][M][N].  Splitting x = x_hi + x_lo (x_hi = fp16(x), x_lo =
+ * fp16(x - x_hi)) gives products of ~22-bit operands.  Needs M >= 1,
+ * N in [16, 256] a multiple of 16, K a multiple of 64, batch <= 65535. */
+int clc_gemm_f16x3(clc_ctx* ctx, const void* a_hi, const void* a_lo, const void* b_hi, const void* b_lo, int M,
+                   int N, int K, int batch, float* d);
+
+/* ------------------------------------------------------------------------ */
 /* Spectra of the final lensing fields (paper Sec. 5)                        */
 
 /* E and B coefficients (packed like clc_sht_analysis, l < 2 zero) of the

@@ -69,6 +69,7 @@ _SIGS = {
     "clc_ray_step": (_i, [_p, _p, ctypes.POINTER(Derivs), _i, _d, _d, _d, ctypes.POINTER(Rays)]),
     "clc_raytrace_planes": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p), _i, _i, ctypes.POINTER(_d),
                                  ctypes.POINTER(Rays)]),
+    "clc_gemm_f16x3": (_i, [_p, _p, _p, _p, _p, _i, _i, _i, _i, _p]),
     "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
     "clc_power_spectrum": (_i, [_p, _p, _p, _i, _p]),
     "clc_lensing_spectra": (_i, [_p, _p, _i, _i, _p]),
@@ -211,6 +212,15 @@ class Context:
         if psi:
             out["psi"] = p
         return out
+
+    def gemm_f16x3(self, a_hi, a_lo, b_hi, b_lo):
+        """d[b] = a_hi b_hi^T + a_hi b_lo^T + a_lo b_hi^T (tcgen05, FP32 accumulate)."""
+        batch, M, K = a_hi.shape
+        N = b_hi.shape[1]
+        d = torch.empty(batch, M, N, dtype=torch.float32, device=self.device)
+        self._check(lib().clc_gemm_f16x3(self.h, _ptr(a_hi), _ptr(a_lo), _ptr(b_hi), _ptr(b_lo), M, N, K, batch,
+                                         _ptr(d)))
+        return d
 
     def eb_analysis(self, g1, g2, nside, lmax):
         n = (lmax + 1) * (lmax + 2) // 2
