@@ -143,9 +143,23 @@ int clc_sht_synthesis(clc_ctx* ctx, const double* alm, int nside, int lmax, doub
  * non-NULL fields of `out` (out may be NULL), the deflection and Hessian at
  * every pixel centre synthesised directly from psi_lm.
  * precision: CLC_FP64 (FP64 Legendre contraction) or CLC_MIXED (split
- * hi + lo FP16 tensor-core contraction with FP32 accumulation). */
+ * hi + lo FP16 tensor-core contraction with FP32 accumulation; needs
+ * nside >= 64, relative L2 error of the outputs about 1e-6).
+ * All maps are device pointers of 12 nside^2 doubles (RING order). */
 int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int lmax, int precision,
                     double* psi, const clc_derivs* out);
+
+/* The pure-SHT plane solve of clc_poisson_sht for nplanes planes of the same
+ * (nside, lmax) (the lens planes of one light cone, Sec. 3.2).  kappa and psi
+ * are HOST arrays of nplanes DEVICE map pointers (psi may be NULL, entries
+ * may not); out is NULL or a host array of nplanes clc_derivs.  With CLC_MIXED
+ * up to 64 planes (21 with derivatives) share one pass over the FP16 lambda
+ * table on the tensor cores; CLC_FP64 solves the planes one by one.  Errors:
+ * CLC_EINVAL for bad sizes, a NULL kappa entry or nside < 64 with CLC_MIXED;
+ * CLC_ENOMEM if the FP16 table (4 bytes per lambda_lm value and ring) does
+ * not fit. */
+int clc_poisson_sht_batch(clc_ctx* ctx, const double* const* kappa, int nplanes, int nside, int lmax,
+                          int precision, double* const* psi, const clc_derivs* out);
 
 /* ------------------------------------------------------------------------ */
 /* Step 3: SHT+MG plane solve (Sec. 3.2)                                      */

@@ -59,6 +59,8 @@ _SIGS = {
     "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
     "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
     "clc_poisson_sht": (_i, [_p, _p, _i, _i, _i, _p, ctypes.POINTER(Derivs)]),
+    "clc_poisson_sht_batch": (_i, [_p, ctypes.POINTER(_p), _i, _i, _i, _i, ctypes.POINTER(_p),
+                                   ctypes.POINTER(Derivs)]),
     "clc_solution_create": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p)]),
     "clc_solution_destroy": (_i, [_p]),
     "clc_solution_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
@@ -211,6 +213,21 @@ class Context:
                                           ctypes.byref(d) if derivatives else None))
         if psi:
             out["psi"] = p
+        return out
+
+    def poisson_sht_batch(self, kappa, nside, lmax, precision=MIXED, derivatives=True, psi=True):
+        """clc_poisson_sht_batch over the rows of kappa[P, 12 nside^2]; returns
+        a dict of [P, 12 nside^2] tensors (psi and/or the five lens fields)."""
+        P, npx = kappa.shape
+        names = ("a_th", "a_ph", "u_tt", "u_pp", "u_tp") if derivatives else ()
+        out = {k: torch.empty(P, npx, dtype=torch.float64, device=self.device) for k in names}
+        if psi:
+            out["psi"] = torch.empty(P, npx, dtype=torch.float64, device=self.device)
+        kp = (_p * P)(*[kappa[i].data_ptr() for i in range(P)])
+        pp = (_p * P)(*[out["psi"][i].data_ptr() for i in range(P)]) if psi else None
+        dd = (Derivs * P)(*[Derivs(*[out[k][i].data_ptr() for k in names]) for i in range(P)]) if derivatives else None
+        _ptr(kappa)
+        self._check(lib().clc_poisson_sht_batch(self.h, kp, P, nside, lmax, precision, pp, dd))
         return out
 
     def gemm_f16x3(self, a_hi, a_lo, b_hi, b_lo):

@@ -30,6 +30,7 @@ struct Buffer {
 
 struct FftPlan;       // ring FFT plan of one Nside (fft.cu)
 struct LegendreTable; // lambda_lm table of one (Nside, lmax) (legendre.cu)
+struct TcTable;       // FP16 hi/lo lambda_lm table for the tensor cores (legendre_tc.cu)
 
 }  // namespace clc
 
@@ -45,6 +46,7 @@ struct clc_ctx {
   std::vector<cudaEvent_t> ev_pool;
   std::map<int, std::shared_ptr<clc::FftPlan>> fft_plans;
   std::map<std::tuple<int, int, int>, std::shared_ptr<clc::LegendreTable>> leg_tables;
+  std::map<std::pair<int, int>, std::shared_ptr<clc::TcTable>> tc_tables;
   // growable scratch buffers, reused across calls on this context's stream
   clc::Buffer scratch[8];
 };

@@ -115,6 +115,7 @@ extern "C" int clc_release_caches(clc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   ctx->fft_plans.clear();
   ctx->leg_tables.clear();
+  ctx->tc_tables.clear();
   return CLC_OK;
 }
 

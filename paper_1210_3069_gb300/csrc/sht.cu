@@ -12,6 +12,9 @@
 
 namespace clc {
 
+int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, int lmax, double* const* psi,
+                   const clc_derivs* out);
+
 // rhs_0 = psi_lm, rhs_1 = b_lm (l <= lmax + 1), rhs_2 = -l(l+1) psi_lm, all
 // packed with band limit lmax + 1.
 __global__ void k_poisson_rhs(const double2* __restrict__ klm, int lmax, double2* __restrict__ rhs, long long Q) {
@@ -125,10 +128,10 @@ extern "C" int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int
   if (!kappa) return set_err(ctx, CLC_EINVAL, "clc_poisson_sht: null kappa");
   if (precision != CLC_FP64 && precision != CLC_MIXED)
     return set_err(ctx, CLC_EINVAL, "clc_poisson_sht: precision must be CLC_FP64 or CLC_MIXED");
-  if (precision == CLC_MIXED) return set_err(ctx, CLC_EINVAL, "clc_poisson_sht: CLC_MIXED not available in this build");
   cudaSetDevice(ctx->device);
   const bool derivs = d && (d->a_th || d->a_ph || d->u_tt || d->u_pp || d->u_tp);
   if (!psi && !derivs) return CLC_OK;
+  if (precision == CLC_MIXED) return poisson_sht_tc(ctx, &kappa, 1, nside, lmax, &psi, derivs ? d : nullptr);
   double2* klm = (double2*)scratch(ctx, 1, sizeof(double2) * (alm_idx(lmax, lmax, lmax) + 1));
   if (!klm) return CLC_ENOMEM;
   if ((rc = sht_analysis(ctx, kappa, nside, lmax, klm))) return rc;
