@@ -22,7 +22,7 @@
 #include <algorithm>
 #include <map>
 
-#include "fft.cuh"
+#include "ring_fft.cuh"
 #include "legendre.cuh"
 #include "umma.cuh"
 
@@ -109,7 +109,7 @@ __device__ __forceinline__ int col_exponent(double mx) {
 }
 
 // analysis data: V[(2m+p)][col][r] from per-plane ring coefficients F[pl][m][ring]
-__global__ void k_tc_pack_analysis(const double2* __restrict__ F, int ldf, size_t fstride, int nside, int lmax, int P,
+__global__ void k_tc_pack_analysis(const float2* __restrict__ F, int ldf, size_t fstride, int nside, int lmax, int P,
                                    int N, int R, __half* __restrict__ vh, __half* __restrict__ vl,
                                    int* __restrict__ vexp) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
@@ -124,11 +124,11 @@ __global__ void k_tc_pack_analysis(const double2* __restrict__ F, int ldf, size_
     if (lane == 0) vexp[grp * N + col] = 0;
     return;
   }
-  const double2* Fm = F + pl * fstride + (size_t)m * ldf;
+  const float2* Fm = F + pl * fstride + (size_t)m * ldf;
   auto val = [&](int r) -> double {
     const int i = r + 1;
-    const double2 fn = Fm[i - 1];
-    double2 fs = make_double2(0.0, 0.0);
+    const float2 fn = Fm[i - 1];
+    float2 fs = make_float2(0.f, 0.f);
     if (i != 2 * nside) fs = Fm[4 * nside - i - 1];
     const double a = im ? fn.y : fn.x, b = im ? fs.y : fs.x;
     return p ? a - b : a + b;
@@ -317,7 +317,7 @@ struct TcSynthesisArgs {
   const int* sexp;
   const long long *off, *soff;
   const int* pad;
-  double2* G;                     // [P][nq][lmax + 2][ld]
+  float2* G;                      // [P][nq][lmax + 2][ld]
   size_t gstride, qstride;
   int R, N, P, nq, lmax, nside, ld;
 };
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_tc_synthesis(TcSynthesisArgs g, int* d_
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma::idesc_f16_f32(128, N);
+  const uint32_t idesc = umma::idesc_f16_f32_amn(128, N);
   uint32_t phase = 0;
   for (int p = 0; p < 2 && !abort_flag; ++p) {
     const int grp = 2 * m + p;
@@ -358,21 +358,15 @@ __global__ void __launch_bounds__(128) k_tc_synthesis(TcSynthesisArgs g, int* d_
     const __half* Sh = g.sh + g.soff[grp];
     const __half* Sl = g.sl + g.soff[grp];
     for (int k0 = 0; k0 < K; k0 += 64) {
-      // A = T^T: table rows k0..k0+63 (k), 128 rings -> smem rows = rings, K-major in k
+      // A = T^T as an MN-major operand, copied without transposition: table
+      // rows k0..k0+63 (K) x rings ring0..ring0+127 (M), two 64-ring atoms
+      // columns 8 KB apart, each [k row][64 rings] in the 128-byte swizzle
       for (int t = threadIdx.x; t < 64 * 16; t += blockDim.x) {
         const int kk = t >> 4, rc = t & 15;
         const size_t o = (trow0 + k0 + kk) * g.R + ring0 + rc * 8;
-        const uint4 vh = *reinterpret_cast<const uint4*>(g.th + o);
-        const uint4 vl = *reinterpret_cast<const uint4*>(g.tl + o);
-        const __half* hh = reinterpret_cast<const __half*>(&vh);
-        const __half* hl = reinterpret_cast<const __half*>(&vl);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int r = rc * 8 + q;
-          const uint32_t so = umma::sw128_offset(r, kk >> 3) + (uint32_t)((kk & 7) * 2);
-          *reinterpret_cast<__half*>(sAh + so) = hh[q];
-          *reinterpret_cast<__half*>(sAl + so) = hl[q];
-        }
+        const uint32_t so = (uint32_t)(rc >> 3) * 8192u + umma::sw128_offset(kk, rc & 7);
+        *reinterpret_cast<uint4*>(sAh + so) = *reinterpret_cast<const uint4*>(g.th + o);
+        *reinterpret_cast<uint4*>(sAl + so) = *reinterpret_cast<const uint4*>(g.tl + o);
       }
       for (int t = threadIdx.x; t < N * 8; t += blockDim.x) {
         const int r = t >> 3, c = t & 7;
@@ -384,15 +378,17 @@ __global__ void __launch_bounds__(128) k_tc_synthesis(TcSynthesisArgs g, int* d_
       __syncthreads();
       if (threadIdx.x == 0) {
         umma::fence_after_sync();
-        const uint64_t dAh = umma::desc_sw128(umma::smem_u32(sAh)), dAl = umma::desc_sw128(umma::smem_u32(sAl));
+        const uint64_t dAh = umma::desc_sw128_mn(umma::smem_u32(sAh), 8192, 1024);
+        const uint64_t dAl = umma::desc_sw128_mn(umma::smem_u32(sAl), 8192, 1024);
         const uint64_t dBh = umma::desc_sw128(umma::smem_u32(sBh)), dBl = umma::desc_sw128(umma::smem_u32(sBl));
         const uint32_t td = tmem + (uint32_t)(p * N);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-          umma::mma_f16(td, dAh + adv, dBh + adv, idesc, (k0 | kk) != 0);
-          umma::mma_f16(td, dAh + adv, dBl + adv, idesc, 1);
-          umma::mma_f16(td, dAl + adv, dBh + adv, idesc, 1);
+          const uint64_t adva = (uint64_t)(kk * 2048) >> 4;   // two 8-row K atoms
+          const uint64_t advb = (uint64_t)(kk * 32) >> 4;     // 16 fp16 along the K-major row
+          umma::mma_f16(td, dAh + adva, dBh + advb, idesc, (k0 | kk) != 0);
+          umma::mma_f16(td, dAh + adva, dBl + advb, idesc, 1);
+          umma::mma_f16(td, dAl + adva, dBh + advb, idesc, 1);
         }
         umma::commit(&mbar);
       }
@@ -428,9 +424,9 @@ __global__ void __launch_bounds__(128) k_tc_synthesis(TcSynthesisArgs g, int* d_
           orr = ldexp((double)vo[c], -kTabExp - eo[c0 + c]);
           oi = ldexp((double)vo[c + 1], -kTabExp - eo[c0 + c + 1]);
         }
-        double2* Gq = g.G + pl * g.gstride + q * g.qstride + (size_t)m * g.ld;
-        Gq[i - 1] = make_double2(er + orr, ei + oi);
-        if (has_s) Gq[4 * g.nside - i - 1] = make_double2(er - orr, ei - oi);
+        float2* Gq = g.G + pl * g.gstride + q * g.qstride + (size_t)m * g.ld;
+        Gq[i - 1] = make_float2((float)(er + orr), (float)(ei + oi));
+        if (has_s) Gq[4 * g.nside - i - 1] = make_float2((float)(er - orr), (float)(ei - oi));
       }
     }
   }
@@ -562,19 +558,19 @@ int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, i
   const size_t qstride = (size_t)ldf * (lmax + 2);
   const size_t gstride = nq * qstride;
   // scratch: F (P planes), packed V (hi, lo), exponents, alm (P), packed S, G (P planes)
-  const size_t bF = sizeof(double2) * fstride * P;
+  const size_t bF = sizeof(float2) * fstride * P;
   const size_t bV = sizeof(__half) * (size_t)G * Na * R;
   const size_t bVe = sizeof(int) * (size_t)G * Na;
   const size_t bA = sizeof(double2) * na * P;
   const size_t bS = sizeof(__half) * (size_t)spad_total;
   const size_t bSe = sizeof(int) * (size_t)G * Ns;
-  const size_t bG = sizeof(double2) * gstride * P;
+  const size_t bG = sizeof(float2) * gstride * P;
   const size_t bSo = sizeof(long long) * G;
   auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
   const size_t total = r256(bF) + 2 * r256(bV) + r256(bVe) + r256(bA) + 2 * r256(bS) + r256(bSe) + r256(bG) + r256(bSo);
   uint8_t* w = (uint8_t*)scratch(ctx, 6, total);
   if (!w) return CLC_ENOMEM;
-  double2* F = (double2*)w; w += r256(bF);
+  float2* F = (float2*)w; w += r256(bF);
   __half* vh = (__half*)w; w += r256(bV);
   __half* vl = (__half*)w; w += r256(bV);
   int* vexp = (int*)w; w += r256(bVe);
@@ -582,13 +578,13 @@ int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, i
   __half* sh = (__half*)w; w += r256(bS);
   __half* sl = (__half*)w; w += r256(bS);
   int* sexp = (int*)w; w += r256(bSe);
-  double2* Gm = (double2*)w; w += r256(bG);
+  float2* Gm = (float2*)w; w += r256(bG);
   long long* d_soff = (long long*)w;
   cudaMemcpyAsync(d_soff, soff.data(), bSo, cudaMemcpyHostToDevice, ctx->stream);
-  // 1. ring FFTs (FP64) of every plane, quadrature weight included
+  // 1. ring FFTs (FP32) of every plane, quadrature weight included
   const double wq = 4.0 * kPi / (12.0 * (double)nside * nside);
   for (int pl = 0; pl < P; ++pl)
-    if ((rc = ring_analysis(ctx, *plan, kappa[pl], lmax, wq, F + pl * fstride, ldf))) return rc;
+    if ((rc = ring_analysis_t<float>(ctx, *plan, kappa[pl], lmax, wq, (C2<float>*)(F + pl * fstride), ldf))) return rc;
   // 2. pack the analysis operand
   {
     const long long warps = (long long)G * Na;
@@ -649,7 +645,7 @@ int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, i
     CLC_LAUNCH(ctx, "k_tc_synthesis", k_tc_synthesis, dim3(R / 128, lmax + 1), 128, smem, s, ctx->d_err);
     if ((rc = launch_check(ctx, "k_tc_synthesis"))) return rc;
   }
-  // 6. ring FFT synthesis (FP64) of every plane
+  // 6. ring FFT synthesis (FP32) of every plane
   for (int pl = 0; pl < P; ++pl) {
     double* o[6] = {psi ? psi[pl] : nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     if (derivs) {
@@ -659,7 +655,8 @@ int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, i
       o[4] = out[pl].u_pp;
       o[5] = out[pl].u_tp;
     }
-    if ((rc = ring_synthesis(ctx, *plan, Gm + pl * gstride, ldf, lmax, derivs ? 1 : 0, o))) return rc;
+    if ((rc = ring_synthesis_t<float>(ctx, *plan, (const C2<float>*)(Gm + pl * gstride), ldf, lmax, derivs ? 1 : 0, o)))
+      return rc;
   }
   return CLC_OK;
 }

@@ -33,10 +33,24 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Descriptor of an MN-major tile in the 128-byte swizzle layout: 1024-byte
+// atoms of 8 K rows x 64 MN elements (128 bytes per row, 16-byte chunk index
+// XOR row), atoms `lbo` bytes apart along MN and `sbo` bytes apart along K.
+__device__ __forceinline__ uint64_t desc_sw128_mn(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: FP16 A and B (K-major), FP32 D, M x N.
 __host__ __device__ constexpr uint32_t idesc_f16_f32(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// The same with A MN-major (transposed A).
+__host__ __device__ constexpr uint32_t idesc_f16_f32_amn(int M, int N) { return idesc_f16_f32(M, N) | (1u << 15); }
 
 // D[tmem] (+)= A * B^T for one K = 16 slice; accumulate != 0 adds to D.
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
