@@ -161,6 +161,37 @@ int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int lmax, int 
 int clc_poisson_sht_batch(clc_ctx* ctx, const double* const* kappa, int nplanes, int nside, int lmax,
                           int precision, double* const* psi, const clc_derivs* out);
 
+/* A reusable plan for a fixed batch of pure-SHT plane solves of mixed sizes
+ * (paper Sec. 3.2; mixed precision only): nplanes planes, plane i of
+ * (nside[i], lmax[i]) with 64 <= nside <= 4096 and lmax <= 4 nside, at most 4
+ * distinct (nside, lmax) and at most 64 planes (21 with derivatives) of each.
+ * Every plane of the batch goes through six persistent launches (ring FFTs,
+ * operand packing, tensor-core analysis, packing, tensor-core synthesis, ring
+ * FFTs) whose work lists span all sizes.  flags: CLC_PLAN_GRAPH captures the
+ * six launches in a CUDA graph on the first execution and replays it;
+ * CLC_PLAN_TUNE times candidate launch shapes (pipeline depth, resident CTAs
+ * per SM) on the first execution and keeps the fastest.  The plan owns its
+ * intermediate buffers (device memory, freed by clc_sht_plan_destroy) and the
+ * shared FP16 tables stay cached in the context.  Errors: CLC_EINVAL for
+ * sizes outside the limits, CLC_ENOMEM if the tables or buffers do not fit. */
+typedef struct clc_sht_plan clc_sht_plan;
+#define CLC_PLAN_GRAPH 1
+#define CLC_PLAN_TUNE 2
+int clc_sht_plan_create(clc_ctx* ctx, int nplanes, const int* nside_host, const int* lmax_host, int derivatives,
+                        int flags, clc_sht_plan** plan);
+/* Solve every plane: kappa, psi are host arrays of nplanes device maps (psi
+ * NULL or entries NULL to skip), out a host array of nplanes clc_derivs (used
+ * when the plan was created with derivatives).  Asynchronous on the context's
+ * stream; the host arrays may be reused as soon as the call returns. */
+int clc_sht_plan_execute(clc_sht_plan* plan, const double* const* kappa, double* const* psi,
+                         const clc_derivs* out);
+/* Launch shapes in use (5 ints: analysis stages, analysis CTAs/SM, synthesis
+ * stages, synthesis CTAs/SM, FFT CTAs/SM), the tuned time of each of the six
+ * launches in ms (0 before tuning), and the device bytes the plan uses
+ * (buffers plus its share of cached tables).  Any output may be NULL. */
+int clc_sht_plan_info(const clc_sht_plan* plan, int* shape5, double* stage_ms6, size_t* device_bytes);
+int clc_sht_plan_destroy(clc_sht_plan* plan);
+
 /* ------------------------------------------------------------------------ */
 /* Step 3: SHT+MG plane solve (Sec. 3.2)                                      */
 

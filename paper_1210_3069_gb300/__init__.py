@@ -20,6 +20,7 @@ _lib = None
 OK, EINVAL, ENOMEM, ECUDA, ENOTCONVERGED, ETIMEOUT = range(6)
 RING, NEST = 0, 1
 FP64, FP32, MIXED = 0, 1, 2
+PLAN_GRAPH, PLAN_TUNE = 1, 2
 SOLVER_SHT, SOLVER_SHTMG = 0, 1
 
 _p = ctypes.c_void_p
@@ -71,6 +72,10 @@ _SIGS = {
     "clc_ray_step": (_i, [_p, _p, ctypes.POINTER(Derivs), _i, _d, _d, _d, ctypes.POINTER(Rays)]),
     "clc_raytrace_planes": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p), _i, _i, ctypes.POINTER(_d),
                                  ctypes.POINTER(Rays)]),
+    "clc_sht_plan_create": (_i, [_p, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), _i, _i, ctypes.POINTER(_p)]),
+    "clc_sht_plan_execute": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(Derivs)]),
+    "clc_sht_plan_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_size_t)]),
+    "clc_sht_plan_destroy": (_i, [_p]),
     "clc_gemm_f16x3": (_i, [_p, _p, _p, _p, _p, _i, _i, _i, _i, _p]),
     "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
     "clc_power_spectrum": (_i, [_p, _p, _p, _i, _p]),
@@ -230,6 +235,9 @@ class Context:
         self._check(lib().clc_poisson_sht_batch(self.h, kp, P, nside, lmax, precision, pp, dd))
         return out
 
+    def sht_plan(self, nsides, lmaxs, derivatives=True, graph=True, tune=False):
+        return ShtPlan(self, nsides, lmaxs, derivatives, graph, tune)
+
     def gemm_f16x3(self, a_hi, a_lo, b_hi, b_lo):
         """d[b] = a_hi b_hi^T + a_hi b_lo^T + a_lo b_hi^T (tcgen05, FP32 accumulate)."""
         batch, M, K = a_hi.shape
@@ -347,6 +355,54 @@ class RayState:
 
     def struct(self):
         return Rays(self.n, _ptr(self.x), _ptr(self.beta), _ptr(self.A), _ptr(self.Ap), _ptr(self.bundle))
+
+
+class ShtPlan:
+    """clc_sht_plan: a fixed batch of mixed-precision pure-SHT plane solves of
+    mixed (nside, lmax), optionally replayed as a CUDA graph and autotuned."""
+
+    def __init__(self, ctx, nsides, lmaxs, derivatives=True, graph=True, tune=False):
+        self.ctx = ctx
+        self.nsides = [int(v) for v in nsides]
+        self.lmaxs = [int(v) for v in lmaxs]
+        self.derivatives = derivatives
+        n = len(self.nsides)
+        h = _p()
+        ns = (_i * n)(*self.nsides)
+        lm = (_i * n)(*self.lmaxs)
+        flags = (PLAN_GRAPH if graph else 0) | (PLAN_TUNE if tune else 0)
+        ctx._check(lib().clc_sht_plan_create(ctx.h, n, ns, lm, 1 if derivatives else 0, flags, ctypes.byref(h)))
+        self.h = h
+
+    def execute(self, kappas, outputs):
+        """kappas: list of device maps; outputs: list of dicts with 'psi' and,
+        for a plan with derivatives, 'a_th', 'a_ph', 'u_tt', 'u_pp', 'u_tp'."""
+        n = len(self.nsides)
+        kp = (_p * n)(*[_ptr(k) for k in kappas])
+        pp = (_p * n)(*[_ptr(o.get("psi")) for o in outputs])
+        dd = None
+        if self.derivatives:
+            dd = (Derivs * n)(*[Derivs(*[_ptr(o.get(k)) for k in ("a_th", "a_ph", "u_tt", "u_pp", "u_tp")])
+                                for o in outputs])
+        self.ctx._check(lib().clc_sht_plan_execute(self.h, kp, pp, dd))
+
+    def info(self):
+        shape = (_i * 5)()
+        ms = (_d * 6)()
+        nb = ctypes.c_size_t()
+        self.ctx._check(lib().clc_sht_plan_info(self.h, shape, ms, ctypes.byref(nb)))
+        return {"shape": list(shape), "stage_ms": list(ms), "device_bytes": nb.value}
+
+    def close(self):
+        if self.h:
+            lib().clc_sht_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mg_params(nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2, max_cycles=60, fixed_cycles=0, tol=1e-10,

@@ -31,6 +31,7 @@ struct Buffer {
 struct FftPlan;       // ring FFT plan of one Nside (fft.cu)
 struct LegendreTable; // lambda_lm table of one (Nside, lmax) (legendre.cu)
 struct TcTable;       // FP16 hi/lo lambda_lm table for the tensor cores (legendre_tc.cu)
+struct TcBatch;       // buffers and launches of a mixed-precision SHT batch (sht_batch.cu)
 
 }  // namespace clc
 
@@ -47,6 +48,7 @@ struct clc_ctx {
   std::map<int, std::shared_ptr<clc::FftPlan>> fft_plans;
   std::map<std::tuple<int, int, int>, std::shared_ptr<clc::LegendreTable>> leg_tables;
   std::map<std::pair<int, int>, std::shared_ptr<clc::TcTable>> tc_tables;
+  std::map<std::tuple<int, int, int, int>, std::shared_ptr<clc::TcBatch>> tc_batches;
   // growable scratch buffers, reused across calls on this context's stream
   clc::Buffer scratch[8];
 };

@@ -103,6 +103,8 @@ extern "C" int clc_destroy(clc_ctx* ctx) {
   cudaStreamSynchronize(ctx->stream);
   prof_reset(ctx);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  ctx->tc_batches.clear();
+  ctx->tc_tables.clear();
   ctx->fft_plans.clear();
   ctx->leg_tables.clear();
   if (ctx->d_err) cudaFree(ctx->d_err);
@@ -114,6 +116,7 @@ extern "C" int clc_release_caches(clc_ctx* ctx) {
   if (!ctx) return CLC_EINVAL;
   cudaStreamSynchronize(ctx->stream);
   ctx->fft_plans.clear();
+  ctx->tc_batches.clear();
   ctx->leg_tables.clear();
   ctx->tc_tables.clear();
   return CLC_OK;

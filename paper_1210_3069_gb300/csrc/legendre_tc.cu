@@ -1,16 +1,16 @@
 // Mixed-precision, batched Legendre transforms of the SHT Poisson solve on the
-// tcgen05 tensor cores (paper Sec. 3.2 transforms; the split-precision
-// contraction follows the precision design of this library: FP64 only for the
-// recurrence that builds the table, the ring FFTs and the final unpacking).
+// tcgen05 tensor cores (paper Sec. 3.2 transforms).  FP64 is used only by the
+// scaled associated-Legendre recurrence that builds the table; the ring FFTs
+// run in FP32 and the contractions as split FP16 hi + lo products with FP32
+// accumulation in tensor memory.
 //
-// For every m the lambda table is split by the parity p of l - m (rows l = m +
-// p + 2k), because the southern mirror ring enters with sign (-1)^(l+m).  The
-// table holds 2^10 lambda_lm as FP16 hi + lo (|lambda_lm| <= sqrt((2l+1)/4 pi)
-// < 52 for l <= 16385, so the scaled values stay below the FP16 maximum 65504
-// and small values keep more bits before lo turns subnormal), rows padded with
-// zeros to a multiple of 64, laid out [m][p][k][ring] with the 2 Nside
-// northern rings contiguous.  A batch of P planes of the same (Nside, lmax) shares it:
-//   analysis   D[k][col]   = sum_ring T[m,p][k][ring] V[m,p][col][ring]
+// For every m the lambda table is split by the parity p of l - m (rows
+// l = m + p + 2k), because the southern mirror ring enters with sign
+// (-1)^(l+m).  The table holds 2^10 lambda_lm as FP16 hi + lo
+// (|lambda_lm| <= sqrt((2l+1)/4 pi) < 52 for l <= 16385, so the scaled values
+// stay below the FP16 maximum and small values keep more bits before lo turns
+// subnormal).  All planes of a batch class share it:
+//   analysis   D[k][col]      = sum_ring T[m,p][k][ring] V[m,p][col][ring]
 //              (col = plane, re/im; V = F_north +- F_south),
 //   synthesis  D_p[ring][col] = sum_k T[m,p][k][ring] S[m,p][col][k]
 //              (col = right-hand side, plane, re/im), both parities in one
@@ -18,10 +18,16 @@
 //              the northern (even + odd) and southern (even - odd) rings.
 // Data operands are split into FP16 hi + lo after scaling each column by a
 // power of two (max -> [2^13, 2^14)); products hi*hi + hi*lo + lo*hi
-// accumulate in FP32 in TMEM.
+// accumulate in FP32.  Every operand tile lives in global memory already in
+// the 128-byte-swizzled shared-memory layout, so a pipeline stage is a few
+// contiguous bulk copies (TMA engine) completing on an mbarrier; one thread
+// issues the copies, another the MMAs, and the four warps read the
+// accumulators back.  All kernels are persistent: each CTA walks a work list
+// spanning every class of the batch.
 #include <algorithm>
 #include <map>
 
+#include "legendre_tc.cuh"
 #include "ring_fft.cuh"
 #include "legendre.cuh"
 #include "umma.cuh"
@@ -29,19 +35,34 @@
 namespace clc {
 
 constexpr long long kTcWaitPolls = 1ll << 26;
-constexpr int kTabExp = 10;   // table values are 2^kTabExp lambda_lm
+constexpr int kTcMaxStages = 4;
 
-struct TcTable {
-  int nside = 0, lmax = 0, R = 0;
-  std::vector<long long> h_off;   // [2 (L+1)] row offset of group (m, p)
-  std::vector<int> h_rows;        // [2 (L+1)] rows of group (m, p) (l <= lmax + 1), before padding
-  std::vector<int> h_pad;         // [2 (L+1)] padded rows (multiple of 64)
-  Buffer off, rows, pad;          // device copies
-  Buffer hi, lo;                  // __half [total_rows + 128][R]
-  Buffer items;                   // int4 (m, p, 128-row tile, 0) work items of the analysis
-  int nitems = 0;
-  long long total_rows = 0;
-};
+// half offset of element (row r, column c < 64) inside a tile of 64-half rows
+// in the 128-byte swizzle (8-row groups of 1024 bytes)
+__host__ __device__ __forceinline__ uint32_t atom_off(int r, int c) {
+  return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + (((c >> 3) ^ (r & 7)) << 3) + (c & 7));
+}
+
+// FP32 x * 2^e, exact while the result is a normal float
+__device__ __forceinline__ float times_pow2f(float x, int e) {
+  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
+  return ldexpf(x, e);
+}
+
+// power-of-two exponent that brings a column maximum into [2^13, 2^14)
+__device__ __forceinline__ int col_exponent(float mx) {
+  if (!(mx > 0.f)) return 0;
+  int ex;
+  frexpf(mx, &ex);
+  return 14 - ex;
+}
+
+__device__ __forceinline__ void put_split2(__half* hi, __half* lo, size_t i, float a, float b) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  *reinterpret_cast<__half2*>(hi + i) = h;
+  *reinterpret_cast<__half2*>(lo + i) = __floats2half2_rn(a - hf.x, b - hf.y);
+}
 
 // ---------------------------------------------------------------------------
 // table build: the FP64 scaled recurrence of legendre.cu, written as FP16 hi/lo
@@ -50,12 +71,6 @@ __device__ __forceinline__ double tc_scale_pow2(double p, int e) {
   if (e >= -1022) return p * __longlong_as_double((long long)(e + 1023) << 52);
   if (e < -1600) return 0.0;
   return (p * __longlong_as_double((long long)(e + 600 + 1023) << 52)) * 0x1p-600;
-}
-
-__device__ __forceinline__ void put_split(__half* hi, __half* lo, size_t i, double v) {
-  const __half h = __double2half(v);
-  hi[i] = h;
-  lo[i] = __double2half(v - (double)__half2float(h));
 }
 
 __global__ void k_tc_table_build(int nside, int lmax, int R, const long long* __restrict__ off,
@@ -71,10 +86,15 @@ __global__ void k_tc_table_build(int nside, int lmax, int R, const long long* __
   int e = (int)floor(l2);
   double p2 = exp2(l2 - (double)e);
   if (m & 1) p2 = -p2;
+  const size_t ratoms = (size_t)(R >> 6);
   auto store = [&](int l, double p) {
     const int par = (l - m) & 1;
-    const size_t row = off[2 * m + par] + (l - m - par) / 2;
-    put_split(hi, lo, row * R + r, tc_scale_pow2(p, e + kTabExp));
+    const long long row = off[2 * m + par] + (l - m - par) / 2;
+    const size_t i = ((size_t)(row >> 6) * ratoms + (size_t)(r >> 6)) * 4096 + atom_off((int)(row & 63), r & 63);
+    const double v = tc_scale_pow2(p, e + kTabExp);
+    const __half h = __double2half(v);
+    hi[i] = h;
+    lo[i] = __double2half(v - (double)__half2float(h));
   };
   store(m, p2);
   if (lt < m + 1) return;
@@ -93,350 +113,6 @@ __global__ void k_tc_table_build(int nside, int lmax, int R, const long long* __
     p1 = p0;
   }
 }
-
-std::shared_ptr<TcTable> get_tc_table(clc_ctx* ctx, int nside, int lmax, int* rc);
-
-// ---------------------------------------------------------------------------
-// operand packing
-
-// One warp per (m, p, col): the column's values v_r, a power-of-two scale
-// 2^e with max |v| 2^e in [2^13, 2^14), then FP16 hi/lo of v 2^e.
-__device__ __forceinline__ int col_exponent(double mx) {
-  if (!(mx > 0.0)) return 0;
-  int ex;
-  frexp(mx, &ex);          // mx in [2^(ex-1), 2^ex)
-  return 14 - ex;
-}
-
-// analysis data: V[(2m+p)][col][r] from per-plane ring coefficients F[pl][m][ring]
-__global__ void k_tc_pack_analysis(const float2* __restrict__ F, int ldf, size_t fstride, int nside, int lmax, int P,
-                                   int N, int R, __half* __restrict__ vh, __half* __restrict__ vl,
-                                   int* __restrict__ vexp) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int ngroups = 2 * (lmax + 1);
-  if (gw >= ngroups * N) return;
-  const int col = gw % N, grp = gw / N;
-  const int m = grp >> 1, p = grp & 1;
-  const int pl = col >> 1, im = col & 1;
-  const size_t base = ((size_t)grp * N + col) * R;
-  if (pl >= P) {
-    for (int r = lane; r < R; r += 32) vh[base + r] = vl[base + r] = __double2half(0.0);
-    if (lane == 0) vexp[grp * N + col] = 0;
-    return;
-  }
-  const float2* Fm = F + pl * fstride + (size_t)m * ldf;
-  auto val = [&](int r) -> double {
-    const int i = r + 1;
-    const float2 fn = Fm[i - 1];
-    float2 fs = make_float2(0.f, 0.f);
-    if (i != 2 * nside) fs = Fm[4 * nside - i - 1];
-    const double a = im ? fn.y : fn.x, b = im ? fs.y : fs.x;
-    return p ? a - b : a + b;
-  };
-  double mx = 0.0;
-  for (int r = lane; r < R; r += 32) mx = fmax(mx, fabs(val(r)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const int e = col_exponent(mx);
-  const double sc = ldexp(1.0, e);
-  for (int r = lane; r < R; r += 32) put_split(vh, vl, base + r, val(r) * sc);
-  if (lane == 0) vexp[grp * N + col] = e;
-}
-
-// synthesis right-hand sides from per-plane a_lm (kappa): psi_lm, b_lm (theta
-// derivative) and kappa_bl, laid out S[(2m+p)][col][k] (k = (l - m - p) / 2,
-// padded rows zero), col = (q * P + pl) * 2 + re/im
-__device__ __forceinline__ double2 tc_psi(const double2* a, int lmax, int l, int m) {
-  if (l < m || l > lmax || l == 0) return make_double2(0.0, 0.0);
-  const double2 k = a[alm_idx(lmax, l, m)];
-  const double d = -1.0 / ((double)l * (l + 1.0));
-  return make_double2(k.x * d, k.y * d);
-}
-
-__device__ __forceinline__ double tc_eps(int l, int m) {
-  if (l <= m) return 0.0;
-  return sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
-}
-
-__global__ void k_tc_pack_synthesis(const double2* __restrict__ alm, size_t astride, int lmax, int P, int nq, int N,
-                                    const long long* __restrict__ soff, const int* __restrict__ pad,
-                                    __half* __restrict__ sh, __half* __restrict__ sl, int* __restrict__ sexp) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int ngroups = 2 * (lmax + 1);
-  if (gw >= ngroups * N) return;
-  const int col = gw % N, grp = gw / N;
-  const int m = grp >> 1, p = grp & 1;
-  const int K = pad[grp];
-  const size_t base = soff[grp] + (size_t)col * K;
-  const int im = col & 1, qp = col >> 1, q = qp / P, pl = qp % P;
-  if (q >= nq || K == 0) {
-    for (int k = lane; k < K; k += 32) sh[base + k] = sl[base + k] = __double2half(0.0);
-    if (lane == 0) sexp[grp * N + col] = 0;
-    return;
-  }
-  const double2* a = alm + pl * astride;
-  auto val = [&](int k) -> double {
-    const int l = m + p + 2 * k;
-    if (l > lmax + 1) return 0.0;
-    double2 v;
-    if (q == 0) {
-      v = tc_psi(a, lmax, l, m);
-    } else if (q == 1) {
-      const double2 pm = tc_psi(a, lmax, l - 1, m), pp = tc_psi(a, lmax, l + 1, m);
-      const double c1 = (l - 1.0) * tc_eps(l, m), c2 = (l + 2.0) * tc_eps(l + 1, m);
-      v = make_double2(c1 * pm.x - c2 * pp.x, c1 * pm.y - c2 * pp.y);
-    } else {
-      const double2 ps = tc_psi(a, lmax, l, m);
-      const double f = -(double)l * (l + 1.0);
-      v = make_double2(f * ps.x, f * ps.y);
-    }
-    if (m == 0) v.y = 0.0;
-    return im ? v.y : v.x;
-  };
-  double mx = 0.0;
-  for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(val(k)));
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  const int e = col_exponent(mx);
-  const double sc = ldexp(1.0, e);
-  for (int k = lane; k < K; k += 32) put_split(sh, sl, base + k, val(k) * sc);
-  if (lane == 0) sexp[grp * N + col] = e;
-}
-
-// ---------------------------------------------------------------------------
-// tensor-core contractions
-
-struct TcAnalysisArgs {
-  const __half *th, *tl;          // table
-  const __half *vh, *vl;          // packed data
-  const int* vexp;
-  const long long* off;
-  const int* rows;
-  const int4* items;              // (m, p, tile, 0)
-  double2* alm;                   // [P][nalm]
-  size_t astride;
-  int R, N, P, lmax;
-};
-
-__global__ void __launch_bounds__(128) k_tc_analysis(TcAnalysisArgs g, int* d_err) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  const uint32_t raw = umma::smem_u32(smem_raw);
-  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  const int N = g.N;
-  uint8_t* sAh = base;
-  uint8_t* sAl = sAh + 16384;
-  uint8_t* sBh = sAl + 16384;
-  uint8_t* sBl = sBh + ((N * 128 + 1023) & ~1023);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int4 it = g.items[blockIdx.x];
-  const int m = it.x, p = it.y, tile = it.z;
-  const int grp = 2 * m + p;
-  const size_t row0 = g.off[grp] + (size_t)tile * 128;
-  const __half* Vh = g.vh + (size_t)grp * N * g.R;
-  const __half* Vl = g.vl + (size_t)grp * N * g.R;
-  int ncols = 32;
-  while (ncols < N) ncols <<= 1;
-  if (threadIdx.x == 0) {
-    umma::mbar_init(&mbar, 1);
-    abort_flag = 0;
-  }
-  if (warp == 0) umma::tmem_alloc(&tmem_base, ncols);
-  umma::fence_before_sync();
-  __syncthreads();
-  umma::fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma::idesc_f16_f32(128, N);
-  uint32_t phase = 0;
-  for (int k0 = 0; k0 < g.R; k0 += 64) {
-    for (int t = threadIdx.x; t < 128 * 8; t += blockDim.x) {
-      const int r = t >> 3, c = t & 7;
-      const size_t o = (row0 + r) * g.R + k0 + c * 8;
-      *reinterpret_cast<uint4*>(sAh + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(g.th + o);
-      *reinterpret_cast<uint4*>(sAl + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(g.tl + o);
-    }
-    for (int t = threadIdx.x; t < N * 8; t += blockDim.x) {
-      const int r = t >> 3, c = t & 7;
-      const size_t o = (size_t)r * g.R + k0 + c * 8;
-      *reinterpret_cast<uint4*>(sBh + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(Vh + o);
-      *reinterpret_cast<uint4*>(sBl + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(Vl + o);
-    }
-    umma::fence_proxy_async();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      umma::fence_after_sync();
-      const uint64_t dAh = umma::desc_sw128(umma::smem_u32(sAh)), dAl = umma::desc_sw128(umma::smem_u32(sAl));
-      const uint64_t dBh = umma::desc_sw128(umma::smem_u32(sBh)), dBl = umma::desc_sw128(umma::smem_u32(sBl));
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t adv = (uint64_t)(kk * 32) >> 4;
-        umma::mma_f16(tmem, dAh + adv, dBh + adv, idesc, (k0 | kk) != 0);
-        umma::mma_f16(tmem, dAh + adv, dBl + adv, idesc, 1);
-        umma::mma_f16(tmem, dAl + adv, dBh + adv, idesc, 1);
-      }
-      umma::commit(&mbar);
-    }
-    if (!umma::mbar_wait(&mbar, phase, kTcWaitPolls)) {
-      if (lane == 0) atomicCAS(d_err, 0, kDevTimeout);
-      abort_flag = 1;
-    }
-    phase ^= 1u;
-    __syncthreads();
-    if (abort_flag) break;
-  }
-  umma::fence_after_sync();
-  if (!abort_flag) {
-    const int k = tile * 128 + warp * 32 + lane;
-    const int l = m + p + 2 * k;
-    const bool valid = k < g.rows[grp] && l <= g.lmax;
-    const int* ve = g.vexp + (size_t)grp * N;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (valid) {
-#pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const int pl = (c0 + i) >> 1;
-          if (pl < g.P) {
-            const double re = ldexp((double)v[i], -kTabExp - ve[c0 + i]);
-            const double imv = ldexp((double)v[i + 1], -kTabExp - ve[c0 + i + 1]);
-            g.alm[pl * g.astride + alm_idx(g.lmax, l, m)] = make_double2(re, imv);
-          }
-        }
-      }
-    }
-  }
-  umma::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, ncols);
-}
-
-struct TcSynthesisArgs {
-  const __half *th, *tl;
-  const __half *sh, *sl;
-  const int* sexp;
-  const long long *off, *soff;
-  const int* pad;
-  float2* G;                      // [P][nq][lmax + 2][ld]
-  size_t gstride, qstride;
-  int R, N, P, nq, lmax, nside, ld;
-};
-
-// Block (ring tile, m): both parities, accumulators at TMEM columns [0, N) and [N, 2N)
-__global__ void __launch_bounds__(128) k_tc_synthesis(TcSynthesisArgs g, int* d_err) {
-  extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  __shared__ int abort_flag;
-  const uint32_t raw = umma::smem_u32(smem_raw);
-  uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
-  const int N = g.N;
-  uint8_t* sAh = base;
-  uint8_t* sAl = sAh + 16384;
-  uint8_t* sBh = sAl + 16384;
-  uint8_t* sBl = sBh + ((N * 128 + 1023) & ~1023);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tile = blockIdx.x, m = blockIdx.y;
-  const int ring0 = tile * 128;
-  int ncols = 32;
-  while (ncols < 2 * N) ncols <<= 1;
-  if (threadIdx.x == 0) {
-    umma::mbar_init(&mbar, 1);
-    abort_flag = 0;
-  }
-  if (warp == 0) umma::tmem_alloc(&tmem_base, ncols);
-  umma::fence_before_sync();
-  __syncthreads();
-  umma::fence_after_sync();
-  const uint32_t tmem = tmem_base;
-  const uint32_t idesc = umma::idesc_f16_f32_amn(128, N);
-  uint32_t phase = 0;
-  for (int p = 0; p < 2 && !abort_flag; ++p) {
-    const int grp = 2 * m + p;
-    const int K = g.pad[grp];
-    const size_t trow0 = g.off[grp];
-    const __half* Sh = g.sh + g.soff[grp];
-    const __half* Sl = g.sl + g.soff[grp];
-    for (int k0 = 0; k0 < K; k0 += 64) {
-      // A = T^T as an MN-major operand, copied without transposition: table
-      // rows k0..k0+63 (K) x rings ring0..ring0+127 (M), two 64-ring atoms
-      // columns 8 KB apart, each [k row][64 rings] in the 128-byte swizzle
-      for (int t = threadIdx.x; t < 64 * 16; t += blockDim.x) {
-        const int kk = t >> 4, rc = t & 15;
-        const size_t o = (trow0 + k0 + kk) * g.R + ring0 + rc * 8;
-        const uint32_t so = (uint32_t)(rc >> 3) * 8192u + umma::sw128_offset(kk, rc & 7);
-        *reinterpret_cast<uint4*>(sAh + so) = *reinterpret_cast<const uint4*>(g.th + o);
-        *reinterpret_cast<uint4*>(sAl + so) = *reinterpret_cast<const uint4*>(g.tl + o);
-      }
-      for (int t = threadIdx.x; t < N * 8; t += blockDim.x) {
-        const int r = t >> 3, c = t & 7;
-        const size_t o = (size_t)r * K + k0 + c * 8;
-        *reinterpret_cast<uint4*>(sBh + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(Sh + o);
-        *reinterpret_cast<uint4*>(sBl + umma::sw128_offset(r, c)) = *reinterpret_cast<const uint4*>(Sl + o);
-      }
-      umma::fence_proxy_async();
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        umma::fence_after_sync();
-        const uint64_t dAh = umma::desc_sw128_mn(umma::smem_u32(sAh), 8192, 1024);
-        const uint64_t dAl = umma::desc_sw128_mn(umma::smem_u32(sAl), 8192, 1024);
-        const uint64_t dBh = umma::desc_sw128(umma::smem_u32(sBh)), dBl = umma::desc_sw128(umma::smem_u32(sBl));
-        const uint32_t td = tmem + (uint32_t)(p * N);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t adva = (uint64_t)(kk * 2048) >> 4;   // two 8-row K atoms
-          const uint64_t advb = (uint64_t)(kk * 32) >> 4;     // 16 fp16 along the K-major row
-          umma::mma_f16(td, dAh + adva, dBh + advb, idesc, (k0 | kk) != 0);
-          umma::mma_f16(td, dAh + adva, dBl + advb, idesc, 1);
-          umma::mma_f16(td, dAl + adva, dBh + advb, idesc, 1);
-        }
-        umma::commit(&mbar);
-      }
-      if (!umma::mbar_wait(&mbar, phase, kTcWaitPolls)) {
-        if (lane == 0) atomicCAS(d_err, 0, kDevTimeout);
-        abort_flag = 1;
-      }
-      phase ^= 1u;
-      __syncthreads();
-      if (abort_flag) break;
-    }
-  }
-  umma::fence_after_sync();
-  if (!abort_flag) {
-    const int r = ring0 + warp * 32 + lane;
-    const int i = r + 1;
-    const bool has_s = i != 2 * g.nside;
-    const int* ee = g.sexp + (size_t)(2 * m) * N;
-    const int* eo = g.sexp + (size_t)(2 * m + 1) * N;
-    const bool odd_exists = g.pad[2 * m + 1] > 0;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float ve[16], vo[16];
-      umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, ve);
-      umma::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(N + c0), vo);
-#pragma unroll
-      for (int c = 0; c < 16; c += 2) {
-        const int qp = (c0 + c) >> 1;
-        const int q = qp / g.P, pl = qp % g.P;
-        if (q >= g.nq) continue;
-        const double er = ldexp((double)ve[c], -kTabExp - ee[c0 + c]), ei = ldexp((double)ve[c + 1], -kTabExp - ee[c0 + c + 1]);
-        double orr = 0.0, oi = 0.0;
-        if (odd_exists) {
-          orr = ldexp((double)vo[c], -kTabExp - eo[c0 + c]);
-          oi = ldexp((double)vo[c + 1], -kTabExp - eo[c0 + c + 1]);
-        }
-        float2* Gq = g.G + pl * g.gstride + q * g.qstride + (size_t)m * g.ld;
-        Gq[i - 1] = make_float2((float)(er + orr), (float)(ei + oi));
-        if (has_s) Gq[4 * g.nside - i - 1] = make_float2((float)(er - orr), (float)(ei - oi));
-      }
-    }
-  }
-  umma::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, ncols);
-}
-
-// ---------------------------------------------------------------------------
-// host
 
 std::shared_ptr<TcTable> get_tc_table(clc_ctx* ctx, int nside, int lmax, int* rc) {
   const auto key = std::make_pair(nside, lmax);
@@ -469,7 +145,8 @@ std::shared_ptr<TcTable> get_tc_table(clc_ctx* ctx, int nside, int lmax, int* rc
   size_t fb = 0, tb = 0;
   cudaMemGetInfo(&fb, &tb);
   if (2 * bytes + (2ull << 30) > fb) {
-    *rc = set_err(ctx, CLC_ENOMEM, "tensor-core Legendre table of " + std::to_string(2 * bytes >> 20) + " MiB does not fit");
+    *rc = set_err(ctx, CLC_ENOMEM,
+                  "tensor-core Legendre table of " + std::to_string(2 * bytes >> 20) + " MiB does not fit");
     return nullptr;
   }
   auto alloc = [&](Buffer& b, size_t n) -> bool {
@@ -497,14 +174,8 @@ std::shared_ptr<TcTable> get_tc_table(clc_ctx* ctx, int nside, int lmax, int* rc
     if (m > 0) ln += 0.5 * std::log2((2.0 * m + 1.0) / (2.0 * m));
     lognorm[m] = ln;
   }
-  std::vector<int4> items;
-  for (int m = 0; m <= lmax; ++m)
-    for (int p = 0; p < 2; ++p)
-      for (int t = 0; t * 128 < T->h_rows[2 * m + p]; ++t)
-        if (m + p + 2 * (t * 128) <= lmax) items.push_back(make_int4(m, p, t, 0));
-  T->nitems = (int)items.size();
   Buffer d_ab, d_ln;
-  if (!alloc(T->items, sizeof(int4) * items.size()) || !alloc(T->hi, bytes) || !alloc(T->lo, bytes) || !alloc(T->off, sizeof(long long) * G) ||
+  if (!alloc(T->hi, bytes) || !alloc(T->lo, bytes) || !alloc(T->off, sizeof(long long) * G) ||
       !alloc(T->rows, sizeof(int) * G) || !alloc(T->pad, sizeof(int) * G) || !alloc(d_ab, sizeof(double2) * ab.size()) ||
       !alloc(d_ln, sizeof(double) * lognorm.size())) {
     *rc = set_err(ctx, CLC_ENOMEM, "tensor-core Legendre table allocation failed");
@@ -517,181 +188,527 @@ std::shared_ptr<TcTable> get_tc_table(clc_ctx* ctx, int nside, int lmax, int* rc
   cudaMemcpyAsync(T->pad.p, T->h_pad.data(), sizeof(int) * G, cudaMemcpyHostToDevice, ctx->stream);
   cudaMemcpyAsync(d_ab.p, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, ctx->stream);
   cudaMemcpyAsync(d_ln.p, lognorm.data(), sizeof(double) * lognorm.size(), cudaMemcpyHostToDevice, ctx->stream);
-  cudaMemcpyAsync(T->items.p, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, ctx->stream);
   dim3 grid((T->R + 127) / 128, lmax + 1);
   CLC_LAUNCH(ctx, "k_tc_table_build", k_tc_table_build, grid, 128, 0, nside, lmax, T->R,
              (const long long*)T->off.p, (const double*)d_ln.p, (const double2*)d_ab.p, (__half*)T->hi.p,
              (__half*)T->lo.p);
   *rc = launch_check(ctx, "k_tc_table_build");
+  // the coefficient buffers are freed on return: wait for the build
   cudaStreamSynchronize(ctx->stream);
   if (*rc) return nullptr;
   ctx->tc_tables[key] = T;
   return T;
 }
 
-static int round16(int v) { return (v + 15) / 16 * 16; }
+// ---------------------------------------------------------------------------
+// flat item spaces over the classes of a batch
 
-// Mixed-precision pure-SHT Poisson solve of P planes of the same (nside, lmax):
-// kappa[pl] (device maps), outputs psi[pl] and the five lens fields per plane.
-int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, int lmax, double* const* psi,
-                   const clc_derivs* out) {
-  int rc;
-  if (nside < 64) return set_err(ctx, CLC_EINVAL, "CLC_MIXED needs nside >= 64");
-  const bool derivs = out != nullptr;
-  const int nq = derivs ? 3 : 1;
-  const int Na = round16(2 * P), Ns = round16(2 * nq * P);
-  if (Na > 256 || 2 * Ns > 256) return set_err(ctx, CLC_EINVAL, "CLC_MIXED: too many planes in one batch");
-  auto plan = get_fft_plan(ctx, nside, &rc);
-  if (rc) return rc;
-  auto T = get_tc_table(ctx, nside, lmax, &rc);
-  if (rc) return rc;
-  const int R = T->R, G = 2 * (lmax + 1);
-  const int ldf = 4 * nside - 1;
-  const size_t fstride = (size_t)ldf * (lmax + 1);
-  const size_t na = (size_t)(lmax + 1) * (lmax + 2) / 2;
-  long long spad_total = 0;
-  std::vector<long long> soff(G);
-  for (int g = 0; g < G; ++g) {
-    soff[g] = spad_total;
-    spad_total += (long long)Ns * T->h_pad[g];
+__device__ __forceinline__ int find_class(const TcBatchDev& b, long long idx, long long TcClass::*first) {
+  int c = 0;
+  while (c + 1 < b.ncls && idx >= b.cls[c + 1].*first) ++c;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// ring FFTs (FP32) of every plane of every class
+
+__global__ void k_tc_ring_analysis(TcBatchDev b) {
+  extern __shared__ __align__(16) unsigned char smem_ra[];
+  C2<float>* s = reinterpret_cast<C2<float>*>(smem_ra);
+  for (long long it = blockIdx.x; it < b.n_ring; it += gridDim.x) {
+    const TcClass& C = b.cls[find_class(b, it, &TcClass::ring0)];
+    const long long loc = it - C.ring0;
+    const int nr = 4 * C.nside - 1;
+    const int pl = (int)(loc / nr), i = (int)(loc % nr) + 1;
+    ring_analysis_ring<float>(b.kappa[C.plane0 + pl], C.nside, C.lmax, C.wq,
+                              reinterpret_cast<C2<float>*>(C.F + pl * C.fstride), C.ldf, C.fft, i, s);
   }
-  const size_t qstride = (size_t)ldf * (lmax + 2);
-  const size_t gstride = nq * qstride;
-  // scratch: F (P planes), packed V (hi, lo), exponents, alm (P), packed S, G (P planes)
-  const size_t bF = sizeof(float2) * fstride * P;
-  const size_t bV = sizeof(__half) * (size_t)G * Na * R;
-  const size_t bVe = sizeof(int) * (size_t)G * Na;
-  const size_t bA = sizeof(double2) * na * P;
-  const size_t bS = sizeof(__half) * (size_t)spad_total;
-  const size_t bSe = sizeof(int) * (size_t)G * Ns;
-  const size_t bG = sizeof(float2) * gstride * P;
-  const size_t bSo = sizeof(long long) * G;
-  auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
-  const size_t total = r256(bF) + 2 * r256(bV) + r256(bVe) + r256(bA) + 2 * r256(bS) + r256(bSe) + r256(bG) + r256(bSo);
-  uint8_t* w = (uint8_t*)scratch(ctx, 6, total);
-  if (!w) return CLC_ENOMEM;
-  float2* F = (float2*)w; w += r256(bF);
-  __half* vh = (__half*)w; w += r256(bV);
-  __half* vl = (__half*)w; w += r256(bV);
-  int* vexp = (int*)w; w += r256(bVe);
-  double2* alm = (double2*)w; w += r256(bA);
-  __half* sh = (__half*)w; w += r256(bS);
-  __half* sl = (__half*)w; w += r256(bS);
-  int* sexp = (int*)w; w += r256(bSe);
-  float2* Gm = (float2*)w; w += r256(bG);
-  long long* d_soff = (long long*)w;
-  cudaMemcpyAsync(d_soff, soff.data(), bSo, cudaMemcpyHostToDevice, ctx->stream);
-  // 1. ring FFTs (FP32) of every plane, quadrature weight included
-  const double wq = 4.0 * kPi / (12.0 * (double)nside * nside);
-  for (int pl = 0; pl < P; ++pl)
-    if ((rc = ring_analysis_t<float>(ctx, *plan, kappa[pl], lmax, wq, (C2<float>*)(F + pl * fstride), ldf))) return rc;
-  // 2. pack the analysis operand
-  {
-    const long long warps = (long long)G * Na;
-    CLC_LAUNCH(ctx, "k_tc_pack_analysis", k_tc_pack_analysis, (int)((warps * 32 + 255) / 256), 256, 0, F, ldf,
-               fstride, nside, lmax, P, Na, R, vh, vl, vexp);
+}
+
+__global__ void k_tc_ring_synthesis(TcBatchDev b) {
+  extern __shared__ __align__(16) unsigned char smem_rs[];
+  C2<float>* s = reinterpret_cast<C2<float>*>(smem_rs);
+  for (long long it = blockIdx.x; it < b.n_ring; it += gridDim.x) {
+    const TcClass& C = b.cls[find_class(b, it, &TcClass::ring0)];
+    const long long loc = it - C.ring0;
+    const int nr = 4 * C.nside - 1;
+    const int pl = (int)(loc / nr), i = (int)(loc % nr) + 1;
+    SynthArgsT<float> a;
+    const float2* Gp = C.G + pl * C.gstride;
+    a.G0 = reinterpret_cast<const C2<float>*>(Gp);
+    a.G1 = reinterpret_cast<const C2<float>*>(Gp + C.qstride);
+    a.G2 = reinterpret_cast<const C2<float>*>(Gp + 2 * C.qstride);
+    a.ld = C.ldf;
+    double* const* o = b.out + (size_t)(C.plane0 + pl) * 6;
+    for (int f = 0; f < 6; ++f) a.out[f] = o[f];
+    ring_synthesis_ring<float>(a, C.nside, C.lmax, b.mode, C.fft, i, s, s + C.mmax);
   }
-  // 3. analysis on the tensor cores: one CTA per (m, p, 128-row tile)
-  {
-    TcAnalysisArgs a;
-    a.th = (const __half*)T->hi.p;
-    a.tl = (const __half*)T->lo.p;
-    a.vh = vh;
-    a.vl = vl;
-    a.vexp = vexp;
-    a.off = (const long long*)T->off.p;
-    a.rows = (const int*)T->rows.p;
-    a.items = (const int4*)T->items.p;
-    a.alm = alm;
-    a.astride = na;
-    a.R = R;
-    a.N = Na;
-    a.P = P;
-    a.lmax = lmax;
-    const int smem = 1024 + 2 * 16384 + 2 * ((Na * 128 + 1023) & ~1023);
-    cudaFuncSetAttribute(k_tc_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    CLC_LAUNCH(ctx, "k_tc_analysis", k_tc_analysis, T->nitems, 128, smem, a, ctx->d_err);
-    if ((rc = launch_check(ctx, "k_tc_analysis"))) return rc;
-  }
-  // 4. Poisson solve and synthesis right-hand sides
-  {
-    const long long warps = (long long)G * Ns;
-    CLC_LAUNCH(ctx, "k_tc_pack_synthesis", k_tc_pack_synthesis, (int)((warps * 32 + 255) / 256), 256, 0, alm, na,
-               lmax, P, nq, Ns, d_soff, (const int*)T->pad.p, sh, sl, sexp);
-  }
-  // 5. synthesis on the tensor cores: one CTA per (128-ring tile, m)
-  {
-    TcSynthesisArgs s;
-    s.th = (const __half*)T->hi.p;
-    s.tl = (const __half*)T->lo.p;
-    s.sh = sh;
-    s.sl = sl;
-    s.sexp = sexp;
-    s.off = (const long long*)T->off.p;
-    s.soff = d_soff;
-    s.pad = (const int*)T->pad.p;
-    s.G = Gm;
-    s.gstride = gstride;
-    s.qstride = qstride;
-    s.R = R;
-    s.N = Ns;
-    s.P = P;
-    s.nq = nq;
-    s.lmax = lmax;
-    s.nside = nside;
-    s.ld = ldf;
-    const int smem = 1024 + 2 * 16384 + 2 * ((Ns * 128 + 1023) & ~1023);
-    cudaFuncSetAttribute(k_tc_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    CLC_LAUNCH(ctx, "k_tc_synthesis", k_tc_synthesis, dim3(R / 128, lmax + 1), 128, smem, s, ctx->d_err);
-    if ((rc = launch_check(ctx, "k_tc_synthesis"))) return rc;
-  }
-  // 6. ring FFT synthesis (FP32) of every plane
-  for (int pl = 0; pl < P; ++pl) {
-    double* o[6] = {psi ? psi[pl] : nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    if (derivs) {
-      o[1] = out[pl].a_th;
-      o[2] = out[pl].a_ph;
-      o[3] = out[pl].u_tt;
-      o[4] = out[pl].u_pp;
-      o[5] = out[pl].u_tp;
+}
+
+// ---------------------------------------------------------------------------
+// operand packing (FP32 arithmetic)
+
+// analysis operand of order m (both parities): V[2m+p][ring block][col][64],
+// col = 2 plane + re/im, values F_north +- F_south of ring r
+__global__ void k_tc_pack_analysis(TcBatchDev b) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long it = blockIdx.x; it < b.n_pa; it += gridDim.x) {
+    const TcClass& C = b.cls[find_class(b, it, &TcClass::pa0)];
+    const int m = (int)(it - C.pa0);
+    const int R = C.R, N = C.Na, ns = C.nside;
+    const size_t blk = (size_t)N * 64;
+    const size_t be = (size_t)(2 * m) * (R / 64) * blk, bo = be + (size_t)(R / 64) * blk;
+    for (int col = warp; col < N; col += nw) {
+      const int pl = col >> 1, im = col & 1;
+      if (pl >= C.P) {
+        for (int r = 2 * lane; r < R; r += 64) {
+          const size_t o = (size_t)(r >> 6) * blk + atom_off(col, r & 63);
+          put_split2(C.vh, C.vl, be + o, 0.f, 0.f);
+          put_split2(C.vh, C.vl, bo + o, 0.f, 0.f);
+        }
+        if (lane == 0) C.vexp[(2 * m) * N + col] = C.vexp[(2 * m + 1) * N + col] = 0;
+        continue;
+      }
+      const float* Fm = reinterpret_cast<const float*>(C.F + pl * C.fstride + (size_t)m * C.ldf) + im;
+      auto vals = [&](int r, float& e, float& o) {
+        const float a = Fm[2 * r];
+        const float s = (r + 1 != 2 * ns) ? Fm[2 * (4 * ns - r - 2)] : 0.f;
+        e = a + s;
+        o = a - s;
+      };
+      float mxe = 0.f, mxo = 0.f;
+      for (int r = 2 * lane; r < R; r += 64) {
+        float e0, o0, e1, o1;
+        vals(r, e0, o0);
+        vals(r + 1, e1, o1);
+        mxe = fmaxf(mxe, fmaxf(fabsf(e0), fabsf(e1)));
+        mxo = fmaxf(mxo, fmaxf(fabsf(o0), fabsf(o1)));
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        mxe = fmaxf(mxe, __shfl_xor_sync(0xffffffffu, mxe, o));
+        mxo = fmaxf(mxo, __shfl_xor_sync(0xffffffffu, mxo, o));
+      }
+      const int xe = col_exponent(mxe), xo = col_exponent(mxo);
+      for (int r = 2 * lane; r < R; r += 64) {
+        float e0, o0, e1, o1;
+        vals(r, e0, o0);
+        vals(r + 1, e1, o1);
+        const size_t o = (size_t)(r >> 6) * blk + atom_off(col, r & 63);
+        put_split2(C.vh, C.vl, be + o, times_pow2f(e0, xe), times_pow2f(e1, xe));
+        put_split2(C.vh, C.vl, bo + o, times_pow2f(o0, xo), times_pow2f(o1, xo));
+      }
+      if (lane == 0) {
+        C.vexp[(2 * m) * N + col] = xe;
+        C.vexp[(2 * m + 1) * N + col] = xo;
+      }
     }
-    if ((rc = ring_synthesis_t<float>(ctx, *plan, (const C2<float>*)(Gm + pl * gstride), ldf, lmax, derivs ? 1 : 0, o)))
-      return rc;
+  }
+}
+
+// synthesis right-hand sides of group (m, p): S[soff + t Ns 64][col][64],
+// col = (q P + plane) 2 + re/im.  With psi_lm = -kappa_lm / (l (l + 1)):
+//   q = 0: psi_lm                              = D0_l kappa_lm,
+//   q = 1: b_lm = (l-1) eps_lm psi_{l-1,m} - (l+2) eps_{l+1,m} psi_{l+1,m}
+//               = A1_l kappa_{l-1,m} + A2_l kappa_{l+1,m},
+//          A1_l = -eps_lm / l, A2_l = eps_{l+1,m} / (l + 1),
+//   q = 2: kappa_bl = -l (l + 1) psi_lm        = kappa_lm for l >= 1,
+// terms outside 1 <= l' <= lmax being zero; eps_lm = sqrt((l^2 - m^2) / (4 l^2 - 1)).
+__device__ __forceinline__ float tc_epsf(int l, int m) {
+  if (l <= m) return 0.f;
+  return sqrtf((float)((l - m) * (l + m)) / (float)((2 * l - 1) * (2 * l + 1)));
+}
+
+__global__ void k_tc_pack_synthesis(TcBatchDev b) {
+  extern __shared__ float coef[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (long long it = blockIdx.x; it < b.n_ps; it += gridDim.x) {
+    const TcClass& C = b.cls[find_class(b, it, &TcClass::ps0)];
+    const int grp = (int)(it - C.ps0);
+    const int m = grp >> 1, p = grp & 1, lmax = C.lmax, N = C.Ns;
+    const int K = C.pad[grp];
+    float* D0 = coef;
+    float* A1 = coef + K;
+    float* A2 = coef + 2 * K;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+      const int l = m + p + 2 * k;
+      float d0 = 0.f, a1 = 0.f, a2 = 0.f;
+      if (l <= lmax + 1) {
+        if (l >= 1 && l <= lmax) d0 = -1.f / ((float)l * (float)(l + 1));
+        if (l - 1 >= 1 && l - 1 <= lmax) a1 = -tc_epsf(l, m) / (float)l;
+        if (l + 1 <= lmax) a2 = tc_epsf(l + 1, m) / (float)(l + 1);
+      }
+      D0[k] = d0;
+      A1[k] = a1;
+      A2[k] = a2;
+    }
+    __syncthreads();
+    const size_t base = C.soff[grp];
+    const size_t blk = (size_t)N * 64;
+    for (int col = warp; col < N; col += nw) {
+      const int im = col & 1, qp = col >> 1, q = qp / C.P, pl = qp % C.P;
+      if (q >= C.nq || (m == 0 && im)) {
+        for (int k = 2 * lane; k < K; k += 64)
+          put_split2(C.sh, C.sl, base + (size_t)(k >> 6) * blk + atom_off(col, k & 63), 0.f, 0.f);
+        if (lane == 0) C.sexp[grp * N + col] = 0;
+        continue;
+      }
+      const float* a = reinterpret_cast<const float*>(C.alm + pl * C.astride) + im;
+      auto kap = [&](int l) -> float { return (l >= m && l <= lmax) ? a[2 * alm_idx(lmax, l, m)] : 0.f; };
+      auto val = [&](int k) -> float {
+        const int l = m + p + 2 * k;
+        if (q == 0) return D0[k] * kap(l);
+        if (q == 1) return A1[k] * kap(l - 1) + A2[k] * kap(l + 1);
+        return D0[k] != 0.f ? kap(l) : 0.f;
+      };
+      float mx = 0.f;
+      for (int k = 2 * lane; k < K; k += 64) mx = fmaxf(mx, fmaxf(fabsf(val(k)), fabsf(val(k + 1))));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      const int x = col_exponent(mx);
+      for (int k = 2 * lane; k < K; k += 64)
+        put_split2(C.sh, C.sl, base + (size_t)(k >> 6) * blk + atom_off(col, k & 63), times_pow2f(val(k), x),
+                   times_pow2f(val(k + 1), x));
+      if (lane == 0) C.sexp[grp * N + col] = x;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core contractions: persistent, bulk-copy pipelined
+//
+// Analysis item (class, group, 128-row tile): K runs over the R rings in
+// stages of 64; A = two 8 KB table atoms (rows 0-63 and 64-127 of the tile),
+// B = the group's operand block of the stage's ring block.
+// Synthesis item (class, m, 128-ring tile): K runs over the padded rows of
+// parity 0 then parity 1; A = the two adjacent atoms of the tile's 128 rings
+// (MN-major), B = the right-hand-side block; parity p accumulates at TMEM
+// columns [p N, (p + 1) N).
+
+template <bool kSyn>
+struct GemmItem {
+  int nk, N;
+  __device__ __forceinline__ void init(const TcBatchDev& b, int4 w) {
+    const TcClass& C = b.cls[w.x];
+    if (kSyn) {
+      N = C.Ns;
+      nk = (C.pad[2 * w.y] + C.pad[2 * w.y + 1]) >> 6;
+    } else {
+      N = C.Na;
+      nk = C.R >> 6;
+    }
+  }
+};
+
+template <bool kSyn>
+__global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __restrict__ items, int nitems, int S,
+                                                 int bB, int tcols, int* d_err) {
+  extern __shared__ __align__(16) uint8_t smem_g[];
+  __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], accb, drainb;
+  __shared__ uint32_t tmem_base;
+  __shared__ volatile int abort_flag;
+  const uint32_t raw = umma::smem_u32(smem_g);
+  uint8_t* base = smem_g + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t stage_bytes = 2u * 16384u + 2u * (uint32_t)bB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(&accb, 1);
+    umma::mbar_init(&drainb, 1);
+    abort_flag = 0;
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) umma::tmem_alloc(&tmem_base, tcols);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = tmem_base;
+  uint32_t it_prod = 0, it_cons = 0, nacc = 0;
+  int last_it[kTcMaxStages];
+  for (int s = 0; s < kTcMaxStages; ++s) last_it[s] = -1;
+  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+    const int4 w = items[item];
+    const TcClass& C = b.cls[w.x];
+    GemmItem<kSyn> gi;
+    gi.init(b, w);
+    const int N = gi.N, nk = gi.nk;
+    const int RA = C.R >> 6;
+    if (threadIdx.x == 0) {
+      // producer: bulk copies of every stage of this item
+      const uint32_t bbytes = (uint32_t)N * 128u;
+      for (int k = 0; k < nk && !abort_flag; ++k, ++it_prod) {
+        const int s = (int)(it_prod % (uint32_t)S);
+        const uint32_t u = it_prod / (uint32_t)S;
+        if (u > 0 && !umma::mbar_wait(&empty[s], (u - 1) & 1u, kTcWaitPolls)) {
+          atomicCAS(d_err, 0, kDevTimeout);
+          abort_flag = 1;
+          break;
+        }
+        uint8_t* st = base + (size_t)s * stage_bytes;
+        umma::mbar_arrive_expect_tx(&full[s], 2u * 16384u + 2u * bbytes);
+        if (kSyn) {
+          const int K0 = C.pad[2 * w.y] >> 6;
+          const int p = k < K0 ? 0 : 1, t = p ? k - K0 : k;
+          const int grp = 2 * w.y + p;
+          const size_t a = ((size_t)(C.off[grp] / 64 + t) * RA + 2 * w.z) * 4096;
+          umma::bulk_g2s(st, C.th + a, 16384u, &full[s]);
+          umma::bulk_g2s(st + 16384, C.tl + a, 16384u, &full[s]);
+          const size_t bo = (size_t)C.soff[grp] + (size_t)t * N * 64;
+          umma::bulk_g2s(st + 32768, C.sh + bo, bbytes, &full[s]);
+          umma::bulk_g2s(st + 32768 + bB, C.sl + bo, bbytes, &full[s]);
+        } else {
+          const size_t rb = (size_t)((C.off[w.y] + (long long)w.z * 128) / 64);
+          const size_t a0 = (rb * RA + k) * 4096, a1 = ((rb + 1) * RA + k) * 4096;
+          umma::bulk_g2s(st, C.th + a0, 8192u, &full[s]);
+          umma::bulk_g2s(st + 8192, C.th + a1, 8192u, &full[s]);
+          umma::bulk_g2s(st + 16384, C.tl + a0, 8192u, &full[s]);
+          umma::bulk_g2s(st + 16384 + 8192, C.tl + a1, 8192u, &full[s]);
+          const size_t bo = ((size_t)w.y * RA + k) * (size_t)N * 64;
+          umma::bulk_g2s(st + 32768, C.vh + bo, bbytes, &full[s]);
+          umma::bulk_g2s(st + 32768 + bB, C.vl + bo, bbytes, &full[s]);
+        }
+        last_it[s] = (int)it_prod;
+      }
+    } else if (threadIdx.x == 32) {
+      // MMA issuer
+      const uint32_t idesc = kSyn ? umma::idesc_f16_f32_amn(128, N) : umma::idesc_f16_f32(128, N);
+      const int K0 = kSyn ? (C.pad[2 * w.y] >> 6) : nk;
+      for (int k = 0; k < nk && !abort_flag; ++k, ++it_cons) {
+        const int s = (int)(it_cons % (uint32_t)S);
+        const uint32_t u = it_cons / (uint32_t)S;
+        if (!umma::mbar_wait(&full[s], u & 1u, kTcWaitPolls)) {
+          atomicCAS(d_err, 0, kDevTimeout);
+          abort_flag = 1;
+          break;
+        }
+        umma::fence_after_sync();
+        uint8_t* st = base + (size_t)s * stage_bytes;
+        const uint32_t sa = umma::smem_u32(st), sb = umma::smem_u32(st + 32768);
+        const int p = (kSyn && k >= K0) ? 1 : 0;
+        const int t = p ? k - K0 : k;
+        const uint32_t td = tmem + (uint32_t)(p * N);
+        uint64_t dAh, dAl;
+        if (kSyn) {
+          dAh = umma::desc_sw128_mn(sa, 8192, 1024);
+          dAl = umma::desc_sw128_mn(sa + 16384, 8192, 1024);
+        } else {
+          dAh = umma::desc_sw128(sa);
+          dAl = umma::desc_sw128(sa + 16384);
+        }
+        const uint64_t dBh = umma::desc_sw128(sb), dBl = umma::desc_sw128(sb + (uint32_t)bB);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t adva = kSyn ? (uint64_t)(kk * 2048) >> 4 : (uint64_t)(kk * 32) >> 4;
+          const uint64_t advb = (uint64_t)(kk * 32) >> 4;
+          umma::mma_f16(td, dAh + adva, dBh + advb, idesc, (t | kk) != 0);
+          umma::mma_f16(td, dAh + adva, dBl + advb, idesc, 1);
+          umma::mma_f16(td, dAl + adva, dBh + advb, idesc, 1);
+        }
+        umma::commit(&empty[s]);
+      }
+      if (!abort_flag) umma::commit(&accb);
+    }
+    // accumulators complete -> epilogue by all four warps
+    if (!umma::mbar_wait(&accb, nacc & 1u, kTcWaitPolls)) {
+      if (lane == 0) atomicCAS(d_err, 0, kDevTimeout);
+      abort_flag = 1;
+    }
+    ++nacc;
+    umma::fence_after_sync();
+    __syncwarp();
+    if (!abort_flag) {
+      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      if (!kSyn) {
+        const int grp = w.y, m = grp >> 1, p = grp & 1;
+        const int k = w.z * 128 + warp * 32 + lane;
+        const int l = m + p + 2 * k;
+        const bool valid = k < C.rows[grp] && l <= C.lmax;
+        const int* ve = C.vexp + (size_t)grp * N;
+        float2* out = C.alm + alm_idx(C.lmax, l < C.lmax ? l : C.lmax, m);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          umma::tmem_ld16(trow + (uint32_t)c0, v);
+          if (valid) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+              const int pl = (c0 + i) >> 1;
+              if (pl < C.P)
+                out[pl * C.astride] = make_float2(times_pow2f(v[i], -kTabExp - ve[c0 + i]),
+                                                  times_pow2f(v[i + 1], -kTabExp - ve[c0 + i + 1]));
+            }
+          }
+        }
+      } else {
+        const int m = w.y;
+        const int i = w.z * 128 + warp * 32 + lane + 1;   // ring
+        const bool has_s = i != 2 * C.nside;
+        const int* ee = C.sexp + (size_t)(2 * m) * N;
+        const int* eo = C.sexp + (size_t)(2 * m + 1) * N;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float ve[16], vo[16];
+          umma::tmem_ld16(trow + (uint32_t)c0, ve);
+          umma::tmem_ld16(trow + (uint32_t)(N + c0), vo);
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {
+            const int qp = (c0 + c) >> 1;
+            const int q = qp / C.P, pl = qp % C.P;
+            if (q >= C.nq) continue;
+            const float er = times_pow2f(ve[c], -kTabExp - ee[c0 + c]);
+            const float ei = times_pow2f(ve[c + 1], -kTabExp - ee[c0 + c + 1]);
+            const float orr = times_pow2f(vo[c], -kTabExp - eo[c0 + c]);
+            const float oi = times_pow2f(vo[c + 1], -kTabExp - eo[c0 + c + 1]);
+            float2* Gq = C.G + pl * C.gstride + q * C.qstride + (size_t)m * C.ldf;
+            Gq[i - 1] = make_float2(er + orr, ei + oi);
+            if (has_s) Gq[4 * C.nside - i - 1] = make_float2(er - orr, ei - oi);
+          }
+        }
+      }
+    }
+    umma::fence_before_sync();
+    const int stop = __syncthreads_or(abort_flag);
+    umma::fence_after_sync();
+    if (stop) break;
+  }
+  if (abort_flag) {
+    // bounded drain: the copies and MMAs this CTA issued land before it exits
+    if (threadIdx.x == 0)
+      for (int s = 0; s < S; ++s)
+        if (last_it[s] >= 0) umma::mbar_wait(&full[s], (uint32_t)(last_it[s] / S) & 1u, kTcWaitPolls);
+    if (threadIdx.x == 32) {
+      umma::commit(&drainb);
+      umma::mbar_wait(&drainb, 0, kTcWaitPolls);
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, tcols);
+}
+
+// ---------------------------------------------------------------------------
+// host
+
+static int pow2_cols(int n) {
+  int c = 32;
+  while (c < n) c <<= 1;
+  return c;
+}
+
+static int stage_b_bytes(int nmax) { return (nmax * 128 + 1023) / 1024 * 1024; }
+
+int tc_build_items(clc_ctx* ctx, const TcBatchDev& b, const std::vector<std::shared_ptr<TcTable>>& tabs,
+                   TcItems* it) {
+  std::vector<std::pair<int, int4>> an, sy;   // (stages, item): longer items first
+  it->na_max = 16;
+  it->ns_max = 16;
+  it->fft_an_smem = it->fft_sy_smem = it->pack_s_smem = 0;
+  for (int c = 0; c < b.ncls; ++c) {
+    const TcClass& C = b.cls[c];
+    const TcTable& T = *tabs[c];
+    it->na_max = std::max(it->na_max, C.Na);
+    it->ns_max = std::max(it->ns_max, C.Ns);
+    it->fft_an_smem = std::max(it->fft_an_smem, C.mmax * (int)sizeof(float2));
+    it->fft_sy_smem = std::max(it->fft_sy_smem, (C.mmax + 2 * C.nside + 1) * (int)sizeof(float2));
+    it->pack_s_smem = std::max(it->pack_s_smem, 3 * T.h_pad[0] * (int)sizeof(float));
+    for (int m = 0; m <= C.lmax; ++m)
+      for (int p = 0; p < 2; ++p)
+        for (int t = 0; t * 128 < T.h_rows[2 * m + p]; ++t)
+          if (m + p + 2 * (t * 128) <= C.lmax) an.push_back({C.R / 64, make_int4(c, 2 * m + p, t, 0)});
+    for (int m = 0; m <= C.lmax; ++m)
+      for (int rt = 0; rt < C.R / 128; ++rt)
+        sy.push_back({(T.h_pad[2 * m] + T.h_pad[2 * m + 1]) / 64, make_int4(c, m, rt, 0)});
+  }
+  auto by_len = [](const std::pair<int, int4>& x, const std::pair<int, int4>& y) { return x.first > y.first; };
+  std::stable_sort(an.begin(), an.end(), by_len);
+  std::stable_sort(sy.begin(), sy.end(), by_len);
+  std::vector<int4> a, s;
+  for (auto& x : an) a.push_back(x.second);
+  for (auto& x : sy) s.push_back(x.second);
+  it->n_an = (int)a.size();
+  it->n_sy = (int)s.size();
+  auto upload = [&](Buffer& buf, const std::vector<int4>& v) -> int {
+    buf.bytes = sizeof(int4) * std::max<size_t>(v.size(), 1);
+    if (cudaMalloc(&buf.p, buf.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      buf.p = nullptr;
+      return set_err(ctx, CLC_ENOMEM, "work-list allocation failed");
+    }
+    return cuda_check(ctx, cudaMemcpy(buf.p, v.data(), sizeof(int4) * v.size(), cudaMemcpyHostToDevice),
+                      "work-list upload");
+  };
+  int rc = upload(it->an, a);
+  if (rc) return rc;
+  return upload(it->sy, s);
+}
+
+// persistent grid: per_sm CTAs on every SM, at most what stays resident
+template <typename K>
+static int grid_of(clc_ctx* ctx, K kern, int threads, int smem, long long items, int per_sm) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    occ = 1;
+  }
+  per_sm = std::max(1, std::min(per_sm, std::max(occ, 1)));
+  const long long g = std::min<long long>(items, (long long)num_sms(ctx) * per_sm);
+  return (int)std::max<long long>(g, 1);
+}
+
+int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcLaunch& L, int stage) {
+  switch (stage) {
+    case 0: {
+      cudaFuncSetAttribute(k_tc_ring_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, it.fft_an_smem);
+      const int g = grid_of(ctx, k_tc_ring_analysis, 256, it.fft_an_smem, b.n_ring, L.fft_ctas);
+      CLC_LAUNCH(ctx, "k_tc_ring_analysis", k_tc_ring_analysis, g, 256, it.fft_an_smem, b);
+      return launch_check(ctx, "k_tc_ring_analysis");
+    }
+    case 1: {
+      const int g = grid_of(ctx, k_tc_pack_analysis, 256, 0, b.n_pa, 8);
+      CLC_LAUNCH(ctx, "k_tc_pack_analysis", k_tc_pack_analysis, g, 256, 0, b);
+      return launch_check(ctx, "k_tc_pack_analysis");
+    }
+    case 2: {
+      const int bB = stage_b_bytes(it.na_max);
+      const int smem = 1024 + L.an_stages * (32768 + 2 * bB);
+      cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      const int tcols = pow2_cols(it.na_max);
+      const int g = grid_of(ctx, k_tc_gemm<false>, 128, smem, it.n_an, std::min(L.an_ctas, 512 / tcols));
+      CLC_LAUNCH(ctx, "k_tc_analysis", (k_tc_gemm<false>), g, 128, smem, b, (const int4*)it.an.p, it.n_an,
+                 L.an_stages, bB, tcols, ctx->d_err);
+      return launch_check(ctx, "k_tc_analysis");
+    }
+    case 3: {
+      cudaFuncSetAttribute(k_tc_pack_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, it.pack_s_smem);
+      const int g = grid_of(ctx, k_tc_pack_synthesis, 256, it.pack_s_smem, b.n_ps, 4);
+      CLC_LAUNCH(ctx, "k_tc_pack_synthesis", k_tc_pack_synthesis, g, 256, it.pack_s_smem, b);
+      return launch_check(ctx, "k_tc_pack_synthesis");
+    }
+    case 4: {
+      const int bB = stage_b_bytes(it.ns_max);
+      const int smem = 1024 + L.sy_stages * (32768 + 2 * bB);
+      cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      const int tcols = pow2_cols(2 * it.ns_max);
+      const int g = grid_of(ctx, k_tc_gemm<true>, 128, smem, it.n_sy, std::min(L.sy_ctas, 512 / tcols));
+      CLC_LAUNCH(ctx, "k_tc_synthesis", (k_tc_gemm<true>), g, 128, smem, b, (const int4*)it.sy.p, it.n_sy,
+                 L.sy_stages, bB, tcols, ctx->d_err);
+      return launch_check(ctx, "k_tc_synthesis");
+    }
+    default: {
+      cudaFuncSetAttribute(k_tc_ring_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, it.fft_sy_smem);
+      const int g = grid_of(ctx, k_tc_ring_synthesis, 256, it.fft_sy_smem, b.n_ring, L.fft_ctas);
+      CLC_LAUNCH(ctx, "k_tc_ring_synthesis", k_tc_ring_synthesis, g, 256, it.fft_sy_smem, b);
+      return launch_check(ctx, "k_tc_ring_synthesis");
+    }
+  }
+}
+
+int tc_run(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcLaunch& L) {
+  for (int s = 0; s < 6; ++s) {
+    const int rc = tc_run_stage(ctx, b, it, L, s);
+    if (rc) return rc;
   }
   return CLC_OK;
 }
 
 }  // namespace clc
-
-using namespace clc;
-
-// planes per tensor-core batch: the synthesis holds two accumulators of
-// round16(2 nq P) FP32 columns each in at most 256 TMEM columns
-int tc_planes_per_batch(bool derivs) { return derivs ? 21 : 64; }
-
-extern "C" int clc_poisson_sht_batch(clc_ctx* ctx, const double* const* kappa, int nplanes, int nside, int lmax,
-                                     int precision, double* const* psi, const clc_derivs* out) {
-  if (!ctx) return CLC_EINVAL;
-  if (!kappa || nplanes < 1 || !valid_nside(nside) || nside > 4096 || lmax < 1 || lmax > 4 * nside)
-    return set_err(ctx, CLC_EINVAL, "clc_poisson_sht_batch: bad arguments");
-  for (int i = 0; i < nplanes; ++i)
-    if (!kappa[i]) return set_err(ctx, CLC_EINVAL, "clc_poisson_sht_batch: null kappa plane");
-  if (precision != CLC_FP64 && precision != CLC_MIXED)
-    return set_err(ctx, CLC_EINVAL, "clc_poisson_sht_batch: precision must be CLC_FP64 or CLC_MIXED");
-  cudaSetDevice(ctx->device);
-  if (precision == CLC_FP64) {
-    for (int i = 0; i < nplanes; ++i) {
-      const int rc = clc_poisson_sht(ctx, kappa[i], nside, lmax, CLC_FP64, psi ? psi[i] : nullptr, out ? &out[i] : nullptr);
-      if (rc) return rc;
-    }
-    return CLC_OK;
-  }
-  if (!psi && !out) return CLC_OK;
-  const int per = tc_planes_per_batch(out != nullptr);
-  for (int i0 = 0; i0 < nplanes; i0 += per) {
-    const int P = std::min(per, nplanes - i0);
-    const int rc = poisson_sht_tc(ctx, kappa + i0, P, nside, lmax, psi ? psi + i0 : nullptr, out ? out + i0 : nullptr);
-    if (rc) return rc;
-  }
-  return CLC_OK;
-}

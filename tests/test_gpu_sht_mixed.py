@@ -137,3 +137,58 @@ def test_mixed_rejects_bad_arguments():
     with pytest.raises(clc.CalclensError) as e:
         c.poisson_sht_batch(k, 64, 128, precision=clc.FP32)
     assert e.value.code == clc.EINVAL
+
+
+def test_plan_mixed_sizes_graph_and_tuning():
+    """One plan over three (nside, lmax) classes, autotuned and replayed as a
+    CUDA graph twice with different maps; every plane checked."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    sizes = [(64, 128), (128, 256), (64, 128), (64, 100), (128, 256), (64, 100), (64, 128)]
+    plan = c.sht_plan([s[0] for s in sizes], [s[1] for s in sizes], derivatives=True, graph=True, tune=True)
+    for rep in range(2):
+        kappas = [_planes(ns, 1, seed0=1000 + 10 * rep + i)[0] for i, (ns, _) in enumerate(sizes)]
+        outs = [{k: torch.empty(hp.npix(ns), dtype=torch.float64, device="cuda") for k in FIELDS} for ns, _ in sizes]
+        plan.execute([k.cuda() for k in kappas], outs)
+        c.sync()
+        for i, (ns, L) in enumerate(sizes):
+            ref = c.poisson_sht(kappas[i].cuda(), ns, L, precision=clc.FP64)
+            c.sync()
+            for k in FIELDS:
+                assert rel_l2(outs[i][k], ref[k]) < TOL_MIXED, (rep, i, k)
+        if rep == 0:
+            want = sht.poisson_sht(kappas[3], 64, 100)
+            for k in FIELDS:
+                assert rel_l2(outs[3][k], want[k]) < TOL_MIXED, k
+    info = plan.info()
+    assert all(v > 0 for v in info["stage_ms"]) and info["device_bytes"] > 0
+    plan.close()
+
+
+def test_plan_potential_only_without_graph():
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    sizes = [(64, 128)] * 5
+    plan = c.sht_plan([s[0] for s in sizes], [s[1] for s in sizes], derivatives=False, graph=False, tune=False)
+    kappa = _planes(64, 5, seed0=77)
+    outs = [{"psi": torch.empty(hp.npix(64), dtype=torch.float64, device="cuda")} for _ in sizes]
+    plan.execute([k.cuda() for k in kappa], outs)
+    c.sync()
+    for i in (0, 4):
+        want = sht.poisson_sht(kappa[i], 64, 128)
+        assert rel_l2(outs[i]["psi"], want["psi"]) < TOL_MIXED
+    plan.close()
+
+
+def test_plan_rejects_bad_batches():
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    with pytest.raises(clc.CalclensError) as e:
+        c.sht_plan([64, 128, 256, 512, 64], [128, 128, 128, 128, 100])
+    assert e.value.code == clc.EINVAL
+    with pytest.raises(clc.CalclensError) as e:
+        c.sht_plan([32], [64])
+    assert e.value.code == clc.EINVAL
+    with pytest.raises(clc.CalclensError) as e:
+        c.sht_plan([64] * 22, [128] * 22, derivatives=True)
+    assert e.value.code == clc.EINVAL
