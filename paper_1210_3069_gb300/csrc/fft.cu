@@ -38,11 +38,11 @@ __global__ void k_bluestein_tables(int nside, PlanDevT<double> P, C2<double>* ch
     C2<double> v = cx<double>(0.0, 0.0);
     if (j < N) v = w[j];
     else if (j > M - N) v = w[M - j];
-    s[brev(j, logM)] = v;
+    s[pidx<double>(brev(j, logM))] = v;
   }
   __syncthreads();
   fft_pow2<double>(s, logM, P);
-  for (int j = threadIdx.x; j < M; j += blockDim.x) filter[c.w + j] = s[j];
+  for (int j = threadIdx.x; j < M; j += blockDim.x) filter[c.w + j] = s[pidx<double>(j)];
 }
 
 __global__ void k_round_to_float(const double2* __restrict__ in, size_t n, float2* __restrict__ out) {
@@ -61,7 +61,7 @@ template <typename T>
 __global__ void k_ring_synthesis(SynthArgsT<T> a, int nside, int lmax, int mode, int mmax_fft, PlanDevT<T> P) {
   extern __shared__ __align__(16) unsigned char smem_fft[];
   C2<T>* s = reinterpret_cast<C2<T>*>(smem_fft);
-  ring_synthesis_ring<T>(a, nside, lmax, mode, P, blockIdx.x + 1, s, s + mmax_fft);
+  ring_synthesis_ring<T>(a, nside, lmax, mode, P, blockIdx.x + 1, s, s + fft_buf_len<T>(mmax_fft));
 }
 
 template <>
@@ -141,7 +141,7 @@ std::shared_ptr<FftPlan> get_fft_plan(clc_ctx* ctx, int nside, int* rc) {
   CLC_LAUNCH(ctx, "k_twiddle", k_twiddle, 64, 256, 0, (double2*)p->twiddle.p, mmax);
   PlanDevT<double> d = plan_dev<double>(*p);
   if (nside > 1 && chirp_n > 0) {
-    const int smem = mmax * (int)sizeof(double2);
+    const int smem = fft_buf_len<double>(mmax) * (int)sizeof(double2);
     cudaFuncSetAttribute(k_bluestein_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     CLC_LAUNCH(ctx, "k_bluestein_tables", k_bluestein_tables, nside - 1, 256, smem, nside, d, (C2<double>*)p->chirp.p,
                (C2<double>*)p->filter.p);
@@ -180,7 +180,9 @@ int ring_synthesis_t(clc_ctx* ctx, const FftPlan& plan, const C2<T>* G, int ld, 
   a.G0 = G;
   a.G1 = G + qstride;
   a.G2 = G + 2 * qstride;
-  a.ld = ld;
+  a.sm = ld;
+  a.sr = 1;
+  a.quad = 0;
   for (int f = 0; f < 6; ++f) a.out[f] = out[f];
   const int smem = ring_synthesis_smem<T>(plan);
   cudaFuncSetAttribute(k_ring_synthesis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -32,14 +32,22 @@ struct PlanDevT {
 };
 
 std::shared_ptr<FftPlan> get_fft_plan(clc_ctx* ctx, int nside, int* rc);
+
+// The shared-memory FFT buffer is padded by one point per 128 bytes
+// (index i stored at i + (i >> shift)) to spread strided butterfly accesses
+// over the banks.
+template <typename T>
+__host__ __device__ constexpr int fft_pad_shift() { return sizeof(T) == 4 ? 4 : 3; }
+template <typename T>
+__host__ __device__ constexpr int fft_buf_len(int m) { return m + (m >> fft_pad_shift<T>()) + 1; }
 template <typename T>
 PlanDevT<T> plan_dev(const FftPlan& p);
 // dynamic shared memory of the ring kernels (analysis: FFT buffer; synthesis:
 // FFT buffer + N + 1 spectrum points)
 template <typename T>
-int ring_analysis_smem(const FftPlan& p) { return p.mmax_fft * (int)sizeof(C2<T>); }
+int ring_analysis_smem(const FftPlan& p) { return fft_buf_len<T>(p.mmax_fft) * (int)sizeof(C2<T>); }
 template <typename T>
-int ring_synthesis_smem(const FftPlan& p) { return (p.mmax_fft + 2 * p.nside + 1) * (int)sizeof(C2<T>); }
+int ring_synthesis_smem(const FftPlan& p) { return (fft_buf_len<T>(p.mmax_fft) + 2 * p.nside + 1) * (int)sizeof(C2<T>); }
 
 // F[m * ldf + (i - 1)] = sum_j map_j e^{-i m phi_j} over ring i, m = 0 .. lmax,
 // times `weight` (all 4 nside - 1 rings; ldf >= 4 nside - 1).

@@ -238,10 +238,12 @@ __global__ void k_tc_ring_synthesis(TcBatchDev b) {
     a.G0 = reinterpret_cast<const C2<float>*>(Gp);
     a.G1 = reinterpret_cast<const C2<float>*>(Gp + C.qstride);
     a.G2 = reinterpret_cast<const C2<float>*>(Gp + 2 * C.qstride);
-    a.ld = C.ldf;
+    a.sm = 4ll * C.ldf;
+    a.sr = 4;
+    a.quad = 1;
     double* const* o = b.out + (size_t)(C.plane0 + pl) * 6;
     for (int f = 0; f < 6; ++f) a.out[f] = o[f];
-    ring_synthesis_ring<float>(a, C.nside, C.lmax, b.mode, C.fft, i, s, s + C.mmax);
+    ring_synthesis_ring<float>(a, C.nside, C.lmax, b.mode, C.fft, i, s, s + fft_buf_len<float>(C.mmax));
   }
 }
 
@@ -559,9 +561,9 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
             const float ei = times_pow2f(ve[c + 1], -kTabExp - ee[c0 + c + 1]);
             const float orr = times_pow2f(vo[c], -kTabExp - eo[c0 + c]);
             const float oi = times_pow2f(vo[c + 1], -kTabExp - eo[c0 + c + 1]);
-            float2* Gq = C.G + pl * C.gstride + q * C.qstride + (size_t)m * C.ldf;
-            Gq[i - 1] = make_float2(er + orr, ei + oi);
-            if (has_s) Gq[4 * C.nside - i - 1] = make_float2(er - orr, ei - oi);
+            float2* Gq = C.G + pl * C.gstride + q * C.qstride + (size_t)(m >> 2) * 4 * C.ldf + (m & 3);
+            Gq[(size_t)(i - 1) * 4] = make_float2(er + orr, ei + oi);
+            if (has_s) Gq[(size_t)(4 * C.nside - i - 1) * 4] = make_float2(er - orr, ei - oi);
           }
         }
       }
@@ -608,8 +610,8 @@ int tc_build_items(clc_ctx* ctx, const TcBatchDev& b, const std::vector<std::sha
     const TcTable& T = *tabs[c];
     it->na_max = std::max(it->na_max, C.Na);
     it->ns_max = std::max(it->ns_max, C.Ns);
-    it->fft_an_smem = std::max(it->fft_an_smem, C.mmax * (int)sizeof(float2));
-    it->fft_sy_smem = std::max(it->fft_sy_smem, (C.mmax + 2 * C.nside + 1) * (int)sizeof(float2));
+    it->fft_an_smem = std::max(it->fft_an_smem, fft_buf_len<float>(C.mmax) * (int)sizeof(float2));
+    it->fft_sy_smem = std::max(it->fft_sy_smem, (fft_buf_len<float>(C.mmax) + 2 * C.nside + 1) * (int)sizeof(float2));
     it->pack_s_smem = std::max(it->pack_s_smem, 3 * T.h_pad[0] * (int)sizeof(float));
     for (int m = 0; m <= C.lmax; ++m)
       for (int p = 0; p < 2; ++p)

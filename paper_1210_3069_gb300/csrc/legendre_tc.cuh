@@ -54,8 +54,9 @@ struct TcClass {
   __half *sh, *sl;                // synthesis operand [soff[g] + t Ns 64][Ns x 64 swizzled]
   int* sexp;                      // [G][Ns]
   const long long* soff;          // [G]
-  float2* G;                      // [P][nq][lmax + 2][ldf] per-ring Legendre sums
+  float2* G;                      // [P][nq][m / 4][ring][m % 4] per-ring Legendre sums
   size_t gstride, qstride;
+  int ldm;                        // lmax + 1 rounded up to a multiple of 4
   long long ring0, pa0, ps0;      // first flat item of the class: ring FFTs, analysis pack, synthesis pack
 };
 

@@ -81,6 +81,25 @@ struct Rot<float> {
   }
 };
 
+// a / b in the arithmetic type (no FP64 division on the FP32 path)
+template <typename T>
+__device__ __forceinline__ T ratio(int a, int b) { return (T)a / (T)b; }
+
+// padded position of FFT point i in shared memory
+template <typename T>
+__device__ __forceinline__ int pidx(int i) { return i + (i >> fft_pad_shift<T>()); }
+
+// FP32 -> FP64 by moving the bits (exact for normal floats; zero and
+// subnormal floats give zero): keeps the output conversion off the FP64 pipe
+__device__ __forceinline__ double to_out(double v) { return v; }
+__device__ __forceinline__ double to_out(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
+
 __device__ __forceinline__ int brev(int j, int logM) { return logM == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logM)); }
 __device__ __forceinline__ bool is_pow2(int v) { return (v & (v - 1)) == 0; }
 
@@ -92,9 +111,9 @@ __device__ void fft_pow2(C2<T>* s, int logM, const PlanDevT<T>& P) {
   int lg = 1;
   if (logM & 1) {
     for (int t = threadIdx.x; t < M / 2; t += blockDim.x) {
-      const C2<T> u = s[2 * t], v = s[2 * t + 1];
-      s[2 * t] = u + v;
-      s[2 * t + 1] = u - v;
+      const C2<T> u = s[pidx<T>(2 * t)], v = s[pidx<T>(2 * t + 1)];
+      s[pidx<T>(2 * t)] = u + v;
+      s[pidx<T>(2 * t + 1)] = u - v;
     }
     __syncthreads();
     lg = 2;
@@ -106,32 +125,33 @@ __device__ void fft_pow2(C2<T>* s, int logM, const PlanDevT<T>& P) {
     for (int t = threadIdx.x; t < M / 4; t += blockDim.x) {
       const int p = t & (h - 1);
       const int i0 = ((t >> (lg - 1)) << (lg + 1)) + p;
-      const C2<T> a0 = s[i0], a1 = s[i0 + h], a2 = s[i0 + 2 * h], a3 = s[i0 + 3 * h];
+      const int j0 = pidx<T>(i0), j1 = pidx<T>(i0 + h), j2 = pidx<T>(i0 + 2 * h), j3 = pidx<T>(i0 + 3 * h);
+      const C2<T> a0 = s[j0], a1 = s[j1], a2 = s[j2], a3 = s[j3];
       const C2<T> w1 = P.tw[p << sh1], w2 = P.tw[p << sh2];
       C2<T> v = a1 * w1;
       const C2<T> b0 = a0 + v, b1 = a0 - v;
       v = a3 * w1;
       const C2<T> b2 = a2 + v, b3 = a2 - v;
       v = b2 * w2;
-      s[i0] = b0 + v;
-      s[i0 + 2 * h] = b0 - v;
+      s[j0] = b0 + v;
+      s[j2] = b0 - v;
       v = b3 * w2;
       v = cx<T>(v.y, -v.x);  // times W_{4h}^h = -i
-      s[i0 + h] = b1 + v;
-      s[i0 + 3 * h] = b1 - v;
+      s[j1] = b1 + v;
+      s[j3] = b1 - v;
     }
     __syncthreads();
   }
 }
 
 // Forward DFT of N points whose value at j is load(j); Z_k (natural order) is
-// left in s[0..N).  load is called by each thread for its j = threadIdx.x,
+// left in s[pidx(0..N)).  load is called by each thread for its j = threadIdx.x,
 // threadIdx.x + blockDim.x, ... < N, in increasing order.
 template <typename T, typename Load>
 __device__ void dft_any(C2<T>* s, int N, int ring_class, const PlanDevT<T>& P, Load load) {
   if (is_pow2(N)) {
     const int logN = 31 - __clz(N);
-    for (int j = threadIdx.x; j < N; j += blockDim.x) s[brev(j, logN)] = load(j);
+    for (int j = threadIdx.x; j < N; j += blockDim.x) s[pidx<T>(brev(j, logN))] = load(j);
     __syncthreads();
     fft_pow2<T>(s, logN, P);
     return;
@@ -140,23 +160,24 @@ __device__ void dft_any(C2<T>* s, int N, int ring_class, const PlanDevT<T>& P, L
   const int M = c.x, logM = c.y;
   const C2<T>* w = P.chirp + c.z;
   const C2<T>* B = P.filter + c.w;
-  for (int j = threadIdx.x; j < M; j += blockDim.x) s[brev(j, logM)] = (j < N) ? load(j) * conj(w[j]) : cx<T>(0, 0);
+  for (int j = threadIdx.x; j < M; j += blockDim.x)
+    s[pidx<T>(brev(j, logM))] = (j < N) ? load(j) * conj(w[j]) : cx<T>(0, 0);
   __syncthreads();
   fft_pow2<T>(s, logM, P);
-  for (int k = threadIdx.x; k < M; k += blockDim.x) s[k] = conj(s[k] * B[k]);
+  for (int k = threadIdx.x; k < M; k += blockDim.x) s[pidx<T>(k)] = conj(s[pidx<T>(k)] * B[k]);
   __syncthreads();
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     const int kr = brev(k, logM);
     if (k < kr) {
-      const C2<T> t = s[k];
-      s[k] = s[kr];
-      s[kr] = t;
+      const C2<T> t = s[pidx<T>(k)];
+      s[pidx<T>(k)] = s[pidx<T>(kr)];
+      s[pidx<T>(kr)] = t;
     }
   }
   __syncthreads();
   fft_pow2<T>(s, logM, P);
   const T invM = (T)(1.0 / (double)M);
-  for (int k = threadIdx.x; k < N; k += blockDim.x) s[k] = (conj(s[k]) * invM) * conj(w[k]);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) s[pidx<T>(k)] = (conj(s[pidx<T>(k)]) * invM) * conj(w[k]);
   __syncthreads();
 }
 
@@ -179,25 +200,29 @@ __device__ void ring_analysis_ring(const double* __restrict__ map, int nside, in
     const int k = m % n;
     const bool cj = k > N;
     const int kk = cj ? n - k : k;
-    const C2<T> Zk = s[kk % N];
-    const C2<T> Zn = conj(s[(N - kk) % N]);
+    const C2<T> Zk = s[pidx<T>(kk % N)];
+    const C2<T> Zn = conj(s[pidx<T>((N - kk) % N)]);
     const C2<T> A = (Zk + Zn) * half;
     const C2<T> Bv = (Zk - Zn) * half;
-    const C2<T> tB = conj(expi_pi<T>((T)(2.0 * (double)kk / (double)n))) * Bv;   // e^{-2 pi i kk / n} Bv
+    const C2<T> tB = conj(expi_pi<T>(ratio<T>(2 * kk, n))) * Bv;                   // e^{-2 pi i kk / n} Bv
     C2<T> X = cx<T>(A.x + tB.y, A.y - tB.x);                                      // A - i tB
     if (cj) X = conj(X);
-    if (shifted) X = X * conj(expi_pi<T>((T)((double)(m % (2 * n)) / (double)n)));  // e^{-i m phi0}
+    if (shifted) X = X * conj(expi_pi<T>(ratio<T>(m % (2 * n), n)));                // e^{-i m phi0}
     F[(size_t)m * ldf + (i - 1)] = X * w;
   }
   __syncthreads();
 }
 
+// Legendre sums G_q of one plane: element (m, ring) at m * sm + ring * sr,
+// or, with quad set, in groups of four orders per ring:
+// ((m / 4) * sm + ring * 4 + m % 4)
 template <typename T>
 struct SynthArgsT {
   const C2<T>* G0;
   const C2<T>* G1;
   const C2<T>* G2;
-  int ld;
+  long long sm, sr;
+  int quad;
   double* out[6];
 };
 
@@ -206,7 +231,8 @@ struct SynthArgsT {
 // c = cos t).
 template <typename T>
 __device__ __forceinline__ C2<T> spec_of(const SynthArgsT<T>& a, int mode, int f, int m, int ring0, T is, T is2, T c) {
-  const size_t idx = (size_t)m * a.ld + ring0;
+  const size_t idx = a.quad ? (size_t)(m >> 2) * a.sm + (size_t)ring0 * 4 + (m & 3)
+                            : (size_t)m * a.sm + (size_t)ring0 * a.sr;
   const C2<T> g0 = a.G0[idx];
   if (mode == 0 || f == 0) return g0;
   const C2<T> g1 = a.G1[idx];
@@ -227,7 +253,7 @@ __device__ __forceinline__ C2<T> spec_of(const SynthArgsT<T>& a, int mode, int f
 }
 
 // Real ring values of every requested output field of ring i.  s: FFT
-// buffer (plan mmax points), Xs: N + 1 points.
+// buffer (fft_buf_len(plan mmax) points), Xs: N + 1 points.
 template <typename T>
 __device__ void ring_synthesis_ring(const SynthArgsT<T>& a, int nside, int lmax, int mode, const PlanDevT<T>& P,
                                     int i, C2<T>* s, C2<T>* Xs) {
@@ -274,8 +300,9 @@ __device__ void ring_synthesis_ring(const SynthArgsT<T>& a, int nside, int lmax,
     });
     double* x = out + r.first;
     for (int j = threadIdx.x; j < N; j += blockDim.x) {
-      x[2 * j] = (double)s[j].x;
-      x[2 * j + 1] = (double)s[j].y;
+      const C2<T> v = s[pidx<T>(j)];
+      x[2 * j] = to_out(v.x);
+      x[2 * j + 1] = to_out(v.y);
     }
     __syncthreads();
   }

@@ -121,7 +121,8 @@ static int tc_batch_build(clc_ctx* ctx, int nplanes, const int* nside, const int
     C.ldf = 4 * ns - 1;
     C.fstride = (size_t)C.ldf * (L + 1);
     C.astride = (size_t)(L + 1) * (L + 2) / 2;
-    C.qstride = (size_t)C.ldf * (L + 2);
+    C.ldm = (L + 1 + 3) / 4 * 4;
+    C.qstride = (size_t)C.ldf * C.ldm;
     C.gstride = (size_t)nq * C.qstride;
     C.ring0 = ring0;
     C.pa0 = pa0;
