@@ -49,6 +49,15 @@ WORKLOADS = {
                                  ncell=256, tol=1e-10, nu1=2, nu2=2, max_cycles=60, seed=1210002),
 }
 
+# batches of pure-SHT plane solves of mixed size (mixed precision, one plan:
+# persistent launches over every plane, CUDA graph, autotuned launch shapes)
+BATCH_WORKLOADS = {
+    "sht_batch_mixed_sizes": dict(sizes=[(512, 1024)] * 32 + [(1024, 2048)] * 24 + [(2048, 4096)] * 8,
+                                  seed=1210004, fp64_sample=2),
+    "sht_batch_small": dict(sizes=[(128, 256)] * 8 + [(256, 512)] * 4, seed=1210004, fp64_sample=2),
+}
+BATCH_METRIC = "lens planes/s (batched mixed-precision SHT Poisson, Nside 512/1024/2048, lmax = 2 Nside)"
+
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 KERNELS = ("k_smooth", "k_restrict", "k_coarse_rhs", "k_prolong", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
@@ -255,6 +264,149 @@ def run_gpu(args, cfg, rank, world):
                 npix=npix, h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
 
 
+def batch_maps(ctx, sizes, seed, dev):
+    """Seeded lognormal density-contrast maps (unit-variance lognormal of a
+    C_l ~ l^-2 Gaussian field) at the RING pixel centres of every plane."""
+    import paper_1210_3069_gb300 as clc
+    centres, maps = {}, []
+    for i, (ns, _) in enumerate(sizes):
+        if ns not in centres:
+            rays = ctx.rays(12 * ns * ns)
+            ctx.rays_init_pixels(rays, ns, 1.0, 0)
+            torch.cuda.synchronize()
+            n = rays.x
+            centres[ns] = (n[2].clone(), torch.remainder(torch.atan2(n[1], n[0]), 2 * math.pi))
+            del rays, n
+        z, phi = centres[ns]
+        modes = synthetic.random_field_modes(256, 2.0, 2.0 * ns, seed + i, device=dev)
+        maps.append(synthetic.lognormal_density(z, phi, modes).double() - 1.0)
+    del clc
+    return maps
+
+
+def run_batch(args, wl):
+    """Throughput of one mixed-size batch plan (all planes per step) and of
+    the FP64 per-plane path on a sample of the same planes."""
+    import paper_1210_3069_gb300 as clc
+    clc.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(0)
+    sizes = wl["sizes"]
+    P = len(sizes)
+    maps = batch_maps(ctx, sizes, wl["seed"], dev)
+    names = ("psi", "a_th", "a_ph", "u_tt", "u_pp", "u_tp")
+    outs = [{k: torch.empty(12 * ns * ns, dtype=torch.float64, device=dev) for k in names} for ns, _ in sizes]
+    t0 = time.perf_counter()
+    plan = ctx.sht_plan([a for a, _ in sizes], [b for _, b in sizes], derivatives=True, graph=True, tune=True)
+    plan.execute(maps, outs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = plan.info()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.execute(maps, outs)
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.execute(maps, outs)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    ctx.profile(False)
+    # end to end: pinned host maps in, potentials out, through the plan
+    host_in = [m.cpu().pin_memory() for m in maps]
+    host_psi = [torch.empty(m.numel(), dtype=torch.float64).pin_memory() for m in maps]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, min(args.steps, 2))):
+        for d, h in zip(maps, host_in):
+            d.copy_(h, non_blocking=True)
+        plan.execute(maps, outs)
+        for h, o in zip(host_psi, outs):
+            h.copy_(o["psi"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / max(1, min(args.steps, 2))
+    h2d = sum(m.numel() * 8 for m in maps)
+    # FP64 per-plane path on a sample of each size (its lambda table must fit)
+    plan.close()
+    ctx.release_caches()
+    fp64 = {}
+    errs = []
+    for ns, L in sorted(set(sizes)):
+        idx = [i for i, s in enumerate(sizes) if s == (ns, L)][:wl["fp64_sample"]]
+        try:
+            for i in idx:
+                ref = ctx.poisson_sht(maps[i], ns, L, precision=clc.FP64)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                ref = ctx.poisson_sht(maps[i], ns, L, precision=clc.FP64)
+                torch.cuda.synchronize()
+                fp64.setdefault(f"{ns}/{L}", []).append((time.perf_counter() - t0) * 1e3)
+                e = {k: float(torch.linalg.vector_norm(outs[i][k] - ref[k]) / torch.linalg.vector_norm(ref[k]))
+                     for k in names}
+                errs.append({"plane": i, "nside": ns, "lmax": L, "rel_l2_vs_fp64": e})
+                del ref
+        except clc.CalclensError as exc:
+            fp64[f"{ns}/{L}"] = f"not run: {str(exc)[:120]}"
+        ctx.release_caches()
+    fp64_ms = {k: (sum(v) / len(v) if isinstance(v, list) else v) for k, v in fp64.items()}
+    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, clocks=clocks.summary(), P=P, info=info,
+                setup_s=setup_s, fp64_ms_per_plane=fp64_ms, errors=errs, h2d=h2d, d2h=h2d)
+
+
+def batch_line(args, wl, r):
+    peaks, peak_kind = load_peaks()
+    sizes = wl["sizes"]
+    value = r["P"] * args.steps / (r["ms"] / 1000.0)
+    fp64 = r["fp64_ms_per_plane"]
+    fp64_total = 0.0
+    fp64_ok = True
+    for ns, L in sizes:
+        v = fp64.get(f"{ns}/{L}")
+        if isinstance(v, float):
+            fp64_total += v
+        else:
+            fp64_ok = False
+    # tensor-core analysis: algorithmic bytes = FP16 hi + lo table + packed operands read + alm written
+    stage = r["info"]["stage_ms"]
+    tab_bytes = 0
+    for ns, L in sorted(set(sizes)):
+        rows = sum(((L + 1 - m - p) // 2 + 1 + 63) // 64 * 64 for m in range(L + 1) for p in (0, 1)
+                   if m + p <= L + 1)
+        tab_bytes += 2 * 2 * rows * 2 * ns
+    ach = tab_bytes / (stage[2] / 1e3) / 1e9
+    pk = peaks.get("hbm_gbs", 6800.0)
+    return {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16x3+f32 (Legendre), f32 (FFT), f64 (tables)", "data": "synthetic",
+        "config": {"workload": args.workload, "planes": r["P"],
+                   "sizes": {f"{a}/{b}": sizes.count((a, b)) for a, b in sorted(set(sizes))},
+                   "outputs": "psi, alpha, U at every pixel", "l2": "inputs larger than L2 (no flush)"},
+        "plan": {"launch_shape": r["info"]["shape"], "tuned_stage_ms": [round(x, 3) for x in stage],
+                 "device_bytes": r["info"]["device_bytes"], "setup_s": round(r["setup_s"], 2)},
+        "fp64_gpu_ms_per_plane": fp64,
+        "fp64_gpu_planes_per_s": (len(sizes) / (fp64_total / 1e3)) if fp64_ok and fp64_total > 0 else None,
+        "errors_vs_fp64": r["errors"],
+        "roofline": {"kernel": "k_tc_analysis", "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                     "frac": ach / pk, "traffic": None,
+                     "peak_source": f"HBM copy, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+        "e2e": {"value": r["P"] / (r["e2e_ms"] / 1000.0), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+    }
+
+
 # ---------------------------------------------------------------------------
 # the FP64 oracle on a bounded sample of the same workload
 
@@ -339,9 +491,18 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
                     help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
-    ap.add_argument("--workload", default="shtmg_plane_nside2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="shtmg_plane_nside2048", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload in BATCH_WORKLOADS:
+        if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": args.impl, "metric": BATCH_METRIC,
+                                  "unavailable": "the batch workload runs on one GPU, mixed precision only"}))
+            return
+        wl = BATCH_WORKLOADS[args.workload]
+        print(json.dumps(batch_line(args, wl, run_batch(args, wl))))
+        return
     cfg = WORKLOADS[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

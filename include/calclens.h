@@ -163,8 +163,9 @@ int clc_poisson_sht_batch(clc_ctx* ctx, const double* const* kappa, int nplanes,
 
 /* A reusable plan for a fixed batch of pure-SHT plane solves of mixed sizes
  * (paper Sec. 3.2; mixed precision only): nplanes planes, plane i of
- * (nside[i], lmax[i]) with 64 <= nside <= 4096 and lmax <= 4 nside, at most 4
- * distinct (nside, lmax) and at most 64 planes (21 with derivatives) of each.
+ * (nside[i], lmax[i]) with 64 <= nside <= 4096 and lmax <= 4 nside, grouped
+ * into at most 8 classes of equal (nside, lmax) holding at most 64 planes
+ * (21 with derivatives) each.
  * Every plane of the batch goes through six persistent launches (ring FFTs,
  * operand packing, tensor-core analysis, packing, tensor-core synthesis, ring
  * FFTs) whose work lists span all sizes.  flags: CLC_PLAN_GRAPH captures the

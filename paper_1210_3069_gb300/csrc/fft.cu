@@ -183,6 +183,9 @@ int ring_synthesis_t(clc_ctx* ctx, const FftPlan& plan, const C2<T>* G, int ld, 
   a.sm = ld;
   a.sr = 1;
   a.quad = 0;
+  a.P01 = nullptr;
+  a.p01q = a.p01m = 0;
+  a.ncap = a.nring = 0;
   for (int f = 0; f < 6; ++f) a.out[f] = out[f];
   const int smem = ring_synthesis_smem<T>(plan);
   cudaFuncSetAttribute(k_ring_synthesis<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

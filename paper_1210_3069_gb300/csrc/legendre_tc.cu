@@ -241,9 +241,92 @@ __global__ void k_tc_ring_synthesis(TcBatchDev b) {
     a.sm = 4ll * C.ldf;
     a.sr = 4;
     a.quad = 1;
+    a.P01 = b.mode ? reinterpret_cast<const C2<double>*>(C.G01 + (size_t)pl * C.nq * 2 * C.ldf) : nullptr;
+    a.p01q = 2ll * C.ldf;
+    a.p01m = C.ldf;
+    a.ncap = C.ncap;
+    a.nring = C.ldf;
     double* const* o = b.out + (size_t)(C.plane0 + pl) * 6;
     for (int f = 0; f < 6; ++f) a.out[f] = o[f];
     ring_synthesis_ring<float>(a, C.nside, C.lmax, b.mode, C.fft, i, s, s + fft_buf_len<float>(C.mmax));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 Legendre sums of the orders m = 0, 1 (derivative mode).  At the rings
+// next to the poles the Hessian terms of these two orders are differences of
+// 1/sin^2(theta)-sized parts, so the synthesis takes them from these sums
+// instead of the tensor-core ones (the FP32 rounding of the latter would be
+// amplified by up to Nside^2).  Only the ncap rings next to each pole
+// (sin theta < 0.29) need them.  One thread per (plane, northern cap ring,
+// which also gives its southern mirror); the unscaled recurrence is safe for
+// m <= 1.
+
+__global__ void k_tc_low_orders(TcBatchDev b) {
+  for (long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x; it < b.n_low;
+       it += (long long)gridDim.x * blockDim.x) {
+    const TcClass& C = b.cls[find_class(b, it, &TcClass::low0)];
+    const long long loc = it - C.low0;
+    const int ns = C.nside, L = C.lmax;
+    const int pl = (int)(loc / C.ncap), i = (int)(loc % C.ncap) + 1;
+    const Ring g = ring_geom(ns, i);
+    const double z = g.z;
+    const bool has_s = i != 2 * ns;
+    const float2* a = C.alm + pl * C.astride;
+    double2* out = C.G01 + (size_t)pl * C.nq * 2 * C.ldf;
+    for (int m = 0; m <= 1; ++m) {
+      const double* co = C.co01 + (size_t)m * (L + 3) * 4;
+      auto kap = [&](int l) -> double2 {
+        if (l < m || l > L || l < 1) return make_double2(0.0, 0.0);
+        const float2 v = a[alm_idx(L, l, m)];
+        return make_double2((double)v.x, m ? (double)v.y : 0.0);
+      };
+      auto psi = [&](int l) -> double2 {
+        const double2 k = kap(l);
+        const double d = (l >= 1 && l <= L) ? co[4 * l + 3] : 0.0;
+        return make_double2(k.x * d, k.y * d);
+      };
+      double2 n0 = make_double2(0, 0), n1 = n0, n2 = n0, s0 = n0, s1 = n0, s2 = n0;
+      double p2 = m == 0 ? 0.28209479177387814347 : -0.34549414947133547927 * g.s;   // lambda_mm
+      double p1 = 0.0;
+      double2 pm1 = psi(m - 1), p0 = psi(m), pp1 = psi(m + 1);
+      for (int l = m; l <= L + 1; ++l) {
+        double lam;
+        if (l == m) {
+          lam = p2;
+        } else if (l == m + 1) {
+          p1 = sqrt(2.0 * m + 3.0) * z * p2;
+          lam = p1;
+        } else {
+          lam = co[4 * l] * (z * p1 - co[4 * l + 1] * p2);
+          p2 = p1;
+          p1 = lam;
+        }
+        const double c1 = (l - 1.0) * co[4 * l + 2], c2 = (l + 2.0) * co[4 * (l + 1) + 2];
+        const double2 bl = make_double2(c1 * pm1.x - c2 * pp1.x, c1 * pm1.y - c2 * pp1.y);
+        const double2 kb = (l >= 1 && l <= L) ? kap(l) : make_double2(0.0, 0.0);
+        const double sg = ((l + m) & 1) ? -1.0 : 1.0;
+        n0.x += p0.x * lam; n0.y += p0.y * lam;
+        n1.x += bl.x * lam; n1.y += bl.y * lam;
+        n2.x += kb.x * lam; n2.y += kb.y * lam;
+        s0.x += sg * p0.x * lam; s0.y += sg * p0.y * lam;
+        s1.x += sg * bl.x * lam; s1.y += sg * bl.y * lam;
+        s2.x += sg * kb.x * lam; s2.y += sg * kb.y * lam;
+        pm1 = p0;
+        p0 = pp1;
+        pp1 = psi(l + 2);
+      }
+      const size_t q = 2 * (size_t)C.ldf, mo = (size_t)m * C.ldf;
+      out[mo + i - 1] = n0;
+      out[q + mo + i - 1] = n1;
+      out[2 * q + mo + i - 1] = n2;
+      if (has_s) {
+        const size_t j = 4 * ns - i - 1;
+        out[mo + j] = s0;
+        out[q + mo + j] = s1;
+        out[2 * q + mo + j] = s2;
+      }
+    }
   }
 }
 
@@ -376,36 +459,57 @@ __global__ void k_tc_pack_synthesis(TcBatchDev b) {
 }
 
 // ---------------------------------------------------------------------------
-// tensor-core contractions: persistent, bulk-copy pipelined
+// tensor-core contractions: persistent, warp-specialised, bulk-copy pipelined
 //
 // Analysis item (class, group, 128-row tile): K runs over the R rings in
 // stages of 64; A = two 8 KB table atoms (rows 0-63 and 64-127 of the tile),
 // B = the group's operand block of the stage's ring block.
 // Synthesis item (class, m, 128-ring tile): K runs over the padded rows of
 // parity 0 then parity 1; A = the two adjacent atoms of the tile's 128 rings
-// (MN-major), B = the right-hand-side block; parity p accumulates at TMEM
-// columns [p N, (p + 1) N).
+// (MN-major), B = the right-hand-side block.
+//
+// The tensor cores add each MMA into the FP32 accumulator with truncation,
+// an error that grows with the number of accumulation steps.  So the MMAs
+// accumulate in TMEM only over a chunk of kFlush stages; the four epilogue
+// warps then add the chunk into a running sum held in a second TMEM region
+// with round-to-nearest FP32 adds, and release the chunk accumulator.
+// Warps 0-3: epilogue (TMEM lanes 32w..32w+31), warp 4: bulk-copy producer,
+// warp 5: MMA issuer.  TMEM columns: chunk [0, W), sum [W, 2W), W = N
+// (analysis) or 2N (synthesis, parity p at p N).
+
+constexpr int kFlush = 2;   // pipeline stages per TMEM accumulation chunk
 
 template <bool kSyn>
 struct GemmItem {
-  int nk, N;
+  int nk, N, K0, nch0, nch;   // stages, columns, parity-0 stages, parity-0 chunks, chunks
   __device__ __forceinline__ void init(const TcBatchDev& b, int4 w) {
     const TcClass& C = b.cls[w.x];
     if (kSyn) {
       N = C.Ns;
-      nk = (C.pad[2 * w.y] + C.pad[2 * w.y + 1]) >> 6;
+      K0 = C.pad[2 * w.y] >> 6;
+      const int K1 = C.pad[2 * w.y + 1] >> 6;
+      nk = K0 + K1;
+      nch0 = (K0 + kFlush - 1) / kFlush;
+      nch = nch0 + (K1 + kFlush - 1) / kFlush;
     } else {
       N = C.Na;
-      nk = C.R >> 6;
+      nk = K0 = C.R >> 6;
+      nch0 = nch = (nk + kFlush - 1) / kFlush;
     }
+  }
+  // chunk of stage k, and whether k starts / ends its chunk
+  __device__ __forceinline__ int chunk(int k) const { return k < K0 ? k / kFlush : nch0 + (k - K0) / kFlush; }
+  __device__ __forceinline__ bool starts(int k) const { return k < K0 ? k % kFlush == 0 : (k - K0) % kFlush == 0; }
+  __device__ __forceinline__ bool ends(int k) const {
+    return k + 1 == nk || k + 1 == K0 || (k < K0 ? (k + 1) % kFlush == 0 : (k + 1 - K0) % kFlush == 0);
   }
 };
 
 template <bool kSyn>
-__global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __restrict__ items, int nitems, int S,
+__global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __restrict__ items, int nitems, int S,
                                                  int bB, int tcols, int* d_err) {
   extern __shared__ __align__(16) uint8_t smem_g[];
-  __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], accb, drainb;
+  __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], chunkb, freeb, drainb;
   __shared__ uint32_t tmem_base;
   __shared__ volatile int abort_flag;
   const uint32_t raw = umma::smem_u32(smem_g);
@@ -417,7 +521,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
       umma::mbar_init(&full[s], 1);
       umma::mbar_init(&empty[s], 1);
     }
-    umma::mbar_init(&accb, 1);
+    umma::mbar_init(&chunkb, 1);
+    umma::mbar_init(&freeb, 128);
     umma::mbar_init(&drainb, 1);
     abort_flag = 0;
     umma::fence_mbar_init();
@@ -427,101 +532,155 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tmem = tmem_base;
-  uint32_t it_prod = 0, it_cons = 0, nacc = 0;
-  int last_it[kTcMaxStages];
-  for (int s = 0; s < kTcMaxStages; ++s) last_it[s] = -1;
-  for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
-    const int4 w = items[item];
-    const TcClass& C = b.cls[w.x];
-    GemmItem<kSyn> gi;
-    gi.init(b, w);
-    const int N = gi.N, nk = gi.nk;
-    const int RA = C.R >> 6;
-    if (threadIdx.x == 0) {
-      // producer: bulk copies of every stage of this item
-      const uint32_t bbytes = (uint32_t)N * 128u;
-      for (int k = 0; k < nk && !abort_flag; ++k, ++it_prod) {
-        const int s = (int)(it_prod % (uint32_t)S);
-        const uint32_t u = it_prod / (uint32_t)S;
-        if (u > 0 && !umma::mbar_wait(&empty[s], (u - 1) & 1u, kTcWaitPolls)) {
-          atomicCAS(d_err, 0, kDevTimeout);
-          abort_flag = 1;
-          break;
+  auto fail = [&]() {
+    atomicCAS(d_err, 0, kDevTimeout);
+    abort_flag = 1;
+  };
+
+  if (warp == 4) {
+    // ---- producer: bulk copies of every stage of every item
+    if (lane == 0) {
+      uint32_t it = 0;
+      int last_it[kTcMaxStages];
+      for (int s = 0; s < kTcMaxStages; ++s) last_it[s] = -1;
+      for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+        const int4 w = items[item];
+        const TcClass& C = b.cls[w.x];
+        GemmItem<kSyn> gi;
+        gi.init(b, w);
+        const int RA = C.R >> 6;
+        const uint32_t bbytes = (uint32_t)gi.N * 128u;
+        for (int k = 0; k < gi.nk; ++k, ++it) {
+          const int s = (int)(it % (uint32_t)S);
+          const uint32_t u = it / (uint32_t)S;
+          if (u > 0 && !umma::mbar_wait(&empty[s], (u - 1) & 1u, kTcWaitPolls)) {
+            fail();
+            break;
+          }
+          uint8_t* st = base + (size_t)s * stage_bytes;
+          umma::mbar_arrive_expect_tx(&full[s], 2u * 16384u + 2u * bbytes);
+          if (kSyn) {
+            const int p = k < gi.K0 ? 0 : 1, t = p ? k - gi.K0 : k;
+            const int grp = 2 * w.y + p;
+            const size_t a = ((size_t)(C.off[grp] / 64 + t) * RA + 2 * w.z) * 4096;
+            umma::bulk_g2s(st, C.th + a, 16384u, &full[s]);
+            umma::bulk_g2s(st + 16384, C.tl + a, 16384u, &full[s]);
+            const size_t bo = (size_t)C.soff[grp] + (size_t)t * gi.N * 64;
+            umma::bulk_g2s(st + 32768, C.sh + bo, bbytes, &full[s]);
+            umma::bulk_g2s(st + 32768 + bB, C.sl + bo, bbytes, &full[s]);
+          } else {
+            const size_t rb = (size_t)((C.off[w.y] + (long long)w.z * 128) / 64);
+            const size_t a0 = (rb * RA + k) * 4096, a1 = ((rb + 1) * RA + k) * 4096;
+            umma::bulk_g2s(st, C.th + a0, 8192u, &full[s]);
+            umma::bulk_g2s(st + 8192, C.th + a1, 8192u, &full[s]);
+            umma::bulk_g2s(st + 16384, C.tl + a0, 8192u, &full[s]);
+            umma::bulk_g2s(st + 16384 + 8192, C.tl + a1, 8192u, &full[s]);
+            const size_t bo = ((size_t)w.y * RA + k) * (size_t)gi.N * 64;
+            umma::bulk_g2s(st + 32768, C.vh + bo, bbytes, &full[s]);
+            umma::bulk_g2s(st + 32768 + bB, C.vl + bo, bbytes, &full[s]);
+          }
+          last_it[s] = (int)it;
         }
-        uint8_t* st = base + (size_t)s * stage_bytes;
-        umma::mbar_arrive_expect_tx(&full[s], 2u * 16384u + 2u * bbytes);
-        if (kSyn) {
-          const int K0 = C.pad[2 * w.y] >> 6;
-          const int p = k < K0 ? 0 : 1, t = p ? k - K0 : k;
-          const int grp = 2 * w.y + p;
-          const size_t a = ((size_t)(C.off[grp] / 64 + t) * RA + 2 * w.z) * 4096;
-          umma::bulk_g2s(st, C.th + a, 16384u, &full[s]);
-          umma::bulk_g2s(st + 16384, C.tl + a, 16384u, &full[s]);
-          const size_t bo = (size_t)C.soff[grp] + (size_t)t * N * 64;
-          umma::bulk_g2s(st + 32768, C.sh + bo, bbytes, &full[s]);
-          umma::bulk_g2s(st + 32768 + bB, C.sl + bo, bbytes, &full[s]);
-        } else {
-          const size_t rb = (size_t)((C.off[w.y] + (long long)w.z * 128) / 64);
-          const size_t a0 = (rb * RA + k) * 4096, a1 = ((rb + 1) * RA + k) * 4096;
-          umma::bulk_g2s(st, C.th + a0, 8192u, &full[s]);
-          umma::bulk_g2s(st + 8192, C.th + a1, 8192u, &full[s]);
-          umma::bulk_g2s(st + 16384, C.tl + a0, 8192u, &full[s]);
-          umma::bulk_g2s(st + 16384 + 8192, C.tl + a1, 8192u, &full[s]);
-          const size_t bo = ((size_t)w.y * RA + k) * (size_t)N * 64;
-          umma::bulk_g2s(st + 32768, C.vh + bo, bbytes, &full[s]);
-          umma::bulk_g2s(st + 32768 + bB, C.vl + bo, bbytes, &full[s]);
-        }
-        last_it[s] = (int)it_prod;
       }
-    } else if (threadIdx.x == 32) {
-      // MMA issuer
-      const uint32_t idesc = kSyn ? umma::idesc_f16_f32_amn(128, N) : umma::idesc_f16_f32(128, N);
-      const int K0 = kSyn ? (C.pad[2 * w.y] >> 6) : nk;
-      for (int k = 0; k < nk && !abort_flag; ++k, ++it_cons) {
-        const int s = (int)(it_cons % (uint32_t)S);
-        const uint32_t u = it_cons / (uint32_t)S;
-        if (!umma::mbar_wait(&full[s], u & 1u, kTcWaitPolls)) {
-          atomicCAS(d_err, 0, kDevTimeout);
-          abort_flag = 1;
+      if (abort_flag)
+        for (int s = 0; s < S; ++s)   // bounded drain of the copies in flight
+          if (last_it[s] >= 0) umma::mbar_wait(&full[s], (uint32_t)(last_it[s] / S) & 1u, kTcWaitPolls);
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer
+    if (lane == 0) {
+      uint32_t it = 0, nchunk = 0;
+      for (int item = blockIdx.x; item < nitems && !abort_flag; item += gridDim.x) {
+        const int4 w = items[item];
+        GemmItem<kSyn> gi;
+        gi.init(b, w);
+        const int N = gi.N;
+        const uint32_t idesc = kSyn ? umma::idesc_f16_f32_amn(128, N) : umma::idesc_f16_f32(128, N);
+        for (int k = 0; k < gi.nk && !abort_flag; ++k, ++it) {
+          const bool first = gi.starts(k);
+          if (first && nchunk > 0 && !umma::mbar_wait(&freeb, (nchunk - 1) & 1u, kTcWaitPolls)) {
+            fail();   // the epilogue has not released the chunk accumulator
+            break;
+          }
+          const int s = (int)(it % (uint32_t)S);
+          if (!umma::mbar_wait(&full[s], (it / (uint32_t)S) & 1u, kTcWaitPolls)) {
+            fail();
+            break;
+          }
+          umma::fence_after_sync();
+          uint8_t* st = base + (size_t)s * stage_bytes;
+          const uint32_t sa = umma::smem_u32(st), sb = umma::smem_u32(st + 32768);
+          const int p = (kSyn && k >= gi.K0) ? 1 : 0;
+          const uint32_t td = tmem + (uint32_t)(p * N);
+          uint64_t dAh, dAl;
+          if (kSyn) {
+            dAh = umma::desc_sw128_mn(sa, 8192, 1024);
+            dAl = umma::desc_sw128_mn(sa + 16384, 8192, 1024);
+          } else {
+            dAh = umma::desc_sw128(sa);
+            dAl = umma::desc_sw128(sa + 16384);
+          }
+          const uint64_t dBh = umma::desc_sw128(sb), dBl = umma::desc_sw128(sb + (uint32_t)bB);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t adva = kSyn ? (uint64_t)(kk * 2048) >> 4 : (uint64_t)(kk * 32) >> 4;
+            const uint64_t advb = (uint64_t)(kk * 32) >> 4;
+            umma::mma_f16(td, dAh + adva, dBh + advb, idesc, (first && kk == 0) ? 0u : 1u);
+            umma::mma_f16(td, dAh + adva, dBl + advb, idesc, 1);
+            umma::mma_f16(td, dAl + adva, dBh + advb, idesc, 1);
+          }
+          umma::commit(&empty[s]);
+          if (gi.ends(k)) {
+            umma::commit(&chunkb);
+            ++nchunk;
+          }
+        }
+      }
+      if (abort_flag) {   // bounded wait for the MMAs in flight
+        umma::commit(&drainb);
+        umma::mbar_wait(&drainb, 0, kTcWaitPolls);
+      }
+    }
+  } else {
+    // ---- epilogue warps 0-3: fold chunks into the running sums, then write out
+    uint32_t nchunk = 0;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int item = blockIdx.x; item < nitems && !__any_sync(0xffffffffu, abort_flag); item += gridDim.x) {
+      const int4 w = items[item];
+      const TcClass& C = b.cls[w.x];
+      GemmItem<kSyn> gi;
+      gi.init(b, w);
+      const int N = gi.N;
+      const uint32_t W = kSyn ? 2u * N : (uint32_t)N;
+      bool ok = true;
+      for (int c = 0; c < gi.nch; ++c, ++nchunk) {
+        // warp-uniform decision: the TMEM accesses below are whole-warp operations
+        const bool got = umma::mbar_wait(&chunkb, nchunk & 1u, kTcWaitPolls);
+        if (!__all_sync(0xffffffffu, got)) {
+          if (lane == 0) fail();
+          ok = false;
           break;
         }
         umma::fence_after_sync();
-        uint8_t* st = base + (size_t)s * stage_bytes;
-        const uint32_t sa = umma::smem_u32(st), sb = umma::smem_u32(st + 32768);
-        const int p = (kSyn && k >= K0) ? 1 : 0;
-        const int t = p ? k - K0 : k;
-        const uint32_t td = tmem + (uint32_t)(p * N);
-        uint64_t dAh, dAl;
-        if (kSyn) {
-          dAh = umma::desc_sw128_mn(sa, 8192, 1024);
-          dAl = umma::desc_sw128_mn(sa + 16384, 8192, 1024);
-        } else {
-          dAh = umma::desc_sw128(sa);
-          dAl = umma::desc_sw128(sa + 16384);
-        }
-        const uint64_t dBh = umma::desc_sw128(sb), dBl = umma::desc_sw128(sb + (uint32_t)bB);
+        const int p = c < gi.nch0 ? 0 : 1;
+        const bool first = c == 0 || c == gi.nch0;
+        const uint32_t cc = (uint32_t)(p * N), sc = W + (uint32_t)(p * N);
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          umma::tmem_ld16(trow + cc + (uint32_t)c0, v);
+          if (!first) {
+            float t[16];
+            umma::tmem_ld16(trow + sc + (uint32_t)c0, t);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t adva = kSyn ? (uint64_t)(kk * 2048) >> 4 : (uint64_t)(kk * 32) >> 4;
-          const uint64_t advb = (uint64_t)(kk * 32) >> 4;
-          umma::mma_f16(td, dAh + adva, dBh + advb, idesc, (t | kk) != 0);
-          umma::mma_f16(td, dAh + adva, dBl + advb, idesc, 1);
-          umma::mma_f16(td, dAl + adva, dBh + advb, idesc, 1);
+            for (int i = 0; i < 16; ++i) v[i] += t[i];
+          }
+          umma::tmem_st16(trow + sc + (uint32_t)c0, v);
         }
-        umma::commit(&empty[s]);
+        umma::fence_before_sync();
+        umma::mbar_arrive(&freeb);
       }
-      if (!abort_flag) umma::commit(&accb);
-    }
-    // accumulators complete -> epilogue by all four warps
-    if (!umma::mbar_wait(&accb, nacc & 1u, kTcWaitPolls)) {
-      if (lane == 0) atomicCAS(d_err, 0, kDevTimeout);
-      abort_flag = 1;
-    }
-    ++nacc;
-    umma::fence_after_sync();
-    __syncwarp();
-    if (!abort_flag) {
-      const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+      if (!ok) break;
+      __syncwarp();
       if (!kSyn) {
         const int grp = w.y, m = grp >> 1, p = grp & 1;
         const int k = w.z * 128 + warp * 32 + lane;
@@ -531,7 +690,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
         float2* out = C.alm + alm_idx(C.lmax, l < C.lmax ? l : C.lmax, m);
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
-          umma::tmem_ld16(trow + (uint32_t)c0, v);
+          umma::tmem_ld16(trow + W + (uint32_t)c0, v);
           if (valid) {
 #pragma unroll
             for (int i = 0; i < 16; i += 2) {
@@ -550,8 +709,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
         const int* eo = C.sexp + (size_t)(2 * m + 1) * N;
         for (int c0 = 0; c0 < N; c0 += 16) {
           float ve[16], vo[16];
-          umma::tmem_ld16(trow + (uint32_t)c0, ve);
-          umma::tmem_ld16(trow + (uint32_t)(N + c0), vo);
+          umma::tmem_ld16(trow + W + (uint32_t)c0, ve);
+          umma::tmem_ld16(trow + W + (uint32_t)(N + c0), vo);
 #pragma unroll
           for (int c = 0; c < 16; c += 2) {
             const int qp = (c0 + c) >> 1;
@@ -567,20 +726,6 @@ __global__ void __launch_bounds__(128) k_tc_gemm(TcBatchDev b, const int4* __res
           }
         }
       }
-    }
-    umma::fence_before_sync();
-    const int stop = __syncthreads_or(abort_flag);
-    umma::fence_after_sync();
-    if (stop) break;
-  }
-  if (abort_flag) {
-    // bounded drain: the copies and MMAs this CTA issued land before it exits
-    if (threadIdx.x == 0)
-      for (int s = 0; s < S; ++s)
-        if (last_it[s] >= 0) umma::mbar_wait(&full[s], (uint32_t)(last_it[s] / S) & 1u, kTcWaitPolls);
-    if (threadIdx.x == 32) {
-      umma::commit(&drainb);
-      umma::mbar_wait(&drainb, 0, kTcWaitPolls);
     }
   }
   umma::fence_before_sync();
@@ -674,13 +819,19 @@ int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcL
       const int bB = stage_b_bytes(it.na_max);
       const int smem = 1024 + L.an_stages * (32768 + 2 * bB);
       cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      const int tcols = pow2_cols(it.na_max);
-      const int g = grid_of(ctx, k_tc_gemm<false>, 128, smem, it.n_an, std::min(L.an_ctas, 512 / tcols));
-      CLC_LAUNCH(ctx, "k_tc_analysis", (k_tc_gemm<false>), g, 128, smem, b, (const int4*)it.an.p, it.n_an,
+      const int tcols = pow2_cols(2 * it.na_max);
+      const int g = grid_of(ctx, k_tc_gemm<false>, 192, smem, it.n_an, std::min(L.an_ctas, 512 / tcols));
+      CLC_LAUNCH(ctx, "k_tc_analysis", (k_tc_gemm<false>), g, 192, smem, b, (const int4*)it.an.p, it.n_an,
                  L.an_stages, bB, tcols, ctx->d_err);
       return launch_check(ctx, "k_tc_analysis");
     }
     case 3: {
+      if (b.mode && b.n_low > 0) {
+        const int g = (int)std::min<long long>((b.n_low + 127) / 128, (long long)num_sms(ctx) * 16);
+        CLC_LAUNCH(ctx, "k_tc_low_orders", k_tc_low_orders, g, 128, 0, b);
+        const int rc = launch_check(ctx, "k_tc_low_orders");
+        if (rc) return rc;
+      }
       cudaFuncSetAttribute(k_tc_pack_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, it.pack_s_smem);
       const int g = grid_of(ctx, k_tc_pack_synthesis, 256, it.pack_s_smem, b.n_ps, 4);
       CLC_LAUNCH(ctx, "k_tc_pack_synthesis", k_tc_pack_synthesis, g, 256, it.pack_s_smem, b);
@@ -690,9 +841,9 @@ int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcL
       const int bB = stage_b_bytes(it.ns_max);
       const int smem = 1024 + L.sy_stages * (32768 + 2 * bB);
       cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      const int tcols = pow2_cols(2 * it.ns_max);
-      const int g = grid_of(ctx, k_tc_gemm<true>, 128, smem, it.n_sy, std::min(L.sy_ctas, 512 / tcols));
-      CLC_LAUNCH(ctx, "k_tc_synthesis", (k_tc_gemm<true>), g, 128, smem, b, (const int4*)it.sy.p, it.n_sy,
+      const int tcols = pow2_cols(4 * it.ns_max);
+      const int g = grid_of(ctx, k_tc_gemm<true>, 192, smem, it.n_sy, std::min(L.sy_ctas, 512 / tcols));
+      CLC_LAUNCH(ctx, "k_tc_synthesis", (k_tc_gemm<true>), g, 192, smem, b, (const int4*)it.sy.p, it.n_sy,
                  L.sy_stages, bB, tcols, ctx->d_err);
       return launch_check(ctx, "k_tc_synthesis");
     }

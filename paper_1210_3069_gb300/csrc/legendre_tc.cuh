@@ -9,7 +9,7 @@
 
 namespace clc {
 
-constexpr int kTcMaxClasses = 4;   // (nside, lmax) classes in one batch
+constexpr int kTcMaxClasses = 8;   // plane classes (same nside, lmax) in one batch
 constexpr int kTabExp = 10;        // table values are 2^kTabExp lambda_lm
 
 // FP16 hi + lo lambda table of one (nside, lmax), grouped by (m, parity of
@@ -57,7 +57,10 @@ struct TcClass {
   float2* G;                      // [P][nq][m / 4][ring][m % 4] per-ring Legendre sums
   size_t gstride, qstride;
   int ldm;                        // lmax + 1 rounded up to a multiple of 4
-  long long ring0, pa0, ps0;      // first flat item of the class: ring FFTs, analysis pack, synthesis pack
+  double2* G01;                   // [P][nq][m = 0, 1][ring] FP64 Legendre sums of the two lowest orders
+  const double* co01;             // [m = 0, 1][l = 0 .. lmax + 2][4] recurrence a_lm, b_lm, eps_lm, -1/(l(l+1))
+  int ncap;                       // rings from each pole that use the FP64 sums
+  long long ring0, pa0, ps0, low0;  // first flat item of the class: ring FFTs, packs, low-order sums
 };
 
 struct TcBatchDev {
@@ -65,7 +68,7 @@ struct TcBatchDev {
   TcClass cls[kTcMaxClasses];
   const double* const* kappa;     // device array [nplanes]
   double* const* out;             // device array [nplanes][6]: psi, a_th, a_ph, u_tt, u_pp, u_tp (NULL = skip)
-  long long n_ring, n_pa, n_ps;   // flat item counts
+  long long n_ring, n_pa, n_ps, n_low;   // flat item counts
   int mode;                       // 0: psi only, 1: psi and derivatives
 };
 

@@ -215,7 +215,9 @@ __device__ void ring_analysis_ring(const double* __restrict__ map, int nside, in
 
 // Legendre sums G_q of one plane: element (m, ring) at m * sm + ring * sr,
 // or, with quad set, in groups of four orders per ring:
-// ((m / 4) * sm + ring * 4 + m % 4)
+// ((m / 4) * sm + ring * 4 + m % 4).  P01 (optional, FP32 path): FP64 sums
+// of orders m = 0, 1 at P01[q * p01q + m * p01m + ring], used instead of G on
+// the ncap rings next to each pole (nring rings in all).
 template <typename T>
 struct SynthArgsT {
   const C2<T>* G0;
@@ -223,33 +225,57 @@ struct SynthArgsT {
   const C2<T>* G2;
   long long sm, sr;
   int quad;
+  const C2<double>* P01;
+  long long p01q, p01m;
+  int ncap, nring;
   double* out[6];
 };
 
 // Fourier coefficient of output field f at order m on one ring from the
-// Legendre sums G_0 = psi, G_1 = sin(t) d_t psi, G_2 = kappa_bl (is = 1 / sin t,
+// Legendre sums g0 = psi, g1 = sin(t) d_t psi, g2 = kappa_bl (is = 1 / sin t,
 // c = cos t).
+template <typename S>
+__device__ __forceinline__ C2<S> spec_combine(int mode, int f, int m, C2<S> g0, C2<S> g1, C2<S> g2, S is, S is2, S c) {
+  if (mode == 0 || f == 0) return g0;
+  const S dm = (S)m;
+  switch (f) {
+    case 1: return cx<S>(-g1.x * is, -g1.y * is);                               // alpha_t
+    case 2: return cx<S>(dm * g0.y * is, -dm * g0.x * is);                       // alpha_p = -i m g0 / s
+    case 3:                                                                      // u_tt = kappa_bl - u_pp
+      return cx<S>(g2.x - (-dm * dm * g0.x + c * g1.x) * is2, g2.y - (-dm * dm * g0.y + c * g1.y) * is2);
+    case 4: return cx<S>((-dm * dm * g0.x + c * g1.x) * is2, (-dm * dm * g0.y + c * g1.y) * is2);
+    default: {                                                                   // u_tp = i m (g1 - c g0) / s^2
+      const C2<S> d = cx<S>(g1.x - c * g0.x, g1.y - c * g0.y);
+      return cx<S>(-dm * d.y * is2, dm * d.x * is2);
+    }
+  }
+}
+
+// Ring geometry factors in the arithmetic type and, for the FP64 orders of
+// the FP32 path, in FP64.
 template <typename T>
-__device__ __forceinline__ C2<T> spec_of(const SynthArgsT<T>& a, int mode, int f, int m, int ring0, T is, T is2, T c) {
+struct RingFac {
+  T is, is2, c;
+  double isd, is2d, cd;
+};
+
+template <typename T>
+__device__ __forceinline__ C2<T> spec_of(const SynthArgsT<T>& a, int mode, int f, int m, int ring0, const RingFac<T>& g) {
+  if (a.P01 && m <= 1 && (ring0 < a.ncap || ring0 >= a.nring - a.ncap)) {
+    // the polar Hessian terms of m = 0, 1 cancel to O(sin^2 t): combine in FP64
+    const C2<double>* P = a.P01 + (size_t)m * a.p01m + ring0;
+    const C2<double> z = cx<double>(0.0, 0.0);
+    const C2<double> h = spec_combine<double>(mode, f, m, P[0], mode ? P[a.p01q] : z, mode ? P[2 * a.p01q] : z, g.isd,
+                                              g.is2d, g.cd);
+    return cx<T>((T)h.x, (T)h.y);
+  }
   const size_t idx = a.quad ? (size_t)(m >> 2) * a.sm + (size_t)ring0 * 4 + (m & 3)
                             : (size_t)m * a.sm + (size_t)ring0 * a.sr;
   const C2<T> g0 = a.G0[idx];
   if (mode == 0 || f == 0) return g0;
   const C2<T> g1 = a.G1[idx];
-  const T dm = (T)m;
-  switch (f) {
-    case 1: return cx<T>(-g1.x * is, -g1.y * is);                               // alpha_t
-    case 2: return cx<T>(dm * g0.y * is, -dm * g0.x * is);                       // alpha_p = -i m g0 / s
-    case 3: {                                                                    // u_tt = kappa_bl - u_pp
-      const C2<T> g2 = a.G2[idx];
-      return cx<T>(g2.x - (-dm * dm * g0.x + c * g1.x) * is2, g2.y - (-dm * dm * g0.y + c * g1.y) * is2);
-    }
-    case 4: return cx<T>((-dm * dm * g0.x + c * g1.x) * is2, (-dm * dm * g0.y + c * g1.y) * is2);
-    default: {                                                                   // u_tp = i m (g1 - c g0) / s^2
-      const C2<T> d = cx<T>(g1.x - c * g0.x, g1.y - c * g0.y);
-      return cx<T>(-dm * d.y * is2, dm * d.x * is2);
-    }
-  }
+  const C2<T> g2 = f == 3 ? a.G2[idx] : cx<T>(0, 0);
+  return spec_combine<T>(mode, f, m, g0, g1, g2, g.is, g.is2, g.c);
 }
 
 // Real ring values of every requested output field of ring i.  s: FFT
@@ -261,7 +287,13 @@ __device__ void ring_synthesis_ring(const SynthArgsT<T>& a, int nside, int lmax,
   const int n = r.npix, N = n / 2;
   const int ring0 = i - 1;
   const bool shifted = r.phi0 != 0.0;
-  const T is = (T)(1.0 / r.s), is2 = is * is, cz = (T)r.z;
+  RingFac<T> gf;
+  gf.isd = 1.0 / r.s;
+  gf.is2d = gf.isd * gf.isd;
+  gf.cd = r.z;
+  gf.is = (T)gf.isd;
+  gf.is2 = gf.is * gf.is;
+  gf.c = (T)r.z;
   const int nf = mode ? 6 : 1;
   for (int f = 0; f < nf; ++f) {
     double* out = a.out[f];
@@ -275,13 +307,13 @@ __device__ void ring_synthesis_ring(const SynthArgsT<T>& a, int nside, int lmax,
       C2<T> X = cx<T>(0, 0);
       int q = 0;
       for (int m = k; m <= lmax; m += n, ++q) {
-        C2<T> g = spec_of<T>(a, mode, f, m, ring0, is, is2, cz);
+        C2<T> g = spec_of<T>(a, mode, f, m, ring0, gf);
         if (m == 0) g.y = (T)0;
         X = (shifted && (q & 1)) ? X - g : X + g;
       }
       q = 1;
       for (int m = (k == 0 ? n : n - k); m <= lmax; m += n, ++q) {
-        const C2<T> g = conj(spec_of<T>(a, mode, f, m, ring0, is, is2, cz));
+        const C2<T> g = conj(spec_of<T>(a, mode, f, m, ring0, gf));
         X = (shifted && (q & 1)) ? X - g : X + g;
       }
       if (shifted) X = X * ck.next();

@@ -8,6 +8,7 @@
 // valid for any maps the caller passes: an execution copies the pointer
 // tables (pinned host staging, one asynchronous copy) and launches the graph.
 #include <algorithm>
+#include <cmath>
 #include <map>
 
 #include "legendre_tc.cuh"
@@ -56,42 +57,45 @@ static int tc_batch_build(clc_ctx* ctx, int nplanes, const int* nside, const int
   B->ctx = ctx;
   B->nplanes = nplanes;
   B->mode = mode;
-  // classes in order of first appearance
+  // classes in order of first appearance; a class holds at most
+  // tc_class_limit planes, further planes of the same size open a new one
+  const int limit = tc_class_limit(mode);
   std::vector<std::pair<int, int>> key;
   std::vector<std::vector<int>> members;
   for (int i = 0; i < nplanes; ++i) {
     if (!valid_nside(nside[i]) || nside[i] < 64 || nside[i] > 4096 || lmax[i] < 1 || lmax[i] > 4 * nside[i])
       return set_err(ctx, CLC_EINVAL, "mixed-precision SHT batch: need 64 <= nside <= 4096 and 1 <= lmax <= 4 nside");
     const auto k = std::make_pair(nside[i], lmax[i]);
-    auto f = std::find(key.begin(), key.end(), k);
-    if (f == key.end()) {
+    int c = -1;
+    for (int j = 0; j < (int)key.size(); ++j)
+      if (key[j] == k && (int)members[j].size() < limit) c = j;
+    if (c < 0) {
       if ((int)key.size() == kTcMaxClasses)
-        return set_err(ctx, CLC_EINVAL, "mixed-precision SHT batch: at most 4 distinct (nside, lmax) per batch");
+        return set_err(ctx, CLC_EINVAL, "mixed-precision SHT batch: more than " + std::to_string(kTcMaxClasses) +
+                                            " plane classes (at most " + std::to_string(limit) +
+                                            " planes of one (nside, lmax) per class)");
       key.push_back(k);
       members.emplace_back();
-      f = key.end() - 1;
+      c = (int)key.size() - 1;
     }
-    members[f - key.begin()].push_back(i);
+    members[c].push_back(i);
   }
   const int nq = mode ? 3 : 1;
-  for (auto& mb : members)
-    if ((int)mb.size() > tc_class_limit(mode))
-      return set_err(ctx, CLC_EINVAL, "mixed-precision SHT batch: more than " + std::to_string(tc_class_limit(mode)) +
-                                          " planes of one (nside, lmax)");
   TcBatchDev& d = B->dev;
   d.ncls = (int)key.size();
   d.mode = mode;
   B->slot.assign(nplanes, 0);
   // sizes of every class buffer
   struct Sz {
-    size_t F, V, Ve, A, S, Se, So, G;
+    size_t F, V, Ve, A, S, Se, So, G, G01, Co;
   };
+  std::vector<std::vector<double>> co01(key.size());
   std::vector<Sz> sz(d.ncls);
   std::vector<std::vector<long long>> soff(d.ncls);
   auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
   size_t total = 0;
   int plane0 = 0;
-  long long ring0 = 0, pa0 = 0, ps0 = 0;
+  long long ring0 = 0, pa0 = 0, ps0 = 0, low0 = 0;
   int rc = CLC_OK;
   for (int c = 0; c < d.ncls; ++c) {
     const int ns = key[c].first, L = key[c].second, P = (int)members[c].size();
@@ -127,6 +131,21 @@ static int tc_batch_build(clc_ctx* ctx, int nplanes, const int* nside, const int
     C.ring0 = ring0;
     C.pa0 = pa0;
     C.ps0 = ps0;
+    C.low0 = low0;
+    // recurrence (a_lm, b_lm), eps_lm and -1/(l(l+1)) of the orders m = 0, 1,
+    // l = 0 .. lmax + 2; FP64 low orders on the rings with sin(theta) < 0.29
+    C.ncap = std::max(1, std::min(2 * ns - 1, (int)std::ceil(0.35 * ns)));
+    co01[c].assign(2 * (size_t)(L + 3) * 4, 0.0);
+    for (int m = 0; m <= 1; ++m)
+      for (int l = 0; l <= L + 2; ++l) {
+        double* e = &co01[c][((size_t)m * (L + 3) + l) * 4];
+        if (l >= 1) e[3] = -1.0 / ((double)l * (l + 1.0));
+        if (l >= m + 2) {
+          e[0] = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+          e[1] = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+        }
+        if (l > m) e[2] = std::sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
+      }
     const int G = 2 * (L + 1);
     long long sacc = 0;
     soff[c].resize(G);
@@ -143,16 +162,20 @@ static int tc_batch_build(clc_ctx* ctx, int nplanes, const int* nside, const int
     z.Se = r256(sizeof(int) * (size_t)G * C.Ns);
     z.So = r256(sizeof(long long) * G);
     z.G = r256(sizeof(float2) * C.gstride * P);
-    total += z.F + 2 * z.V + z.Ve + z.A + 2 * z.S + z.Se + z.So + z.G;
+    z.G01 = r256(sizeof(double2) * (size_t)P * nq * 2 * C.ldf);
+    z.Co = r256(sizeof(double) * co01[c].size());
+    total += z.F + 2 * z.V + z.Ve + z.A + 2 * z.S + z.Se + z.So + z.G + z.G01 + z.Co;
     for (int j = 0; j < P; ++j) B->slot[members[c][j]] = plane0 + j;
     plane0 += P;
     ring0 += (long long)P * (4 * ns - 1);
     pa0 += L + 1;
     ps0 += G;
+    low0 += (long long)P * C.ncap;
   }
   d.n_ring = ring0;
   d.n_pa = pa0;
   d.n_ps = ps0;
+  d.n_low = low0;
   size_t fb = 0, tb = 0;
   cudaMemGetInfo(&fb, &tb);
   if (total + (1ull << 30) > fb)
@@ -192,6 +215,13 @@ static int tc_batch_build(clc_ctx* ctx, int nplanes, const int* nside, const int
     w += z.So;
     C.G = (float2*)w;
     w += z.G;
+    C.G01 = (double2*)w;
+    w += z.G01;
+    C.co01 = (const double*)w;
+    if ((rc = cuda_check(ctx, cudaMemcpy(w, co01[c].data(), sizeof(double) * co01[c].size(), cudaMemcpyHostToDevice),
+                         "batch coefficient upload")))
+      return rc;
+    w += z.Co;
   }
   // pointer tables: kappa[n], out[n][6]
   B->ptr_bytes = sizeof(void*) * (size_t)nplanes * 7;
