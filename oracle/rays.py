@@ -144,3 +144,44 @@ def map_lens(nside, fields):
                 "u_pp": torch.einsum("mi,mij,mj->m", p, U, p),
                 "u_tp": torch.einsum("mi,mij,mj->m", t, U, p)}
     return lens
+
+
+def galaxy_bins(chi, gchi):
+    """Plane n of each galaxy: chi[n] <= chi_g < chi[n + 1], n = 0 .. N - 1
+    (a galaxy on the last sphere belongs to plane N - 1); -1 in front of the
+    first plane (no lensing)."""
+    chi_t = torch.as_tensor(chi, dtype=F64)
+    N = chi_t.numel() - 1
+    b = torch.searchsorted(chi_t, gchi, right=True) - 1
+    return torch.where(gchi < chi_t[0], torch.full_like(b, -1), b.clamp(max=N - 1))
+
+
+def galaxy_shear(kappas, nside, lmax, chi, gz, gphi, gchi):
+    """Shear (gamma_1, gamma_2)[2, M] of M galaxies at (gz, gphi) and comoving
+    distance gchi: rays start at the galaxy directions on plane 0, each plane's
+    lens fields come from the pure-SHT solve of kappas[n] (Sec. 3.2), the rays
+    follow the plane recursion (Sec. 2.2, Appendix B) and each galaxy takes
+    A_g between the two planes that bracket it (Appendix D, Eq. gatraj), its
+    shear from Eq. invmagmat.  Differentiable with respect to kappas."""
+    from . import healpix as hp
+    from . import sht
+    chi = [float(c) for c in chi]
+    N = len(kappas)
+    s = torch.sqrt((1 - gz) * (1 + gz))
+    n0 = torch.stack([s * torch.cos(gphi), s * torch.sin(gphi), gz], -1)
+    bins = galaxy_bins(chi, gchi)
+    st = init_rays(n0, chi[0])
+    g1 = torch.zeros(gz.shape, dtype=F64)
+    g2 = torch.zeros(gz.shape, dtype=F64)
+    for m in range(N):
+        fields = sht.poisson_sht(kappas[m], nside, lmax)
+        chi_prev = chi[m - 1] if m > 0 else 0.0
+        st = step(st, map_lens(nside, fields), chi_prev, chi[m], chi[m + 1])
+        sel = bins == m
+        Ag = galaxy_interp(st["Ap"], st["A"], torch.full_like(gchi, chi[m]), torch.full_like(gchi, chi[m + 1]),
+                           torch.where(sel, gchi, torch.full_like(gchi, chi[m + 1])))
+        _, a1, a2, _ = decompose(Ag)
+        g1 = g1 + torch.where(sel, a1, torch.zeros_like(a1))
+        g2 = g2 + torch.where(sel, a2, torch.zeros_like(a2))
+    del hp
+    return torch.stack([g1, g2])
