@@ -265,6 +265,33 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
                         const double* chi_host, clc_rays* rays);
 
 /* ------------------------------------------------------------------------ */
+/* Differentiation: galaxy shears and their adjoint (Sec. 2.2, 3.2, App. D)   */
+
+/* Shears of ngal galaxies through nplanes pure-SHT planes: one ray per
+ * galaxy starts at its direction (gz = cos theta, gphi) on the sphere of
+ * chi_host[0]; plane m's lens fields come from clc_poisson_sht of
+ * kappa[m] (device RING map of nside, band limit lmax, CLC_FP64 or
+ * CLC_MIXED) and the rays follow the plane recursion of clc_ray_step.  A
+ * galaxy at comoving distance gchi with chi[n] <= gchi < chi[n + 1] takes
+ * A_g = (1 - t) A^(n) + t A^(n+1), t = (chi[n+1] / gchi)(gchi - chi[n]) /
+ * (chi[n+1] - chi[n]) (Appendix D); gamma (device, [2][ngal]) receives
+ * gamma_1 = -(A_g00 - A_g11) / 2, gamma_2 = -(A_g01 + A_g10) / 2 (zero for
+ * galaxies in front of chi[0]).  With tape != NULL the ray states entering
+ * every plane (14 doubles per galaxy and plane) are kept in a new tape for
+ * clc_gal_trace_adjoint; the kappa maps must stay alive until then. */
+typedef struct clc_gal_tape clc_gal_tape;
+int clc_gal_trace(clc_ctx* ctx, int nplanes, const double* const* kappa_host, int nside, int lmax, int precision,
+                  const double* chi_host, int64_t ngal, const double* gz, const double* gphi, const double* gchi,
+                  double* gamma, clc_gal_tape** tape);
+/* Gradient of a loss with respect to every kappa map, given
+ * gamma_bar = dLoss / dgamma (device, [2][ngal]): the planes are revisited
+ * last to first, each plane's lens maps recomputed, each ray step
+ * differentiated from its checkpoint and the adjoint of the SHT Poisson solve
+ * applied.  kappa_bar is a host array of nplanes device maps (written). */
+int clc_gal_trace_adjoint(clc_gal_tape* tape, const double* gamma_bar, double* const* kappa_bar_host);
+int clc_gal_tape_destroy(clc_gal_tape* tape);
+
+/* ------------------------------------------------------------------------ */
 /* Split-precision tensor-core contraction (the building block of the        */
 /* mixed-precision Legendre transforms; the paper is all FP64)               */
 

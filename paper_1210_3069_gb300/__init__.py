@@ -76,6 +76,10 @@ _SIGS = {
     "clc_sht_plan_execute": (_i, [_p, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.POINTER(Derivs)]),
     "clc_sht_plan_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(ctypes.c_size_t)]),
     "clc_sht_plan_destroy": (_i, [_p]),
+    "clc_gal_trace": (_i, [_p, _i, ctypes.POINTER(_p), _i, _i, _i, ctypes.POINTER(_d), _i64, _p, _p, _p, _p,
+                           ctypes.POINTER(_p)]),
+    "clc_gal_trace_adjoint": (_i, [_p, _p, ctypes.POINTER(_p)]),
+    "clc_gal_tape_destroy": (_i, [_p]),
     "clc_gemm_f16x3": (_i, [_p, _p, _p, _p, _p, _i, _i, _i, _i, _p]),
     "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
     "clc_power_spectrum": (_i, [_p, _p, _p, _i, _p]),
@@ -235,6 +239,20 @@ class Context:
         self._check(lib().clc_poisson_sht_batch(self.h, kp, P, nside, lmax, precision, pp, dd))
         return out
 
+    def gal_trace(self, kappas, nside, lmax, chi, gz, gphi, gchi, precision=FP64, tape=True):
+        """Galaxy shears gamma[2, ngal] through the planes kappas[N, Npix]
+        (clc_gal_trace); returns (gamma, GalTape or None)."""
+        N = kappas.shape[0]
+        n = gz.numel()
+        gamma = torch.empty(2, n, dtype=torch.float64, device=self.device)
+        kp = (_p * N)(*[kappas[i].data_ptr() for i in range(N)])
+        _ptr(kappas)
+        ch = (_d * (N + 1))(*[float(c) for c in chi])
+        h = _p()
+        self._check(lib().clc_gal_trace(self.h, N, kp, nside, lmax, precision, ch, n, _ptr(gz), _ptr(gphi),
+                                        _ptr(gchi), _ptr(gamma), ctypes.byref(h) if tape else None))
+        return gamma, (GalTape(self, h, kappas) if tape else None)
+
     def sht_plan(self, nsides, lmaxs, derivatives=True, graph=True, tune=False):
         return ShtPlan(self, nsides, lmaxs, derivatives, graph, tune)
 
@@ -355,6 +373,54 @@ class RayState:
 
     def struct(self):
         return Rays(self.n, _ptr(self.x), _ptr(self.beta), _ptr(self.A), _ptr(self.Ap), _ptr(self.bundle))
+
+
+class GalTape:
+    """Checkpoints of one clc_gal_trace for its adjoint."""
+
+    def __init__(self, ctx, h, kappas):
+        self.ctx, self.h, self.kappas = ctx, h, kappas
+
+    def adjoint(self, gamma_bar):
+        kb = torch.empty_like(self.kappas)
+        N = kb.shape[0]
+        ptrs = (_p * N)(*[kb[i].data_ptr() for i in range(N)])
+        self.ctx._check(lib().clc_gal_trace_adjoint(self.h, _ptr(gamma_bar.contiguous()), ptrs))
+        return kb
+
+    def close(self):
+        if self.h:
+            lib().clc_gal_tape_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GalaxyShear(torch.autograd.Function):
+    """gamma[2, ngal] = galaxy shears through the pure-SHT planes kappas[N, Npix];
+    the backward pass is the library's adjoint (checkpointed ray states,
+    recomputed lens maps, transposed SHT)."""
+
+    @staticmethod
+    def forward(fctx, kappas, lib_ctx, nside, lmax, chi, gz, gphi, gchi, precision):
+        gamma, tape = lib_ctx.gal_trace(kappas.detach().contiguous(), nside, lmax, chi, gz, gphi, gchi, precision)
+        fctx.tape = tape
+        return gamma
+
+    @staticmethod
+    def backward(fctx, gbar):
+        kb = fctx.tape.adjoint(gbar)
+        fctx.tape.close()
+        return kb, None, None, None, None, None, None, None, None
+
+
+def galaxy_shear(lib_ctx, kappas, nside, lmax, chi, gz, gphi, gchi, precision=FP64):
+    """Differentiable galaxy shears (see GalaxyShear)."""
+    return GalaxyShear.apply(kappas, lib_ctx, nside, lmax, chi, gz, gphi, gchi, precision)
 
 
 class ShtPlan:

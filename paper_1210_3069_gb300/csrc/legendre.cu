@@ -134,11 +134,11 @@ std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int l
 // Block (l-block, m): 8 warps, each warp one l at a time; lanes over rings.
 __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long* __restrict__ off,
                                     const double* __restrict__ tab, const double2* __restrict__ F, int ldf,
-                                    double2* __restrict__ alm) {
+                                    double2* __restrict__ alm, int ltop, int lpack) {
   extern __shared__ double2 V[];  // V[0..R) even (N + S), V[R..2R) odd (N - S)
   const int m = blockIdx.y;
   const int l0 = m + blockIdx.x * 64;
-  if (l0 > lmax) return;
+  if (l0 > ltop) return;
   const double2* Fm = F + (size_t)m * ldf;
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
     const int i = r + 1;
@@ -151,7 +151,7 @@ __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long*
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* col = tab + off[m];
-  for (int l = l0 + warp; l <= lmax && l < l0 + 64; l += 8) {
+  for (int l = l0 + warp; l <= ltop && l < l0 + 64; l += 8) {
     const double* row = col + (size_t)(l - m) * R;
     const double2* v = V + (((l + m) & 1) ? R : 0);
     double ax = 0.0, ay = 0.0;
@@ -165,17 +165,18 @@ __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long*
       ax += __shfl_xor_sync(0xffffffffu, ax, o);
       ay += __shfl_xor_sync(0xffffffffu, ay, o);
     }
-    if (lane == 0) alm[alm_idx(lmax, l, m)] = make_double2(ax, ay);
+    if (lane == 0) alm[alm_idx(lpack, l, m)] = make_double2(ax, ay);
   }
 }
 
-int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, int ldf, double2* alm) {
+int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, int ldf, double2* alm, int ltop) {
   const int L = T.lmax;
-  dim3 grid((L + 1 + 63) / 64, L + 1);
+  if (ltop < 0) ltop = L;
+  dim3 grid((ltop + 1 + 63) / 64, L + 1);
   const int smem = 2 * T.R * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   CLC_LAUNCH(ctx, "k_legendre_analysis", k_legendre_analysis, grid, 256, smem, T.nside, L, T.R, (const long long*)T.offsets.p,
-                                                        (const double*)T.data.p, F, ldf, alm);
+                                                        (const double*)T.data.p, F, ldf, alm, ltop, ltop);
   return launch_check(ctx, "k_legendre_analysis");
 }
 

@@ -23,8 +23,9 @@ __host__ __device__ __forceinline__ long long alm_idx(int lmax, int l, int m) {
 }
 
 // alm[idx(l, m)] = sum_r lambda_lm(r) V_m^{(l+m) % 2}(r) from ring Fourier
-// coefficients F[m * ldf + ring] (weights already applied).
-int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, int ldf, double2* alm);
+// coefficients F[m * ldf + ring] (weights already applied), for l <= ltop
+// (lmax by default, at most lmax + 1), packed with band limit ltop.
+int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, int ldf, double2* alm, int ltop = -1);
 
 // G_q[m][ring] = sum_l lambda_lm(ring) rhs_q[idx'(l, m)] for q < nq, where
 // rhs_q is packed with band limit lmax + 1 (idx' = alm_idx(lmax + 1, l, m)) and
