@@ -58,6 +58,16 @@ BATCH_WORKLOADS = {
 }
 BATCH_METRIC = "lens planes/s (batched mixed-precision SHT Poisson, Nside 512/1024/2048, lmax = 2 Nside)"
 
+# gradient of a galaxy-shear loss with respect to every plane's convergence
+# map (pure-SHT planes, FP64), checkpointed per plane
+ADJOINT_WORKLOADS = {
+    "gal_adjoint_nside1024": dict(nplanes=16, nside=1024, lmax=2048, ngal=1_000_000, z_lo=0.3, z_hi=1.5,
+                                  seed=1210005, fd_pixels=4),
+    "gal_adjoint_small": dict(nplanes=4, nside=128, lmax=256, ngal=100_000, z_lo=0.3, z_hi=1.5, seed=1210005,
+                              fd_pixels=4),
+}
+ADJOINT_METRIC = "loss+gradient evaluations/s (galaxy shear through SHT planes, adjoint w.r.t. all kappa maps)"
+
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 KERNELS = ("k_smooth", "k_restrict", "k_coarse_rhs", "k_prolong", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
@@ -363,6 +373,111 @@ def run_batch(args, wl):
                 setup_s=setup_s, fp64_ms_per_plane=fp64_ms, errors=errs, h2d=h2d, d2h=h2d)
 
 
+def run_adjoint(args, wl):
+    """Forward shears and the adjoint gradient of L = sum (gamma - gamma_target)^2
+    over all planes (one step = forward + backward); FD check of the gradient
+    at a few pixels (central, step 1e-6)."""
+    import paper_1210_3069_gb300 as clc
+    clc.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(0)
+    N, ns, L = wl["nplanes"], wl["nside"], wl["lmax"]
+    om = 0.25
+    chi_max = cosmology.chi_of_z(wl["z_hi"], om)
+    pl = cosmology.lens_planes(N, chi_max / N, om)
+    chi = pl["chi"]
+    rays = ctx.rays(12 * ns * ns)
+    ctx.rays_init_pixels(rays, ns, 1.0, 0)
+    torch.cuda.synchronize()
+    zc, pc = rays.x[2].clone(), torch.remainder(torch.atan2(rays.x[1], rays.x[0]), 2 * math.pi)
+    del rays
+
+    def planes(seed):
+        out = []
+        for m in range(N):
+            modes = synthetic.random_field_modes(256, 2.0, 2.0 * ns, seed + m, device=dev)
+            delta = synthetic.lognormal_density(zc, pc, modes).double() - 1.0
+            out.append(pl["scale"][m] * pl["growth"][m] * delta)
+        return torch.stack(out)
+
+    kappas = planes(wl["seed"])
+    gz, gphi = synthetic.uniform_sphere(wl["ngal"], wl["seed"] + 100, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(wl["seed"] + 200)
+    zg = wl["z_lo"] + (wl["z_hi"] - wl["z_lo"]) * torch.rand(wl["ngal"], generator=gen, dtype=torch.float64,
+                                                              device=dev)
+    zgrid = torch.linspace(0.0, wl["z_hi"] + 0.01, 2048, dtype=torch.float64)
+    cgrid = torch.tensor([cosmology.chi_of_z(float(z), om) for z in zgrid], dtype=torch.float64)
+    gchi = torch.from_numpy(__import__("numpy").interp(zg.cpu().numpy(), zgrid.numpy(), cgrid.numpy())).to(dev)
+    with torch.no_grad():
+        target, _ = ctx.gal_trace(planes(wl["seed"] + 5000), ns, L, chi, gz, gphi, gchi, tape=False)
+
+    def step():
+        k = kappas.clone().requires_grad_(True)
+        g = clc.galaxy_shear(ctx, k, ns, L, chi, gz, gphi, gchi)
+        loss = ((g - target) ** 2).sum()
+        loss.backward()
+        return loss.detach(), k.grad
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            loss, grad = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    # forward alone
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    ctx.gal_trace(kappas, ns, L, chi, gz, gphi, gchi, tape=False)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = f0.elapsed_time(f1)
+    # finite differences of the loss at a few pixels (largest gradient entries)
+    def lossv(k):
+        g, _ = ctx.gal_trace(k, ns, L, chi, gz, gphi, gchi, tape=False)
+        return float(((g - target) ** 2).sum())
+    def central(m, p, h):
+        kp, km = kappas.clone(), kappas.clone()
+        kp[m, p] += h
+        km[m, p] -= h
+        return (lossv(kp) - lossv(km)) / (2 * h)
+
+    fd = []
+    for j in range(wl["fd_pixels"]):
+        m = j % N
+        p = int(grad[m].abs().argmax())
+        a = float(grad[m, p])
+        f6 = central(m, p, 1e-6)
+        # a 10x larger step has 10x less rounding and still negligible truncation
+        f5 = central(m, p, 1e-5)
+        fd.append({"plane": m, "pixel": p, "adjoint": a, "fd_h1e-6": f6, "rel_diff_h1e-6": abs(f6 - a) / abs(a),
+                   "fd_h1e-5": f5, "rel_diff_h1e-5": abs(f5 - a) / abs(a)})
+    return dict(ms=ms, fwd_ms=fwd_ms, launches=launches, clocks=clocks.summary(), loss=float(loss), fd=fd)
+
+
+def adjoint_line(args, wl, r):
+    return {
+        "metric": ADJOINT_METRIC, "value": args.steps / (r["ms"] / 1000.0), "unit": "gradients/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, **{k: v for k, v in wl.items() if k != "seed"},
+                   "loss": "sum of squared shear differences from a catalogue traced through other seeded planes",
+                   "checkpoints": "ray state entering every plane; lens maps recomputed",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "forward_ms": r["fwd_ms"], "loss": r["loss"], "fd_check": r["fd"],
+        "e2e": None, "gpu_launches": r["launches"], "clocks": r["clocks"],
+    }
+
+
 def batch_line(args, wl, r):
     peaks, peak_kind = load_peaks()
     sizes = wl["sizes"]
@@ -491,9 +606,19 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
                     help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
-    ap.add_argument("--workload", default="shtmg_plane_nside2048", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default="shtmg_plane_nside2048",
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.workload in ADJOINT_WORKLOADS:
+        if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": args.impl, "metric": ADJOINT_METRIC,
+                                  "unavailable": "the adjoint workload runs on one GPU"}))
+            return
+        wl = ADJOINT_WORKLOADS[args.workload]
+        print(json.dumps(adjoint_line(args, wl, run_adjoint(args, wl))))
+        return
     if args.workload in BATCH_WORKLOADS:
         if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
             if int(os.environ.get("RANK", "0")) == 0:
