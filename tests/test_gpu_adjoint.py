@@ -66,7 +66,7 @@ def test_adjoint_matches_oracle_gradient():
     c.sync()
     assert abs(float(lg.detach()) - float(lo.detach())) <= 1e-10 * abs(float(lo.detach()))
     for m in range(3):
-        assert rel_l2(kg.grad[m], ko[m].grad) < 1e-8, m
+        assert rel_l2(kg.grad[m], ko[m].grad) < 1e-10, m
 
 
 @pytest.mark.parametrize("nside,lmax,nplanes,ngal", [(16, 32, 3, 400), (64, 128, 4, 20000)])
