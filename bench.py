@@ -145,7 +145,8 @@ def kernel_models(cfg, precision, cycles, nsteps):
     as 2.  Red-black smoothing per updated cell: 3 FMA + 1 add + 1 multiply
     (8 flops) in FP64; in FP32 it streams the level once per colour:
     8 bytes per cell per launch (u read, f and u of that colour).  The FP64
-    residual of the mixed path: 11 flops per fine cell."""
+    residual of the mixed path (float-float on the FP32 pipe): 32 bytes per
+    fine cell per refinement (one refinement per two V-cycles, plus the first)."""
     npatch = 12 * cfg["nside_bundle"] ** 2
     sweeps = cfg["nu1"] + cfg["nu2"]
     cells_cycle = 0
@@ -160,8 +161,10 @@ def kernel_models(cfg, precision, cycles, nsteps):
     else:
         out["k_smooth"] = ("hbm", 8.0 * 2 * sweeps * cells_cycle * ncyc, "byte")
     if precision == "mixed":
+        # float-float residual: e (8 B) and d (4 B) in, source (8 B) in, e (8 B) and r (4 B) out per fine cell
         n0 = cfg["ncell"]
-        out["k_resid_mixed"] = ("alu", 11.0 * npatch * n0 * n0 * (ncyc + nsteps), "flop")
+        nres = sum((c + 1) // 2 + 1 for c in cycles)
+        out["k_resid_mixed"] = ("hbm", 32.0 * npatch * n0 * n0 * nres, "byte")
     return out
 
 

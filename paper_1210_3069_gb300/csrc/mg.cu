@@ -38,6 +38,51 @@ MGView mg_view(const clc_plane_solution* sol) {
 // one patch, blockIdx.z = patch (no 64-bit index division anywhere).
 constexpr int kBX = 32, kBY = 8;
 
+// Float-float ("double-float") arithmetic: a value is hi + lo with two FP32
+// words, |lo| <= ulp(hi) / 2 (about 48 significant bits).  Sums by Knuth's
+// two-sum, products by the FMA-based exact product (Dekker's splitting made
+// unnecessary by fmaf), each renormalised with Dekker's fast two-sum.  Used
+// for the FP64-accurate residual of the mixed MG path, which would otherwise
+// run on the FP64 pipe (1/58 of the FP32 rate on this GPU).
+__device__ __forceinline__ float2 ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return make_float2(s, (a - (s - bb)) + (b - bb));
+}
+__device__ __forceinline__ float2 ff_fast_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return make_float2(s, b - (s - a));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+  float2 s = ff_two_sum(a.x, b.x);
+  const float2 t = ff_two_sum(a.y, b.y);
+  s.y += t.x;
+  s = ff_fast_sum(s.x, s.y);
+  s.y += t.y;
+  return ff_fast_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 ff_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 ff_add_f(float2 a, float b) {
+  float2 s = ff_two_sum(a.x, b);
+  s.y += a.y;
+  return ff_fast_sum(s.x, s.y);
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+  const float p = a.x * b.x;
+  float e = fmaf(a.x, b.x, -p);
+  e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+  return ff_fast_sum(p, e);
+}
+
+// store a value computed in FP64 in the solver's storage type
+template <typename T>
+__device__ __forceinline__ T from_double(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ float2 from_double<float2>(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
+}
+
 __global__ void k_mg_rotations(int nb, int npatch, double* rot) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= npatch) return;
@@ -98,7 +143,7 @@ __global__ void k_mg_setup_defect(int n, const double* __restrict__ rot, const d
     const double src = interp_map_tab(kappa, nf, ring_th, th, ph);
     const double* U = base + (size_t)b * side * side;
     const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
-    f[(size_t)b * n * n + (size_t)i * n + j] = (T)(src - (nb - diag[i * n + j] * U[cell]));
+    f[(size_t)b * n * n + (size_t)i * n + j] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
     ff = src * src;
   }
   for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
@@ -162,7 +207,7 @@ __global__ void k_mg_setup_defect_plan(int n, const int4* __restrict__ idx, cons
     const int cell = (i + 1) * side + (j + 1);
     const double* U = base + (size_t)b * side * side;
     const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
-    f[pos] = (T)(src - (nb - diag[i * n + j] * U[cell]));
+    f[pos] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
     ff = src * src;
   }
   for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
@@ -341,42 +386,58 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
 }
 
 // Mixed refinement step, fused: e_new = e_old + d (d = the last FP32
-// V-cycle's correction, NULL before the first cycle), r = f' - L e_new in
-// FP64, r in FP32 as the next V-cycle's source, ||r||^2 per patch.  Each
-// thread handles kRows rows of one column, so the warp reduction is paid once
-// per kRows cells.
+// V-cycle's correction, NULL before the first cycle), r = f' - L e_new with
+// e, f' and the operator in float-float (FP64-level accuracy on the FP32
+// pipe), r rounded to FP32 as the next V-cycle's source, ||r||^2 per patch.
+// Each thread handles kRows rows of one column, so the warp reduction is
+// paid once per kRows cells.
 constexpr int kRows = 4;
 
-__global__ void k_resid_mixed(const double* __restrict__ e_old, const float* __restrict__ d,
-                              const double* __restrict__ fd, const double* __restrict__ coef,
-                              const double* __restrict__ diag, int n, double* __restrict__ e_new,
-                              float* __restrict__ r32, double* __restrict__ norms) {
+__global__ void k_resid_ff(const float2* __restrict__ e_old, const float* __restrict__ d,
+                           const float2* __restrict__ fd, const float2* __restrict__ coef,
+                           const float2* __restrict__ diag, int n, float2* __restrict__ e_new,
+                           float* __restrict__ r32, double* __restrict__ norms) {
   const int b = blockIdx.z;
   const int j = blockIdx.x * kBX + threadIdx.x;
   const size_t side = n + 2;
-  const double* E = e_old + (size_t)b * side * side;
+  const float2* E = e_old + (size_t)b * side * side;
   const float* D = d ? d + (size_t)b * side * side : nullptr;
-  double rr = 0.0;
+  float rr = 0.f;
 #pragma unroll
   for (int k = 0; k < kRows; ++k) {
     const int i = (blockIdx.y * kRows + k) * kBY + threadIdx.y;
     if (i < n && j < n) {
       const size_t c = (size_t)(i + 1) * side + (j + 1);
-      double eC = E[c], eS = E[c + side], eN = E[c - side], eE = E[c + 1], eW = E[c - 1];
+      float2 eC = E[c], eS = E[c + side], eN = E[c - side], eE = E[c + 1], eW = E[c - 1];
       if (D) {
-        eC += (double)D[c]; eS += (double)D[c + side]; eN += (double)D[c - side];
-        eE += (double)D[c + 1]; eW += (double)D[c - 1];
+        eC = ff_add_f(eC, D[c]);
+        eS = ff_add_f(eS, D[c + side]);
+        eN = ff_add_f(eN, D[c - side]);
+        eE = ff_add_f(eE, D[c + 1]);
+        eW = ff_add_f(eW, D[c - 1]);
       }
-      const double nb = fma(coef[2 * n + i], eE + eW, fma(coef[n + i], eN, fma(coef[i], eS, -diag[i * n + j] * eC)));
+      // L e = aS eS + aN eN + b (eE + eW) - diag eC
+      const float2 nb = ff_add(ff_add(ff_mul(coef[i], eS), ff_mul(coef[n + i], eN)),
+                               ff_add(ff_mul(coef[2 * n + i], ff_add(eE, eW)), ff_neg(ff_mul(diag[i * n + j], eC))));
       const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
-      const double r = fd[pos] - nb;
-      r32[pos] = (float)r;
+      const float2 r = ff_add(fd[pos], ff_neg(nb));
+      r32[pos] = r.x + r.y;
       e_new[(size_t)b * side * side + c] = eC;
-      rr = fma(r, r, rr);
+      rr = fmaf(r.x, r.x, rr);
     }
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-  if (threadIdx.x == 0 && rr != 0.0) atomicAdd(norms + b, rr);
+  if (threadIdx.x == 0 && rr != 0.f) atomicAdd(norms + b, (double)rr);
+}
+
+// final potential u = base + e for a float-float correction
+__global__ void k_combine_ff(double* __restrict__ base, const float2* __restrict__ e, int n) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
+  const size_t side = n + 2;
+  const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
+  base[c] += (double)e[c].x + (double)e[c].y;
 }
 
 // final potential u = base + e (interior cells)
@@ -570,7 +631,7 @@ struct MG {
   // base (SHT solution + edge values), defect source f' = kappa - L base,
   // ||kappa||^2 per patch, and a zero starting correction
   int setup(const double* kappa_fine) {
-    if (mixed) return setup_t<double>(kappa_fine, (double*)s->fd64.p);
+    if (mixed) return setup_t<float2>(kappa_fine, (float2*)s->fd64.p);
     return setup_t<T>(kappa_fine, F(0));
   }
 
@@ -600,14 +661,15 @@ struct MG {
     return launch_check(ctx, "MG setup");
   }
 
-  // CLC_MIXED: r = f' - L e64 in FP64 (also the next FP32 source), FP32
-  // V-cycle on L d = r from d = 0, e64 += d; u = base + e64 at the end
-  int residual_mixed(const double* e_old, const float* d, double* e_new, double* ratio_host) {
+  // CLC_MIXED: r = f' - L e in float-float (also the next FP32 source), FP32
+  // V-cycle on L d = r from d = 0, e += d; u = base + e at the end
+  int residual_mixed(const float2* e_old, const float* d, float2* e_new, double* ratio_host) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
     const dim3 grid((n + kBX - 1) / kBX, (n + kBY * kRows - 1) / (kBY * kRows), s->npatch);
-    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_mixed, grid, dim3(kBX, kBY), 0, e_old, d, (const double*)s->fd64.p,
-               C64(0), G64(0), n, e_new, (float*)s->f[0].p, (double*)s->norms.p);
+    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_ff, grid, dim3(kBX, kBY), 0, e_old, d, (const float2*)s->fd64.p,
+               (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, n, e_new, (float*)s->f[0].p,
+               (double*)s->norms.p);
     CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
                s->npatch, (double*)s->ratio.p);
     int rc = launch_check(ctx, "MG mixed residual");
@@ -624,8 +686,8 @@ struct MG {
     s->cycles = 0;
     const int n = s->sizes[0];
     const bool fixed = s->p.fixed_cycles > 0;
-    double* cur = (double*)s->e64.p;
-    double* nxt = (double*)s->e64b.p;
+    float2* cur = (float2*)s->e64.p;
+    float2* nxt = (float2*)s->e64b.p;
     if ((rc = residual_mixed(cur, nullptr, nxt, &rr))) return rc;
     std::swap(cur, nxt);
     while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= s->p.tol && s->cycles < s->p.max_cycles)) {
@@ -641,8 +703,8 @@ struct MG {
       ++s->cycles;
     }
     s->residual = rr;
-    CLC_LAUNCH(ctx, "k_combine", k_combine<double>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p,
-               (const double*)cur, n);
+    CLC_LAUNCH(ctx, "k_combine", k_combine_ff, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p,
+               (const float2*)cur, n);
     if ((rc = launch_check(ctx, "MG combine"))) return rc;
     if (!fixed && rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
     return CLC_OK;
@@ -760,6 +822,20 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     };
     ok = put(s->coef[l], s->coef32[l], lc.coef) && put(s->invd[l], s->invd32[l], lc.invd) &&
          put(s->diag[l], s->diag32[l], lc.diag) && put(s->rden[l], s->rden32[l], lc.rden);
+    if (ok && l == 0 && p->precision == CLC_MIXED) {
+      // the finest operator as float-float pairs for the mixed residual
+      auto put_ff = [&](Buffer& bf, const std::vector<double>& v) -> bool {
+        std::vector<float2> w(v.size());
+        for (size_t k = 0; k < v.size(); ++k) {
+          w[k].x = (float)v[k];
+          w[k].y = (float)(v[k] - (double)w[k].x);
+        }
+        if (!alloc(bf, w.size() * sizeof(float2))) return false;
+        cudaMemcpy(bf.p, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        return true;
+      };
+      ok = put_ff(s->coef_ff, lc.coef) && put_ff(s->diag_ff, lc.diag);
+    }
   }
   const size_t n0 = s->sizes[0];
   ok = ok && alloc(s->base, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&

@@ -25,7 +25,8 @@ struct clc_plane_solution {
   clc::Buffer diag[16];         // double[n][n] per level: diagonal
   clc::Buffer rden[16];         // double[n/2] per level: 1 / (2 (area_2I + area_2I+1))
   clc::Buffer coef32[16], invd32[16], diag32[16], rden32[16];  // float copies
-  clc::Buffer e64, e64b, fd64;  // CLC_MIXED: FP64 correction, ping-pong (ghost-ring layout), defect source
+  clc::Buffer e64, e64b, fd64;  // CLC_MIXED: float-float correction, ping-pong (ghost-ring layout), defect source
+  clc::Buffer coef_ff, diag_ff; // CLC_MIXED: finest-level operator coefficients as float-float pairs
   clc::Buffer rot;              // double[npatch][9]: R_b (global -> patch frame)
   clc::Buffer coarse_inv;       // double[nc^2][nc^2]
   clc::Buffer psi_sht;          // double[12 nside_sht^2]
