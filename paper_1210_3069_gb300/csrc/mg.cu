@@ -74,6 +74,13 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   return ff_fast_sum(p, e);
 }
 
+// Position of cell (i, j) in a patch's source array (n x n cells, n even):
+// the red cells ((i + j) even) first, then the black ones, each colour row by
+// row, so that a colour's sweep reads its sources contiguously.
+__host__ __device__ __forceinline__ size_t fidx(int n, int i, int j) {
+  return ((size_t)((i + j) & 1) * n + i) * (size_t)(n >> 1) + (size_t)(j >> 1);
+}
+
 // store a value computed in FP64 in the solver's storage type
 template <typename T>
 __device__ __forceinline__ T from_double(double v) { return (T)v; }
@@ -143,7 +150,7 @@ __global__ void k_mg_setup_defect(int n, const double* __restrict__ rot, const d
     const double src = interp_map_tab(kappa, nf, ring_th, th, ph);
     const double* U = base + (size_t)b * side * side;
     const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
-    f[(size_t)b * n * n + (size_t)i * n + j] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
+    f[(size_t)b * n * n + fidx(n, i, j)] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
     ff = src * src;
   }
   for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
@@ -207,7 +214,7 @@ __global__ void k_mg_setup_defect_plan(int n, const int4* __restrict__ idx, cons
     const int cell = (i + 1) * side + (j + 1);
     const double* U = base + (size_t)b * side * side;
     const double nb = coef[i] * U[cell + side] + coef[n + i] * U[cell - side] + coef[2 * n + i] * (U[cell + 1] + U[cell - 1]);
-    f[pos] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
+    f[(size_t)b * n * n + fidx(n, i, j)] = from_double<T>(src - (nb - diag[i * n + j] * U[cell]));
     ff = src * src;
   }
   for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
@@ -227,7 +234,7 @@ __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __
   const size_t c = (size_t)(i + 1) * side + (j + 1);
   const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
   // (aS uS + aN uN + b (uE + uW) - f) / diag as three fused multiply-adds
-  const T t = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -f[(size_t)b * n * n + (size_t)i * n + j])));
+  const T t = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -f[(size_t)b * n * n + fidx(n, i, j)])));
   U[c] = t * invd[i * n + j];
 }
 
@@ -257,7 +264,7 @@ __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, con
       const T ucv = U[c];
       // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
       const T nb = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -diag[i * n + j] * ucv)));
-      rs += Fb[(size_t)i * n + j] - nb;
+      rs += Fb[fidx(n, i, j)] - nb;
       us += ucv;
     }
     nr = fma(area, rs, nr);
@@ -267,7 +274,7 @@ __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, con
   const T ur = nu * rd;
   uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
   uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
-  fc[(size_t)b * nc * nc + (size_t)I * nc + J] = nr * rd;
+  fc[(size_t)b * nc * nc + fidx(nc, I, J)] = nr * rd;
 }
 
 // f_c += L_c(u_c) (the FAS coarse-grid source)
@@ -281,7 +288,7 @@ __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T
   const T* U = u + (size_t)b * side * side;
   const size_t c = (size_t)(i + 1) * side + (j + 1);
   const T nb = fma(coef[2 * n + i], U[c + 1] + U[c - 1], fma(coef[n + i], U[c - side], fma(coef[i], U[c + side], -diag[i * n + j] * U[c])));
-  T* Fp = f + (size_t)b * n * n + (size_t)i * n + j;
+  T* Fp = f + (size_t)b * n * n + fidx(n, i, j);
   *Fp = *Fp + nb;
 }
 
@@ -337,7 +344,7 @@ __global__ void k_coarse_solve(T* __restrict__ u, const T* __restrict__ f, const
     if (i == 0) g += coef[nc + i] * (double)U[(size_t)i * side + (j + 1)];
     if (j == nc - 1) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + (j + 2)];
     if (j == 0) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + j];
-    rhs[t] = (double)f[b * nn + t] - g;
+    rhs[t] = (double)f[b * nn + fidx(nc, i, j)] - g;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
@@ -360,7 +367,7 @@ __global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, cons
     const size_t c = (size_t)(i + 1) * side + (j + 1);
     const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
                       coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
-    const double r = (double)f[(size_t)b * n * n + (size_t)i * n + j] - (nb - (double)U[c] * diag[i * n + j]);
+    const double r = (double)f[(size_t)b * n * n + fidx(n, i, j)] - (nb - (double)U[c] * diag[i * n + j]);
     rr = r * r;
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -419,7 +426,7 @@ __global__ void k_resid_ff(const float2* __restrict__ e_old, const float* __rest
       // L e = aS eS + aN eN + b (eE + eW) - diag eC
       const float2 nb = ff_add(ff_add(ff_mul(coef[i], eS), ff_mul(coef[n + i], eN)),
                                ff_add(ff_mul(coef[2 * n + i], ff_add(eE, eW)), ff_neg(ff_mul(diag[i * n + j], eC))));
-      const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
+      const size_t pos = (size_t)b * n * n + fidx(n, i, j);
       const float2 r = ff_add(fd[pos], ff_neg(nb));
       r32[pos] = r.x + r.y;
       e_new[(size_t)b * side * side + c] = eC;
