@@ -221,21 +221,34 @@ __global__ void k_mg_setup_defect_plan(int n, const int4* __restrict__ idx, cons
   if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
 }
 
-// One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 == colour.
+// One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 ==
+// colour.  Each thread updates the colour's cell of its column pair in
+// kSmoothRows rows (rows blockIdx.y * kSmoothRows * kBY + k * kBY + threadIdx.y),
+// so that several independent cells' loads are in flight per thread.
+constexpr int kSmoothRows = 4;
+constexpr int kGridRows = 4;     // coarse rows per thread in the prolongation
+constexpr int kRestrictRows = 1; // coarse rows per thread in the restriction
+
 template <typename T>
 __global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ coef,
                          const T* __restrict__ invd, int n, int colour) {
   const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y;
-  const int j = 2 * (blockIdx.x * kBX + threadIdx.x) + ((i + colour) & 1);
-  if (i >= n || j >= n) return;
   const size_t side = n + 2;
   T* U = u + (size_t)b * side * side;
-  const size_t c = (size_t)(i + 1) * side + (j + 1);
-  const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
-  // (aS uS + aN uN + b (uE + uW) - f) / diag as three fused multiply-adds
-  const T t = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -f[(size_t)b * n * n + fidx(n, i, j)])));
-  U[c] = t * invd[i * n + j];
+  const T* Fb = f + (size_t)b * n * n;
+  const int t = blockIdx.x * kBX + threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < kSmoothRows; ++k) {
+    const int i = (blockIdx.y * kSmoothRows + k) * kBY + threadIdx.y;
+    const int j = 2 * t + ((i + colour) & 1);
+    if (i < n && j < n) {
+      const size_t c = (size_t)(i + 1) * side + (j + 1);
+      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
+      // (aS uS + aN uN + b (uE + uW) - f) / diag as three fused multiply-adds
+      const T v = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -Fb[fidx(n, i, j)])));
+      U[c] = v * invd[i * n + j];
+    }
+  }
 }
 
 // FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
@@ -246,35 +259,39 @@ __global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, con
                            T* __restrict__ uc0, T* __restrict__ fc) {
   const int nc = n / 2;
   const int b = blockIdx.z;
-  const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
-  if (I >= nc || J >= nc) return;
+  const int J = blockIdx.x * kBX + threadIdx.x;
   const size_t side = n + 2, sidec = nc + 2;
   const T* U = u + (size_t)b * side * side;
   const T* Fb = f + (size_t)b * n * n;
-  T nr = 0, nu = 0;
 #pragma unroll
-  for (int di = 0; di < 2; ++di) {
-    const int i = 2 * I + di;
-    const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
-    T rs = 0, us = 0;
+  for (int kr = 0; kr < kRestrictRows; ++kr) {
+    const int I = (blockIdx.y * kRestrictRows + kr) * kBY + threadIdx.y;
+    if (I >= nc || J >= nc) continue;
+    T nr = 0, nu = 0;
 #pragma unroll
-    for (int dj = 0; dj < 2; ++dj) {
-      const int j = 2 * J + dj;
-      const size_t c = (size_t)(i + 1) * side + (j + 1);
-      const T ucv = U[c];
-      // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
-      const T nb = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -diag[i * n + j] * ucv)));
-      rs += Fb[fidx(n, i, j)] - nb;
-      us += ucv;
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * I + di;
+      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+      T rs = 0, us = 0;
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = 2 * J + dj;
+        const size_t c = (size_t)(i + 1) * side + (j + 1);
+        const T ucv = U[c];
+        // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
+        const T nb = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -diag[i * n + j] * ucv)));
+        rs += Fb[fidx(n, i, j)] - nb;
+        us += ucv;
+      }
+      nr = fma(area, rs, nr);
+      nu = fma(area, us, nu);
     }
-    nr = fma(area, rs, nr);
-    nu = fma(area, us, nu);
+    const T rd = rden[I];   // 1 / (2 (area_{2I} + area_{2I+1}))
+    const T ur = nu * rd;
+    uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+    uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
+    fc[(size_t)b * nc * nc + fidx(nc, I, J)] = nr * rd;
   }
-  const T rd = rden[I];   // 1 / (2 (area_{2I} + area_{2I+1}))
-  const T ur = nu * rd;
-  uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
-  uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
-  fc[(size_t)b * nc * nc + fidx(nc, I, J)] = nr * rd;
 }
 
 // f_c += L_c(u_c) (the FAS coarse-grid source)
@@ -298,33 +315,37 @@ template <typename T>
 __global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n) {
   const int nc = n / 2;
   const int b = blockIdx.z;
-  const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
-  if (I >= nc || J >= nc) return;
+  const int J = blockIdx.x * kBX + threadIdx.x;
   const size_t side = n + 2, sidec = nc + 2;
   const T* C = uc + (size_t)b * sidec * sidec;
   const T* C0 = uc0 + (size_t)b * nc * nc;
-  T e[3][3];
-#pragma unroll
-  for (int di = -1; di <= 1; ++di)
-#pragma unroll
-    for (int dj = -1; dj <= 1; ++dj) {
-      const int a = min(max(I + di, 0), nc - 1), c = min(max(J + dj, 0), nc - 1);
-      e[di + 1][dj + 1] = C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c];
-    }
   T* U = u + (size_t)b * side * side;
 #pragma unroll
-  for (int fa = 0; fa < 2; ++fa)
+  for (int kr = 0; kr < kGridRows; ++kr) {
+    const int I = (blockIdx.y * kGridRows + kr) * kBY + threadIdx.y;
+    if (I >= nc || J >= nc) continue;
+    T e[3][3];
 #pragma unroll
-    for (int fc = 0; fc < 2; ++fc) {
-      const int i = 2 * I + fa, j = 2 * J + fc;
-      const int di = fa ? 2 : 0, dj = fc ? 2 : 0;   // neighbour index in e[][]
-      T corr;
-      if (i == 0 || j == 0 || i == n - 1 || j == n - 1)
-        corr = e[1][1];
-      else
-        corr = fma((T)9, e[1][1], fma((T)3, e[di][1] + e[1][dj], e[di][dj])) * (T)0.0625;
-      U[(size_t)(i + 1) * side + (j + 1)] += corr;
-    }
+    for (int di = -1; di <= 1; ++di)
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj) {
+        const int a = min(max(I + di, 0), nc - 1), c = min(max(J + dj, 0), nc - 1);
+        e[di + 1][dj + 1] = C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c];
+      }
+#pragma unroll
+    for (int fa = 0; fa < 2; ++fa)
+#pragma unroll
+      for (int fc = 0; fc < 2; ++fc) {
+        const int i = 2 * I + fa, j = 2 * J + fc;
+        const int di = fa ? 2 : 0, dj = fc ? 2 : 0;   // neighbour index in e[][]
+        T corr;
+        if (i == 0 || j == 0 || i == n - 1 || j == n - 1)
+          corr = e[1][1];
+        else
+          corr = fma((T)9, e[1][1], fma((T)3, e[di][1] + e[1][dj], e[di][dj])) * (T)0.0625;
+        U[(size_t)(i + 1) * side + (j + 1)] += corr;
+      }
+  }
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -597,8 +618,9 @@ struct MG {
     const int n = s->sizes[l];
     for (int k = 0; k < nu; ++k)
       for (int colour = 0; colour < 2; ++colour)
-        CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>, grid3(n / 2, n, s->npatch), dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l),
-                   n, colour);
+        CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>,
+                   dim3((n / 2 + kBX - 1) / kBX, (n + kBY * kSmoothRows - 1) / (kBY * kSmoothRows), s->npatch),
+                   dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l), n, colour);
   }
 
   void vcycle(int l) {
@@ -611,12 +633,14 @@ struct MG {
     }
     smooth(l, s->p.nu1);
     const int nc = n / 2;
-    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), F(l), C(l), G(l), RD(l), n,
-               U(l + 1), U0(l + 1), F(l + 1));
+    const dim3 gr((nc + kBX - 1) / kBX, (nc + kBY * kRestrictRows - 1) / (kBY * kRestrictRows), s->npatch);
+    const dim3 gp((nc + kBX - 1) / kBX, (nc + kBY * kGridRows - 1) / (kBY * kGridRows), s->npatch);
+    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, gr, blk, 0, U(l), F(l), C(l), G(l), RD(l), n, U(l + 1), U0(l + 1),
+               F(l + 1));
     CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
                G(l + 1), nc);
     vcycle(l + 1);
-    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, grid3(nc, nc, s->npatch), blk, 0, U(l), U(l + 1), U0(l + 1), n);
+    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, gp, blk, 0, U(l), U(l + 1), U0(l + 1), n);
     smooth(l, s->p.nu2);
   }
 
