@@ -474,8 +474,11 @@ __global__ void k_tc_pack_synthesis(TcBatchDev b) {
 // warps then add the chunk into a running sum held in a second TMEM region
 // with round-to-nearest FP32 adds, and release the chunk accumulator.
 // Warps 0-3: epilogue (TMEM lanes 32w..32w+31), warp 4: bulk-copy producer,
-// warp 5: MMA issuer.  TMEM columns: chunk [0, W), sum [W, 2W), W = N
-// (analysis) or 2N (synthesis, parity p at p N).
+// warp 5: MMA issuer.  TMEM columns: chunk [0, W), sum [W, 2W), W = Nmax
+// (analysis) or 2 Nmax (synthesis, parity p at p Nmax), Nmax the widest
+// operand of the launch: the next item's first chunk may be accumulating
+// while the epilogue still reads the previous item's sums, so the regions
+// must not move with the width of the item.
 
 constexpr int kFlush = 2;   // pipeline stages per TMEM accumulation chunk
 
@@ -507,7 +510,7 @@ struct GemmItem {
 
 template <bool kSyn>
 __global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __restrict__ items, int nitems, int S,
-                                                 int bB, int tcols, int* d_err) {
+                                                 int bB, int nmax, int tcols, int* d_err) {
   extern __shared__ __align__(16) uint8_t smem_g[];
   __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], chunkb, freeb, drainb;
   __shared__ uint32_t tmem_base;
@@ -611,7 +614,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __res
           uint8_t* st = base + (size_t)s * stage_bytes;
           const uint32_t sa = umma::smem_u32(st), sb = umma::smem_u32(st + 32768);
           const int p = (kSyn && k >= gi.K0) ? 1 : 0;
-          const uint32_t td = tmem + (uint32_t)(p * N);
+          const uint32_t td = tmem + (uint32_t)(p * nmax);
           uint64_t dAh, dAl;
           if (kSyn) {
             dAh = umma::desc_sw128_mn(sa, 8192, 1024);
@@ -651,7 +654,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __res
       GemmItem<kSyn> gi;
       gi.init(b, w);
       const int N = gi.N;
-      const uint32_t W = kSyn ? 2u * N : (uint32_t)N;
+      const uint32_t W = kSyn ? 2u * (uint32_t)nmax : (uint32_t)nmax;
       bool ok = true;
       for (int c = 0; c < gi.nch; ++c, ++nchunk) {
         // warp-uniform decision: the TMEM accesses below are whole-warp operations
@@ -664,7 +667,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __res
         umma::fence_after_sync();
         const int p = c < gi.nch0 ? 0 : 1;
         const bool first = c == 0 || c == gi.nch0;
-        const uint32_t cc = (uint32_t)(p * N), sc = W + (uint32_t)(p * N);
+        const uint32_t cc = (uint32_t)(p * nmax), sc = W + (uint32_t)(p * nmax);
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           umma::tmem_ld16(trow + cc + (uint32_t)c0, v);
@@ -710,7 +713,7 @@ __global__ void __launch_bounds__(192) k_tc_gemm(TcBatchDev b, const int4* __res
         for (int c0 = 0; c0 < N; c0 += 16) {
           float ve[16], vo[16];
           umma::tmem_ld16(trow + W + (uint32_t)c0, ve);
-          umma::tmem_ld16(trow + W + (uint32_t)(N + c0), vo);
+          umma::tmem_ld16(trow + W + (uint32_t)(nmax + c0), vo);
 #pragma unroll
           for (int c = 0; c < 16; c += 2) {
             const int qp = (c0 + c) >> 1;
@@ -822,7 +825,7 @@ int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcL
       const int tcols = pow2_cols(2 * it.na_max);
       const int g = grid_of(ctx, k_tc_gemm<false>, 192, smem, it.n_an, std::min(L.an_ctas, 512 / tcols));
       CLC_LAUNCH(ctx, "k_tc_analysis", (k_tc_gemm<false>), g, 192, smem, b, (const int4*)it.an.p, it.n_an,
-                 L.an_stages, bB, tcols, ctx->d_err);
+                 L.an_stages, bB, it.na_max, tcols, ctx->d_err);
       return launch_check(ctx, "k_tc_analysis");
     }
     case 3: {
@@ -844,7 +847,7 @@ int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcL
       const int tcols = pow2_cols(4 * it.ns_max);
       const int g = grid_of(ctx, k_tc_gemm<true>, 192, smem, it.n_sy, std::min(L.sy_ctas, 512 / tcols));
       CLC_LAUNCH(ctx, "k_tc_synthesis", (k_tc_gemm<true>), g, 192, smem, b, (const int4*)it.sy.p, it.n_sy,
-                 L.sy_stages, bB, tcols, ctx->d_err);
+                 L.sy_stages, bB, it.ns_max, tcols, ctx->d_err);
       return launch_check(ctx, "k_tc_synthesis");
     }
     default: {

@@ -187,6 +187,32 @@ def test_plan_mixed_sizes_graph_and_tuning():
     plan.close()
 
 
+@pytest.mark.parametrize("order", ["narrow_first", "wide_first"])
+def test_plan_classes_of_different_widths_match_single_planes(order):
+    """A class of few planes with long contractions (8 planes, 48 operand
+    columns) beside a class of many planes with short ones (21 planes, 128
+    columns): the work lists interleave items of both widths on each CTA.
+    Every plane must come out exactly as the single-plane tensor-core solve
+    gives it: the per-column arithmetic is the same, only the batching
+    differs."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    narrow, wide = [(512, 1024)] * 8, [(256, 512)] * 21
+    sizes = narrow + wide if order == "narrow_first" else wide + narrow
+    kappas = [_planes(ns, 1, seed0=3000 + i)[0].cuda() for i, (ns, _) in enumerate(sizes)]
+    outs = [{k: torch.empty(hp.npix(ns), dtype=torch.float64, device="cuda") for k in FIELDS} for ns, _ in sizes]
+    plan = c.sht_plan([s[0] for s in sizes], [s[1] for s in sizes], derivatives=True)
+    plan.execute(kappas, outs)
+    c.sync()
+    plan.close()
+    for i in sorted({0, 7, 8, 20, len(sizes) - 1}):
+        ns, L = sizes[i]
+        ref = c.poisson_sht(kappas[i], ns, L, precision=clc.MIXED)
+        c.sync()
+        for k in FIELDS:
+            assert rel_l2(outs[i][k], ref[k]) <= 1e-13, (order, i, k, rel_l2(outs[i][k], ref[k]))
+
+
 def test_plan_splits_large_classes():
     """23 planes of one size with derivatives: two classes (21 + 2) in one plan."""
     import paper_1210_3069_gb300 as clc
