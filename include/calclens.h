@@ -133,6 +133,13 @@ int clc_degrade(clc_ctx* ctx, const double* map_fine, int nside_fine, double* ma
 /* ------------------------------------------------------------------------ */
 /* Step 2: spherical-harmonic transforms and the SHT Poisson solve (Sec. 3.2) */
 
+/* Limit the FP64 Legendre table (sum over m of (lmax + 2 - m) * 2 nside
+ * doubles; 262 GB at nside 2048, lmax 4096) to `bytes` (0 = the free device
+ * memory decides).  Larger tables are built and used one order range m0..m1
+ * at a time inside each FP64 SHT call (same results; the recurrence is then
+ * recomputed per call). */
+int clc_set_table_budget(clc_ctx* ctx, size_t bytes);
+
 /* a_lm = (4 pi / Npix) sum_p map[p] Y*_lm(p) (uniform quadrature). */
 int clc_sht_analysis(clc_ctx* ctx, const double* map, int nside, int lmax, double* alm);
 /* map[p] = sum_lm a_lm Y_lm(p) for a real field (m < 0 implied). */

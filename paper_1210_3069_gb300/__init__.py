@@ -57,6 +57,7 @@ _SIGS = {
     "clc_bin_particles": (_i, [_p, _p, _p, _i64, _i, _i, _p]),
     "clc_counts_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
     "clc_degrade": (_i, [_p, _p, _i, _p, _i]),
+    "clc_set_table_budget": (_i, [_p, ctypes.c_size_t]),
     "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
     "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
     "clc_poisson_sht": (_i, [_p, _p, _i, _i, _i, _p, ctypes.POINTER(Derivs)]),
@@ -203,6 +204,11 @@ class Context:
         alm = torch.empty((lmax + 1) * (lmax + 2) // 2, dtype=torch.complex128, device=self.device)
         self._check(lib().clc_sht_analysis(self.h, _ptr(m), nside, lmax, _ptr(alm)))
         return alm
+
+    def set_table_budget(self, nbytes):
+        """Limit the FP64 Legendre table to nbytes (0: automatic); larger
+        tables are processed one order range at a time."""
+        self._check(lib().clc_set_table_budget(self.h, int(nbytes)))
 
     def sht_synthesis(self, alm, nside, lmax):
         out = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)

@@ -48,6 +48,7 @@ struct clc_ctx {
   std::map<int, std::shared_ptr<clc::FftPlan>> fft_plans;
   std::map<std::tuple<int, int, int>, std::shared_ptr<clc::LegendreTable>> leg_tables;
   std::map<std::pair<int, int>, std::shared_ptr<clc::TcTable>> tc_tables;
+  size_t table_budget = 0;  // FP64 Legendre table limit in bytes (0: device memory decides)
   std::map<std::tuple<int, int, int, int>, std::shared_ptr<clc::TcBatch>> tc_batches;
   // growable scratch buffers, reused across calls on this context's stream
   clc::Buffer scratch[8];

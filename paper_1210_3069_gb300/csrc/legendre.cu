@@ -26,14 +26,14 @@ __device__ __forceinline__ double scale_pow2(double p, int e) {
 
 __global__ void k_legendre_build(int nside, int lmax, int R, const long long* __restrict__ off,
                                  const double* __restrict__ lognorm, const double2* __restrict__ ab,
-                                 double* __restrict__ tab) {
-  const int m = blockIdx.y;
+                                 double* __restrict__ tab, int m0) {
+  const int m = m0 + blockIdx.y;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= R) return;
   const Ring g = ring_geom(nside, r + 1);
   const double z = g.z;
   const int lt = lmax + 1;  // table band limit
-  double* col = tab + off[m];
+  double* col = tab + off[m - m0];
   const double l2 = lognorm[m] + (double)m * log2(g.s);
   int e = (int)floor(l2);
   double p2 = exp2(l2 - (double)e);
@@ -57,32 +57,32 @@ __global__ void k_legendre_build(int nside, int lmax, int R, const long long* __
   }
 }
 
-std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int lmax, int* rc) {
-  const auto key = std::make_tuple(nside, lmax, 0);
-  auto it = ctx->leg_tables.find(key);
-  if (it != ctx->leg_tables.end()) {
-    *rc = CLC_OK;
-    return it->second;
-  }
-  auto T = std::make_shared<LegendreTable>();
+size_t legendre_table_bytes(int nside, int lmax, int m0, int m1) {
+  const int lt = lmax + 1;
+  size_t e = 0;
+  for (int m = m0; m < m1; ++m) e += (size_t)(lt - m + 1) * 2 * nside;
+  return e * sizeof(double);
+}
+
+int build_legendre_table(clc_ctx* ctx, int nside, int lmax, int m0, int m1, LegendreTable* T) {
   T->nside = nside;
   T->lmax = lmax;
   T->R = 2 * nside;
+  T->m0 = m0;
+  T->m1 = m1;
   const int lt = lmax + 1;
-  T->h_offsets.resize(lmax + 1);
+  T->h_offsets.resize(m1 - m0);
   long long acc = 0;
-  for (int m = 0; m <= lmax; ++m) {
-    T->h_offsets[m] = acc;
+  for (int m = m0; m < m1; ++m) {
+    T->h_offsets[m - m0] = acc;
     acc += (long long)(lt - m + 1) * T->R;
   }
   T->elems = (size_t)acc;
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
   const size_t bytes = T->elems * sizeof(double);
-  if (bytes + (size_t)(1ull << 30) > freeb) {
-    *rc = set_err(ctx, CLC_ENOMEM, "Legendre table of " + std::to_string(bytes >> 20) + " MiB does not fit");
-    return nullptr;
-  }
+  if (bytes + (size_t)(1ull << 30) > freeb)
+    return set_err(ctx, CLC_ENOMEM, "Legendre table of " + std::to_string(bytes >> 20) + " MiB does not fit");
   // recurrence coefficients a_lm = sqrt((4l^2 - 1) / (l^2 - m^2)),
   // b_lm = sqrt(((l-1)^2 - m^2) / (4 (l-1)^2 - 1)), packed with band limit lt
   std::vector<double2> ab((size_t)alm_idx(lt, lt, lt) + 1);
@@ -112,20 +112,31 @@ std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int l
     }
     return true;
   };
-  if (!alloc(T->data, bytes) || !alloc(T->offsets, sizeof(long long) * (lmax + 1)) ||
-      !alloc(d_ab, sizeof(double2) * ab.size()) || !alloc(d_ln, sizeof(double) * lognorm.size())) {
-    *rc = set_err(ctx, CLC_ENOMEM, "Legendre table allocation failed");
-    return nullptr;
-  }
-  cudaMemcpyAsync(T->offsets.p, T->h_offsets.data(), sizeof(long long) * (lmax + 1), cudaMemcpyHostToDevice, ctx->stream);
+  if (!alloc(T->data, bytes) || !alloc(T->offsets, sizeof(long long) * (m1 - m0)) ||
+      !alloc(d_ab, sizeof(double2) * ab.size()) || !alloc(d_ln, sizeof(double) * lognorm.size()))
+    return set_err(ctx, CLC_ENOMEM, "Legendre table allocation failed");
+  cudaMemcpyAsync(T->offsets.p, T->h_offsets.data(), sizeof(long long) * (m1 - m0), cudaMemcpyHostToDevice,
+                  ctx->stream);
   cudaMemcpyAsync(d_ab.p, ab.data(), sizeof(double2) * ab.size(), cudaMemcpyHostToDevice, ctx->stream);
   cudaMemcpyAsync(d_ln.p, lognorm.data(), sizeof(double) * lognorm.size(), cudaMemcpyHostToDevice, ctx->stream);
-  dim3 grid((T->R + 127) / 128, lmax + 1);
+  dim3 grid((T->R + 127) / 128, m1 - m0);
   CLC_LAUNCH(ctx, "k_legendre_build", k_legendre_build, grid, 128, 0, nside, lmax, T->R, (const long long*)T->offsets.p,
-                                                  (const double*)d_ln.p, (const double2*)d_ab.p, (double*)T->data.p);
-  *rc = launch_check(ctx, "k_legendre_build");
+             (const double*)d_ln.p, (const double2*)d_ab.p, (double*)T->data.p, m0);
+  const int rc = launch_check(ctx, "k_legendre_build");
   // the coefficient buffers are freed when this function returns: wait for the build
   cudaStreamSynchronize(ctx->stream);
+  return rc;
+}
+
+std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int lmax, int* rc) {
+  const auto key = std::make_tuple(nside, lmax, 0);
+  auto it = ctx->leg_tables.find(key);
+  if (it != ctx->leg_tables.end()) {
+    *rc = CLC_OK;
+    return it->second;
+  }
+  auto T = std::make_shared<LegendreTable>();
+  *rc = build_legendre_table(ctx, nside, lmax, 0, lmax + 1, T.get());
   if (*rc) return nullptr;
   ctx->leg_tables[key] = T;
   return T;
@@ -134,9 +145,9 @@ std::shared_ptr<LegendreTable> get_legendre_table(clc_ctx* ctx, int nside, int l
 // Block (l-block, m): 8 warps, each warp one l at a time; lanes over rings.
 __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long* __restrict__ off,
                                     const double* __restrict__ tab, const double2* __restrict__ F, int ldf,
-                                    double2* __restrict__ alm, int ltop, int lpack) {
+                                    double2* __restrict__ alm, int ltop, int lpack, int m0) {
   extern __shared__ double2 V[];  // V[0..R) even (N + S), V[R..2R) odd (N - S)
-  const int m = blockIdx.y;
+  const int m = m0 + blockIdx.y;
   const int l0 = m + blockIdx.x * 64;
   if (l0 > ltop) return;
   const double2* Fm = F + (size_t)m * ldf;
@@ -150,7 +161,7 @@ __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long*
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const double* col = tab + off[m];
+  const double* col = tab + off[m - m0];
   for (int l = l0 + warp; l <= ltop && l < l0 + 64; l += 8) {
     const double* row = col + (size_t)(l - m) * R;
     const double2* v = V + (((l + m) & 1) ? R : 0);
@@ -172,11 +183,11 @@ __global__ void k_legendre_analysis(int nside, int lmax, int R, const long long*
 int legendre_analysis(clc_ctx* ctx, const LegendreTable& T, const double2* F, int ldf, double2* alm, int ltop) {
   const int L = T.lmax;
   if (ltop < 0) ltop = L;
-  dim3 grid((ltop + 1 + 63) / 64, L + 1);
+  dim3 grid((ltop + 1 + 63) / 64, T.m1 - T.m0);
   const int smem = 2 * T.R * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_analysis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   CLC_LAUNCH(ctx, "k_legendre_analysis", k_legendre_analysis, grid, 256, smem, T.nside, L, T.R, (const long long*)T.offsets.p,
-                                                        (const double*)T.data.p, F, ldf, alm, ltop, ltop);
+                                                        (const double*)T.data.p, F, ldf, alm, ltop, ltop, T.m0);
   return launch_check(ctx, "k_legendre_analysis");
 }
 
@@ -189,9 +200,10 @@ struct SynthRhs {
 // Block (ring chunk, m); thread per northern ring; the alm columns of this m
 // are staged in shared memory.
 __global__ void k_legendre_synthesis(int nside, int lmax, int R, const long long* __restrict__ off,
-                                     const double* __restrict__ tab, SynthRhs s, double2* __restrict__ G, int ld) {
+                                     const double* __restrict__ tab, SynthRhs s, double2* __restrict__ G, int ld,
+                                     int m0) {
   extern __shared__ double2 A[];  // A[q * (lt - m + 1) + (l - m)]
-  const int m = blockIdx.y;
+  const int m = m0 + blockIdx.y;
   const int lt = lmax + 1;
   const int nl = lt - m + 1;
   for (int t = threadIdx.x; t < s.nq * nl; t += blockDim.x) {
@@ -204,7 +216,7 @@ __global__ void k_legendre_synthesis(int nside, int lmax, int R, const long long
   if (r >= R) return;
   int lmax_used = 0;
   for (int q = 0; q < s.nq; ++q) lmax_used = max(lmax_used, s.lq[q]);
-  const double* col = tab + off[m];
+  const double* col = tab + off[m - m0];
   double acc[3][2][2];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -243,11 +255,11 @@ int legendre_synthesis(clc_ctx* ctx, const LegendreTable& T, const double2* rhs,
   s.rhs = rhs;
   s.nq = nq;
   for (int q = 0; q < 3; ++q) s.lq[q] = q < nq ? lq[q] : 0;
-  dim3 grid((T.R + 127) / 128, L + 1);
+  dim3 grid((T.R + 127) / 128, T.m1 - T.m0);
   const int smem = nq * (L + 2) * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   CLC_LAUNCH(ctx, "k_legendre_synthesis", k_legendre_synthesis, grid, 128, smem, T.nside, L, T.R, (const long long*)T.offsets.p,
-                                                         (const double*)T.data.p, s, G, ld);
+                                                         (const double*)T.data.p, s, G, ld, T.m0);
   return launch_check(ctx, "k_legendre_synthesis");
 }
 

@@ -7,6 +7,8 @@
 // phi derivatives multiply the ring Fourier coefficients by i m, and the
 // theta-theta component of the Hessian follows from the Laplacian:
 // U_tt = kappa_bl - U_pp with kappa_bl = sum -l(l+1) psi_lm Y_lm.
+#include <algorithm>
+
 #include "fft.cuh"
 #include "legendre.cuh"
 
@@ -17,8 +19,9 @@ int poisson_sht_tc(clc_ctx* ctx, const double* const* kappa, int P, int nside, i
 
 // rhs_0 = psi_lm, rhs_1 = b_lm (l <= lmax + 1), rhs_2 = -l(l+1) psi_lm, all
 // packed with band limit lmax + 1.
-__global__ void k_poisson_rhs(const double2* __restrict__ klm, int lmax, double2* __restrict__ rhs, long long Q) {
-  const int m = blockIdx.y;
+__global__ void k_poisson_rhs(const double2* __restrict__ klm, int lmax, double2* __restrict__ rhs, long long Q,
+                              int m0) {
+  const int m = m0 + blockIdx.y;
   const int lt = lmax + 1;
   const int l = m + blockIdx.x * blockDim.x + threadIdx.x;
   if (l > lt) return;
@@ -60,19 +63,55 @@ static int check_sht_args(clc_ctx* ctx, int nside, int lmax, const char* who) {
   return CLC_OK;
 }
 
+// Run fn on FP64 Legendre tables covering every order m <= lmax: the cached
+// whole table when it fits in device memory, otherwise tables of consecutive
+// order ranges built one after the other (each freed before the next; the
+// recurrence cost is then paid per call).
+template <typename Fn>
+static int for_each_table(clc_ctx* ctx, int nside, int lmax, Fn fn) {
+  int rc;
+  const bool cached = ctx->leg_tables.count(std::make_tuple(nside, lmax, 0)) > 0;
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  const size_t whole = legendre_table_bytes(nside, lmax, 0, lmax + 1);
+  const bool limited = ctx->table_budget > 0 && whole > ctx->table_budget;
+  if (!limited && (cached || whole + (2ull << 30) <= freeb)) {
+    auto T = get_legendre_table(ctx, nside, lmax, &rc);
+    if (rc) return rc;
+    return fn(*T);
+  }
+  size_t budget = std::min<size_t>(freeb > (8ull << 30) ? freeb - (8ull << 30) : (freeb / 2), 48ull << 30);
+  if (ctx->table_budget > 0) budget = std::min(budget, ctx->table_budget);
+  int m0 = 0;
+  while (m0 <= lmax) {
+    int m1 = m0 + 1;
+    size_t b = legendre_table_bytes(nside, lmax, m0, m1);
+    while (m1 <= lmax) {
+      const size_t nb = legendre_table_bytes(nside, lmax, m1, m1 + 1);
+      if (b + nb > budget) break;
+      b += nb;
+      ++m1;
+    }
+    LegendreTable T;
+    if ((rc = build_legendre_table(ctx, nside, lmax, m0, m1, &T))) return rc;
+    if ((rc = fn(T))) return rc;
+    if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "table chunk"))) return rc;
+    m0 = m1;
+  }
+  return CLC_OK;
+}
+
 // analysis into a device alm buffer (band limit lmax)
 int sht_analysis(clc_ctx* ctx, const double* map, int nside, int lmax, double2* alm) {
   int rc;
   auto plan = get_fft_plan(ctx, nside, &rc);
-  if (rc) return rc;
-  auto T = get_legendre_table(ctx, nside, lmax, &rc);
   if (rc) return rc;
   const int ldf = 4 * nside - 1;
   double2* F = (double2*)scratch(ctx, 0, sizeof(double2) * (size_t)ldf * (lmax + 1));
   if (!F) return CLC_ENOMEM;
   const double w = 4.0 * kPi / (12.0 * (double)nside * nside);
   if ((rc = ring_analysis(ctx, *plan, map, lmax, w, F, ldf))) return rc;
-  return legendre_analysis(ctx, *T, F, ldf, alm);
+  return for_each_table(ctx, nside, lmax, [&](const LegendreTable& T) { return legendre_analysis(ctx, T, F, ldf, alm); });
 }
 
 // synthesis of nq right-hand sides (lmax + 1 packing) and the ring FFTs
@@ -81,18 +120,24 @@ int sht_synthesis_rhs(clc_ctx* ctx, const double2* rhs, int nq, const int* lq, i
   int rc;
   auto plan = get_fft_plan(ctx, nside, &rc);
   if (rc) return rc;
-  auto T = get_legendre_table(ctx, nside, lmax, &rc);
-  if (rc) return rc;
   const int ld = 4 * nside - 1;
   double2* G = (double2*)scratch(ctx, 3, sizeof(double2) * (size_t)nq * ld * (lmax + 2));
   if (!G) return CLC_ENOMEM;
-  if ((rc = legendre_synthesis(ctx, *T, rhs, nq, lq, G, ld))) return rc;
+  if ((rc = for_each_table(ctx, nside, lmax,
+                           [&](const LegendreTable& T) { return legendre_synthesis(ctx, T, rhs, nq, lq, G, ld); })))
+    return rc;
   return ring_synthesis(ctx, *plan, G, ld, lmax, mode, out);
 }
 
 }  // namespace clc
 
 using namespace clc;
+
+extern "C" int clc_set_table_budget(clc_ctx* ctx, size_t bytes) {
+  if (!ctx) return CLC_EINVAL;
+  ctx->table_budget = bytes;
+  return CLC_OK;
+}
 
 extern "C" int clc_sht_analysis(clc_ctx* ctx, const double* map, int nside, int lmax, double* alm) {
   if (!ctx) return CLC_EINVAL;
@@ -134,19 +179,35 @@ extern "C" int clc_poisson_sht(clc_ctx* ctx, const double* kappa, int nside, int
   if (precision == CLC_MIXED) return poisson_sht_tc(ctx, &kappa, 1, nside, lmax, &psi, derivs ? d : nullptr);
   double2* klm = (double2*)scratch(ctx, 1, sizeof(double2) * (alm_idx(lmax, lmax, lmax) + 1));
   if (!klm) return CLC_ENOMEM;
-  if ((rc = sht_analysis(ctx, kappa, nside, lmax, klm))) return rc;
   const long long Q = alm_idx(lmax + 1, lmax + 1, lmax + 1) + 1;
   double2* rhs = (double2*)scratch(ctx, 2, sizeof(double2) * Q * 3);
   if (!rhs) return CLC_ENOMEM;
-  dim3 grid((lmax + 2 + 127) / 128, lmax + 1);
-  CLC_LAUNCH(ctx, "k_poisson_rhs", k_poisson_rhs, grid, 128, 0, klm, lmax, rhs, Q);
-  if ((rc = launch_check(ctx, "k_poisson_rhs"))) return rc;
+  auto plan = get_fft_plan(ctx, nside, &rc);
+  if (rc) return rc;
+  const int ld = 4 * nside - 1;
+  double2* F = (double2*)scratch(ctx, 0, sizeof(double2) * (size_t)ld * (lmax + 1));
+  if (!F) return CLC_ENOMEM;
+  const int nq = derivs ? 3 : 1;
+  double2* G = (double2*)scratch(ctx, 3, sizeof(double2) * (size_t)nq * ld * (lmax + 2));
+  if (!G) return CLC_ENOMEM;
+  const double w = 4.0 * kPi / (12.0 * (double)nside * nside);
+  if ((rc = ring_analysis(ctx, *plan, kappa, lmax, w, F, ld))) return rc;
+  const int lq1[1] = {lmax};
+  const int lq3[3] = {lmax, lmax + 1, lmax};
+  // per table (or order range): analysis, Poisson right-hand sides, synthesis
+  rc = for_each_table(ctx, nside, lmax, [&](const LegendreTable& T) {
+    int r = legendre_analysis(ctx, T, F, ld, klm);
+    if (r) return r;
+    dim3 grid((lmax + 2 + 127) / 128, T.m1 - T.m0);
+    CLC_LAUNCH(ctx, "k_poisson_rhs", k_poisson_rhs, grid, 128, 0, klm, lmax, rhs, Q, T.m0);
+    if ((r = launch_check(ctx, "k_poisson_rhs"))) return r;
+    return legendre_synthesis(ctx, T, rhs, nq, derivs ? lq3 : lq1, G, ld);
+  });
+  if (rc) return rc;
   if (!derivs) {
-    const int lq[1] = {lmax};
     double* out[6] = {psi, nullptr, nullptr, nullptr, nullptr, nullptr};
-    return sht_synthesis_rhs(ctx, rhs, 1, lq, nside, lmax, 0, out);
+    return ring_synthesis(ctx, *plan, G, ld, lmax, 0, out);
   }
-  const int lq[3] = {lmax, lmax + 1, lmax};
   double* out[6] = {psi, d->a_th, d->a_ph, d->u_tt, d->u_pp, d->u_tp};
-  return sht_synthesis_rhs(ctx, rhs, 3, lq, nside, lmax, 1, out);
+  return ring_synthesis(ctx, *plan, G, ld, lmax, 1, out);
 }
