@@ -70,7 +70,7 @@ typedef struct clc_mg_params {
   int lmax;         /* SHT band limit, lmax <= 4 nside_sht                   */
   int nside_bundle; /* Nside of the bundle cells; one MG patch per bundle    */
   int ncell;        /* cells per patch side on the finest level (power of 2, >= 16) */
-  int nu1, nu2;     /* red-black Gauss-Seidel sweeps before / after the coarse step */
+  int nu1, nu2;     /* red-black Gauss-Seidel sweeps before / after the coarse step, 0..8, sum >= 1 */
   int max_cycles;   /* V-cycle cap when iterating to tol                     */
   int fixed_cycles; /* > 0: run exactly this many V-cycles, ignore tol       */
   double tol;       /* stop when max over patches ||f - L u||_2 / ||f||_2 < tol */

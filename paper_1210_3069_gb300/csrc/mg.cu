@@ -221,76 +221,210 @@ __global__ void k_mg_setup_defect_plan(int n, const int4* __restrict__ idx, cons
   if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
 }
 
-// One colour of a red-black Gauss-Seidel sweep: cells with (i + j) % 2 ==
-// colour.  Each thread updates the colour's cell of its column pair in
-// kSmoothRows rows (rows blockIdx.y * kSmoothRows * kBY + k * kBY + threadIdx.y),
-// so that several independent cells' loads are in flight per thread.
-constexpr int kSmoothRows = 4;
-constexpr int kGridRows = 4;     // coarse rows per thread in the prolongation
-constexpr int kRestrictRows = 1; // coarse rows per thread in the restriction
+// ---------------------------------------------------------------------------
+// Fused tile kernels of the V-cycle (red-black Gauss-Seidel, FAS restriction
+// and prolongation of Sec. 3.2).  A CTA owns a kTile x kTile block of one
+// patch (the whole patch when n < kTile) and stages the block with a halo of
+// cells in shared memory, the two colours in separate arrays (region cell
+// (r, c) at [(r + c) & 1][r][c / 2]).  Half-sweep h of a kernel updates the
+// colour's cells of the region shrunk to halo - 1 - h cells around the block,
+// so every value it reads is exact for that half-sweep: after the last one
+// the block (and in the pre-smoothing kernel one more ring of cells) holds
+// the values that the same half-sweeps over the whole patch give.  The
+// arithmetic per cell is that of a plain sweep.  The kernels read the
+// correction from one buffer and write their block to the other (the halo
+// belongs to neighbouring CTAs, which may already have finished).
+
+constexpr int kTile = 64;       // cells per block side
+constexpr int kMaxSweeps = 8;   // nu1, nu2 limit (halo 2 nu + 1 <= 17 cells)
 
 template <typename T>
-__global__ void k_smooth(T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ coef,
-                         const T* __restrict__ invd, int n, int colour) {
-  const int b = blockIdx.z;
+struct alignas(4 * sizeof(T)) Quad {
+  T x, y, z, w;
+};
+
+template <typename T>
+struct Tile {
+  Quad<T>* ra;   // per region row: aS, aN, b, 1 / diagonal (interior columns)
+  Quad<T>* rb;   // per region row: 1 / diagonal (edge columns), diagonal (interior), diagonal (edge), area
+  T* u;          // [2][W][W / 2]
+  T* f;          // [2][W][W / 2]
+  int n, W, hw, gi0, gj0;
+  __device__ __forceinline__ int at(int r, int c) const { return (((r + c) & 1) * W + r) * hw + (c >> 1); }
+};
+
+__host__ __device__ constexpr int tile_side(int n) { return n < kTile ? n : kTile; }
+
+template <typename T>
+__host__ __device__ constexpr size_t tile_smem(int n, int halo) {
+  return 2 * (size_t)(tile_side(n) + 2 * halo) * sizeof(Quad<T>) +
+         2 * (size_t)(tile_side(n) + 2 * halo) * (tile_side(n) + 2 * halo) * sizeof(T);
+}
+
+template <typename T>
+__device__ __forceinline__ Tile<T> tile_carve(unsigned char* sm, int n, int halo) {
+  Tile<T> t;
+  const int ts = tile_side(n), tiles = n / ts;
+  t.n = n;
+  t.W = ts + 2 * halo;
+  t.hw = t.W >> 1;
+  t.gi0 = (int)(blockIdx.x / tiles) * ts - halo;
+  t.gj0 = (int)(blockIdx.x % tiles) * ts - halo;
+  t.ra = reinterpret_cast<Quad<T>*>(sm);
+  t.rb = t.ra + t.W;
+  t.u = reinterpret_cast<T*>(t.rb + t.W);
+  t.f = t.u + (size_t)t.W * t.W;
+  return t;
+}
+
+// Stage the row coefficients, u over the region (zero beyond the ghost ring)
+// and f over the region shrunk by fh cells.  The diagonal of a row takes one
+// value in the interior columns and another in the two edge columns.
+template <typename T>
+__device__ __forceinline__ void tile_load(const Tile<T>& t, const T* __restrict__ U, const T* __restrict__ Fb,
+                                          const T* __restrict__ coef, const T* __restrict__ invd,
+                                          const T* __restrict__ diag, int fh) {
+  const int n = t.n, tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const size_t side = n + 2;
-  T* U = u + (size_t)b * side * side;
-  const T* Fb = f + (size_t)b * n * n;
-  const int t = blockIdx.x * kBX + threadIdx.x;
-#pragma unroll
-  for (int k = 0; k < kSmoothRows; ++k) {
-    const int i = (blockIdx.y * kSmoothRows + k) * kBY + threadIdx.y;
-    const int j = 2 * t + ((i + colour) & 1);
-    if (i < n && j < n) {
-      const size_t c = (size_t)(i + 1) * side + (j + 1);
-      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i];
-      // (aS uS + aN uN + b (uE + uW) - f) / diag as three fused multiply-adds
-      const T v = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -Fb[fidx(n, i, j)])));
-      U[c] = v * invd[i * n + j];
+  for (int r = tid; r < t.W; r += nt) {
+    const int gi = t.gi0 + r;
+    Quad<T> a{0, 0, 0, 0}, b{0, 0, 0, 0};
+    if (gi >= 0 && gi < n) {
+      const size_t row = (size_t)gi * n;
+      a = Quad<T>{coef[gi], coef[n + gi], coef[2 * n + gi], invd[row + 1]};
+      b = Quad<T>{invd[row], diag[row + 1], diag[row], coef[3 * n + gi]};
+    }
+    t.ra[r] = a;
+    t.rb[r] = b;
+  }
+  for (int r = threadIdx.y; r < t.W; r += blockDim.y) {
+    const int gi = t.gi0 + r;
+    const bool urow = gi >= -1 && gi <= n;
+    const bool frow = gi >= 0 && gi < n && r >= fh && r < t.W - fh;
+    const T* Ur = U + (size_t)(gi + 1) * side + 1;
+    for (int c = threadIdx.x; c < t.W; c += blockDim.x) {
+      const int gj = t.gj0 + c;
+      T v = 0, w = 0;
+      if (urow && gj >= -1 && gj <= n) v = Ur[gj];
+      if (frow && gj >= 0 && gj < n && c >= fh && c < t.W - fh) w = Fb[fidx(n, gi, gj)];
+      const int o = t.at(r, c);
+      t.u[o] = v;
+      t.f[o] = w;
     }
   }
 }
 
-// FAS restriction: coarse cell (I, J) gets the area-weighted averages of the
-// fine residual and of the correction over its 2 x 2 children.
+// One colour of a red-black sweep over the region cells lo <= r, c < hi that
+// lie inside the patch: u = (aS uS + aN uN + b (uE + uW) - f) / diagonal.
+// Cells are dealt out flat over the CTA (row, colour index), so no lane idles
+// on the short rows.
 template <typename T>
-__global__ void k_restrict(const T* __restrict__ u, const T* __restrict__ f, const T* __restrict__ coef,
-                           const T* __restrict__ diag, const T* __restrict__ rden, int n, T* __restrict__ uc,
-                           T* __restrict__ uc0, T* __restrict__ fc) {
-  const int nc = n / 2;
-  const int b = blockIdx.z;
-  const int J = blockIdx.x * kBX + threadIdx.x;
-  const size_t side = n + 2, sidec = nc + 2;
-  const T* U = u + (size_t)b * side * side;
-  const T* Fb = f + (size_t)b * n * n;
-#pragma unroll
-  for (int kr = 0; kr < kRestrictRows; ++kr) {
-    const int I = (blockIdx.y * kRestrictRows + kr) * kBY + threadIdx.y;
-    if (I >= nc || J >= nc) continue;
-    T nr = 0, nu = 0;
+__device__ __forceinline__ void tile_half_sweep(const Tile<T>& t, int colour, int lo, int hi) {
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+  const int kc = (hi - lo) >> 1, total = (hi - lo) * kc;
+  const int dq = nt / kc, dr = nt - dq * kc;
+  int rr = tid / kc, kk = tid - rr * kc;
+  const size_t plane = (size_t)t.W * t.hw;
+  T* uc = t.u + colour * plane;
+  const T* uo = t.u + (colour ^ 1) * plane;
+  const T* fc = t.f + colour * plane;
+  for (int idx = tid; idx < total; idx += nt) {
+    const int r = lo + rr;
+    const int p = (colour + r) & 1;          // column parity of the colour in row r
+    const int k = ((lo - p + 1) >> 1) + kk;  // colour index of the cell in its row
+    const int c = 2 * k + p;
+    const int gi = t.gi0 + r, gj = t.gj0 + c;
+    if (gi >= 0 && gi < t.n && gj >= 0 && gj < t.n) {
+      const Quad<T> q = t.ra[r];
+      const int row = r * t.hw;
+      const T uE = uo[row + k + p], uW = uo[row + k + p - 1];
+      const T uS = uo[row + t.hw + k], uN = uo[row - t.hw + k];
+      const T v = fma(q.z, uE + uW, fma(q.y, uN, fma(q.x, uS, -fc[row + k])));
+      uc[row + k] = v * ((gj == 0 || gj == t.n - 1) ? t.rb[r].x : q.w);
+    }
+    rr += dq;
+    kk += dr;
+    if (kk >= kc) {
+      kk -= kc;
+      ++rr;
+    }
+  }
+}
+
+// nu red-black sweeps; the region of half-sweep h is the block plus e0 - h cells
+template <typename T>
+__device__ __forceinline__ void tile_sweeps(const Tile<T>& t, int halo, int nu, int e0) {
+  const int ts = t.W - 2 * halo;
+  for (int h = 0; h < 2 * nu; ++h) {
+    const int e = e0 - h;
+    tile_half_sweep(t, h & 1, halo - e, halo + ts + e);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_store(const Tile<T>& t, int halo, T* __restrict__ U) {
+  const size_t side = t.n + 2;
+  const int ts = t.W - 2 * halo;
+  for (int r = halo + threadIdx.y; r < halo + ts; r += blockDim.y) {
+    T* Ur = U + (size_t)(t.gi0 + r + 1) * side + 1;
+    for (int c = halo + threadIdx.x; c < halo + ts; c += blockDim.x) Ur[t.gj0 + c] = t.u[t.at(r, c)];
+  }
+}
+
+// Pre-smoothing and FAS restriction: nu red-black sweeps on u_in (written to
+// u_out), then coarse cell (I, J) of the block gets the area-weighted
+// averages of the fine residual and of the correction over its 2 x 2
+// children: uc = uc0 = R u, fc = R (f - L u).
+template <typename T>
+__global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
+    const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int n, int nu,
+    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc) {
+  extern __shared__ __align__(16) unsigned char smem_sr[];
+  const int halo = 2 * nu + 1;
+  const Tile<T> t = tile_carve<T>(smem_sr, n, halo);
+  const size_t b = blockIdx.z, side = n + 2;
+  tile_load(t, u_in + b * side * side, f + b * n * n, coef, invd, diag, 1);
+  __syncthreads();
+  tile_sweeps(t, halo, nu, halo - 1);
+  tile_store(t, halo, u_out + b * side * side);
+  const int ts = t.W - 2 * halo, tc = ts >> 1, nc = n >> 1;
+  const int I0 = (t.gi0 + halo) >> 1, J0 = (t.gj0 + halo) >> 1;
+  const size_t sidec = nc + 2;
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
+  const size_t plane = (size_t)t.W * t.hw;
+  for (int idx = tid; idx < tc * tc; idx += nt) {
+    const int a = idx / tc, bb = idx - a * tc;
+    T nr = 0, nu_ = 0;
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di;
-      const T aS = coef[i], aN = coef[n + i], bb = coef[2 * n + i], area = coef[3 * n + i];
+      const int r = halo + 2 * a + di;
+      const Quad<T> q = t.ra[r], q2 = t.rb[r];
       T rs = 0, us = 0;
 #pragma unroll
       for (int dj = 0; dj < 2; ++dj) {
-        const int j = 2 * J + dj;
-        const size_t c = (size_t)(i + 1) * side + (j + 1);
-        const T ucv = U[c];
+        const int c = halo + 2 * bb + dj, gj = t.gj0 + c;
+        const int col = (r + c) & 1, k = c >> 1, row = r * t.hw;
+        const T* uo = t.u + (col ^ 1) * plane;
+        const T ucv = t.u[col * plane + row + k];
+        const T uE = uo[row + ((c + 1) >> 1)], uW = uo[row + ((c - 1) >> 1)];
+        const T uS = uo[row + t.hw + k], uN = uo[row - t.hw + k];
+        const T dg = (gj == 0 || gj == n - 1) ? q2.z : q2.y;
         // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
-        const T nb = fma(bb, U[c + 1] + U[c - 1], fma(aN, U[c - side], fma(aS, U[c + side], -diag[i * n + j] * ucv)));
-        rs += Fb[fidx(n, i, j)] - nb;
+        const T nb = fma(q.z, uE + uW, fma(q.y, uN, fma(q.x, uS, -dg * ucv)));
+        rs += t.f[col * plane + row + k] - nb;
         us += ucv;
       }
-      nr = fma(area, rs, nr);
-      nu = fma(area, us, nu);
+      nr = fma(q2.w, rs, nr);
+      nu_ = fma(q2.w, us, nu_);
     }
-    const T rd = rden[I];   // 1 / (2 (area_{2I} + area_{2I+1}))
-    const T ur = nu * rd;
-    uc[(size_t)b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
-    uc0[(size_t)b * nc * nc + (size_t)I * nc + J] = ur;
-    fc[(size_t)b * nc * nc + fidx(nc, I, J)] = nr * rd;
+    const int I = I0 + a, J = J0 + bb;
+    const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
+    const T ur = nu_ * rd;
+    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+    uc0[b * nc * nc + (size_t)I * nc + J] = ur;
+    fc[b * nc * nc + fidx(nc, I, J)] = nr * rd;
   }
 }
 
@@ -309,43 +443,389 @@ __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T
   *Fp = *Fp + nb;
 }
 
-// u_fine += P(u_c - u_c0): cell-centred bilinear, injection next to the edge;
-// one thread per coarse cell updates its 2 x 2 fine children.
+// Prolongation and post-smoothing: u_out = u_in + P(u_c - u_c0) (cell-centred
+// bilinear, injection next to the patch edge), then nu red-black sweeps.
+// The coarse differences of the region (clamped to the coarse patch) are
+// staged in shared memory after the fine arrays.
 template <typename T>
-__global__ void k_prolong(T* __restrict__ u, const T* __restrict__ uc, const T* __restrict__ uc0, int n) {
-  const int nc = n / 2;
-  const int b = blockIdx.z;
-  const int J = blockIdx.x * kBX + threadIdx.x;
-  const size_t side = n + 2, sidec = nc + 2;
-  const T* C = uc + (size_t)b * sidec * sidec;
-  const T* C0 = uc0 + (size_t)b * nc * nc;
-  T* U = u + (size_t)b * side * side;
-#pragma unroll
-  for (int kr = 0; kr < kGridRows; ++kr) {
-    const int I = (blockIdx.y * kGridRows + kr) * kBY + threadIdx.y;
-    if (I >= nc || J >= nc) continue;
-    T e[3][3];
-#pragma unroll
-    for (int di = -1; di <= 1; ++di)
-#pragma unroll
-      for (int dj = -1; dj <= 1; ++dj) {
-        const int a = min(max(I + di, 0), nc - 1), c = min(max(J + dj, 0), nc - 1);
-        e[di + 1][dj + 1] = C[(size_t)(a + 1) * sidec + (c + 1)] - C0[(size_t)a * nc + c];
-      }
-#pragma unroll
-    for (int fa = 0; fa < 2; ++fa)
-#pragma unroll
-      for (int fc = 0; fc < 2; ++fc) {
-        const int i = 2 * I + fa, j = 2 * J + fc;
-        const int di = fa ? 2 : 0, dj = fc ? 2 : 0;   // neighbour index in e[][]
-        T corr;
-        if (i == 0 || j == 0 || i == n - 1 || j == n - 1)
-          corr = e[1][1];
-        else
-          corr = fma((T)9, e[1][1], fma((T)3, e[di][1] + e[1][dj], e[di][dj])) * (T)0.0625;
-        U[(size_t)(i + 1) * side + (j + 1)] += corr;
-      }
+__global__ void __launch_bounds__(kBX * kBY) k_prolong_smooth(
+    const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, const T* __restrict__ uc0,
+    int n, int nu) {
+  extern __shared__ __align__(16) unsigned char smem_ps[];
+  const int halo = 2 * nu;
+  const Tile<T> t = tile_carve<T>(smem_ps, n, halo);
+  const size_t b = blockIdx.z, side = n + 2;
+  const int nc = n >> 1;
+  const size_t sidec = nc + 2;
+  tile_load(t, u_in + b * side * side, f + b * n * n, coef, invd, diag, halo > 0 ? 1 : t.W);
+  // coarse differences: rows / columns (gi0 / 2 - 1) .. (gi0 / 2 - 1 + Wc - 1)
+  T* E = t.f + (size_t)t.W * t.W;
+  const int Wc = t.hw + 2, Ic0 = (t.gi0 >> 1) - 1, Jc0 = (t.gj0 >> 1) - 1;
+  const T* C = uc + b * sidec * sidec;
+  const T* C0 = uc0 + b * nc * nc;
+  for (int a = threadIdx.y; a < Wc; a += blockDim.y) {
+    const int I = min(max(Ic0 + a, 0), nc - 1);
+    for (int c = threadIdx.x; c < Wc; c += blockDim.x) {
+      const int J = min(max(Jc0 + c, 0), nc - 1);
+      E[a * Wc + c] = C[(size_t)(I + 1) * sidec + (J + 1)] - C0[(size_t)I * nc + J];
+    }
   }
+  __syncthreads();
+  for (int r = threadIdx.y; r < t.W; r += blockDim.y) {
+    const int i = t.gi0 + r;
+    if (i < 0 || i >= n) continue;
+    const int a = (i >> 1) - Ic0, da = (i & 1) ? a + 1 : a - 1;
+    for (int c = threadIdx.x; c < t.W; c += blockDim.x) {
+      const int j = t.gj0 + c;
+      if (j < 0 || j >= n) continue;
+      const int bc = (j >> 1) - Jc0, db = (j & 1) ? bc + 1 : bc - 1;
+      const T e11 = E[a * Wc + bc];
+      T corr;
+      if (i == 0 || j == 0 || i == n - 1 || j == n - 1)
+        corr = e11;
+      else
+        corr = fma((T)9, e11, fma((T)3, E[da * Wc + bc] + E[a * Wc + db], E[da * Wc + db])) * (T)0.0625;
+      t.u[t.at(r, c)] += corr;
+    }
+  }
+  __syncthreads();
+  tile_sweeps(t, halo, nu, halo - 1);
+  tile_store(t, halo, u_out + b * side * side);
+}
+
+// ---------------------------------------------------------------------------
+// Band form of the two fused kernels for patches of at most kBandMaxN cells a
+// side: a CTA owns kBandRows whole rows of a patch, so the halo is needed
+// only above and below (the patch's own edges are the Dirichlet ghost
+// ring).  Colour arrays hold a row as [n / 2 + 2] with a zero entry at each
+// end for the ghost columns.  In a half-sweep each warp owns 32 colour
+// columns and walks a run of consecutive rows, keeping the other colour's
+// values of rows i - 1, i, i + 1 of its column in registers: one cell costs
+// two shared-memory loads of u, one of f and one store.
+
+constexpr int kBandRows = 32;
+constexpr int kBandMaxN = 256;
+constexpr int kBandThreads = 512;
+
+template <typename T>
+struct Vec2T;
+template <>
+struct Vec2T<float> {
+  using type = float2;
+};
+template <>
+struct Vec2T<double> {
+  using type = double2;
+};
+
+template <typename T>
+struct Band {
+  Quad<T>* ra;   // per region row: aS, aN, b, 1 / diagonal (interior columns)
+  Quad<T>* rb;   // per region row: 1 / diagonal (edge columns), diagonal (interior), diagonal (edge), area
+  T* u;          // [2][W][P], P = n / 2 + 2; cell (i, j) at [(i + j) & 1][i - gi0][j / 2 + 1]
+  T* f;          // [2][W][n / 2]
+  int n, nh, P, W, gi0, bi0, br, uplane, fplane;
+  // the two colour rows of region row r: columns 2m - 1 (index m) and 2m (index m + 1)
+  __device__ __forceinline__ T* row_odd(int r) const { return u + (((B_gi(r) + 1) & 1) * uplane) + r * P; }
+  __device__ __forceinline__ T* row_even(int r) const { return u + ((B_gi(r) & 1) * uplane) + r * P; }
+  __device__ __forceinline__ int B_gi(int r) const { return gi0 + r; }
+};
+
+__host__ __device__ constexpr int band_rows(int n) { return n < kBandRows ? n : kBandRows; }
+
+template <typename T>
+__host__ __device__ constexpr size_t band_smem(int n, int halo) {
+  return 2 * (size_t)(band_rows(n) + 2 * halo) *
+         (sizeof(Quad<T>) + (size_t)(n / 2 + 2) * sizeof(T) + (size_t)(n / 2) * sizeof(T));
+}
+
+template <typename T>
+__device__ __forceinline__ Band<T> band_carve(unsigned char* sm, int n, int halo) {
+  Band<T> B;
+  B.n = n;
+  B.nh = n >> 1;
+  B.P = B.nh + 2;
+  B.br = band_rows(n);
+  B.W = B.br + 2 * halo;
+  B.bi0 = (int)blockIdx.x * B.br;
+  B.gi0 = B.bi0 - halo;
+  B.ra = reinterpret_cast<Quad<T>*>(sm);
+  B.rb = B.ra + B.W;
+  B.u = reinterpret_cast<T*>(B.rb + B.W);
+  B.uplane = B.W * B.P;
+  B.f = B.u + 2 * B.uplane;
+  B.fplane = B.W * B.nh;
+  return B;
+}
+
+// Stage the row coefficients, u of the region rows (zero outside the patch
+// and its ghost ring; a row including its ghost columns is read as nh + 1
+// pairs (2m - 1, 2m), one into each colour array) and f of the rows
+// gi0 + fh .. gi0 + W - fh - 1.
+template <typename T>
+__device__ __forceinline__ void band_load(const Band<T>& B, const T* __restrict__ U, const T* __restrict__ Fb,
+                                          const T* __restrict__ coef, const T* __restrict__ invd,
+                                          const T* __restrict__ diag, int fh) {
+  using V2 = typename Vec2T<T>::type;
+  const int n = B.n, tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+  const size_t side = n + 2;
+  for (int r = tid; r < B.W; r += nt) {
+    const int gi = B.gi0 + r;
+    Quad<T> a{0, 0, 0, 0}, b{0, 0, 0, 0};
+    if (gi >= 0 && gi < n) {
+      const size_t row = (size_t)gi * n;
+      a = Quad<T>{coef[gi], coef[n + gi], coef[2 * n + gi], invd[row + 1]};
+      b = Quad<T>{invd[row], diag[row + 1], diag[row], coef[3 * n + gi]};
+    }
+    B.ra[r] = a;
+    B.rb[r] = b;
+  }
+  for (int r = warp; r < B.W; r += nw) {
+    const int gi = B.gi0 + r;
+    T* ua = B.row_odd(r);
+    T* ub = B.row_even(r) + 1;
+    if (gi >= -1 && gi <= n) {
+      const V2* src = reinterpret_cast<const V2*>(U + (size_t)(gi + 1) * side);
+#pragma unroll 4
+      for (int m = lane; m <= B.nh; m += 32) {
+        const V2 v = src[m];
+        ua[m] = v.x;
+        ub[m] = v.y;
+      }
+    } else {
+      for (int m = lane; m <= B.nh; m += 32) {
+        ua[m] = 0;
+        ub[m] = 0;
+      }
+    }
+    if (gi >= 0 && gi < n && r >= fh && r < B.W - fh) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const T* src = Fb + ((size_t)c * n + gi) * B.nh;
+        T* dst = B.f + c * B.fplane + r * B.nh;
+        if (sizeof(T) == 4) {
+          for (int k = 4 * lane; k < B.nh; k += 128)
+            *reinterpret_cast<float4*>(dst + k) = *reinterpret_cast<const float4*>(src + k);
+        } else {
+          for (int k = 2 * lane; k < B.nh; k += 64)
+            *reinterpret_cast<double2*>(dst + k) = *reinterpret_cast<const double2*>(src + k);
+        }
+      }
+    }
+  }
+}
+
+template <int V>
+struct IntC {
+  static constexpr int value = V;
+};
+
+// One colour of a red-black sweep over the patch rows ga .. gb - 1 (all
+// inside the patch, all columns).  The column parity of the colour flips
+// from row to row, so rows are taken in pairs with the parity fixed at
+// compile time.
+template <typename T>
+__device__ __forceinline__ void band_half_sweep(const Band<T>& B, int colour, int ga, int gb) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int cg = (B.nh + 31) >> 5, rg = (blockDim.x >> 5) / cg;
+  const int chunk = (gb - ga + rg - 1) / rg;
+  const int r0 = ga + (warp / cg) * chunk, r1 = min(gb, r0 + chunk);
+  const int k = 32 * (warp % cg) + lane;
+  if (r0 >= r1 || k >= B.nh) return;
+  const int P = B.P, nh = B.nh;
+  const T* O = B.u + (colour ^ 1) * B.uplane;   // the other colour
+  T* C = B.u + colour * B.uplane;
+  const T* F = B.f + colour * B.fplane;
+  const bool left = k == 0, right = k == nh - 1;
+  int lr = r0 - B.gi0;
+  int o = lr * P + k + 1, fo = lr * nh + k;
+  T on = O[o - P], oc = O[o];
+  auto step = [&](auto pc) {
+    constexpr int p = decltype(pc)::value;   // column parity of the colour in this row
+    const T os = O[o + P];
+    const T x = O[o + 2 * p - 1];
+    const T uE = p ? x : oc, uW = p ? oc : x;
+    const Quad<T> q = B.ra[lr];
+    const T id = (p ? right : left) ? B.rb[lr].x : q.w;
+    const T v = fma(q.z, uE + uW, fma(q.y, on, fma(q.x, os, -F[fo])));
+    C[o] = v * id;
+    on = oc;
+    oc = os;
+    o += P;
+    fo += nh;
+    ++lr;
+  };
+  int cnt = r1 - r0;
+  if (((colour + r0) & 1) == 0) {
+    for (; cnt >= 2; cnt -= 2) {
+      step(IntC<0>{});
+      step(IntC<1>{});
+    }
+    if (cnt) step(IntC<0>{});
+  } else {
+    for (; cnt >= 2; cnt -= 2) {
+      step(IntC<1>{});
+      step(IntC<0>{});
+    }
+    if (cnt) step(IntC<1>{});
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void band_sweeps(const Band<T>& B, int nu, int e0) {
+  for (int h = 0; h < 2 * nu; ++h) {
+    const int e = e0 - h;
+    band_half_sweep(B, h & 1, max(0, B.bi0 - e), min(B.n, B.bi0 + B.br + e));
+    __syncthreads();
+  }
+}
+
+// the band's own rows back to global memory (pairs, ghost columns included)
+template <typename T>
+__device__ __forceinline__ void band_store(const Band<T>& B, T* __restrict__ U) {
+  using V2 = typename Vec2T<T>::type;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const size_t side = B.n + 2;
+  for (int gi = B.bi0 + warp; gi < B.bi0 + B.br; gi += nw) {
+    const int r = gi - B.gi0;
+    const T* ua = B.row_odd(r);
+    const T* ub = B.row_even(r) + 1;
+    V2* dst = reinterpret_cast<V2*>(U + (size_t)(gi + 1) * side);
+#pragma unroll 4
+    for (int m = lane; m <= B.nh; m += 32) {
+      V2 v;
+      v.x = ua[m];
+      v.y = ub[m];
+      dst[m] = v;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
+    const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int n, int nu,
+    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc) {
+  extern __shared__ __align__(16) unsigned char smem_bsr[];
+  const int halo = 2 * nu + 1;
+  const Band<T> B = band_carve<T>(smem_bsr, n, halo);
+  const size_t b = blockIdx.z, side = n + 2;
+  band_load(B, u_in + b * side * side, f + b * n * n, coef, invd, diag, 1);
+  __syncthreads();
+  band_sweeps(B, nu, halo - 1);
+  band_store(B, u_out + b * side * side);
+  // Restriction of the band's rows.  Thread (J, run) walks coarse rows of
+  // its run; fine columns 2J, 2J + 1 of fine row i are entry J + 1 of the
+  // colour arrays i & 1 and (i + 1) & 1, their outer neighbours 2J - 1 and
+  // 2J + 2 entries J and J + 2 of the other array.
+  const int nc = n >> 1, ncr = B.br >> 1;
+  const int runs = max(1, (int)blockDim.x / nc), per = (ncr + runs - 1) / runs;
+  const int J = threadIdx.x % nc, run = threadIdx.x / nc;
+  const int Ia = (B.bi0 >> 1) + run * per, Ib = min((B.bi0 >> 1) + ncr, Ia + per);
+  if (run >= runs || Ia >= Ib) return;
+  const size_t sidec = nc + 2;
+  const int P = B.P;
+  auto pair = [&](int i, T& c0, T& c1) {   // u(i, 2J), u(i, 2J + 1)
+    const int r = i - B.gi0;
+    c0 = B.u[(i & 1) * B.uplane + r * P + J + 1];
+    c1 = B.u[((i + 1) & 1) * B.uplane + r * P + J + 1];
+  };
+  T n0, n1, a0, a1;
+  pair(2 * Ia - 1, n0, n1);
+  pair(2 * Ia, a0, a1);
+  const bool eL = J == 0, eR = J == nc - 1;
+  for (int I = Ia; I < Ib; ++I) {
+    T b0, b1, s0, s1;
+    pair(2 * I + 1, b0, b1);
+    pair(2 * I + 2, s0, s1);
+    T nr = 0, nu_ = 0;
+#pragma unroll
+    for (int di = 0; di < 2; ++di) {
+      const int i = 2 * I + di, r = i - B.gi0;
+      const T c0 = di ? b0 : a0, c1 = di ? b1 : a1;           // this row
+      const T N0 = di ? a0 : n0, N1 = di ? a1 : n1;           // row i - 1
+      const T S0 = di ? s0 : b0, S1 = di ? s1 : b1;           // row i + 1
+      const T w = B.u[((i + 1) & 1) * B.uplane + r * P + J];      // u(i, 2J - 1)
+      const T e = B.u[(i & 1) * B.uplane + r * P + J + 2];        // u(i, 2J + 2)
+      const T f0 = B.f[(i & 1) * B.fplane + r * B.nh + J];
+      const T f1 = B.f[((i + 1) & 1) * B.fplane + r * B.nh + J];
+      const Quad<T> q = B.ra[r], q2 = B.rb[r];
+      // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
+      const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
+      const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
+      T rs = 0, us = 0;
+      rs += f0 - nb0;
+      us += c0;
+      rs += f1 - nb1;
+      us += c1;
+      nr = fma(q2.w, rs, nr);
+      nu_ = fma(q2.w, us, nu_);
+    }
+    const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
+    const T ur = nu_ * rd;
+    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+    uc0[b * nc * nc + (size_t)I * nc + J] = ur;
+    fc[b * nc * nc + fidx(nc, I, J)] = nr * rd;
+    n0 = b0;
+    n1 = b1;
+    a0 = s0;
+    a1 = s1;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
+    const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, const T* __restrict__ uc0,
+    int n, int nu) {
+  extern __shared__ __align__(16) unsigned char smem_bps[];
+  const int halo = 2 * nu;
+  const Band<T> B = band_carve<T>(smem_bps, n, halo);
+  const size_t b = blockIdx.z, side = n + 2;
+  const int nc = n >> 1;
+  const size_t sidec = nc + 2;
+  band_load(B, u_in + b * side * side, f + b * n * n, coef, invd, diag, halo > 0 ? 1 : B.W);
+  // coarse differences of coarse rows gi0 / 2 - 1 .. gi0 / 2 - 1 + Wc - 1 and
+  // columns -1 .. nc (both clamped to the patch) at E[row][J + 1]
+  T* E = B.f + 2 * B.fplane;
+  const int Wc = (B.W >> 1) + 2, Pc = nc + 2, Ic0 = (B.gi0 >> 1) - 1;
+  const T* Cc = uc + b * sidec * sidec;
+  const T* C0 = uc0 + b * nc * nc;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int a = warp; a < Wc; a += nw) {
+    const int I = min(max(Ic0 + a, 0), nc - 1);
+    for (int c = lane; c < Pc; c += 32) {
+      const int J = min(max(c - 1, 0), nc - 1);
+      E[a * Pc + c] = Cc[(size_t)(I + 1) * sidec + (J + 1)] - C0[(size_t)I * nc + J];
+    }
+  }
+  __syncthreads();
+  // u += P(e) for the region cells in the patch: fine columns 2J, 2J + 1 of
+  // a row take the coarse columns J - 1, J, J + 1 of two coarse rows
+  for (int r = warp; r < B.W; r += nw) {
+    const int i = B.gi0 + r;
+    if (i < 0 || i >= n) continue;
+    const int a = (i >> 1) - Ic0, da = (i & 1) ? a + 1 : a - 1;
+    const T* Ea = E + a * Pc;
+    const T* Ed = E + da * Pc;
+    T* u0 = B.u + (i & 1) * B.uplane + r * B.P;         // column 2J at J + 1
+    T* u1 = B.u + ((i + 1) & 1) * B.uplane + r * B.P;   // column 2J + 1 at J + 1
+    const bool rowedge = i == 0 || i == n - 1;
+    for (int J = lane; J < nc; J += 32) {
+      const int bc = J + 1;
+      const T e11 = Ea[bc], d11 = Ed[bc];
+      const T c0 = (rowedge || J == 0) ? e11
+                                         : fma((T)9, e11, fma((T)3, d11 + Ea[bc - 1], Ed[bc - 1])) * (T)0.0625;
+      const T c1 = (rowedge || J == nc - 1) ? e11
+                                              : fma((T)9, e11, fma((T)3, d11 + Ea[bc + 1], Ed[bc + 1])) * (T)0.0625;
+      u0[bc] += c0;
+      u1[bc] += c1;
+    }
+  }
+  __syncthreads();
+  band_sweeps(B, nu, halo - 1);
+  band_store(B, u_out + b * side * side);
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -603,6 +1083,7 @@ struct MG {
   clc_ctx* ctx;
   bool mixed = false;  // FP32 V-cycles on an FP64 residual equation
   T* U(int l) { return (T*)s->u[l].p; }
+  T* U2(int l) { return (T*)s->u2[l].p; }
   T* F(int l) { return (T*)s->f[l].p; }
   T* U0(int l) { return (T*)s->u0[l].p; }
   static constexpr bool kF32 = sizeof(T) == 4;
@@ -614,13 +1095,49 @@ struct MG {
   const double* G64(int l) { return (const double*)s->diag[l].p; }
 
   // nu red-black sweeps at level l, one colour per launch
-  void smooth(int l, int nu) {
-    const int n = s->sizes[l];
-    for (int k = 0; k < nu; ++k)
-      for (int colour = 0; colour < 2; ++colour)
-        CLC_LAUNCH(ctx, "k_smooth", k_smooth<T>,
-                   dim3((n / 2 + kBX - 1) / kBX, (n + kBY * kSmoothRows - 1) / (kBY * kSmoothRows), s->npatch),
-                   dim3(kBX, kBY), 0, U(l), F(l), C(l), D(l), n, colour);
+  // shared memory a CTA may use (opt-in limit of the device)
+  size_t smem_cap() {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    return (size_t)v;
+  }
+
+  // pre-smoothing (u -> u2) and restriction to level l + 1: row bands for
+  // patches up to kBandMaxN cells wide, square blocks beyond
+  void smooth_restrict(int l) {
+    const int n = s->sizes[l], nu = s->p.nu1;
+    const size_t smb = band_smem<T>(n, 2 * nu + 1);
+    if (n <= kBandMaxN && smb <= smem_cap()) {
+      cudaFuncSetAttribute(k_band_smooth_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+      CLC_LAUNCH(ctx, "k_smooth_restrict", k_band_smooth_restrict<T>, dim3(n / band_rows(n), 1, s->npatch),
+                 dim3(kBandThreads), smb, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), n, nu, U(l + 1), U0(l + 1),
+                 F(l + 1));
+      return;
+    }
+    const int ts = tile_side(n);
+    const size_t sm = tile_smem<T>(n, 2 * nu + 1);
+    cudaFuncSetAttribute(k_smooth_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    CLC_LAUNCH(ctx, "k_smooth_restrict", k_smooth_restrict<T>, dim3((n / ts) * (n / ts), 1, s->npatch),
+               dim3(kBX, kBY), sm, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), n, nu, U(l + 1), U0(l + 1), F(l + 1));
+  }
+
+  // prolongation of the level l + 1 correction and post-smoothing (u2 -> u)
+  void prolong_smooth(int l) {
+    const int n = s->sizes[l], nu = s->p.nu2;
+    const int wcb = (band_rows(n) + 4 * nu) / 2 + 2;
+    const size_t smb = band_smem<T>(n, 2 * nu) + (size_t)wcb * (n / 2 + 2) * sizeof(T);
+    if (n <= kBandMaxN && smb <= smem_cap()) {
+      cudaFuncSetAttribute(k_band_prolong_smooth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+      CLC_LAUNCH(ctx, "k_prolong_smooth", k_band_prolong_smooth<T>, dim3(n / band_rows(n), 1, s->npatch),
+                 dim3(kBandThreads), smb, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), n, nu);
+      return;
+    }
+    const int ts = tile_side(n);
+    const int wc = (ts + 4 * nu) / 2 + 2;
+    const size_t sm = tile_smem<T>(n, 2 * nu) + (size_t)wc * wc * sizeof(T);
+    cudaFuncSetAttribute(k_prolong_smooth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    CLC_LAUNCH(ctx, "k_prolong_smooth", k_prolong_smooth<T>, dim3((n / ts) * (n / ts), 1, s->npatch),
+               dim3(kBX, kBY), sm, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), n, nu);
   }
 
   void vcycle(int l) {
@@ -631,17 +1148,12 @@ struct MG {
                  (const double*)s->coarse_inv.p, n);
       return;
     }
-    smooth(l, s->p.nu1);
+    smooth_restrict(l);
     const int nc = n / 2;
-    const dim3 gr((nc + kBX - 1) / kBX, (nc + kBY * kRestrictRows - 1) / (kBY * kRestrictRows), s->npatch);
-    const dim3 gp((nc + kBX - 1) / kBX, (nc + kBY * kGridRows - 1) / (kBY * kGridRows), s->npatch);
-    CLC_LAUNCH(ctx, "k_restrict", k_restrict<T>, gr, blk, 0, U(l), F(l), C(l), G(l), RD(l), n, U(l + 1), U0(l + 1),
-               F(l + 1));
     CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
                G(l + 1), nc);
     vcycle(l + 1);
-    CLC_LAUNCH(ctx, "k_prolong", k_prolong<T>, gp, blk, 0, U(l), U(l + 1), U0(l + 1), n);
-    smooth(l, s->p.nu2);
+    prolong_smooth(l);
   }
 
   int residual(double* ratio_host) {
@@ -783,8 +1295,9 @@ static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
   if (p->lmax < 1 || p->lmax > 4 * p->nside_sht) return set_err(ctx, CLC_EINVAL, "MG: lmax must be in [1, 4 nside_sht]");
   if (p->ncell < 16 || p->ncell > 4096 || (p->ncell & (p->ncell - 1)))
     return set_err(ctx, CLC_EINVAL, "MG: ncell must be a power of two in [16, 4096]");
-  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1 || p->max_cycles < 0 || p->fixed_cycles < 0)
-    return set_err(ctx, CLC_EINVAL, "MG: bad sweep / cycle counts");
+  if (p->nu1 < 0 || p->nu2 < 0 || p->nu1 + p->nu2 < 1 || p->nu1 > kMaxSweeps || p->nu2 > kMaxSweeps ||
+      p->max_cycles < 0 || p->fixed_cycles < 0)
+    return set_err(ctx, CLC_EINVAL, "MG: need 0 <= nu1, nu2 <= 8, nu1 + nu2 >= 1 and cycle counts >= 0");
   if (p->precision != CLC_FP64 && p->precision != CLC_FP32 && p->precision != CLC_MIXED)
     return set_err(ctx, CLC_EINVAL, "MG: bad precision");
   return CLC_OK;
@@ -815,7 +1328,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   size_t need = 0;
   for (int l = 0; l < s->nlev; ++l) {
     const size_t n = s->sizes[l];
-    need += s->npatch * ((n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
+    need += s->npatch * (2 * (n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
   }
   need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double) *
           (p->precision == CLC_MIXED ? 4 : 1);
@@ -839,10 +1352,12 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const size_t n = s->sizes[l];
     const double hl = s->h * (p->ncell / (int)n);
     ok = alloc(s->u[l], s->npatch * (n + 2) * (n + 2) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
-         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es));
+         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) &&
+         (l == s->nlev - 1 || alloc(s->u2[l], s->npatch * (n + 2) * (n + 2) * es));
     if (!ok) break;
     // the ghost rings of the correction stay zero (homogeneous Dirichlet data)
     cudaMemset(s->u[l].p, 0, s->u[l].bytes);
+    if (l < s->nlev - 1) cudaMemset(s->u2[l].p, 0, s->u2[l].bytes);
     LevelCoef lc = level_coef((int)n, hl);
     auto put = [&](Buffer& b64, Buffer& b32, const std::vector<double>& v) -> bool {
       if (!alloc(b64, v.size() * sizeof(double)) || !alloc(b32, v.size() * sizeof(float))) return false;

@@ -11,6 +11,7 @@ struct clc_plane_solution {
   double h = 0;                 // finest cell size (radians)
   std::vector<int> sizes;       // cells per side per level
   clc::Buffer u[16], f[16], u0[16];  // per level: correction e (zero ghost ring), source, restricted e
+  clc::Buffer u2[16];           // per level but the coarsest: second correction buffer (pre-smoothed e)
   clc::Buffer base;             // double[npatch][(n+2)^2]: SHT solution inside, 2 g on the ring; final u
   clc::Buffer pvec;             // double[(n+2)^2][3]: patch-frame unit vectors of the finest level
   clc::Buffer ring_th_sht, ring_th_fine;  // ring colatitude tables

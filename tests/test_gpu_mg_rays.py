@@ -32,16 +32,29 @@ def _pixel_home(nf, nb):
     return omg.home_bundle(nf, nb, nest), hp.pix2vec_ring(nf, p)
 
 
-@pytest.mark.parametrize("nf,ns,lmax,nb,ncell,cycles", [(64, 16, 32, 4, 32, 3), (32, 8, 16, 2, 64, 2)])
-def test_shtmg_fixed_cycles_matches_oracle(nf, ns, lmax, nb, ncell, cycles):
+@pytest.mark.parametrize("nf,ns,lmax,nb,ncell,cycles,nu1,nu2", [
+    (64, 16, 32, 4, 32, 3, 2, 2),
+    (32, 8, 16, 2, 64, 2, 2, 2),
+    # several 64 x 64 blocks per patch on the two finest levels, unequal
+    # halos (2 nu1 + 1 = 7 before, 2 nu2 = 2 after the coarse step)
+    (64, 16, 32, 2, 256, 2, 3, 1),
+    # no pre-smoothing (restriction only) / no post-smoothing
+    (32, 8, 16, 2, 128, 2, 0, 2),
+    (32, 8, 16, 2, 128, 2, 2, 0),
+    # finest level wider than a row band: square blocks there, bands below
+    (64, 16, 32, 2, 512, 1, 2, 2),
+    # 8 sweeps: the FP64 row band would not fit in shared memory, square blocks
+    (32, 8, 16, 2, 256, 1, 8, 1),
+])
+def test_shtmg_fixed_cycles_matches_oracle(nf, ns, lmax, nb, ncell, cycles, nu1, nu2):
     import paper_1210_3069_gb300 as clc
     c = ctx()
     kappa = _kappa(nf, 21)
-    P = _params(clc, ns, lmax, nb, ncell, fixed=cycles)
+    P = _params(clc, ns, lmax, nb, ncell, fixed=cycles, nu1=nu1, nu2=nu2)
     sol = c.solution(nf, P)
     got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
     c.sync()
-    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, fixed_cycles=cycles)
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, nu1=nu1, nu2=nu2, fixed_cycles=cycles)
     home, nv = _pixel_home(nf, nb)
     want = omg.fields_at(ref, nb, nv, home)
     for k in KEYS:
@@ -191,3 +204,5 @@ def test_invalid_mg_parameters():
         c.solution(64, _params(clc, 16, 100, 4, 32))      # lmax > 4 nside_sht
     with pytest.raises(clc.CalclensError):
         c.solution(64, _params(clc, 16, 32, 4, 48))       # ncell not a power of two
+    with pytest.raises(clc.CalclensError):
+        c.solution(64, _params(clc, 16, 32, 4, 32, nu1=9))  # more sweeps than the block halo allows
