@@ -20,6 +20,7 @@
 
 #include "mg.cuh"
 #include "patch_fd.cuh"
+#include "umma.cuh"
 
 
 namespace clc {
@@ -79,6 +80,21 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
 // row, so that a colour's sweep reads its sources contiguously.
 __host__ __device__ __forceinline__ size_t fidx(int n, int i, int j) {
   return ((size_t)((i + j) & 1) * n + i) * (size_t)(n >> 1) + (size_t)(j >> 1);
+}
+
+// Layout of a correction array (one patch of n x n cells): the two colours
+// apart, each as rows i = -1 - kUHalo .. n + kUHalo of upitch(n) entries;
+// cell (i, j), -1 <= j <= n, at entry j / 2 + 1 of row i of colour
+// (i + j) & 1.  Entries outside the patch and its ghost ring are zero.  The
+// rows of one colour are contiguous, so a band of rows (with the halo of up
+// to kUHalo rows that the fused smoothing kernels read) moves in one bulk
+// copy per colour, and the row pitch keeps every row 16-byte aligned.
+constexpr int kUHalo = 17;   // 2 nu + 1 for the largest sweep count (8)
+__host__ __device__ __forceinline__ int upitch(int n) { return n / 2 + 4; }
+__host__ __device__ __forceinline__ size_t uplane_of(int n) { return (size_t)(n + 2 + 2 * kUHalo) * upitch(n); }
+__host__ __device__ __forceinline__ size_t upatch(int n) { return 2 * uplane_of(n); }
+__host__ __device__ __forceinline__ size_t uidx(int n, int i, int j) {
+  return (size_t)((i + j) & 1) * uplane_of(n) + (size_t)(i + 1 + kUHalo) * upitch(n) + (size_t)((j >> 1) + 1);
 }
 
 // store a value computed in FP64 in the solver's storage type
@@ -285,7 +301,6 @@ __device__ __forceinline__ void tile_load(const Tile<T>& t, const T* __restrict_
                                           const T* __restrict__ coef, const T* __restrict__ invd,
                                           const T* __restrict__ diag, int fh) {
   const int n = t.n, tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
-  const size_t side = n + 2;
   for (int r = tid; r < t.W; r += nt) {
     const int gi = t.gi0 + r;
     Quad<T> a{0, 0, 0, 0}, b{0, 0, 0, 0};
@@ -301,11 +316,10 @@ __device__ __forceinline__ void tile_load(const Tile<T>& t, const T* __restrict_
     const int gi = t.gi0 + r;
     const bool urow = gi >= -1 && gi <= n;
     const bool frow = gi >= 0 && gi < n && r >= fh && r < t.W - fh;
-    const T* Ur = U + (size_t)(gi + 1) * side + 1;
     for (int c = threadIdx.x; c < t.W; c += blockDim.x) {
       const int gj = t.gj0 + c;
       T v = 0, w = 0;
-      if (urow && gj >= -1 && gj <= n) v = Ur[gj];
+      if (urow && gj >= -1 && gj <= n) v = U[uidx(n, gi, gj)];
       if (frow && gj >= 0 && gj < n && c >= fh && c < t.W - fh) w = Fb[fidx(n, gi, gj)];
       const int o = t.at(r, c);
       t.u[o] = v;
@@ -364,12 +378,9 @@ __device__ __forceinline__ void tile_sweeps(const Tile<T>& t, int halo, int nu, 
 
 template <typename T>
 __device__ __forceinline__ void tile_store(const Tile<T>& t, int halo, T* __restrict__ U) {
-  const size_t side = t.n + 2;
   const int ts = t.W - 2 * halo;
-  for (int r = halo + threadIdx.y; r < halo + ts; r += blockDim.y) {
-    T* Ur = U + (size_t)(t.gi0 + r + 1) * side + 1;
-    for (int c = halo + threadIdx.x; c < halo + ts; c += blockDim.x) Ur[t.gj0 + c] = t.u[t.at(r, c)];
-  }
+  for (int r = halo + threadIdx.y; r < halo + ts; r += blockDim.y)
+    for (int c = halo + threadIdx.x; c < halo + ts; c += blockDim.x) U[uidx(t.n, t.gi0 + r, t.gj0 + c)] = t.u[t.at(r, c)];
 }
 
 // Pre-smoothing and FAS restriction: nu red-black sweeps on u_in (written to
@@ -384,14 +395,13 @@ __global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
   extern __shared__ __align__(16) unsigned char smem_sr[];
   const int halo = 2 * nu + 1;
   const Tile<T> t = tile_carve<T>(smem_sr, n, halo);
-  const size_t b = blockIdx.z, side = n + 2;
-  tile_load(t, u_in + b * side * side, f + b * n * n, coef, invd, diag, 1);
+  const size_t b = blockIdx.z;
+  tile_load(t, u_in + b * upatch(n), f + b * n * n, coef, invd, diag, 1);
   __syncthreads();
   tile_sweeps(t, halo, nu, halo - 1);
-  tile_store(t, halo, u_out + b * side * side);
+  tile_store(t, halo, u_out + b * upatch(n));
   const int ts = t.W - 2 * halo, tc = ts >> 1, nc = n >> 1;
   const int I0 = (t.gi0 + halo) >> 1, J0 = (t.gj0 + halo) >> 1;
-  const size_t sidec = nc + 2;
   const int tid = threadIdx.x + blockDim.x * threadIdx.y, nt = blockDim.x * blockDim.y;
   const size_t plane = (size_t)t.W * t.hw;
   for (int idx = tid; idx < tc * tc; idx += nt) {
@@ -422,7 +432,7 @@ __global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
     const int I = I0 + a, J = J0 + bb;
     const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
     const T ur = nu_ * rd;
-    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
+    uc[b * upatch(nc) + uidx(nc, I, J)] = ur;
     uc0[b * nc * nc + (size_t)I * nc + J] = ur;
     fc[b * nc * nc + fidx(nc, I, J)] = nr * rd;
   }
@@ -435,10 +445,9 @@ __global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T
   const int b = blockIdx.z;
   const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
   if (i >= n || j >= n) return;
-  const size_t side = n + 2;
-  const T* U = u + (size_t)b * side * side;
-  const size_t c = (size_t)(i + 1) * side + (j + 1);
-  const T nb = fma(coef[2 * n + i], U[c + 1] + U[c - 1], fma(coef[n + i], U[c - side], fma(coef[i], U[c + side], -diag[i * n + j] * U[c])));
+  const T* U = u + (size_t)b * upatch(n);
+  const T nb = fma(coef[2 * n + i], U[uidx(n, i, j + 1)] + U[uidx(n, i, j - 1)],
+                   fma(coef[n + i], U[uidx(n, i - 1, j)], fma(coef[i], U[uidx(n, i + 1, j)], -diag[i * n + j] * U[uidx(n, i, j)])));
   T* Fp = f + (size_t)b * n * n + fidx(n, i, j);
   *Fp = *Fp + nb;
 }
@@ -455,20 +464,19 @@ __global__ void __launch_bounds__(kBX * kBY) k_prolong_smooth(
   extern __shared__ __align__(16) unsigned char smem_ps[];
   const int halo = 2 * nu;
   const Tile<T> t = tile_carve<T>(smem_ps, n, halo);
-  const size_t b = blockIdx.z, side = n + 2;
+  const size_t b = blockIdx.z;
   const int nc = n >> 1;
-  const size_t sidec = nc + 2;
-  tile_load(t, u_in + b * side * side, f + b * n * n, coef, invd, diag, halo > 0 ? 1 : t.W);
+  tile_load(t, u_in + b * upatch(n), f + b * n * n, coef, invd, diag, halo > 0 ? 1 : t.W);
   // coarse differences: rows / columns (gi0 / 2 - 1) .. (gi0 / 2 - 1 + Wc - 1)
   T* E = t.f + (size_t)t.W * t.W;
   const int Wc = t.hw + 2, Ic0 = (t.gi0 >> 1) - 1, Jc0 = (t.gj0 >> 1) - 1;
-  const T* C = uc + b * sidec * sidec;
+  const T* C = uc + b * upatch(nc);
   const T* C0 = uc0 + b * nc * nc;
   for (int a = threadIdx.y; a < Wc; a += blockDim.y) {
     const int I = min(max(Ic0 + a, 0), nc - 1);
     for (int c = threadIdx.x; c < Wc; c += blockDim.x) {
       const int J = min(max(Jc0 + c, 0), nc - 1);
-      E[a * Wc + c] = C[(size_t)(I + 1) * sidec + (J + 1)] - C0[(size_t)I * nc + J];
+      E[a * Wc + c] = C[uidx(nc, I, J)] - C0[(size_t)I * nc + J];
     }
   }
   __syncthreads();
@@ -491,129 +499,111 @@ __global__ void __launch_bounds__(kBX * kBY) k_prolong_smooth(
   }
   __syncthreads();
   tile_sweeps(t, halo, nu, halo - 1);
-  tile_store(t, halo, u_out + b * side * side);
+  tile_store(t, halo, u_out + b * upatch(n));
 }
 
 // ---------------------------------------------------------------------------
 // Band form of the two fused kernels for patches of at most kBandMaxN cells a
 // side: a CTA owns kBandRows whole rows of a patch, so the halo is needed
-// only above and below (the patch's own edges are the Dirichlet ghost
-// ring).  Colour arrays hold a row as [n / 2 + 2] with a zero entry at each
-// end for the ghost columns.  In a half-sweep each warp owns 32 colour
-// columns and walks a run of consecutive rows, keeping the other colour's
-// values of rows i - 1, i, i + 1 of its column in registers: one cell costs
-// two shared-memory loads of u, one of f and one store.
+// only above and below (the patch's own edges are the Dirichlet ghost ring).
+// Shared memory holds the region rows in the global layout of a correction
+// array, so the region arrives by two bulk copies (one per colour, TMA
+// engine, completion on an mbarrier) and the band's rows leave the same way;
+// f arrives by two more.  In a half-sweep each warp owns 32 colour columns
+// and walks a run of consecutive rows, keeping the other colour's values of
+// rows i - 1, i, i + 1 of its column in registers.  The patch size is a
+// template parameter, so every pitch is an immediate.
 
 constexpr int kBandRows = 32;
 constexpr int kBandMaxN = 256;
 constexpr int kBandThreads = 512;
+constexpr long long kMgWaitPolls = 1ll << 24;
 
-template <typename T>
-struct Vec2T;
-template <>
-struct Vec2T<float> {
-  using type = float2;
+template <int N>
+struct BandGeo {
+  static constexpr int nh = N / 2;                          // colour cells per row
+  static constexpr int P = N / 2 + 4;                       // row pitch (upitch)
+  static constexpr int br = N < kBandRows ? N : kBandRows;  // band rows
+  static constexpr int cg = nh >= 32 ? nh / 32 : 1;         // warps across a row
+  static constexpr int rg = (kBandThreads / 32) / cg;       // runs of rows per half-sweep
 };
-template <>
-struct Vec2T<double> {
-  using type = double2;
-};
-
-template <typename T>
-struct Band {
-  Quad<T>* ra;   // per region row: aS, aN, b, 1 / diagonal (interior columns)
-  Quad<T>* rb;   // per region row: 1 / diagonal (edge columns), diagonal (interior), diagonal (edge), area
-  T* u;          // [2][W][P], P = n / 2 + 2; cell (i, j) at [(i + j) & 1][i - gi0][j / 2 + 1]
-  T* f;          // [2][W][n / 2]
-  int n, nh, P, W, gi0, bi0, br, uplane, fplane;
-  // the two colour rows of region row r: columns 2m - 1 (index m) and 2m (index m + 1)
-  __device__ __forceinline__ T* row_odd(int r) const { return u + (((B_gi(r) + 1) & 1) * uplane) + r * P; }
-  __device__ __forceinline__ T* row_even(int r) const { return u + ((B_gi(r) & 1) * uplane) + r * P; }
-  __device__ __forceinline__ int B_gi(int r) const { return gi0 + r; }
-};
-
-__host__ __device__ constexpr int band_rows(int n) { return n < kBandRows ? n : kBandRows; }
 
 template <typename T>
 __host__ __device__ constexpr size_t band_smem(int n, int halo) {
-  return 2 * (size_t)(band_rows(n) + 2 * halo) *
-         (sizeof(Quad<T>) + (size_t)(n / 2 + 2) * sizeof(T) + (size_t)(n / 2) * sizeof(T));
+  return 2 * (size_t)((n < kBandRows ? n : kBandRows) + 2 * halo) *
+         (sizeof(Quad<T>) + (size_t)(n / 2 + 4) * sizeof(T) + (size_t)(n / 2) * sizeof(T));
 }
 
-template <typename T>
-__device__ __forceinline__ Band<T> band_carve(unsigned char* sm, int n, int halo) {
-  Band<T> B;
-  B.n = n;
-  B.nh = n >> 1;
-  B.P = B.nh + 2;
-  B.br = band_rows(n);
-  B.W = B.br + 2 * halo;
-  B.bi0 = (int)blockIdx.x * B.br;
+template <typename T, int N>
+struct Band {
+  using G = BandGeo<N>;
+  Quad<T>* ra;   // per region row: aS, aN, b, 1 / diagonal (interior columns)
+  Quad<T>* rb;   // per region row: 1 / diagonal (edge columns), diagonal (interior), diagonal (edge), area
+  T* u;          // [2][W][P]: region rows gi0 .. gi0 + W - 1 of the two colours
+  T* f;          // [2][W][nh]
+  int W, gi0, bi0, uplane, fplane;
+};
+
+template <typename T, int N>
+__device__ __forceinline__ Band<T, N> band_carve(unsigned char* sm, int halo) {
+  using G = BandGeo<N>;
+  Band<T, N> B;
+  B.W = G::br + 2 * halo;
+  B.bi0 = (int)blockIdx.x * G::br;
   B.gi0 = B.bi0 - halo;
   B.ra = reinterpret_cast<Quad<T>*>(sm);
   B.rb = B.ra + B.W;
   B.u = reinterpret_cast<T*>(B.rb + B.W);
-  B.uplane = B.W * B.P;
+  B.uplane = B.W * G::P;
   B.f = B.u + 2 * B.uplane;
-  B.fplane = B.W * B.nh;
+  B.fplane = B.W * G::nh;
   return B;
 }
 
-// Stage the row coefficients, u of the region rows (zero outside the patch
-// and its ghost ring; a row including its ghost columns is read as nh + 1
-// pairs (2m - 1, 2m), one into each colour array) and f of the rows
-// gi0 + fh .. gi0 + W - fh - 1.
-template <typename T>
-__device__ __forceinline__ void band_load(const Band<T>& B, const T* __restrict__ U, const T* __restrict__ Fb,
-                                          const T* __restrict__ coef, const T* __restrict__ invd,
-                                          const T* __restrict__ diag, int fh) {
-  using V2 = typename Vec2T<T>::type;
-  const int n = B.n, tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
-  const size_t side = n + 2;
-  for (int r = tid; r < B.W; r += nt) {
+// Start the bulk copies of the region (u of rows gi0 .. gi0 + W - 1, f of the
+// patch rows among gi0 + fh .. gi0 + W - fh - 1) and stage the row
+// coefficients; band_wait completes the load.
+template <typename T, int N>
+__device__ __forceinline__ void band_issue(const Band<T, N>& B, uint64_t* bar, const T* __restrict__ Ub,
+                                           const T* __restrict__ Fb, const T* __restrict__ coef,
+                                           const T* __restrict__ invd, const T* __restrict__ diag, int fh) {
+  using G = BandGeo<N>;
+  if (threadIdx.x == 0) {
+    umma::mbar_init(bar, 1);
+    umma::fence_mbar_init();
+    const int fa = max(B.gi0 + fh, 0), fb = min(B.gi0 + B.W - fh, N);
+    const uint32_t ubytes = (uint32_t)(B.uplane * sizeof(T));
+    const uint32_t fbytes = fb > fa ? (uint32_t)((fb - fa) * G::nh * sizeof(T)) : 0u;
+    umma::mbar_arrive_expect_tx(bar, 2 * ubytes + 2 * fbytes);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      umma::bulk_g2s(B.u + c * B.uplane, Ub + c * uplane_of(N) + (size_t)(B.gi0 + 1 + kUHalo) * G::P, ubytes, bar);
+      if (fbytes)
+        umma::bulk_g2s(B.f + c * B.fplane + (fa - B.gi0) * G::nh, Fb + ((size_t)c * N + fa) * G::nh, fbytes, bar);
+    }
+  }
+  for (int r = threadIdx.x; r < B.W; r += blockDim.x) {
     const int gi = B.gi0 + r;
     Quad<T> a{0, 0, 0, 0}, b{0, 0, 0, 0};
-    if (gi >= 0 && gi < n) {
-      const size_t row = (size_t)gi * n;
-      a = Quad<T>{coef[gi], coef[n + gi], coef[2 * n + gi], invd[row + 1]};
-      b = Quad<T>{invd[row], diag[row + 1], diag[row], coef[3 * n + gi]};
+    if (gi >= 0 && gi < N) {
+      const size_t row = (size_t)gi * N;
+      a = Quad<T>{coef[gi], coef[N + gi], coef[2 * N + gi], invd[row + 1]};
+      b = Quad<T>{invd[row], diag[row + 1], diag[row], coef[3 * N + gi]};
     }
     B.ra[r] = a;
     B.rb[r] = b;
   }
-  for (int r = warp; r < B.W; r += nw) {
-    const int gi = B.gi0 + r;
-    T* ua = B.row_odd(r);
-    T* ub = B.row_even(r) + 1;
-    if (gi >= -1 && gi <= n) {
-      const V2* src = reinterpret_cast<const V2*>(U + (size_t)(gi + 1) * side);
-#pragma unroll 4
-      for (int m = lane; m <= B.nh; m += 32) {
-        const V2 v = src[m];
-        ua[m] = v.x;
-        ub[m] = v.y;
-      }
-    } else {
-      for (int m = lane; m <= B.nh; m += 32) {
-        ua[m] = 0;
-        ub[m] = 0;
-      }
-    }
-    if (gi >= 0 && gi < n && r >= fh && r < B.W - fh) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const T* src = Fb + ((size_t)c * n + gi) * B.nh;
-        T* dst = B.f + c * B.fplane + r * B.nh;
-        if (sizeof(T) == 4) {
-          for (int k = 4 * lane; k < B.nh; k += 128)
-            *reinterpret_cast<float4*>(dst + k) = *reinterpret_cast<const float4*>(src + k);
-        } else {
-          for (int k = 2 * lane; k < B.nh; k += 64)
-            *reinterpret_cast<double2*>(dst + k) = *reinterpret_cast<const double2*>(src + k);
-        }
-      }
-    }
+}
+
+// Wait (bounded) for the region; false on every thread if it did not arrive.
+__device__ __forceinline__ bool band_wait(uint64_t* bar, int* d_err) {
+  __syncthreads();   // also publishes the coefficient rows and the barrier initialisation
+  const bool ok = __syncthreads_and(umma::mbar_wait(bar, 0, kMgWaitPolls));
+  if (!ok && threadIdx.x == 0) {
+    record_error(d_err, kDevTimeout);
+    umma::mbar_wait(bar, 0, kMgWaitPolls);   // the copies in flight still target this CTA's memory
   }
+  return ok;
 }
 
 template <int V>
@@ -625,36 +615,38 @@ struct IntC {
 // inside the patch, all columns).  The column parity of the colour flips
 // from row to row, so rows are taken in pairs with the parity fixed at
 // compile time.
-template <typename T>
-__device__ __forceinline__ void band_half_sweep(const Band<T>& B, int colour, int ga, int gb) {
+template <typename T, int N>
+__device__ __forceinline__ void band_half_sweep(const Band<T, N>& B, int colour, int ga, int gb) {
+  using G = BandGeo<N>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cg = (B.nh + 31) >> 5, rg = (blockDim.x >> 5) / cg;
-  const int chunk = (gb - ga + rg - 1) / rg;
-  const int r0 = ga + (warp / cg) * chunk, r1 = min(gb, r0 + chunk);
-  const int k = 32 * (warp % cg) + lane;
-  if (r0 >= r1 || k >= B.nh) return;
-  const int P = B.P, nh = B.nh;
-  const T* O = B.u + (colour ^ 1) * B.uplane;   // the other colour
-  T* C = B.u + colour * B.uplane;
-  const T* F = B.f + colour * B.fplane;
-  const bool left = k == 0, right = k == nh - 1;
-  int lr = r0 - B.gi0;
-  int o = lr * P + k + 1, fo = lr * nh + k;
-  T on = O[o - P], oc = O[o];
+  const int chunk = (gb - ga + G::rg - 1) / G::rg;
+  const int r0 = ga + (warp / G::cg) * chunk, r1 = min(gb, r0 + chunk);
+  const int k = 32 * (warp % G::cg) + lane;
+  if (r0 >= r1 || k >= G::nh) return;
+  const int lr = r0 - B.gi0;
+  const T* O = B.u + (colour ^ 1) * B.uplane + lr * G::P + k + 1;   // the other colour, row r0, column k
+  T* C = B.u + colour * B.uplane + lr * G::P + k + 1;
+  const T* F = B.f + colour * B.fplane + lr * G::nh + k;
+  const Quad<T>* Q = B.ra + lr;
+  const Quad<T>* R = B.rb + lr;
+  const bool left = k == 0, right = k == G::nh - 1;
+  T on = O[-G::P], oc = O[0];
   auto step = [&](auto pc) {
     constexpr int p = decltype(pc)::value;   // column parity of the colour in this row
-    const T os = O[o + P];
-    const T x = O[o + 2 * p - 1];
+    const T os = O[G::P];
+    const T x = O[2 * p - 1];
     const T uE = p ? x : oc, uW = p ? oc : x;
-    const Quad<T> q = B.ra[lr];
-    const T id = (p ? right : left) ? B.rb[lr].x : q.w;
-    const T v = fma(q.z, uE + uW, fma(q.y, on, fma(q.x, os, -F[fo])));
-    C[o] = v * id;
+    const Quad<T> q = *Q;
+    const T id = (p ? right : left) ? R->x : q.w;
+    const T v = fma(q.z, uE + uW, fma(q.y, on, fma(q.x, os, -F[0])));
+    C[0] = v * id;
     on = oc;
     oc = os;
-    o += P;
-    fo += nh;
-    ++lr;
+    O += G::P;
+    C += G::P;
+    F += G::nh;
+    ++Q;
+    ++R;
   };
   int cnt = r1 - r0;
   if (((colour + r0) & 1) == 0) {
@@ -672,152 +664,148 @@ __device__ __forceinline__ void band_half_sweep(const Band<T>& B, int colour, in
   }
 }
 
-template <typename T>
-__device__ __forceinline__ void band_sweeps(const Band<T>& B, int nu, int e0) {
+template <typename T, int N>
+__device__ __forceinline__ void band_sweeps(const Band<T, N>& B, int nu, int e0) {
+  using G = BandGeo<N>;
   for (int h = 0; h < 2 * nu; ++h) {
     const int e = e0 - h;
-    band_half_sweep(B, h & 1, max(0, B.bi0 - e), min(B.n, B.bi0 + B.br + e));
+    band_half_sweep(B, h & 1, max(0, B.bi0 - e), min(N, B.bi0 + G::br + e));
     __syncthreads();
   }
 }
 
-// the band's own rows back to global memory (pairs, ghost columns included)
-template <typename T>
-__device__ __forceinline__ void band_store(const Band<T>& B, T* __restrict__ U) {
-  using V2 = typename Vec2T<T>::type;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const size_t side = B.n + 2;
-  for (int gi = B.bi0 + warp; gi < B.bi0 + B.br; gi += nw) {
-    const int r = gi - B.gi0;
-    const T* ua = B.row_odd(r);
-    const T* ub = B.row_even(r) + 1;
-    V2* dst = reinterpret_cast<V2*>(U + (size_t)(gi + 1) * side);
-#pragma unroll 4
-    for (int m = lane; m <= B.nh; m += 32) {
-      V2 v;
-      v.x = ua[m];
-      v.y = ub[m];
-      dst[m] = v;
-    }
+// Start the bulk copy of the band's own rows to global memory (thread 0
+// waits for it at the end of the kernel).
+template <typename T, int N>
+__device__ __forceinline__ void band_store(const Band<T, N>& B, T* __restrict__ Ub) {
+  using G = BandGeo<N>;
+  umma::fence_proxy_async();   // this thread's shared-memory writes, visible to the bulk copy
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      umma::bulk_s2g(Ub + c * uplane_of(N) + (size_t)(B.bi0 + 1 + kUHalo) * G::P,
+                     B.u + c * B.uplane + (B.bi0 - B.gi0) * G::P, (uint32_t)(G::br * G::P * sizeof(T)));
+    umma::bulk_commit();
   }
 }
 
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
-    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int n, int nu,
-    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc) {
-  extern __shared__ __align__(16) unsigned char smem_bsr[];
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int nu,
+    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc, int* d_err) {
+  using G = BandGeo<N>;
+  constexpr int NC = N / 2;
+  extern __shared__ __align__(128) unsigned char smem_bsr[];
+  __shared__ uint64_t bar;
   const int halo = 2 * nu + 1;
-  const Band<T> B = band_carve<T>(smem_bsr, n, halo);
-  const size_t b = blockIdx.z, side = n + 2;
-  band_load(B, u_in + b * side * side, f + b * n * n, coef, invd, diag, 1);
-  __syncthreads();
+  const Band<T, N> B = band_carve<T, N>(smem_bsr, halo);
+  const size_t b = blockIdx.z;
+  band_issue(B, &bar, u_in + b * upatch(N), f + b * N * N, coef, invd, diag, 1);
+  if (!band_wait(&bar, d_err)) return;
   band_sweeps(B, nu, halo - 1);
-  band_store(B, u_out + b * side * side);
+  band_store(B, u_out + b * upatch(N));
   // Restriction of the band's rows.  Thread (J, run) walks coarse rows of
   // its run; fine columns 2J, 2J + 1 of fine row i are entry J + 1 of the
   // colour arrays i & 1 and (i + 1) & 1, their outer neighbours 2J - 1 and
   // 2J + 2 entries J and J + 2 of the other array.
-  const int nc = n >> 1, ncr = B.br >> 1;
-  const int runs = max(1, (int)blockDim.x / nc), per = (ncr + runs - 1) / runs;
-  const int J = threadIdx.x % nc, run = threadIdx.x / nc;
+  constexpr int ncr = G::br / 2;
+  constexpr int runs = kBandThreads / NC > 0 ? kBandThreads / NC : 1;
+  constexpr int per = (ncr + runs - 1) / runs;
+  const int J = threadIdx.x % NC, run = threadIdx.x / NC;
   const int Ia = (B.bi0 >> 1) + run * per, Ib = min((B.bi0 >> 1) + ncr, Ia + per);
-  if (run >= runs || Ia >= Ib) return;
-  const size_t sidec = nc + 2;
-  const int P = B.P;
-  auto pair = [&](int i, T& c0, T& c1) {   // u(i, 2J), u(i, 2J + 1)
-    const int r = i - B.gi0;
-    c0 = B.u[(i & 1) * B.uplane + r * P + J + 1];
-    c1 = B.u[((i + 1) & 1) * B.uplane + r * P + J + 1];
-  };
-  T n0, n1, a0, a1;
-  pair(2 * Ia - 1, n0, n1);
-  pair(2 * Ia, a0, a1);
-  const bool eL = J == 0, eR = J == nc - 1;
-  for (int I = Ia; I < Ib; ++I) {
-    T b0, b1, s0, s1;
-    pair(2 * I + 1, b0, b1);
-    pair(2 * I + 2, s0, s1);
-    T nr = 0, nu_ = 0;
+  if (Ia < Ib) {
+    auto at = [&](int i, int col, int e) -> T { return B.u[col * B.uplane + (i - B.gi0) * G::P + e]; };
+    T n0 = at(2 * Ia - 1, (2 * Ia - 1) & 1, J + 1), n1 = at(2 * Ia - 1, (2 * Ia) & 1, J + 1);
+    T a0 = at(2 * Ia, 0, J + 1), a1 = at(2 * Ia, 1, J + 1);
+    const bool eL = J == 0, eR = J == NC - 1;
+    for (int I = Ia; I < Ib; ++I) {
+      // rows 2I - 1 (n), 2I (a), 2I + 1 (b), 2I + 2 (s): u(i, 2J), u(i, 2J + 1)
+      const T b0 = at(2 * I + 1, 1, J + 1), b1 = at(2 * I + 1, 0, J + 1);
+      const T s0 = at(2 * I + 2, 0, J + 1), s1 = at(2 * I + 2, 1, J + 1);
+      T nr = 0, nu_ = 0;
 #pragma unroll
-    for (int di = 0; di < 2; ++di) {
-      const int i = 2 * I + di, r = i - B.gi0;
-      const T c0 = di ? b0 : a0, c1 = di ? b1 : a1;           // this row
-      const T N0 = di ? a0 : n0, N1 = di ? a1 : n1;           // row i - 1
-      const T S0 = di ? s0 : b0, S1 = di ? s1 : b1;           // row i + 1
-      const T w = B.u[((i + 1) & 1) * B.uplane + r * P + J];      // u(i, 2J - 1)
-      const T e = B.u[(i & 1) * B.uplane + r * P + J + 2];        // u(i, 2J + 2)
-      const T f0 = B.f[(i & 1) * B.fplane + r * B.nh + J];
-      const T f1 = B.f[((i + 1) & 1) * B.fplane + r * B.nh + J];
-      const Quad<T> q = B.ra[r], q2 = B.rb[r];
-      // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
-      const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
-      const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
-      T rs = 0, us = 0;
-      rs += f0 - nb0;
-      us += c0;
-      rs += f1 - nb1;
-      us += c1;
-      nr = fma(q2.w, rs, nr);
-      nu_ = fma(q2.w, us, nu_);
+      for (int di = 0; di < 2; ++di) {
+        const int i = 2 * I + di, r = i - B.gi0;
+        const T c0 = di ? b0 : a0, c1 = di ? b1 : a1;   // this row
+        const T N0 = di ? a0 : n0, N1 = di ? a1 : n1;   // row i - 1
+        const T S0 = di ? s0 : b0, S1 = di ? s1 : b1;   // row i + 1
+        const T w = at(i, di ^ 1, J);                   // u(i, 2J - 1)
+        const T e = at(i, di, J + 2);                   // u(i, 2J + 2)
+        const T f0 = B.f[di * B.fplane + r * G::nh + J];
+        const T f1 = B.f[(di ^ 1) * B.fplane + r * G::nh + J];
+        const Quad<T> q = B.ra[r], q2 = B.rb[r];
+        // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
+        const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
+        const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
+        T rs = 0, us = 0;
+        rs += f0 - nb0;
+        us += c0;
+        rs += f1 - nb1;
+        us += c1;
+        nr = fma(q2.w, rs, nr);
+        nu_ = fma(q2.w, us, nu_);
+      }
+      const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
+      const T ur = nu_ * rd;
+      uc[b * upatch(NC) + uidx(NC, I, J)] = ur;
+      uc0[b * NC * NC + (size_t)I * NC + J] = ur;
+      fc[b * NC * NC + fidx(NC, I, J)] = nr * rd;
+      n0 = b0;
+      n1 = b1;
+      a0 = s0;
+      a1 = s1;
     }
-    const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
-    const T ur = nu_ * rd;
-    uc[b * sidec * sidec + (size_t)(I + 1) * sidec + (J + 1)] = ur;
-    uc0[b * nc * nc + (size_t)I * nc + J] = ur;
-    fc[b * nc * nc + fidx(nc, I, J)] = nr * rd;
-    n0 = b0;
-    n1 = b1;
-    a0 = s0;
-    a1 = s1;
   }
+  if (threadIdx.x == 0) umma::bulk_wait_all();
 }
 
-template <typename T>
+template <typename T, int N>
 __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
     const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, const T* __restrict__ uc0,
-    int n, int nu) {
-  extern __shared__ __align__(16) unsigned char smem_bps[];
+    int nu, int* d_err) {
+  using G = BandGeo<N>;
+  constexpr int NC = N / 2, Pc = NC + 2;
+  extern __shared__ __align__(128) unsigned char smem_bps[];
+  __shared__ uint64_t bar;
   const int halo = 2 * nu;
-  const Band<T> B = band_carve<T>(smem_bps, n, halo);
-  const size_t b = blockIdx.z, side = n + 2;
-  const int nc = n >> 1;
-  const size_t sidec = nc + 2;
-  band_load(B, u_in + b * side * side, f + b * n * n, coef, invd, diag, halo > 0 ? 1 : B.W);
-  // coarse differences of coarse rows gi0 / 2 - 1 .. gi0 / 2 - 1 + Wc - 1 and
-  // columns -1 .. nc (both clamped to the patch) at E[row][J + 1]
+  const Band<T, N> B = band_carve<T, N>(smem_bps, halo);
+  const size_t b = blockIdx.z;
+  band_issue(B, &bar, u_in + b * upatch(N), f + b * N * N, coef, invd, diag, halo > 0 ? 1 : B.W);
+  // while the region arrives: coarse differences of coarse rows gi0 / 2 - 1 ..
+  // gi0 / 2 - 1 + Wc - 1 and columns -1 .. NC (both clamped to the patch) at E[row][J + 1]
   T* E = B.f + 2 * B.fplane;
-  const int Wc = (B.W >> 1) + 2, Pc = nc + 2, Ic0 = (B.gi0 >> 1) - 1;
-  const T* Cc = uc + b * sidec * sidec;
-  const T* C0 = uc0 + b * nc * nc;
+  const int Wc = (B.W >> 1) + 2, Ic0 = (B.gi0 >> 1) - 1;
+  const T* Cc = uc + b * upatch(NC);
+  const T* C0 = uc0 + b * NC * NC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int a = warp; a < Wc; a += nw) {
-    const int I = min(max(Ic0 + a, 0), nc - 1);
+    const int I = min(max(Ic0 + a, 0), NC - 1);
     for (int c = lane; c < Pc; c += 32) {
-      const int J = min(max(c - 1, 0), nc - 1);
-      E[a * Pc + c] = Cc[(size_t)(I + 1) * sidec + (J + 1)] - C0[(size_t)I * nc + J];
+      const int J = min(max(c - 1, 0), NC - 1);
+      E[a * Pc + c] = Cc[uidx(NC, I, J)] - C0[(size_t)I * NC + J];
     }
   }
-  __syncthreads();
+  if (!band_wait(&bar, d_err)) return;
   // u += P(e) for the region cells in the patch: fine columns 2J, 2J + 1 of
   // a row take the coarse columns J - 1, J, J + 1 of two coarse rows
   for (int r = warp; r < B.W; r += nw) {
     const int i = B.gi0 + r;
-    if (i < 0 || i >= n) continue;
+    if (i < 0 || i >= N) continue;
     const int a = (i >> 1) - Ic0, da = (i & 1) ? a + 1 : a - 1;
     const T* Ea = E + a * Pc;
     const T* Ed = E + da * Pc;
-    T* u0 = B.u + (i & 1) * B.uplane + r * B.P;         // column 2J at J + 1
-    T* u1 = B.u + ((i + 1) & 1) * B.uplane + r * B.P;   // column 2J + 1 at J + 1
-    const bool rowedge = i == 0 || i == n - 1;
-    for (int J = lane; J < nc; J += 32) {
+    T* u0 = B.u + (i & 1) * B.uplane + r * G::P;         // column 2J at J + 1
+    T* u1 = B.u + ((i + 1) & 1) * B.uplane + r * G::P;   // column 2J + 1 at J + 1
+    const bool rowedge = i == 0 || i == N - 1;
+    for (int J = lane; J < NC; J += 32) {
       const int bc = J + 1;
       const T e11 = Ea[bc], d11 = Ed[bc];
       const T c0 = (rowedge || J == 0) ? e11
                                          : fma((T)9, e11, fma((T)3, d11 + Ea[bc - 1], Ed[bc - 1])) * (T)0.0625;
-      const T c1 = (rowedge || J == nc - 1) ? e11
+      const T c1 = (rowedge || J == NC - 1) ? e11
                                               : fma((T)9, e11, fma((T)3, d11 + Ea[bc + 1], Ed[bc + 1])) * (T)0.0625;
       u0[bc] += c0;
       u1[bc] += c1;
@@ -825,7 +813,8 @@ __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
   }
   __syncthreads();
   band_sweeps(B, nu, halo - 1);
-  band_store(B, u_out + b * side * side);
+  band_store(B, u_out + b * upatch(N));
+  if (threadIdx.x == 0) umma::bulk_wait_all();
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -836,22 +825,21 @@ __global__ void k_coarse_solve(T* __restrict__ u, const T* __restrict__ f, const
   extern __shared__ double rhs[];
   const size_t b = blockIdx.x;
   const int nn = nc * nc;
-  const size_t side = nc + 2;
-  T* U = u + b * side * side;
+  T* U = u + b * upatch(nc);
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     const int i = t / nc, j = t % nc;
     double g = 0.0;
-    if (i == nc - 1) g += coef[i] * (double)U[(size_t)(i + 2) * side + (j + 1)];
-    if (i == 0) g += coef[nc + i] * (double)U[(size_t)i * side + (j + 1)];
-    if (j == nc - 1) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + (j + 2)];
-    if (j == 0) g += coef[2 * nc + i] * (double)U[(size_t)(i + 1) * side + j];
+    if (i == nc - 1) g += coef[i] * (double)U[uidx(nc, i + 1, j)];
+    if (i == 0) g += coef[nc + i] * (double)U[uidx(nc, i - 1, j)];
+    if (j == nc - 1) g += coef[2 * nc + i] * (double)U[uidx(nc, i, j + 1)];
+    if (j == 0) g += coef[2 * nc + i] * (double)U[uidx(nc, i, j - 1)];
     rhs[t] = (double)f[b * nn + fidx(nc, i, j)] - g;
   }
   __syncthreads();
   for (int t = threadIdx.x; t < nn; t += blockDim.x) {
     double acc = 0.0;
     for (int k = 0; k < nn; ++k) acc += minv[(size_t)t * nn + k] * rhs[k];
-    U[(size_t)(t / nc + 1) * side + (t % nc + 1)] = (T)acc;
+    U[uidx(nc, t / nc, t % nc)] = (T)acc;
   }
 }
 
@@ -863,12 +851,10 @@ __global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, cons
   const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
   double rr = 0.0;
   if (i < n && j < n) {
-    const size_t side = n + 2;
-    const T* U = u + (size_t)b * side * side;
-    const size_t c = (size_t)(i + 1) * side + (j + 1);
-    const double nb = coef[i] * (double)U[c + side] + coef[n + i] * (double)U[c - side] +
-                      coef[2 * n + i] * ((double)U[c + 1] + (double)U[c - 1]);
-    const double r = (double)f[(size_t)b * n * n + fidx(n, i, j)] - (nb - (double)U[c] * diag[i * n + j]);
+    const T* U = u + (size_t)b * upatch(n);
+    const double nb = coef[i] * (double)U[uidx(n, i + 1, j)] + coef[n + i] * (double)U[uidx(n, i - 1, j)] +
+                      coef[2 * n + i] * ((double)U[uidx(n, i, j + 1)] + (double)U[uidx(n, i, j - 1)]);
+    const double r = (double)f[(size_t)b * n * n + fidx(n, i, j)] - (nb - (double)U[uidx(n, i, j)] * diag[i * n + j]);
     rr = r * r;
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -897,41 +883,52 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
 // V-cycle's correction, NULL before the first cycle), r = f' - L e_new with
 // e, f' and the operator in float-float (FP64-level accuracy on the FP32
 // pipe), r rounded to FP32 as the next V-cycle's source, ||r||^2 per patch.
-// Each thread handles kRows rows of one column, so the warp reduction is
-// paid once per kRows cells.
+// e is kept in the layout of the correction arrays (colour-split rows).  A
+// thread takes the cells (i, 2k) and (i, 2k + 1), which sit at the same
+// entry of the two colour rows of row i, and kRows rows of that column pair;
+// every load and store of a warp is then contiguous.
 constexpr int kRows = 4;
 
 __global__ void k_resid_ff(const float2* __restrict__ e_old, const float* __restrict__ d,
                            const float2* __restrict__ fd, const float2* __restrict__ coef,
                            const float2* __restrict__ diag, int n, float2* __restrict__ e_new,
                            float* __restrict__ r32, double* __restrict__ norms) {
-  const int b = blockIdx.z;
-  const int j = blockIdx.x * kBX + threadIdx.x;
-  const size_t side = n + 2;
-  const float2* E = e_old + (size_t)b * side * side;
-  const float* D = d ? d + (size_t)b * side * side : nullptr;
+  const int b = blockIdx.z, nh = n >> 1;
+  const int k = blockIdx.x * kBX + threadIdx.x;
+  const size_t pb = (size_t)b * upatch(n), pl = uplane_of(n), P = upitch(n);
+  const float2* E = e_old + pb;
+  const float* D = d ? d + pb : nullptr;
   float rr = 0.f;
+  auto ld = [&](size_t o) -> float2 {
+    float2 v = E[o];
+    if (D) v = ff_add_f(v, D[o]);
+    return v;
+  };
 #pragma unroll
-  for (int k = 0; k < kRows; ++k) {
-    const int i = (blockIdx.y * kRows + k) * kBY + threadIdx.y;
-    if (i < n && j < n) {
-      const size_t c = (size_t)(i + 1) * side + (j + 1);
-      float2 eC = E[c], eS = E[c + side], eN = E[c - side], eE = E[c + 1], eW = E[c - 1];
-      if (D) {
-        eC = ff_add_f(eC, D[c]);
-        eS = ff_add_f(eS, D[c + side]);
-        eN = ff_add_f(eN, D[c - side]);
-        eE = ff_add_f(eE, D[c + 1]);
-        eW = ff_add_f(eW, D[c - 1]);
+  for (int kr = 0; kr < kRows; ++kr) {
+    const int i = (blockIdx.y * kRows + kr) * kBY + threadIdx.y;
+    if (i < n && k < nh) {
+      const size_t o = (size_t)(i + 1 + kUHalo) * P + k + 1;
+      const size_t ca = (size_t)(i & 1) * pl + o, cb = (size_t)((i + 1) & 1) * pl + o;   // (i, 2k), (i, 2k + 1)
+      const float2 eA = ld(ca), eB = ld(cb);
+      const float2 eW = ld(cb - 1), eE = ld(ca + 1);     // (i, 2k - 1), (i, 2k + 2)
+      const float2 nA = ld(cb - P), nB = ld(ca - P);     // row i - 1
+      const float2 sA = ld(cb + P), sB = ld(ca + P);     // row i + 1
+      const float2 cS = coef[i], cN = coef[n + i], cb2 = coef[2 * n + i];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * k + h;
+        const float2 eC = h ? eB : eA, eS = h ? sB : sA, eN = h ? nB : nA;
+        const float2 eEh = h ? eE : eB, eWh = h ? eA : eW;
+        // L e = aS eS + aN eN + b (eE + eW) - diag eC
+        const float2 nb = ff_add(ff_add(ff_mul(cS, eS), ff_mul(cN, eN)),
+                                 ff_add(ff_mul(cb2, ff_add(eEh, eWh)), ff_neg(ff_mul(diag[i * n + j], eC))));
+        const size_t pos = (size_t)b * n * n + fidx(n, i, j);
+        const float2 r = ff_add(fd[pos], ff_neg(nb));
+        r32[pos] = r.x + r.y;
+        e_new[pb + (h ? cb : ca)] = eC;
+        rr = fmaf(r.x, r.x, rr);
       }
-      // L e = aS eS + aN eN + b (eE + eW) - diag eC
-      const float2 nb = ff_add(ff_add(ff_mul(coef[i], eS), ff_mul(coef[n + i], eN)),
-                               ff_add(ff_mul(coef[2 * n + i], ff_add(eE, eW)), ff_neg(ff_mul(diag[i * n + j], eC))));
-      const size_t pos = (size_t)b * n * n + fidx(n, i, j);
-      const float2 r = ff_add(fd[pos], ff_neg(nb));
-      r32[pos] = r.x + r.y;
-      e_new[(size_t)b * side * side + c] = eC;
-      rr = fmaf(r.x, r.x, rr);
     }
   }
   for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
@@ -945,7 +942,8 @@ __global__ void k_combine_ff(double* __restrict__ base, const float2* __restrict
   if (i >= n || j >= n) return;
   const size_t side = n + 2;
   const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
-  base[c] += (double)e[c].x + (double)e[c].y;
+  const float2 v = e[(size_t)b * upatch(n) + uidx(n, i, j)];
+  base[c] += (double)v.x + (double)v.y;
 }
 
 // final potential u = base + e (interior cells)
@@ -956,7 +954,7 @@ __global__ void k_combine(double* __restrict__ base, const T* __restrict__ e, in
   if (i >= n || j >= n) return;
   const size_t side = n + 2;
   const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
-  base[c] += (double)e[c];
+  base[c] += (double)e[(size_t)b * upatch(n) + uidx(n, i, j)];
 }
 
 // lens fields at every pixel centre of nside_fine, each in its own bundle's patch
@@ -1102,17 +1100,35 @@ struct MG {
     return (size_t)v;
   }
 
+  template <int N>
+  void band_smooth_restrict(int l, size_t smb) {
+    cudaFuncSetAttribute(k_band_smooth_restrict<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    CLC_LAUNCH(ctx, "k_smooth_restrict", (k_band_smooth_restrict<T, N>), dim3(N / BandGeo<N>::br, 1, s->npatch),
+               dim3(kBandThreads), smb, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), s->p.nu1, U(l + 1), U0(l + 1),
+               F(l + 1), ctx->d_err);
+  }
+  template <int N>
+  void band_prolong_smooth(int l, size_t smb) {
+    cudaFuncSetAttribute(k_band_prolong_smooth<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    CLC_LAUNCH(ctx, "k_prolong_smooth", (k_band_prolong_smooth<T, N>), dim3(N / BandGeo<N>::br, 1, s->npatch),
+               dim3(kBandThreads), smb, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), s->p.nu2,
+               ctx->d_err);
+  }
+
   // pre-smoothing (u -> u2) and restriction to level l + 1: row bands for
-  // patches up to kBandMaxN cells wide, square blocks beyond
+  // patches of 16 .. kBandMaxN cells a side, square blocks beyond
   void smooth_restrict(int l) {
     const int n = s->sizes[l], nu = s->p.nu1;
     const size_t smb = band_smem<T>(n, 2 * nu + 1);
-    if (n <= kBandMaxN && smb <= smem_cap()) {
-      cudaFuncSetAttribute(k_band_smooth_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-      CLC_LAUNCH(ctx, "k_smooth_restrict", k_band_smooth_restrict<T>, dim3(n / band_rows(n), 1, s->npatch),
-                 dim3(kBandThreads), smb, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), n, nu, U(l + 1), U0(l + 1),
-                 F(l + 1));
-      return;
+    if (n >= 16 && n <= kBandMaxN && smb <= smem_cap()) {
+      switch (n) {
+        case 16: band_smooth_restrict<16>(l, smb); return;
+        case 32: band_smooth_restrict<32>(l, smb); return;
+        case 64: band_smooth_restrict<64>(l, smb); return;
+        case 128: band_smooth_restrict<128>(l, smb); return;
+        case 256: band_smooth_restrict<256>(l, smb); return;
+        default: break;
+      }
     }
     const int ts = tile_side(n);
     const size_t sm = tile_smem<T>(n, 2 * nu + 1);
@@ -1124,13 +1140,17 @@ struct MG {
   // prolongation of the level l + 1 correction and post-smoothing (u2 -> u)
   void prolong_smooth(int l) {
     const int n = s->sizes[l], nu = s->p.nu2;
-    const int wcb = (band_rows(n) + 4 * nu) / 2 + 2;
+    const int wcb = ((n < kBandRows ? n : kBandRows) + 4 * nu) / 2 + 2;
     const size_t smb = band_smem<T>(n, 2 * nu) + (size_t)wcb * (n / 2 + 2) * sizeof(T);
-    if (n <= kBandMaxN && smb <= smem_cap()) {
-      cudaFuncSetAttribute(k_band_prolong_smooth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-      CLC_LAUNCH(ctx, "k_prolong_smooth", k_band_prolong_smooth<T>, dim3(n / band_rows(n), 1, s->npatch),
-                 dim3(kBandThreads), smb, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), n, nu);
-      return;
+    if (n >= 16 && n <= kBandMaxN && smb <= smem_cap()) {
+      switch (n) {
+        case 16: band_prolong_smooth<16>(l, smb); return;
+        case 32: band_prolong_smooth<32>(l, smb); return;
+        case 64: band_prolong_smooth<64>(l, smb); return;
+        case 128: band_prolong_smooth<128>(l, smb); return;
+        case 256: band_prolong_smooth<256>(l, smb); return;
+        default: break;
+      }
     }
     const int ts = tile_side(n);
     const int wc = (ts + 4 * nu) / 2 + 2;
@@ -1209,7 +1229,7 @@ struct MG {
   int residual_mixed(const float2* e_old, const float* d, float2* e_new, double* ratio_host) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
-    const dim3 grid((n + kBX - 1) / kBX, (n + kBY * kRows - 1) / (kBY * kRows), s->npatch);
+    const dim3 grid((n / 2 + kBX - 1) / kBX, (n + kBY * kRows - 1) / (kBY * kRows), s->npatch);
     CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_ff, grid, dim3(kBX, kBY), 0, e_old, d, (const float2*)s->fd64.p,
                (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, n, e_new, (float*)s->f[0].p,
                (double*)s->norms.p);
@@ -1328,7 +1348,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   size_t need = 0;
   for (int l = 0; l < s->nlev; ++l) {
     const size_t n = s->sizes[l];
-    need += s->npatch * (2 * (n + 2) * (n + 2) + n * n + (l ? n * n : 0)) * es;
+    need += s->npatch * (2 * upatch((int)n) + n * n + (l ? n * n : 0)) * es;
   }
   need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double) *
           (p->precision == CLC_MIXED ? 4 : 1);
@@ -1351,9 +1371,9 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   for (int l = 0; l < s->nlev && ok; ++l) {
     const size_t n = s->sizes[l];
     const double hl = s->h * (p->ncell / (int)n);
-    ok = alloc(s->u[l], s->npatch * (n + 2) * (n + 2) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
+    ok = alloc(s->u[l], s->npatch * upatch((int)n) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
          (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) &&
-         (l == s->nlev - 1 || alloc(s->u2[l], s->npatch * (n + 2) * (n + 2) * es));
+         (l == s->nlev - 1 || alloc(s->u2[l], s->npatch * upatch((int)n) * es));
     if (!ok) break;
     // the ghost rings of the correction stay zero (homogeneous Dirichlet data)
     cudaMemset(s->u[l].p, 0, s->u[l].bytes);
@@ -1388,8 +1408,8 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
        alloc(s->pvec, (n0 + 2) * (n0 + 2) * 3 * sizeof(double)) &&
        alloc(s->ring_th_sht, (4 * p->nside_sht - 1) * sizeof(double)) &&
        alloc(s->ring_th_fine, (4 * nf - 1) * sizeof(double)) && alloc(s->fnorm, s->npatch * sizeof(double)) &&
-       (p->precision != CLC_MIXED || (alloc(s->e64, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
-                                     alloc(s->e64b, s->npatch * (n0 + 2) * (n0 + 2) * sizeof(double)) &&
+       (p->precision != CLC_MIXED || (alloc(s->e64, s->npatch * upatch(n0) * sizeof(float2)) &&
+                                     alloc(s->e64b, s->npatch * upatch(n0) * sizeof(float2)) &&
                                      alloc(s->fd64, s->npatch * n0 * n0 * sizeof(double))));
   if (ok && p->precision == CLC_MIXED) cudaMemset(s->e64b.p, 0, s->e64b.bytes);
   if (ok) {
