@@ -69,7 +69,7 @@ ADJOINT_WORKLOADS = {
 ADJOINT_METRIC = "loss+gradient evaluations/s (galaxy shear through SHT planes, adjoint w.r.t. all kappa maps)"
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_rhs", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
+KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
            "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",
            "k_degrade", "k_rays_init", "k_counts_to_kappa", "k_max_ratio")
@@ -141,14 +141,16 @@ def plane_geometry():
 
 def kernel_models(cfg, precision, cycles, nsteps):
     """Algorithmic work of the modelled kernels over the timed steps:
-    {name: (bound, amount, unit)}, summed over the levels that run the tile
+    {name: (bound, amount, unit)}, summed over the levels that run the fused
     kernels (all but the coarsest).  FP32 (HBM-bound), per cell of the level
-    and V-cycle: pre-smoothing + restriction reads u and f and writes u
-    (12 B) and the coarse u, u0 and f (3 B); prolongation + post-smoothing
-    reads u, f and the coarse u, u0 (10 B) and writes u (4 B).  FP64
-    (FP64-ALU-bound, an FMA counts 2 flops): 8 flops per cell and sweep
-    (3 FMA + 1 add + 1 multiply), 11 per cell for the restriction (residual
-    and two area-weighted sums) and 7 for the prolongation.  The FP64
+    and V-cycle: pre-smoothing + restriction reads f and, unless the
+    correction starts at zero (coarse levels; the first V-cycle of each
+    mixed refinement on the finest level), u; it writes u and the coarse
+    source (9 or 13 B); prolongation + post-smoothing reads u, f and the
+    coarse correction and writes u (13 B).  FP64 (FP64-ALU-bound, an FMA
+    counts 2 flops): 8 flops per cell and sweep (3 FMA + 1 add + 1
+    multiply), 10 per cell for the restricted residual and 7 for the
+    prolongation.  The FP64
     residual of the mixed path (float-float on the FP32 pipe): 32 bytes per
     fine cell per refinement (one refinement per two V-cycles, plus the first)."""
     npatch = 12 * cfg["nside_bundle"] ** 2
@@ -157,14 +159,16 @@ def kernel_models(cfg, precision, cycles, nsteps):
     while n > 8:
         cells_cycle += npatch * n * n
         n //= 2
+    cells0 = npatch * cfg["ncell"] ** 2
     ncyc = sum(cycles)
+    nzero = sum((c + 1) // 2 for c in cycles) if precision == "mixed" else 0
     out = {}
     if precision == "fp64":
-        out["k_smooth_restrict"] = ("alu", (8.0 * cfg["nu1"] + 11.0) * cells_cycle * ncyc, "flop")
+        out["k_smooth_restrict"] = ("alu", (8.0 * cfg["nu1"] + 10.0) * cells_cycle * ncyc, "flop")
         out["k_prolong_smooth"] = ("alu", (8.0 * cfg["nu2"] + 7.0) * cells_cycle * ncyc, "flop")
     else:
-        out["k_smooth_restrict"] = ("hbm", 15.0 * cells_cycle * ncyc, "byte")
-        out["k_prolong_smooth"] = ("hbm", 14.0 * cells_cycle * ncyc, "byte")
+        out["k_smooth_restrict"] = ("hbm", 9.0 * cells_cycle * ncyc + 4.0 * cells0 * (ncyc - nzero), "byte")
+        out["k_prolong_smooth"] = ("hbm", 13.0 * cells_cycle * ncyc, "byte")
     if precision == "mixed":
         # float-float residual: e (8 B) and d (4 B) in, source (8 B) in, e (8 B) and r (4 B) out per fine cell
         n0 = cfg["ncell"]

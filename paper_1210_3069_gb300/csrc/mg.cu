@@ -319,7 +319,7 @@ __device__ __forceinline__ void tile_load(const Tile<T>& t, const T* __restrict_
     for (int c = threadIdx.x; c < t.W; c += blockDim.x) {
       const int gj = t.gj0 + c;
       T v = 0, w = 0;
-      if (urow && gj >= -1 && gj <= n) v = U[uidx(n, gi, gj)];
+      if (U && urow && gj >= -1 && gj <= n) v = U[uidx(n, gi, gj)];
       if (frow && gj >= 0 && gj < n && c >= fh && c < t.W - fh) w = Fb[fidx(n, gi, gj)];
       const int o = t.at(r, c);
       t.u[o] = v;
@@ -383,20 +383,20 @@ __device__ __forceinline__ void tile_store(const Tile<T>& t, int halo, T* __rest
     for (int c = halo + threadIdx.x; c < halo + ts; c += blockDim.x) U[uidx(t.n, t.gi0 + r, t.gj0 + c)] = t.u[t.at(r, c)];
 }
 
-// Pre-smoothing and FAS restriction: nu red-black sweeps on u_in (written to
-// u_out), then coarse cell (I, J) of the block gets the area-weighted
-// averages of the fine residual and of the correction over its 2 x 2
-// children: uc = uc0 = R u, fc = R (f - L u).
+// Pre-smoothing and restriction: nu red-black sweeps on u_in (zero when
+// u_in is NULL; written to u_out), then coarse cell (I, J) of the block gets
+// the area-weighted average of the fine residual over its 2 x 2 children,
+// fc = R (f - L u), the source of the coarse correction equation.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
     const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int n, int nu,
-    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc) {
+    T* __restrict__ fc) {
   extern __shared__ __align__(16) unsigned char smem_sr[];
   const int halo = 2 * nu + 1;
   const Tile<T> t = tile_carve<T>(smem_sr, n, halo);
   const size_t b = blockIdx.z;
-  tile_load(t, u_in + b * upatch(n), f + b * n * n, coef, invd, diag, 1);
+  tile_load(t, u_in ? u_in + b * upatch(n) : nullptr, f + b * n * n, coef, invd, diag, 1);
   __syncthreads();
   tile_sweeps(t, halo, nu, halo - 1);
   tile_store(t, halo, u_out + b * upatch(n));
@@ -406,12 +406,12 @@ __global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
   const size_t plane = (size_t)t.W * t.hw;
   for (int idx = tid; idx < tc * tc; idx += nt) {
     const int a = idx / tc, bb = idx - a * tc;
-    T nr = 0, nu_ = 0;
+    T nr = 0;
 #pragma unroll
     for (int di = 0; di < 2; ++di) {
       const int r = halo + 2 * a + di;
       const Quad<T> q = t.ra[r], q2 = t.rb[r];
-      T rs = 0, us = 0;
+      T rs = 0;
 #pragma unroll
       for (int dj = 0; dj < 2; ++dj) {
         const int c = halo + 2 * bb + dj, gj = t.gj0 + c;
@@ -424,59 +424,37 @@ __global__ void __launch_bounds__(kBX * kBY) k_smooth_restrict(
         // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
         const T nb = fma(q.z, uE + uW, fma(q.y, uN, fma(q.x, uS, -dg * ucv)));
         rs += t.f[col * plane + row + k] - nb;
-        us += ucv;
       }
       nr = fma(q2.w, rs, nr);
-      nu_ = fma(q2.w, us, nu_);
     }
     const int I = I0 + a, J = J0 + bb;
-    const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
-    const T ur = nu_ * rd;
-    uc[b * upatch(nc) + uidx(nc, I, J)] = ur;
-    uc0[b * nc * nc + (size_t)I * nc + J] = ur;
-    fc[b * nc * nc + fidx(nc, I, J)] = nr * rd;
+    fc[b * nc * nc + fidx(nc, I, J)] = nr * rden[I];   // rden = 1 / (2 (area_2I + area_2I+1))
   }
 }
 
-// f_c += L_c(u_c) (the FAS coarse-grid source)
-template <typename T>
-__global__ void k_coarse_rhs(const T* __restrict__ u, T* __restrict__ f, const T* __restrict__ coef,
-                             const T* __restrict__ diag, int n) {
-  const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
-  if (i >= n || j >= n) return;
-  const T* U = u + (size_t)b * upatch(n);
-  const T nb = fma(coef[2 * n + i], U[uidx(n, i, j + 1)] + U[uidx(n, i, j - 1)],
-                   fma(coef[n + i], U[uidx(n, i - 1, j)], fma(coef[i], U[uidx(n, i + 1, j)], -diag[i * n + j] * U[uidx(n, i, j)])));
-  T* Fp = f + (size_t)b * n * n + fidx(n, i, j);
-  *Fp = *Fp + nb;
-}
-
-// Prolongation and post-smoothing: u_out = u_in + P(u_c - u_c0) (cell-centred
+// Prolongation and post-smoothing: u_out = u_in + P(e_c) (cell-centred
 // bilinear, injection next to the patch edge), then nu red-black sweeps.
-// The coarse differences of the region (clamped to the coarse patch) are
+// The coarse correction of the region (clamped to the coarse patch) is
 // staged in shared memory after the fine arrays.
 template <typename T>
 __global__ void __launch_bounds__(kBX * kBY) k_prolong_smooth(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
-    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, const T* __restrict__ uc0,
-    int n, int nu) {
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, int n, int nu) {
   extern __shared__ __align__(16) unsigned char smem_ps[];
   const int halo = 2 * nu;
   const Tile<T> t = tile_carve<T>(smem_ps, n, halo);
   const size_t b = blockIdx.z;
   const int nc = n >> 1;
   tile_load(t, u_in + b * upatch(n), f + b * n * n, coef, invd, diag, halo > 0 ? 1 : t.W);
-  // coarse differences: rows / columns (gi0 / 2 - 1) .. (gi0 / 2 - 1 + Wc - 1)
+  // coarse correction: rows / columns (gi0 / 2 - 1) .. (gi0 / 2 - 1 + Wc - 1)
   T* E = t.f + (size_t)t.W * t.W;
   const int Wc = t.hw + 2, Ic0 = (t.gi0 >> 1) - 1, Jc0 = (t.gj0 >> 1) - 1;
   const T* C = uc + b * upatch(nc);
-  const T* C0 = uc0 + b * nc * nc;
   for (int a = threadIdx.y; a < Wc; a += blockDim.y) {
     const int I = min(max(Ic0 + a, 0), nc - 1);
     for (int c = threadIdx.x; c < Wc; c += blockDim.x) {
       const int J = min(max(Jc0 + c, 0), nc - 1);
-      E[a * Wc + c] = C[uidx(nc, I, J)] - C0[(size_t)I * nc + J];
+      E[a * Wc + c] = C[uidx(nc, I, J)];
     }
   }
   __syncthreads();
@@ -560,9 +538,9 @@ __device__ __forceinline__ Band<T, N> band_carve(unsigned char* sm, int halo) {
   return B;
 }
 
-// Start the bulk copies of the region (u of rows gi0 .. gi0 + W - 1, f of the
-// patch rows among gi0 + fh .. gi0 + W - fh - 1) and stage the row
-// coefficients; band_wait completes the load.
+// Start the bulk copies of the region (u of rows gi0 .. gi0 + W - 1, or zeros
+// when Ub is NULL; f of the patch rows among gi0 + fh .. gi0 + W - fh - 1)
+// and stage the row coefficients; band_wait completes the load.
 template <typename T, int N>
 __device__ __forceinline__ void band_issue(const Band<T, N>& B, uint64_t* bar, const T* __restrict__ Ub,
                                            const T* __restrict__ Fb, const T* __restrict__ coef,
@@ -572,12 +550,13 @@ __device__ __forceinline__ void band_issue(const Band<T, N>& B, uint64_t* bar, c
     umma::mbar_init(bar, 1);
     umma::fence_mbar_init();
     const int fa = max(B.gi0 + fh, 0), fb = min(B.gi0 + B.W - fh, N);
-    const uint32_t ubytes = (uint32_t)(B.uplane * sizeof(T));
+    const uint32_t ubytes = Ub ? (uint32_t)(B.uplane * sizeof(T)) : 0u;
     const uint32_t fbytes = fb > fa ? (uint32_t)((fb - fa) * G::nh * sizeof(T)) : 0u;
     umma::mbar_arrive_expect_tx(bar, 2 * ubytes + 2 * fbytes);
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      umma::bulk_g2s(B.u + c * B.uplane, Ub + c * uplane_of(N) + (size_t)(B.gi0 + 1 + kUHalo) * G::P, ubytes, bar);
+      if (ubytes)
+        umma::bulk_g2s(B.u + c * B.uplane, Ub + c * uplane_of(N) + (size_t)(B.gi0 + 1 + kUHalo) * G::P, ubytes, bar);
       if (fbytes)
         umma::bulk_g2s(B.f + c * B.fplane + (fa - B.gi0) * G::nh, Fb + ((size_t)c * N + fa) * G::nh, fbytes, bar);
     }
@@ -593,6 +572,8 @@ __device__ __forceinline__ void band_issue(const Band<T, N>& B, uint64_t* bar, c
     B.ra[r] = a;
     B.rb[r] = b;
   }
+  if (!Ub)
+    for (int e = threadIdx.x; e < 2 * B.uplane; e += blockDim.x) B.u[e] = 0;
 }
 
 // Wait (bounded) for the region; false on every thread if it did not arrive.
@@ -694,7 +675,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
     const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ rden, int nu,
-    T* __restrict__ uc, T* __restrict__ uc0, T* __restrict__ fc, int* d_err) {
+    T* __restrict__ fc, int* d_err) {
   using G = BandGeo<N>;
   constexpr int NC = N / 2;
   extern __shared__ __align__(128) unsigned char smem_bsr[];
@@ -702,7 +683,7 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
   const int halo = 2 * nu + 1;
   const Band<T, N> B = band_carve<T, N>(smem_bsr, halo);
   const size_t b = blockIdx.z;
-  band_issue(B, &bar, u_in + b * upatch(N), f + b * N * N, coef, invd, diag, 1);
+  band_issue(B, &bar, u_in ? u_in + b * upatch(N) : nullptr, f + b * N * N, coef, invd, diag, 1);
   if (!band_wait(&bar, d_err)) return;
   band_sweeps(B, nu, halo - 1);
   band_store(B, u_out + b * upatch(N));
@@ -724,7 +705,7 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
       // rows 2I - 1 (n), 2I (a), 2I + 1 (b), 2I + 2 (s): u(i, 2J), u(i, 2J + 1)
       const T b0 = at(2 * I + 1, 1, J + 1), b1 = at(2 * I + 1, 0, J + 1);
       const T s0 = at(2 * I + 2, 0, J + 1), s1 = at(2 * I + 2, 1, J + 1);
-      T nr = 0, nu_ = 0;
+      T nr = 0;
 #pragma unroll
       for (int di = 0; di < 2; ++di) {
         const int i = 2 * I + di, r = i - B.gi0;
@@ -739,19 +720,12 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
         // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
         const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
         const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
-        T rs = 0, us = 0;
+        T rs = 0;
         rs += f0 - nb0;
-        us += c0;
         rs += f1 - nb1;
-        us += c1;
         nr = fma(q2.w, rs, nr);
-        nu_ = fma(q2.w, us, nu_);
       }
-      const T rd = rden[I];   // 1 / (2 (area_2I + area_2I+1))
-      const T ur = nu_ * rd;
-      uc[b * upatch(NC) + uidx(NC, I, J)] = ur;
-      uc0[b * NC * NC + (size_t)I * NC + J] = ur;
-      fc[b * NC * NC + fidx(NC, I, J)] = nr * rd;
+      fc[b * NC * NC + fidx(NC, I, J)] = nr * rden[I];   // rden = 1 / (2 (area_2I + area_2I+1))
       n0 = b0;
       n1 = b1;
       a0 = s0;
@@ -764,8 +738,7 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
 template <typename T, int N>
 __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
     const T* __restrict__ u_in, T* __restrict__ u_out, const T* __restrict__ f, const T* __restrict__ coef,
-    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, const T* __restrict__ uc0,
-    int nu, int* d_err) {
+    const T* __restrict__ invd, const T* __restrict__ diag, const T* __restrict__ uc, int nu, int* d_err) {
   using G = BandGeo<N>;
   constexpr int NC = N / 2, Pc = NC + 2;
   extern __shared__ __align__(128) unsigned char smem_bps[];
@@ -774,18 +747,17 @@ __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
   const Band<T, N> B = band_carve<T, N>(smem_bps, halo);
   const size_t b = blockIdx.z;
   band_issue(B, &bar, u_in + b * upatch(N), f + b * N * N, coef, invd, diag, halo > 0 ? 1 : B.W);
-  // while the region arrives: coarse differences of coarse rows gi0 / 2 - 1 ..
+  // while the region arrives: coarse correction of coarse rows gi0 / 2 - 1 ..
   // gi0 / 2 - 1 + Wc - 1 and columns -1 .. NC (both clamped to the patch) at E[row][J + 1]
   T* E = B.f + 2 * B.fplane;
   const int Wc = (B.W >> 1) + 2, Ic0 = (B.gi0 >> 1) - 1;
   const T* Cc = uc + b * upatch(NC);
-  const T* C0 = uc0 + b * NC * NC;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int a = warp; a < Wc; a += nw) {
     const int I = min(max(Ic0 + a, 0), NC - 1);
     for (int c = lane; c < Pc; c += 32) {
       const int J = min(max(c - 1, 0), NC - 1);
-      E[a * Pc + c] = Cc[uidx(NC, I, J)] - C0[(size_t)I * NC + J];
+      E[a * Pc + c] = Cc[uidx(NC, I, J)];
     }
   }
   if (!band_wait(&bar, d_err)) return;
@@ -1083,7 +1055,6 @@ struct MG {
   T* U(int l) { return (T*)s->u[l].p; }
   T* U2(int l) { return (T*)s->u2[l].p; }
   T* F(int l) { return (T*)s->f[l].p; }
-  T* U0(int l) { return (T*)s->u0[l].p; }
   static constexpr bool kF32 = sizeof(T) == 4;
   const T* C(int l) { return (const T*)(kF32 ? s->coef32[l].p : s->coef[l].p); }
   const T* D(int l) { return (const T*)(kF32 ? s->invd32[l].p : s->invd[l].p); }
@@ -1101,32 +1072,32 @@ struct MG {
   }
 
   template <int N>
-  void band_smooth_restrict(int l, size_t smb) {
+  void band_smooth_restrict(int l, bool zero, size_t smb) {
     cudaFuncSetAttribute(k_band_smooth_restrict<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     CLC_LAUNCH(ctx, "k_smooth_restrict", (k_band_smooth_restrict<T, N>), dim3(N / BandGeo<N>::br, 1, s->npatch),
-               dim3(kBandThreads), smb, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), s->p.nu1, U(l + 1), U0(l + 1),
+               dim3(kBandThreads), smb, zero ? nullptr : U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), s->p.nu1,
                F(l + 1), ctx->d_err);
   }
   template <int N>
   void band_prolong_smooth(int l, size_t smb) {
     cudaFuncSetAttribute(k_band_prolong_smooth<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
     CLC_LAUNCH(ctx, "k_prolong_smooth", (k_band_prolong_smooth<T, N>), dim3(N / BandGeo<N>::br, 1, s->npatch),
-               dim3(kBandThreads), smb, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), s->p.nu2,
-               ctx->d_err);
+               dim3(kBandThreads), smb, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), s->p.nu2, ctx->d_err);
   }
 
-  // pre-smoothing (u -> u2) and restriction to level l + 1: row bands for
-  // patches of 16 .. kBandMaxN cells a side, square blocks beyond
-  void smooth_restrict(int l) {
+  // pre-smoothing (u -> u2; u taken as zero when `zero`) and restriction of
+  // the residual to level l + 1: row bands for patches of 16 .. kBandMaxN
+  // cells a side, square blocks beyond
+  void smooth_restrict(int l, bool zero) {
     const int n = s->sizes[l], nu = s->p.nu1;
     const size_t smb = band_smem<T>(n, 2 * nu + 1);
     if (n >= 16 && n <= kBandMaxN && smb <= smem_cap()) {
       switch (n) {
-        case 16: band_smooth_restrict<16>(l, smb); return;
-        case 32: band_smooth_restrict<32>(l, smb); return;
-        case 64: band_smooth_restrict<64>(l, smb); return;
-        case 128: band_smooth_restrict<128>(l, smb); return;
-        case 256: band_smooth_restrict<256>(l, smb); return;
+        case 16: band_smooth_restrict<16>(l, zero, smb); return;
+        case 32: band_smooth_restrict<32>(l, zero, smb); return;
+        case 64: band_smooth_restrict<64>(l, zero, smb); return;
+        case 128: band_smooth_restrict<128>(l, zero, smb); return;
+        case 256: band_smooth_restrict<256>(l, zero, smb); return;
         default: break;
       }
     }
@@ -1134,7 +1105,7 @@ struct MG {
     const size_t sm = tile_smem<T>(n, 2 * nu + 1);
     cudaFuncSetAttribute(k_smooth_restrict<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     CLC_LAUNCH(ctx, "k_smooth_restrict", k_smooth_restrict<T>, dim3((n / ts) * (n / ts), 1, s->npatch),
-               dim3(kBX, kBY), sm, U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), n, nu, U(l + 1), U0(l + 1), F(l + 1));
+               dim3(kBX, kBY), sm, zero ? nullptr : U(l), U2(l), F(l), C(l), D(l), G(l), RD(l), n, nu, F(l + 1));
   }
 
   // prolongation of the level l + 1 correction and post-smoothing (u2 -> u)
@@ -1157,22 +1128,23 @@ struct MG {
     const size_t sm = tile_smem<T>(n, 2 * nu) + (size_t)wc * wc * sizeof(T);
     cudaFuncSetAttribute(k_prolong_smooth<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     CLC_LAUNCH(ctx, "k_prolong_smooth", k_prolong_smooth<T>, dim3((n / ts) * (n / ts), 1, s->npatch),
-               dim3(kBX, kBY), sm, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), U0(l + 1), n, nu);
+               dim3(kBX, kBY), sm, U2(l), U(l), F(l), C(l), D(l), G(l), U(l + 1), n, nu);
   }
 
-  void vcycle(int l) {
+  // V-cycle at level l on L e = f; `zero`: e starts at zero (coarse levels,
+  // and the finest one when its correction was just reset).  For the linear
+  // operator the coarse equation of the full approximation scheme, written
+  // for e_c = u_c - R u, is L_c e_c = R (f - L u) from e_c = 0: the same
+  // iterates with no restricted copy of u and no coarse source update.
+  void vcycle(int l, bool zero) {
     const int n = s->sizes[l];
-    const dim3 blk(kBX, kBY);
     if (l == s->nlev - 1) {
       CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C64(l),
                  (const double*)s->coarse_inv.p, n);
       return;
     }
-    smooth_restrict(l);
-    const int nc = n / 2;
-    CLC_LAUNCH(ctx, "k_coarse_rhs", k_coarse_rhs<T>, grid3(nc, nc, s->npatch), blk, 0, U(l + 1), F(l + 1), C(l + 1),
-               G(l + 1), nc);
-    vcycle(l + 1);
+    smooth_restrict(l, zero);
+    vcycle(l + 1, true);
     prolong_smooth(l);
   }
 
@@ -1256,9 +1228,8 @@ struct MG {
     while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= s->p.tol && s->cycles < s->p.max_cycles)) {
       // two FP32 V-cycles on L d = r (the second continues from the first)
       // per FP64 refinement: the FP64 residual is the ALU-bound part
-      cudaMemsetAsync(s->u[0].p, 0, s->u[0].bytes, ctx->stream);
       const int inner = (fixed ? s->p.fixed_cycles - s->cycles : s->p.max_cycles - s->cycles) >= 2 ? 2 : 1;
-      for (int k = 0; k < inner; ++k) vcycle(0);
+      for (int k = 0; k < inner; ++k) vcycle(0, k == 0);   // d starts at zero in each refinement
       s->cycles += inner - 1;
       if ((rc = launch_check(ctx, "mixed V-cycle"))) return rc;
       if ((rc = residual_mixed(cur, (const float*)s->u[0].p, nxt, &rr))) return rc;
@@ -1286,7 +1257,7 @@ struct MG {
     int st = CLC_OK;
     if (s->p.fixed_cycles > 0) {
       for (int k = 0; k < s->p.fixed_cycles; ++k) {
-        vcycle(0);
+        vcycle(0, false);
         if ((rc = launch_check(ctx, "V-cycle"))) return rc;
       }
       s->cycles = s->p.fixed_cycles;
@@ -1294,7 +1265,7 @@ struct MG {
     } else {
       if ((rc = residual(&rr))) return rc;
       while (rr >= s->p.tol && s->cycles < s->p.max_cycles) {
-        vcycle(0);
+        vcycle(0, false);
         if ((rc = launch_check(ctx, "V-cycle"))) return rc;
         ++s->cycles;
         if ((rc = residual(&rr))) return rc;
@@ -1348,7 +1319,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   size_t need = 0;
   for (int l = 0; l < s->nlev; ++l) {
     const size_t n = s->sizes[l];
-    need += s->npatch * (2 * upatch((int)n) + n * n + (l ? n * n : 0)) * es;
+    need += s->npatch * (2 * upatch((int)n) + n * n) * es;
   }
   need += (size_t)s->npatch * (p->ncell + 2) * (p->ncell + 2) * sizeof(double) *
           (p->precision == CLC_MIXED ? 4 : 1);
@@ -1372,7 +1343,6 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const size_t n = s->sizes[l];
     const double hl = s->h * (p->ncell / (int)n);
     ok = alloc(s->u[l], s->npatch * upatch((int)n) * es) && alloc(s->f[l], s->npatch * n * n * es) &&
-         (l == 0 || alloc(s->u0[l], s->npatch * n * n * es)) &&
          (l == s->nlev - 1 || alloc(s->u2[l], s->npatch * upatch((int)n) * es));
     if (!ok) break;
     // the ghost rings of the correction stay zero (homogeneous Dirichlet data)

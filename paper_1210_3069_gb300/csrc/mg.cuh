@@ -10,7 +10,7 @@ struct clc_plane_solution {
   int npatch = 0, nlev = 0;
   double h = 0;                 // finest cell size (radians)
   std::vector<int> sizes;       // cells per side per level
-  clc::Buffer u[16], f[16], u0[16];  // per level: correction e (zero ghost ring), source, restricted e
+  clc::Buffer u[16], f[16];     // per level: correction e (colour-split rows, zero ghost ring), source
   clc::Buffer u2[16];           // per level but the coarsest: second correction buffer (pre-smoothed e)
   clc::Buffer base;             // double[npatch][(n+2)^2]: SHT solution inside, 2 g on the ring; final u
   clc::Buffer pvec;             // double[(n+2)^2][3]: patch-frame unit vectors of the finest level
