@@ -30,6 +30,7 @@ MGView mg_view(const clc_plane_solution* sol) {
   v.npatch = sol->npatch;
   v.n = sol->sizes[0];
   v.h = sol->h;
+  v.inv_h = 1.0 / sol->h;
   v.rot = (const double*)sol->rot.p;
   v.u = (const double*)sol->base.p;
   return v;

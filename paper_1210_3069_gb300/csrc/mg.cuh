@@ -44,6 +44,7 @@ struct MGView {
   int npatch;
   int n;           // finest cells per side
   double h;        // finest cell size
+  double inv_h;    // 1 / h
   const double* rot;
   const double* u; // finest level potential u = u_SHT + e (ghost-ring layout)
 };

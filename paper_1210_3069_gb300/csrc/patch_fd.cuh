@@ -41,35 +41,55 @@ __device__ __forceinline__ double uat(const T* u, int n, int i, int j) {
   return (double)u[(size_t)(i + 1) * (n + 2) + (j + 1)];
 }
 
-// psi_t', psi_p', psi_t't', psi_p'p', psi_t'p' at cell (i, j)
-template <typename T>
-__device__ __forceinline__ void cell_partials(const T* u, int n, int i, int j, double inv_h, double p[5]) {
-  double wi1[5], wj1[5], wi2[5], wj2[5];
-  const int bi1 = fd_stencil(i, n, 1, wi1), bj1 = fd_stencil(j, n, 1, wj1);
-  const int bi2 = fd_stencil(i, n, 2, wi2), bj2 = fd_stencil(j, n, 2, wj2);
-  double pt = 0, pp = 0, ptt = 0, ppp = 0, ptp = 0;
-#pragma unroll
-  for (int t = 0; t < 5; ++t) {
-    pt += wi1[t] * uat(u, n, bi1 + t, j);
-    ptt += wi2[t] * uat(u, n, bi2 + t, j);
-    pp += wj1[t] * uat(u, n, i, bj1 + t);
-    ppp += wj2[t] * uat(u, n, i, bj2 + t);
-    double row = 0;
-#pragma unroll
-    for (int s = 0; s < 5; ++s) row += wj1[s] * uat(u, n, bi1 + t, bj1 + s);
-    ptp += wi1[t] * row;
+// Bilinear blend of the stencils of cells k and k + 1 (weights 1 - f, f) as
+// one stencil on the six points first .. first + 5: w1 (first derivative),
+// w2 (second derivative), both x 12.  The second cell's stencil starts at
+// the same point as the first one's or one later (offset known only at run
+// time, so both placements are formed and selected).
+__device__ __forceinline__ int fd_blend(int k, int n, double f, double w1[6], double w2[6]) {
+  const double g = 1.0 - f;
+  if (k >= 2 && k + 1 <= n - 3) {   // both central: the second is shifted by one point
+    w1[0] = g * 1.0;
+    w1[1] = g * -8.0 + f * 1.0;
+    w1[2] = g * 0.0 + f * -8.0;
+    w1[3] = g * 8.0 + f * 0.0;
+    w1[4] = g * -1.0 + f * 8.0;
+    w1[5] = f * -1.0;
+    w2[0] = g * -1.0;
+    w2[1] = g * 16.0 + f * -1.0;
+    w2[2] = g * -30.0 + f * 16.0;
+    w2[3] = g * 16.0 + f * -30.0;
+    w2[4] = g * -1.0 + f * 16.0;
+    w2[5] = f * -1.0;
+    return k - 2;
   }
-  const double c1 = inv_h / 12.0, c2 = inv_h * inv_h / 12.0;
-  p[0] = pt * c1;
-  p[1] = pp * c1;
-  p[2] = ptt * c2;
-  p[3] = ppp * c2;
-  p[4] = ptp * c1 * inv_h / 12.0;
+  double a1[5], a2[5], b1[5], b2[5];
+  const int ba = fd_stencil(k, n, 1, a1), bb = fd_stencil(k + 1, n, 1, b1);
+  fd_stencil(k, n, 2, a2);
+  fd_stencil(k + 1, n, 2, b2);
+  const int first = min(ba, bb);
+  const bool sa = ba > first, sb = bb > first;   // stencil starts one point later
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double a1t = t < 5 ? a1[t] : 0.0, a1s = t >= 1 ? a1[t - 1] : 0.0;
+    const double a2t = t < 5 ? a2[t] : 0.0, a2s = t >= 1 ? a2[t - 1] : 0.0;
+    const double b1t = t < 5 ? b1[t] : 0.0, b1s = t >= 1 ? b1[t - 1] : 0.0;
+    const double b2t = t < 5 ? b2[t] : 0.0, b2s = t >= 1 ? b2[t - 1] : 0.0;
+    w1[t] = g * (sa ? a1s : a1t) + f * (sb ? b1s : b1t);
+    w2[t] = g * (sa ? a2s : a2t) + f * (sb ? b2s : b2t);
+  }
+  return first;
 }
 
+// Lens fields at unit vector nv from patch potential u (n x n cells of size
+// h, ghost-ring layout), R the patch rotation.  The five partials of the four
+// cells around the point are blended bilinearly; since each partial is a
+// tensor-product stencil, the blend is one tensor-product stencil on a 6 x 6
+// block of cells.  The patch angles' sines and cosines come from the
+// components of the rotated unit vector.
 template <typename T>
-__device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h, const double* R, const double nv[3],
-                                                    double out[5]) {
+__device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h, double inv_h, const double* R,
+                                                    const double nv[3], double out[5]) {
   // patch-frame vector and angles
   const double vx = R[0] * nv[0] + R[1] * nv[1] + R[2] * nv[2];
   const double vy = R[3] * nv[0] + R[4] * nv[1] + R[5] * nv[2];
@@ -77,32 +97,60 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   const double rho = sqrt(vx * vx + vy * vy);
   const double thp = atan2(rho, vz);
   const double php = atan2(vy, vx);
-  const double x = (thp - 0.5 * kPi) / h + 0.5 * n - 0.5;
-  const double y = php / h + 0.5 * n - 0.5;
+  const double x = (thp - 0.5 * kPi) * inv_h + 0.5 * n - 0.5;
+  const double y = php * inv_h + 0.5 * n - 0.5;
   double i0 = floor(x), j0 = floor(y);
   i0 = fmin(fmax(i0, 0.0), (double)(n - 2));
   j0 = fmin(fmax(j0, 0.0), (double)(n - 2));
   const double fx = x - i0, fy = y - j0;
   const int ii = (int)i0, jj = (int)j0;
-  double v[5] = {0, 0, 0, 0, 0};
-  const double inv_h = 1.0 / h;
-  double p[5];
-  const double wts[4] = {(1 - fx) * (1 - fy), fx * (1 - fy), (1 - fx) * fy, fx * fy};
+  // blended stencils (rows: theta', columns: phi')
+  double A1[6], A2[6], B1[6], B2[6];
+  const int r0 = fd_blend(ii, n, fx, A1, A2);
+  const int c0 = fd_blend(jj, n, fy, B1, B2);
+  const size_t pitch = (size_t)n + 2;
+  const T* ub = u + (size_t)(r0 + 1) * pitch + (c0 + 1);
+  const int ci = jj - c0, ri = ii - r0;   // the bilinear cells inside the 6 x 6 block
+  double pt = 0, ptt = 0, ptp = 0, pp = 0, ppp = 0;
+  double rl[6] = {0, 0, 0, 0, 0, 0};      // rows ii, ii + 1 blended, per column
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    cell_partials(u, n, ii + (c & 1), jj + (c >> 1), inv_h, p);
+  for (int a = 0; a < 6; ++a) {
+    const T* row = ub + (size_t)a * pitch;
+    double v[6];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) v[k] += wts[c] * p[k];
+    for (int b = 0; b < 6; ++b) v[b] = (double)row[b];
+    // columns jj, jj + 1 blended in this row
+    double cl = 0.0, mix = 0.0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b) {
+      if (b == ci) cl += (1.0 - fy) * v[b];
+      if (b == ci + 1) cl += fy * v[b];
+      mix += B1[b] * v[b];
+    }
+    pt += A1[a] * cl;
+    ptt += A2[a] * cl;
+    ptp += A1[a] * mix;
+    const double wr = (a == ri) ? 1.0 - fx : (a == ri + 1 ? fx : 0.0);
+#pragma unroll
+    for (int b = 0; b < 6; ++b) rl[b] += wr * v[b];
   }
-  // Appendix A in the patch basis at the point
-  const double s = sin(thp), co = cos(thp);
-  const double is = 1.0 / s;
-  const double a_t = -v[0], a_p = -v[1] * is;
-  const double u_tt = v[2];
-  const double u_pp = v[3] * is * is + co * is * v[0];
-  const double u_tp = v[4] * is - co * v[1] * is * is;
+#pragma unroll
+  for (int b = 0; b < 6; ++b) {
+    pp += B1[b] * rl[b];
+    ppp += B2[b] * rl[b];
+  }
+  const double c1 = inv_h / 12.0, c2 = inv_h * inv_h / 12.0;
+  const double v0 = pt * c1, v1 = pp * c1, v2 = ptt * c2, v3 = ppp * c2, v4 = ptp * c1 * inv_h / 12.0;
+  // Appendix A in the patch basis at the point: sin(theta') = rho, cos(theta') = vz
+  // (the rotated vector is a unit vector), sin(phi') = vy / rho, cos(phi') = vx / rho
+  const double s = rho, co = vz;
+  const double is = 1.0 / rho;
+  const double a_t = -v0, a_p = -v1 * is;
+  const double u_tt = v2;
+  const double u_pp = v3 * is * is + co * is * v0;
+  const double u_tp = v4 * is - co * v1 * is * is;
   // patch basis vectors at the point, mapped to global coordinates (R^T)
-  const double sp = sin(php), cp = cos(php);
+  const double sp = vy * is, cp = vx * is;
   const double tl[3] = {co * cp, co * sp, -s};
   const double pl[3] = {-sp, cp, 0.0};
   double tg[3], pg[3];
@@ -111,9 +159,9 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
     tg[k] = R[k] * tl[0] + R[3 + k] * tl[1] + R[6 + k] * tl[2];
     pg[k] = R[k] * pl[0] + R[3 + k] * pl[1] + R[6 + k] * pl[2];
   }
-  const double gr = sqrt(nv[0] * nv[0] + nv[1] * nv[1]);
-  const double et[3] = {nv[2] * nv[0] / gr, nv[2] * nv[1] / gr, -gr};
-  const double ep[3] = {-nv[1] / gr, nv[0] / gr, 0.0};
+  const double gr = sqrt(nv[0] * nv[0] + nv[1] * nv[1]), igr = 1.0 / gr;
+  const double et[3] = {nv[2] * nv[0] * igr, nv[2] * nv[1] * igr, -gr};
+  const double ep[3] = {-nv[1] * igr, nv[0] * igr, 0.0};
   const double q00 = et[0] * tg[0] + et[1] * tg[1] + et[2] * tg[2];
   const double q01 = et[0] * pg[0] + et[1] * pg[1] + et[2] * pg[2];
   const double q10 = ep[0] * tg[0] + ep[1] * tg[1] + ep[2] * tg[2];
@@ -130,7 +178,7 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
 
 __device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], double out[5]) {
   const size_t stride = (size_t)(V.n + 2) * (V.n + 2);
-  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.rot + 9 * (size_t)b, nv, out);
+  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.inv_h, V.rot + 9 * (size_t)b, nv, out);
 }
 
 }  // namespace clc

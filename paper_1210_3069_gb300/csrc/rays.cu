@@ -59,9 +59,9 @@ __global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
 }
 
 __device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
-  const double rho = sqrt(n[0] * n[0] + n[1] * n[1]);
-  t[0] = n[2] * n[0] / rho; t[1] = n[2] * n[1] / rho; t[2] = -rho;
-  p[0] = -n[1] / rho; p[1] = n[0] / rho; p[2] = 0.0;
+  const double rho = sqrt(n[0] * n[0] + n[1] * n[1]), ir = 1.0 / rho;
+  t[0] = n[2] * n[0] * ir; t[1] = n[2] * n[1] * ir; t[2] = -rho;
+  p[0] = -n[1] * ir; p[1] = n[0] * ir; p[2] = 0.0;
 }
 
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
@@ -142,7 +142,8 @@ __device__ __forceinline__ void transport_q(const double n0[3], const double n1[
   tangent_basis(n1, t1, p1);
   double tr[3], pr[3];
   if (s > 0.0) {
-    const double k[3] = {cr[0] / s, cr[1] / s, cr[2] / s};
+    const double is = 1.0 / s;
+    const double k[3] = {cr[0] * is, cr[1] * is, cr[2] * is};
     rodrigues(t0, k, c, s, tr);
     rodrigues(p0, k, c, s, pr);
   } else {
@@ -170,8 +171,8 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     for (int c = 0; c < 3; ++c) { x[c] = R.x[c * n + k]; be[c] = R.beta[c * n + k]; }
 #pragma unroll
     for (int c = 0; c < 4; ++c) { A[c] = R.A[c * n + k]; Ap[c] = R.Ap[c * n + k]; }
-    const double xn = sqrt(dot3(x, x));
-    const double nv[3] = {x[0] / xn, x[1] / xn, x[2] / xn};
+    const double ixn = 1.0 / sqrt(dot3(x, x));
+    const double nv[3] = {x[0] * ixn, x[1] * ixn, x[2] * ixn};
     double L[5];
     if (kMG) patch_lens_fields(V, R.bundle[k], nv, L);
     else map_lens_fields(M, nside_maps, nv, L);
@@ -191,7 +192,8 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     if (am > 0.0) {
       double kx[3];
       cross3(nv, av, kx);
-      const double kk[3] = {kx[0] / am, kx[1] / am, kx[2] / am};
+      const double iam = 1.0 / am;
+      const double kk[3] = {kx[0] * iam, kx[1] * iam, kx[2] * iam};
       double sn, cs;
       sincos(am, &sn, &cs);
       rodrigues(be, kk, cs, sn, bn);
@@ -202,8 +204,8 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     double x1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) x1[c] = x[c] + lam * bn[c];
-    const double x1n = sqrt(dot3(x1, x1));
-    const double n1[3] = {x1[0] / x1n, x1[1] / x1n, x1[2] / x1n};
+    const double ix1 = 1.0 / sqrt(dot3(x1, x1));
+    const double n1[3] = {x1[0] * ix1, x1[1] * ix1, x1[2] * ix1};
     // Appendix B: transport A^(n+1) and A^(n) to the basis at the new point
     double Q[4], Ao[4], Apo[4];
     transport_q(nv, n1, Q);
