@@ -944,7 +944,9 @@ __global__ void k_fields_at_pixels(MGView V, int nf, int nb, double* a_th, doubl
     const int b = (int)(pn >> shift);
     const double nv[3] = {r.s * cos(phi), r.s * sin(phi), r.z};
     double o[5];
-    patch_lens_fields(V, b, nv, o);
+    double et[3], ep[3];
+    tangent_basis(nv, et, ep);
+    patch_lens_fields(V, b, nv, et, ep, o);
     if (a_th) a_th[p] = o[0];
     if (a_ph) a_ph[p] = o[1];
     if (u_tt) u_tt[p] = o[2];
@@ -961,7 +963,9 @@ __global__ void k_fields_at_points(MGView V, const double* z, const double* phi,
     const double nv[3] = {s * cos(pp), s * sin(pp), zz};
     const int b = bundle ? bundle[k] : (int)ang2pix_nest(nb, zz, pp);
     double o[5];
-    patch_lens_fields(V, b, nv, o);
+    double et[3], ep[3];
+    tangent_basis(nv, et, ep);
+    patch_lens_fields(V, b, nv, et, ep, o);
     if (a_th) a_th[k] = o[0];
     if (a_ph) a_ph[k] = o[1];
     if (u_tt) u_tt[k] = o[2];

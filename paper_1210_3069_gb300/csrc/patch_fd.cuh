@@ -36,6 +36,13 @@ __device__ __forceinline__ int fd_stencil(int k, int n, int order, double w[5]) 
   return n - 5;
 }
 
+// Tangent basis (theta-hat, phi-hat) at the unit vector n.
+__device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
+  const double r2 = n[0] * n[0] + n[1] * n[1], ir = rsqrt(r2), rho = r2 * ir;
+  t[0] = n[2] * n[0] * ir; t[1] = n[2] * n[1] * ir; t[2] = -rho;
+  p[0] = -n[1] * ir; p[1] = n[0] * ir; p[2] = 0.0;
+}
+
 template <typename T>
 __device__ __forceinline__ double uat(const T* u, int n, int i, int j) {
   return (double)u[(size_t)(i + 1) * (n + 2) + (j + 1)];
@@ -81,20 +88,21 @@ __device__ __forceinline__ int fd_blend(int k, int n, double f, double w1[6], do
   return first;
 }
 
-// Lens fields at unit vector nv from patch potential u (n x n cells of size
-// h, ghost-ring layout), R the patch rotation.  The five partials of the four
+// Lens fields at unit vector nv (tangent basis et, ep there) from patch
+// potential u (n x n cells of size h, ghost-ring layout), R the patch rotation.  The five partials of the four
 // cells around the point are blended bilinearly; since each partial is a
 // tensor-product stencil, the blend is one tensor-product stencil on a 6 x 6
 // block of cells.  The patch angles' sines and cosines come from the
 // components of the rotated unit vector.
 template <typename T>
 __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h, double inv_h, const double* R,
-                                                    const double nv[3], double out[5]) {
+                                                    const double nv[3], const double et[3], const double ep[3],
+                                                    double out[5]) {
   // patch-frame vector and angles
   const double vx = R[0] * nv[0] + R[1] * nv[1] + R[2] * nv[2];
   const double vy = R[3] * nv[0] + R[4] * nv[1] + R[5] * nv[2];
   const double vz = R[6] * nv[0] + R[7] * nv[1] + R[8] * nv[2];
-  const double rho = sqrt(vx * vx + vy * vy);
+  const double r2 = vx * vx + vy * vy, is = rsqrt(r2), rho = r2 * is;
   const double thp = atan2(rho, vz);
   const double php = atan2(vy, vx);
   const double x = (thp - 0.5 * kPi) * inv_h + 0.5 * n - 0.5;
@@ -144,7 +152,6 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   // Appendix A in the patch basis at the point: sin(theta') = rho, cos(theta') = vz
   // (the rotated vector is a unit vector), sin(phi') = vy / rho, cos(phi') = vx / rho
   const double s = rho, co = vz;
-  const double is = 1.0 / rho;
   const double a_t = -v0, a_p = -v1 * is;
   const double u_tt = v2;
   const double u_pp = v3 * is * is + co * is * v0;
@@ -159,9 +166,6 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
     tg[k] = R[k] * tl[0] + R[3 + k] * tl[1] + R[6 + k] * tl[2];
     pg[k] = R[k] * pl[0] + R[3 + k] * pl[1] + R[6 + k] * pl[2];
   }
-  const double gr = sqrt(nv[0] * nv[0] + nv[1] * nv[1]), igr = 1.0 / gr;
-  const double et[3] = {nv[2] * nv[0] * igr, nv[2] * nv[1] * igr, -gr};
-  const double ep[3] = {-nv[1] * igr, nv[0] * igr, 0.0};
   const double q00 = et[0] * tg[0] + et[1] * tg[1] + et[2] * tg[2];
   const double q01 = et[0] * pg[0] + et[1] * pg[1] + et[2] * pg[2];
   const double q10 = ep[0] * tg[0] + ep[1] * tg[1] + ep[2] * tg[2];
@@ -176,9 +180,10 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   out[4] = m00 * q10 + m01 * q11;            // U_tp
 }
 
-__device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], double out[5]) {
+__device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], const double et[3],
+                                                  const double ep[3], double out[5]) {
   const size_t stride = (size_t)(V.n + 2) * (V.n + 2);
-  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.inv_h, V.rot + 9 * (size_t)b, nv, out);
+  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.inv_h, V.rot + 9 * (size_t)b, nv, et, ep, out);
 }
 
 }  // namespace clc

@@ -58,12 +58,6 @@ __global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
   }
 }
 
-__device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
-  const double rho = sqrt(n[0] * n[0] + n[1] * n[1]), ir = 1.0 / rho;
-  t[0] = n[2] * n[0] * ir; t[1] = n[2] * n[1] * ir; t[2] = -rho;
-  p[0] = -n[1] * ir; p[1] = n[0] * ir; p[2] = 0.0;
-}
-
 __device__ __forceinline__ void cross3(const double a[3], const double b[3], double c[3]) {
   c[0] = a[1] * b[2] - a[2] * b[1];
   c[1] = a[2] * b[0] - a[0] * b[2];
@@ -131,26 +125,45 @@ struct StepCoef {
   double c, d, dchi2;
 };
 
-// transport matrix Q (2x2) from the basis at n0 to the basis at n1
-__device__ __forceinline__ void transport_q(const double n0[3], const double n1[3], double Q[4]) {
+// Transport matrix Q (2x2) from the basis (t0, p0) at n0 to the basis at n1
+// along the great circle: the rotation R taking n0 to n1 maps (t0, p0, n0)
+// to the right-handed frame (R t0, n1 x R t0, n1) of the tangent plane at n1,
+// so Q is the plane rotation [[c, -s], [s, c]] with c = t1 . R t0,
+// s = p1 . R t0.
+__device__ __forceinline__ void transport_q(const double n0[3], const double t0[3], const double n1[3],
+                                            double Q[4]) {
   double cr[3];
   cross3(n0, n1, cr);
-  const double s = sqrt(dot3(cr, cr));
+  const double s2 = dot3(cr, cr);
   const double c = dot3(n0, n1);
-  double t0[3], p0[3], t1[3], p1[3];
-  tangent_basis(n0, t0, p0);
+  double t1[3], p1[3];
   tangent_basis(n1, t1, p1);
-  double tr[3], pr[3];
-  if (s > 0.0) {
-    const double is = 1.0 / s;
+  double tr[3];
+  if (s2 > 0.0) {
+    const double is = rsqrt(s2), s = s2 * is;
     const double k[3] = {cr[0] * is, cr[1] * is, cr[2] * is};
     rodrigues(t0, k, c, s, tr);
-    rodrigues(p0, k, c, s, pr);
   } else {
-    for (int i = 0; i < 3; ++i) { tr[i] = t0[i]; pr[i] = p0[i]; }
+    for (int i = 0; i < 3; ++i) tr[i] = t0[i];
   }
-  Q[0] = dot3(t1, tr); Q[1] = dot3(t1, pr);
-  Q[2] = dot3(p1, tr); Q[3] = dot3(p1, pr);
+  Q[0] = dot3(t1, tr);
+  Q[2] = dot3(p1, tr);
+  Q[1] = -Q[2];
+  Q[3] = Q[0];
+}
+
+// sin and cos of an angle, by their Taylor series through x^9 and x^10 for
+// |x| < 2^-5 (first omitted terms below 1e-22 relative), else by sincos
+__device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
+  if (fabs(x) < 0.03125) {
+    const double x2 = x * x;
+    *s = x * (1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0) * (1.0 - x2 * (1.0 / 72.0)))));
+    *c = 1.0 - x2 * 0.5 *
+                   (1.0 - x2 * (1.0 / 12.0) *
+                              (1.0 - x2 * (1.0 / 30.0) * (1.0 - x2 * (1.0 / 56.0) * (1.0 - x2 * (1.0 / 90.0)))));
+  } else {
+    sincos(x, s, c);
+  }
 }
 
 __device__ __forceinline__ void qaqt(const double Q[4], const double A[4], double o[4]) {
@@ -171,10 +184,12 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     for (int c = 0; c < 3; ++c) { x[c] = R.x[c * n + k]; be[c] = R.beta[c * n + k]; }
 #pragma unroll
     for (int c = 0; c < 4; ++c) { A[c] = R.A[c * n + k]; Ap[c] = R.Ap[c * n + k]; }
-    const double ixn = 1.0 / sqrt(dot3(x, x));
+    const double ixn = rsqrt(dot3(x, x));
     const double nv[3] = {x[0] * ixn, x[1] * ixn, x[2] * ixn};
+    double t[3], q[3];
+    tangent_basis(nv, t, q);
     double L[5];
-    if (kMG) patch_lens_fields(V, R.bundle[k], nv, L);
+    if (kMG) patch_lens_fields(V, R.bundle[k], nv, t, q, L);
     else map_lens_fields(M, nside_maps, nv, L);
     // Eq. Atraj in the basis at n
     const double U[4] = {L[2], L[4], L[4], L[3]};
@@ -184,18 +199,16 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     An[2] = (1.0 - sc.c) * Ap[2] + sc.c * A[2] - sc.d * (U[2] * A[0] + U[3] * A[2]);
     An[3] = (1.0 - sc.c) * Ap[3] + sc.c * A[3] - sc.d * (U[2] * A[1] + U[3] * A[3]);
     // Eq. betaprop: rotate beta about n x alpha by |alpha|
-    double t[3], q[3];
-    tangent_basis(nv, t, q);
     const double av[3] = {L[0] * t[0] + L[1] * q[0], L[0] * t[1] + L[1] * q[1], L[0] * t[2] + L[1] * q[2]};
-    const double am = sqrt(dot3(av, av));
+    const double a2 = dot3(av, av);
     double bn[3] = {be[0], be[1], be[2]};
-    if (am > 0.0) {
+    if (a2 > 0.0) {
       double kx[3];
       cross3(nv, av, kx);
-      const double iam = 1.0 / am;
+      const double iam = rsqrt(a2), am = a2 * iam;
       const double kk[3] = {kx[0] * iam, kx[1] * iam, kx[2] * iam};
       double sn, cs;
-      sincos(am, &sn, &cs);
+      sincos_small(am, &sn, &cs);
       rodrigues(be, kk, cs, sn, bn);
     }
     // Eq. posprop: lambda > 0 root, rationalised
@@ -204,11 +217,11 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     double x1[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) x1[c] = x[c] + lam * bn[c];
-    const double ix1 = 1.0 / sqrt(dot3(x1, x1));
+    const double ix1 = rsqrt(dot3(x1, x1));
     const double n1[3] = {x1[0] * ix1, x1[1] * ix1, x1[2] * ix1};
     // Appendix B: transport A^(n+1) and A^(n) to the basis at the new point
     double Q[4], Ao[4], Apo[4];
-    transport_q(nv, n1, Q);
+    transport_q(nv, t, n1, Q);
     qaqt(Q, An, Ao);
     qaqt(Q, A, Apo);
 #pragma unroll
