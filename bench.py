@@ -72,7 +72,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop
 KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
            "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",
-           "k_degrade", "k_rays_init", "k_counts_to_kappa", "k_max_ratio")
+           "k_degrade", "k_rays_init", "k_counts_to_kappa", "k_max_ratio", "k_split_ff")
 
 
 def load_peaks():

@@ -174,10 +174,19 @@ __global__ void k_mg_setup_defect(int n, const double* __restrict__ rot, const d
   if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
 }
 
+// Float-float form of the four weights of a plan entry (same 32 bytes as
+// the FP64 form), for the mixed-precision set-up.
+struct alignas(32) FF4 {
+  float2 w[4];
+};
+
 // Interpolation plan of one map for the positions of a patch level: either
 // all (n+2)^2 positions (ring = 1) or the n^2 interior cells (ring = 0).
+// ffw: weights stored as float-float pairs.  Entries that need the 8-pixel
+// polar stencil keep (theta, phi) in FP64 with index -1.
 __global__ void k_mg_plan(int n, int ring, const double* __restrict__ rot, const double* __restrict__ pvec, int nside,
-                          const double* __restrict__ ring_th, int4* __restrict__ idx, double4_32a* __restrict__ w) {
+                          const double* __restrict__ ring_th, int ffw, int4* __restrict__ idx,
+                          double4_32a* __restrict__ w) {
   const int b = blockIdx.z;
   const int side = n + 2;
   const int m = ring ? side : n;
@@ -194,7 +203,77 @@ __global__ void k_mg_plan(int n, int ring, const double* __restrict__ rot, const
     return;
   }
   idx[pos] = make_int4((int)o.p[0], (int)o.p[1], (int)o.p[2], (int)o.p[3]);
-  w[pos] = double4_32a{o.w[0], o.w[1], o.w[2], o.w[3]};
+  if (ffw) {
+    FF4 q;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q.w[k] = from_double<float2>(o.w[k]);
+    reinterpret_cast<FF4*>(w)[pos] = q;
+  } else {
+    w[pos] = double4_32a{o.w[0], o.w[1], o.w[2], o.w[3]};
+  }
+}
+
+// FP64 map -> float-float pairs
+__global__ void k_split_ff(const double* __restrict__ src, float2* __restrict__ dst, int64_t n) {
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = from_double<float2>(src[k]);
+}
+
+// plan interpolation in float-float arithmetic (FP32 pipe); polar entries in FP64
+__device__ __forceinline__ float2 apply_plan_ff(const float2* __restrict__ map_ff, const double* __restrict__ map,
+                                                int nside, const double* __restrict__ ring_th, int4 ix,
+                                                const double4_32a* __restrict__ wp, size_t pos) {
+  if (ix.x < 0) {
+    const double4_32a w = wp[pos];
+    return from_double<float2>(interp_map_tab(map, nside, ring_th, w.x, w.y));
+  }
+  const FF4 q = reinterpret_cast<const FF4*>(wp)[pos];
+  float2 v = ff_mul(q.w[0], map_ff[ix.x]);
+  v = ff_add(v, ff_mul(q.w[1], map_ff[ix.y]));
+  v = ff_add(v, ff_mul(q.w[2], map_ff[ix.z]));
+  return ff_add(v, ff_mul(q.w[3], map_ff[ix.w]));
+}
+
+// Mixed set-up, float-float: base = psi_SHT interpolated (2 psi_SHT on the
+// ghost ring), kept both as float-float pairs and as their FP64 sum.
+__global__ void k_mg_setup_base_ff(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
+                                   const float2* __restrict__ psi_ff, const double* __restrict__ psi, int ns,
+                                   const double* __restrict__ ring_th, float2* __restrict__ base_ff,
+                                   double* __restrict__ base) {
+  const int b = blockIdx.z;
+  const int k1 = blockIdx.y * kBY + threadIdx.y, k2 = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  if (k1 >= side || k2 >= side) return;
+  const size_t pos = (size_t)b * side * side + (size_t)k1 * side + k2;
+  float2 v = apply_plan_ff(psi_ff, psi, ns, ring_th, idx[pos], w, pos);
+  if (k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1) v = make_float2(2.f * v.x, 2.f * v.y);
+  base_ff[pos] = v;
+  base[pos] = (double)v.x + (double)v.y;
+}
+
+// Mixed set-up, float-float: defect source f' = kappa - L base at the cells,
+// ||kappa||^2 per patch.
+__global__ void k_mg_setup_defect_ff(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
+                                     const float2* __restrict__ kap_ff, const double* __restrict__ kappa, int nf,
+                                     const double* __restrict__ ring_th, const float2* __restrict__ base_ff,
+                                     const float2* __restrict__ coef, const float2* __restrict__ diag,
+                                     float2* __restrict__ f, double* __restrict__ fnorm) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  const int side = n + 2;
+  float ff = 0.f;
+  if (i < n && j < n) {
+    const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
+    const float2 src = apply_plan_ff(kap_ff, kappa, nf, ring_th, idx[pos], w, pos);
+    const float2* U = base_ff + (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
+    // L base = aS uS + aN uN + b (uE + uW) - diag uC
+    const float2 nb = ff_add(ff_add(ff_mul(coef[i], U[side]), ff_mul(coef[n + i], U[-side])),
+                             ff_add(ff_mul(coef[2 * n + i], ff_add(U[1], U[-1])), ff_neg(ff_mul(diag[i * n + j], U[0]))));
+    f[(size_t)b * n * n + fidx(n, i, j)] = ff_add(src, ff_neg(nb));
+    ff = src.x * src.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  if (threadIdx.x == 0 && ff != 0.f) atomicAdd(fnorm + b, (double)ff);
 }
 
 __device__ __forceinline__ double apply_plan(const double* __restrict__ map, int nside, const double* __restrict__ ring_th,
@@ -503,7 +582,8 @@ struct BandGeo {
   static constexpr int nh = N / 2;                          // colour cells per row
   static constexpr int P = N / 2 + 4;                       // row pitch (upitch)
   static constexpr int br = N < kBandRows ? N : kBandRows;  // band rows
-  static constexpr int cg = nh >= 32 ? nh / 32 : 1;         // warps across a row
+  static constexpr int kc = nh >= 64 ? 2 : 1;               // columns per thread in a half-sweep (32 apart)
+  static constexpr int cg = nh >= 32 * kc ? nh / (32 * kc) : 1;   // warps across a row
   static constexpr int rg = (kBandThreads / 32) / cg;       // runs of rows per half-sweep
 };
 
@@ -594,16 +674,17 @@ struct IntC {
 };
 
 // One colour of a red-black sweep over the patch rows ga .. gb - 1 (all
-// inside the patch, all columns).  The column parity of the colour flips
-// from row to row, so rows are taken in pairs with the parity fixed at
-// compile time.
+// inside the patch, all columns).  A thread owns kc columns 32 apart and
+// walks a run of rows; the column parity of the colour flips from row to
+// row, so rows are taken in pairs with the parity fixed at compile time.
 template <typename T, int N>
 __device__ __forceinline__ void band_half_sweep(const Band<T, N>& B, int colour, int ga, int gb) {
   using G = BandGeo<N>;
+  constexpr int KC = G::kc;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunk = (gb - ga + G::rg - 1) / G::rg;
   const int r0 = ga + (warp / G::cg) * chunk, r1 = min(gb, r0 + chunk);
-  const int k = 32 * (warp % G::cg) + lane;
+  const int k = 32 * KC * (warp % G::cg) + lane;
   if (r0 >= r1 || k >= G::nh) return;
   const int lr = r0 - B.gi0;
   const T* O = B.u + (colour ^ 1) * B.uplane + lr * G::P + k + 1;   // the other colour, row r0, column k
@@ -611,19 +692,29 @@ __device__ __forceinline__ void band_half_sweep(const Band<T, N>& B, int colour,
   const T* F = B.f + colour * B.fplane + lr * G::nh + k;
   const Quad<T>* Q = B.ra + lr;
   const Quad<T>* R = B.rb + lr;
-  const bool left = k == 0, right = k == G::nh - 1;
-  T on = O[-G::P], oc = O[0];
+  const bool left = k == 0, right = k + 32 * (KC - 1) == G::nh - 1;
+  T on[KC], oc[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    on[c] = O[32 * c - G::P];
+    oc[c] = O[32 * c];
+  }
   auto step = [&](auto pc) {
     constexpr int p = decltype(pc)::value;   // column parity of the colour in this row
-    const T os = O[G::P];
-    const T x = O[2 * p - 1];
-    const T uE = p ? x : oc, uW = p ? oc : x;
     const Quad<T> q = *Q;
-    const T id = (p ? right : left) ? R->x : q.w;
-    const T v = fma(q.z, uE + uW, fma(q.y, on, fma(q.x, os, -F[0])));
-    C[0] = v * id;
-    on = oc;
-    oc = os;
+    const bool edge = p ? right : left;
+    const T ide = edge ? R->x : q.w;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      const T os = O[32 * c + G::P];
+      const T x = O[32 * c + 2 * p - 1];
+      const T uE = p ? x : oc[c], uW = p ? oc[c] : x;
+      const T id = (p ? c == KC - 1 : c == 0) ? ide : q.w;
+      const T v = fma(q.z, uE + uW, fma(q.y, on[c], fma(q.x, os, -F[32 * c])));
+      C[32 * c] = v * id;
+      on[c] = oc[c];
+      oc[c] = os;
+    }
     O += G::P;
     C += G::P;
     F += G::nh;
@@ -1171,8 +1262,32 @@ struct MG {
   // base (SHT solution + edge values), defect source f' = kappa - L base,
   // ||kappa||^2 per patch, and a zero starting correction
   int setup(const double* kappa_fine) {
+    if (mixed && s->plan) return setup_ff(kappa_fine);
     if (mixed) return setup_t<float2>(kappa_fine, (float2*)s->fd64.p);
     return setup_t<T>(kappa_fine, F(0));
+  }
+
+  // mixed set-up in float-float arithmetic: both maps split once, then the
+  // plans applied on the FP32 pipe
+  int setup_ff(const double* kappa_fine) {
+    const int n = s->sizes[0];
+    const dim3 blk(kBX, kBY);
+    const int64_t ns2 = 12ll * s->p.nside_sht * s->p.nside_sht, nf2 = 12ll * s->nside_fine * s->nside_fine;
+    cudaMemsetAsync(s->fnorm.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    CLC_LAUNCH(ctx, "k_split_ff", k_split_ff, blocks_for(ctx, ns2, 256), 256, 0, (const double*)s->psi_sht.p,
+               (float2*)s->psi_ff.p, ns2);
+    CLC_LAUNCH(ctx, "k_split_ff", k_split_ff, blocks_for(ctx, nf2, 256), 256, 0, kappa_fine, (float2*)s->kap_ff.p,
+               nf2);
+    CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base_ff, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
+               (const int4*)s->plan_psi_idx.p, (const double4_32a*)s->plan_psi_w.p, (const float2*)s->psi_ff.p,
+               (const double*)s->psi_sht.p, s->p.nside_sht, (const double*)s->ring_th_sht.p, (float2*)s->base_ff.p,
+               (double*)s->base.p);
+    CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect_ff, grid3(n, n, s->npatch), blk, 0, n,
+               (const int4*)s->plan_kap_idx.p, (const double4_32a*)s->plan_kap_w.p, (const float2*)s->kap_ff.p,
+               kappa_fine, s->nside_fine, (const double*)s->ring_th_fine.p, (const float2*)s->base_ff.p,
+               (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, (float2*)s->fd64.p, (double*)s->fnorm.p);
+    cudaMemsetAsync(s->e64.p, 0, s->e64.bytes, ctx->stream);
+    return launch_check(ctx, "MG set-up (float-float)");
   }
 
   template <typename S>
@@ -1453,15 +1568,20 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     const size_t bytes = (pr + pk) * (sizeof(int4) + 4 * sizeof(double));
     size_t fb = 0, tb = 0;
     cudaMemGetInfo(&fb, &tb);
-    if (bytes + (4ull << 30) < fb && alloc(s->plan_psi_idx, pr * sizeof(int4)) &&
+    const bool mx = p->precision == CLC_MIXED;
+    const int64_t ns2 = 12ll * p->nside_sht * p->nside_sht, nf2 = 12ll * nf * nf;
+    const size_t ffb = mx ? (pr + ns2 + nf2) * sizeof(float2) : 0;   // base, psi and kappa as float-float
+    if (bytes + ffb + (4ull << 30) < fb && alloc(s->plan_psi_idx, pr * sizeof(int4)) &&
         alloc(s->plan_psi_w, pr * 4 * sizeof(double)) && alloc(s->plan_kap_idx, pk * sizeof(int4)) &&
-        alloc(s->plan_kap_w, pk * 4 * sizeof(double))) {
+        alloc(s->plan_kap_w, pk * 4 * sizeof(double)) &&
+        (!mx || (alloc(s->base_ff, pr * sizeof(float2)) && alloc(s->psi_ff, ns2 * sizeof(float2)) &&
+                 alloc(s->kap_ff, nf2 * sizeof(float2))))) {
       const dim3 blk(kBX, kBY);
       CLC_LAUNCH(ctx, "k_mg_plan", k_mg_plan, grid3(n0 + 2, n0 + 2, s->npatch), blk, 0, (int)n0, 1,
                  (const double*)s->rot.p, (const double*)s->pvec.p, p->nside_sht, (const double*)s->ring_th_sht.p,
-                 (int4*)s->plan_psi_idx.p, (double4_32a*)s->plan_psi_w.p);
+                 (int)mx, (int4*)s->plan_psi_idx.p, (double4_32a*)s->plan_psi_w.p);
       CLC_LAUNCH(ctx, "k_mg_plan", k_mg_plan, grid3(n0, n0, s->npatch), blk, 0, (int)n0, 0, (const double*)s->rot.p,
-                 (const double*)s->pvec.p, nf, (const double*)s->ring_th_fine.p, (int4*)s->plan_kap_idx.p,
+                 (const double*)s->pvec.p, nf, (const double*)s->ring_th_fine.p, (int)mx, (int4*)s->plan_kap_idx.p,
                  (double4_32a*)s->plan_kap_w.p);
       s->plan = true;
     }

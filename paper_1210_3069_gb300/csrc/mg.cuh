@@ -21,6 +21,9 @@ struct clc_plane_solution {
   bool plan = false;
   clc::Buffer plan_psi_idx, plan_psi_w;   // [npatch][(n+2)^2]: int4, double[4]
   clc::Buffer plan_kap_idx, plan_kap_w;   // [npatch][n^2]
+  // CLC_MIXED with plans: plan weights as float-float pairs, and float-float
+  // copies of base, psi_SHT and kappa for the set-up on the FP32 pipe
+  clc::Buffer base_ff, psi_ff, kap_ff;
   clc::Buffer coef[16];         // double[4][n] per level: aS, aN, b, area
   clc::Buffer invd[16];         // double[n][n] per level: 1 / diagonal
   clc::Buffer diag[16];         // double[n][n] per level: diagonal

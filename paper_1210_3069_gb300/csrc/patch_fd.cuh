@@ -36,6 +36,14 @@ __device__ __forceinline__ int fd_stencil(int k, int n, int order, double w[5]) 
   return n - 5;
 }
 
+// atan(t) by the Gregory series through t^13 for |t| < 0.04 (first omitted
+// term below 1e-20 relative).
+__device__ __forceinline__ double atan_small(double t) {
+  const double t2 = t * t;
+  return t * (1.0 - t2 * ((1.0 / 3.0) - t2 * ((1.0 / 5.0) - t2 * ((1.0 / 7.0) - t2 * ((1.0 / 9.0) -
+                                                                                    t2 * ((1.0 / 11.0) - t2 * (1.0 / 13.0)))))));
+}
+
 // Tangent basis (theta-hat, phi-hat) at the unit vector n.
 __device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
   const double r2 = n[0] * n[0] + n[1] * n[1], ir = rsqrt(r2), rho = r2 * ir;
@@ -103,9 +111,12 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   const double vy = R[3] * nv[0] + R[4] * nv[1] + R[5] * nv[2];
   const double vz = R[6] * nv[0] + R[7] * nv[1] + R[8] * nv[2];
   const double r2 = vx * vx + vy * vy, is = rsqrt(r2), rho = r2 * is;
-  const double thp = atan2(rho, vz);
-  const double php = atan2(vy, vx);
-  const double x = (thp - 0.5 * kPi) * inv_h + 0.5 * n - 0.5;
+  // theta' - pi/2 = -atan(vz / rho) and phi' = atan(vy / vx): near the patch
+  // centre (theta', phi') = (pi/2, 0) both ratios are small
+  const double tz = vz * is, ty = vx > 0.0 ? vy / vx : 1.0;
+  const double dth = fabs(tz) < 0.04 ? -atan_small(tz) : atan2(rho, vz) - 0.5 * kPi;
+  const double php = fabs(ty) < 0.04 ? atan_small(ty) : atan2(vy, vx);
+  const double x = dth * inv_h + 0.5 * n - 0.5;
   const double y = php * inv_h + 0.5 * n - 0.5;
   double i0 = floor(x), j0 = floor(y);
   i0 = fmin(fmax(i0, 0.0), (double)(n - 2));
