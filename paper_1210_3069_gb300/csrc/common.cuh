@@ -217,6 +217,52 @@ __device__ __forceinline__ int64_t nest2ring(int nside, int64_t pix) {
   return nbefore + jp - 1;
 }
 
+// NEST index of the RING pixel at position j (0-based) of ring i (1-based):
+// base face and in-face coordinates by inverting the ring / position
+// formulas of nest2ring, integer arithmetic only.  In the polar caps the face
+// is j / (pixels per face in the ring); in the equatorial belt the face row
+// (north, equatorial, south faces) follows from the ring, and the face is the
+// one whose in-face coordinates (S +- D) / 2 lie inside [0, nside).
+__device__ __forceinline__ int64_t ring_pos2nest(int nside, int i, int64_t j) {
+  const int64_t n = nside;
+  int64_t f = 0, ix = 0, iy = 0;
+  if (i < nside) {                 // north cap, faces 0..3: ring i holds i pixels of each
+    const int64_t nr = i;
+    f = j / nr;
+    const int64_t b = j - f * nr;
+    ix = n - nr + b;
+    iy = n - 1 - b;
+  } else if (i > 3 * nside) {      // south cap, faces 8..11
+    const int64_t nr = 4 * n - i;
+    const int64_t q = j / nr;
+    f = 8 + q;
+    ix = j - q * nr;
+    iy = nr - 1 - ix;
+  } else {                         // equatorial belt
+    const int kshift = (i - nside) & 1;
+    const int64_t t = 2 * j + 1 - kshift;
+    bool found = false;
+    for (int row = 2; row <= 4 && !found; ++row) {
+      const int64_t S = row * n - i - 1;   // ix + iy on this face row
+      if (S < 0 || S > 2 * n - 2) continue;
+      for (int q = 0; q < 4; ++q) {
+        const int64_t jpll = row == 3 ? 2 * q : 2 * q + 1;
+        int64_t D = t - jpll * n;         // ix - iy, up to a multiple of 8 nside
+        if (D > 4 * n) D -= 8 * n;
+        if (D <= -4 * n) D += 8 * n;
+        if (((S + D) & 1) == 0 && D <= S && -D <= S && D <= 2 * n - 2 - S && -D <= 2 * n - 2 - S) {
+          f = 4 * (row - 2) + q;
+          ix = (S + D) / 2;
+          iy = (S - D) / 2;
+          found = true;
+          break;
+        }
+      }
+    }
+  }
+  return f * n * n + spread_bits(ix) + (spread_bits(iy) << 1);
+}
+
 // Geometry of ring i (1-based, 1 <= i <= 4 nside - 1)
 struct Ring {
   double z, s;      // cos / sin theta of the ring

@@ -236,6 +236,9 @@ __device__ __forceinline__ float2 apply_plan_ff(const float2* __restrict__ map_f
 
 // Mixed set-up, float-float: base = psi_SHT interpolated (2 psi_SHT on the
 // ghost ring), kept both as float-float pairs and as their FP64 sum.
+// Rows per thread of the defect set-up (independent kappa gathers in flight).
+constexpr int kSetupRows = 4;
+
 __global__ void k_mg_setup_base_ff(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
                                    const float2* __restrict__ psi_ff, const double* __restrict__ psi, int ns,
                                    const double* __restrict__ ring_th, float2* __restrict__ base_ff,
@@ -259,10 +262,13 @@ __global__ void k_mg_setup_defect_ff(int n, const int4* __restrict__ idx, const 
                                      const float2* __restrict__ coef, const float2* __restrict__ diag,
                                      float2* __restrict__ f, double* __restrict__ fnorm) {
   const int b = blockIdx.z;
-  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  const int j = blockIdx.x * kBX + threadIdx.x;
   const int side = n + 2;
   float ff = 0.f;
-  if (i < n && j < n) {
+#pragma unroll
+  for (int kr = 0; kr < kSetupRows; ++kr) {
+    const int i = (blockIdx.y * kSetupRows + kr) * kBY + threadIdx.y;
+    if (i >= n || j >= n) continue;
     const size_t pos = (size_t)b * n * n + (size_t)i * n + j;
     const float2 src = apply_plan_ff(kap_ff, kappa, nf, ring_th, idx[pos], w, pos);
     const float2* U = base_ff + (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
@@ -270,7 +276,7 @@ __global__ void k_mg_setup_defect_ff(int n, const int4* __restrict__ idx, const 
     const float2 nb = ff_add(ff_add(ff_mul(coef[i], U[side]), ff_mul(coef[n + i], U[-side])),
                              ff_add(ff_mul(coef[2 * n + i], ff_add(U[1], U[-1])), ff_neg(ff_mul(diag[i * n + j], U[0]))));
     f[(size_t)b * n * n + fidx(n, i, j)] = ff_add(src, ff_neg(nb));
-    ff = src.x * src.x;
+    ff = fmaf(src.x, src.x, ff);
   }
   for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
   if (threadIdx.x == 0 && ff != 0.f) atomicAdd(fnorm + b, (double)ff);
@@ -1278,11 +1284,13 @@ struct MG {
                (float2*)s->psi_ff.p, ns2);
     CLC_LAUNCH(ctx, "k_split_ff", k_split_ff, blocks_for(ctx, nf2, 256), 256, 0, kappa_fine, (float2*)s->kap_ff.p,
                nf2);
-    CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base_ff, grid3(n + 2, n + 2, s->npatch), blk, 0, n,
+    const dim3 gb = grid3(n + 2, n + 2, s->npatch);
+    const dim3 gd((n + kBX - 1) / kBX, (n + kBY * kSetupRows - 1) / (kBY * kSetupRows), s->npatch);
+    CLC_LAUNCH(ctx, "k_mg_setup_base", k_mg_setup_base_ff, gb, blk, 0, n,
                (const int4*)s->plan_psi_idx.p, (const double4_32a*)s->plan_psi_w.p, (const float2*)s->psi_ff.p,
                (const double*)s->psi_sht.p, s->p.nside_sht, (const double*)s->ring_th_sht.p, (float2*)s->base_ff.p,
                (double*)s->base.p);
-    CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect_ff, grid3(n, n, s->npatch), blk, 0, n,
+    CLC_LAUNCH(ctx, "k_mg_setup_defect", k_mg_setup_defect_ff, gd, blk, 0, n,
                (const int4*)s->plan_kap_idx.p, (const double4_32a*)s->plan_kap_w.p, (const float2*)s->kap_ff.p,
                kappa_fine, s->nside_fine, (const double*)s->ring_th_fine.p, (const float2*)s->base_ff.p,
                (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, (float2*)s->fd64.p, (double*)s->fnorm.p);

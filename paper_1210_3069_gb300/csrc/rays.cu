@@ -39,22 +39,28 @@ __global__ void k_rays_init(const double* __restrict__ z, const double* __restri
   }
 }
 
-// rays at every RING pixel centre of nside
+// rays at every RING pixel centre of nside: one CTA per ring, so the ring
+// geometry is computed once; longitudes by sincospi of (2 j + shift) / npix
+// and bundles by the integer RING -> NEST conversion
 __global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
   const int64_t n = R.n;
-  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j;
-    const int i = pix2ring(nside, k, &j);
-    const Ring r = ring_geom(nside, i);
-    const double pp = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
-    const double v[3] = {r.s * cos(pp), r.s * sin(pp), r.z};
+  const int i = blockIdx.x + 1;
+  const Ring r = ring_geom(nside, i);
+  const double inv = 1.0 / (double)r.npix;
+  const int shift = r.phi0 != 0.0 ? 1 : 0;
+  const int bshift = nb > 0 ? 2 * (ilog2(nside) - ilog2(nb)) : 0;
+  for (int j = threadIdx.x; j < r.npix; j += blockDim.x) {
+    const int64_t k = r.first + j;
+    double sp, cp;
+    sincospi((double)(2 * j + shift) * inv, &sp, &cp);
+    const double v[3] = {r.s * cp, r.s * sp, r.z};
     for (int c = 0; c < 3; ++c) {
       R.x[c * n + k] = chi0 * v[c];
       R.beta[c * n + k] = v[c];
     }
     R.A[k] = 1.0; R.A[n + k] = 0.0; R.A[2 * n + k] = 0.0; R.A[3 * n + k] = 1.0;
     R.Ap[k] = 1.0; R.Ap[n + k] = 0.0; R.Ap[2 * n + k] = 0.0; R.Ap[3 * n + k] = 1.0;
-    if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)(ang2pix_nest(nside, r.z, pp) >> (2 * (ilog2(nside) - ilog2(nb))));
+    if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)(ring_pos2nest(nside, i, j) >> bshift);
   }
 }
 
@@ -274,7 +280,7 @@ extern "C" int clc_rays_init_pixels(clc_ctx* ctx, int nside, double chi0, int nb
       r->n != 12ll * nside * nside)
     return set_err(ctx, CLC_EINVAL, "clc_rays_init_pixels: need n = 12 nside^2, chi0 > 0, nside_bundle <= nside");
   cudaSetDevice(ctx->device);
-  CLC_LAUNCH(ctx, "k_rays_init", k_rays_init_pixels, blocks(ctx, r->n, 256), 256, 0, nside, chi0, nb, ray_ptrs(r));
+  CLC_LAUNCH(ctx, "k_rays_init", k_rays_init_pixels, 4 * nside - 1, 256, 0, nside, chi0, nb, ray_ptrs(r));
   return launch_check(ctx, "k_rays_init_pixels");
 }
 

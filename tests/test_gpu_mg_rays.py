@@ -168,6 +168,27 @@ def test_rays_sht_path_matches_oracle():
     assert torch.allclose(rs2.A, rs.A, rtol=0, atol=1e-13)
 
 
+@pytest.mark.parametrize("nside,nb", [(8, 1), (64, 4), (256, 16)])
+def test_rays_at_pixel_centres(nside, nb):
+    """Rays started at every RING pixel centre: positions chi0 n_p, unit
+    directions, identity Jacobians, and the bundle = the pixel's NEST index at
+    the bundle resolution (exact)."""
+    c = ctx()
+    chi0 = 123.0
+    rs = c.rays(hp.npix(nside))
+    c.rays_init_pixels(rs, nside, chi0, nb)
+    c.sync()
+    p = torch.arange(hp.npix(nside))
+    nv = hp.pix2vec_ring(nside, p)
+    # a few units in the last place: sincospi against the oracle's cos / sin
+    assert float((rs.x.T.cpu() - chi0 * nv).abs().max()) <= 4e-15 * chi0
+    assert float((rs.beta.T.cpu() - nv).abs().max()) <= 4e-15
+    eye = torch.tensor([1.0, 0.0, 0.0, 1.0], dtype=torch.float64)
+    assert torch.equal(rs.A.T.cpu(), eye.expand(p.numel(), 4)) and torch.equal(rs.Ap.T.cpu(), eye.expand(p.numel(), 4))
+    shift = 2 * (hp.nside_order(nside) - hp.nside_order(nb))
+    assert torch.equal(rs.bundle.cpu().long(), hp.ring2nest(nside, p) >> shift)
+
+
 def test_rays_mg_path_matches_oracle():
     import paper_1210_3069_gb300 as clc
     c = ctx()
