@@ -55,6 +55,8 @@ BATCH_WORKLOADS = {
     "sht_batch_mixed_sizes": dict(sizes=[(512, 1024)] * 32 + [(1024, 2048)] * 24 + [(2048, 4096)] * 8,
                                   seed=1210004, fp64_sample=2),
     "sht_batch_small": dict(sizes=[(128, 256)] * 8 + [(256, 512)] * 4, seed=1210004, fp64_sample=2),
+    # one full class (21 planes with derivatives) at Nside 512: the profiling case of the batch kernels
+    "sht_batch_nside512": dict(sizes=[(512, 1024)] * 21, seed=1210004, fp64_sample=1),
 }
 BATCH_METRIC = "lens planes/s (batched mixed-precision SHT Poisson, Nside 512/1024/2048, lmax = 2 Nside)"
 

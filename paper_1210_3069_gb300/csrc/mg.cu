@@ -788,7 +788,10 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
   // Restriction of the band's rows.  Thread (J, run) walks coarse rows of
   // its run; fine columns 2J, 2J + 1 of fine row i are entry J + 1 of the
   // colour arrays i & 1 and (i + 1) & 1, their outer neighbours 2J - 1 and
-  // 2J + 2 entries J and J + 2 of the other array.
+  // 2J + 2 entries J and J + 2 of the other array.  After a black half-sweep
+  // the residual of every black cell is zero (up to rounding: the cell was
+  // just relaxed against its current neighbours), so with nu >= 1 only the
+  // red children (2I, 2J) and (2I + 1, 2J + 1) contribute.
   constexpr int ncr = G::br / 2;
   constexpr int runs = kBandThreads / NC > 0 ? kBandThreads / NC : 1;
   constexpr int per = (ncr + runs - 1) / runs;
@@ -804,24 +807,39 @@ __global__ void __launch_bounds__(kBandThreads) k_band_smooth_restrict(
       const T b0 = at(2 * I + 1, 1, J + 1), b1 = at(2 * I + 1, 0, J + 1);
       const T s0 = at(2 * I + 2, 0, J + 1), s1 = at(2 * I + 2, 1, J + 1);
       T nr = 0;
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        const int i = 2 * I + di, r = i - B.gi0;
-        const T c0 = di ? b0 : a0, c1 = di ? b1 : a1;   // this row
-        const T N0 = di ? a0 : n0, N1 = di ? a1 : n1;   // row i - 1
-        const T S0 = di ? s0 : b0, S1 = di ? s1 : b1;   // row i + 1
-        const T w = at(i, di ^ 1, J);                   // u(i, 2J - 1)
-        const T e = at(i, di, J + 2);                   // u(i, 2J + 2)
-        const T f0 = B.f[di * B.fplane + r * G::nh + J];
-        const T f1 = B.f[(di ^ 1) * B.fplane + r * G::nh + J];
-        const Quad<T> q = B.ra[r], q2 = B.rb[r];
+      if (nu > 0) {
+        // red child of row 2I: column 2J; red child of row 2I + 1: column 2J + 1
+        const int r0 = 2 * I - B.gi0, r1 = r0 + 1;
+        const T w = at(2 * I, 1, J);          // u(2I, 2J - 1)
+        const T e = at(2 * I + 1, 1, J + 2);  // u(2I + 1, 2J + 2)
+        const Quad<T> q0 = B.ra[r0], p0 = B.rb[r0], q1 = B.ra[r1], p1 = B.rb[r1];
         // r = f - (aS uS + aN uN + b (uE + uW) - diag u)
-        const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
-        const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
-        T rs = 0;
-        rs += f0 - nb0;
-        rs += f1 - nb1;
-        nr = fma(q2.w, rs, nr);
+        const T nb0 = fma(q0.z, a1 + w, fma(q0.y, n0, fma(q0.x, b0, -(eL ? p0.z : p0.y) * a0)));
+        const T nb1 = fma(q1.z, e + b0, fma(q1.y, a1, fma(q1.x, s1, -(eR ? p1.z : p1.y) * b1)));
+        T rs0 = 0, rs1 = 0;
+        rs0 += B.f[r0 * G::nh + J] - nb0;
+        rs1 += B.f[r1 * G::nh + J] - nb1;
+        nr = fma(p0.w, rs0, nr);
+        nr = fma(p1.w, rs1, nr);
+      } else {
+#pragma unroll
+        for (int di = 0; di < 2; ++di) {
+          const int i = 2 * I + di, r = i - B.gi0;
+          const T c0 = di ? b0 : a0, c1 = di ? b1 : a1;   // this row
+          const T N0 = di ? a0 : n0, N1 = di ? a1 : n1;   // row i - 1
+          const T S0 = di ? s0 : b0, S1 = di ? s1 : b1;   // row i + 1
+          const T w = at(i, di ^ 1, J);                   // u(i, 2J - 1)
+          const T e = at(i, di, J + 2);                   // u(i, 2J + 2)
+          const T f0 = B.f[di * B.fplane + r * G::nh + J];
+          const T f1 = B.f[(di ^ 1) * B.fplane + r * G::nh + J];
+          const Quad<T> q = B.ra[r], q2 = B.rb[r];
+          const T nb0 = fma(q.z, c1 + w, fma(q.y, N0, fma(q.x, S0, -(eL ? q2.z : q2.y) * c0)));
+          const T nb1 = fma(q.z, e + c0, fma(q.y, N1, fma(q.x, S1, -(eR ? q2.z : q2.y) * c1)));
+          T rs = 0;
+          rs += f0 - nb0;
+          rs += f1 - nb1;
+          nr = fma(q2.w, rs, nr);
+        }
       }
       fc[b * NC * NC + fidx(NC, I, J)] = nr * rden[I];   // rden = 1 / (2 (area_2I + area_2I+1))
       n0 = b0;
@@ -860,7 +878,10 @@ __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
   }
   if (!band_wait(&bar, d_err)) return;
   // u += P(e) for the region cells in the patch: fine columns 2J, 2J + 1 of
-  // a row take the coarse columns J - 1, J, J + 1 of two coarse rows
+  // a row take the coarse columns J - 1, J, J + 1 of two coarse rows.  With
+  // nu >= 1 the first (red) half-sweep overwrites every red cell it reaches
+  // without reading it, and the red cells it does not reach are never read:
+  // only black cells need the correction.
   for (int r = warp; r < B.W; r += nw) {
     const int i = B.gi0 + r;
     if (i < 0 || i >= N) continue;
@@ -870,15 +891,15 @@ __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
     T* u0 = B.u + (i & 1) * B.uplane + r * G::P;         // column 2J at J + 1
     T* u1 = B.u + ((i + 1) & 1) * B.uplane + r * G::P;   // column 2J + 1 at J + 1
     const bool rowedge = i == 0 || i == N - 1;
+    const bool do0 = nu == 0 || (i & 1), do1 = nu == 0 || !(i & 1);   // column 2J black in odd rows
     for (int J = lane; J < NC; J += 32) {
       const int bc = J + 1;
       const T e11 = Ea[bc], d11 = Ed[bc];
-      const T c0 = (rowedge || J == 0) ? e11
-                                         : fma((T)9, e11, fma((T)3, d11 + Ea[bc - 1], Ed[bc - 1])) * (T)0.0625;
-      const T c1 = (rowedge || J == NC - 1) ? e11
-                                              : fma((T)9, e11, fma((T)3, d11 + Ea[bc + 1], Ed[bc + 1])) * (T)0.0625;
-      u0[bc] += c0;
-      u1[bc] += c1;
+      if (do0)
+        u0[bc] += (rowedge || J == 0) ? e11 : fma((T)9, e11, fma((T)3, d11 + Ea[bc - 1], Ed[bc - 1])) * (T)0.0625;
+      if (do1)
+        u1[bc] += (rowedge || J == NC - 1) ? e11
+                                             : fma((T)9, e11, fma((T)3, d11 + Ea[bc + 1], Ed[bc + 1])) * (T)0.0625;
     }
   }
   __syncthreads();
