@@ -45,6 +45,16 @@ __device__ __forceinline__ C2<T> expi_pi(T t) {
   sc_pi(t, &s, &c);
   return cx<T>(c, s);
 }
+// FP32: t reduced to [-1, 1], then the fast sincos intrinsic on pi t
+// (absolute error about 2^-21 on [-pi, pi], far inside the mixed path's
+// error budget)
+template <>
+__device__ __forceinline__ C2<float> expi_pi<float>(float t) {
+  const float r = t - 2.f * rintf(0.5f * t);
+  float s, c;
+  __sincosf(3.14159265358979f * r, &s, &c);
+  return cx<float>(c, s);
+}
 
 // e^{i pi a k / n} along k = k0, k0 + dk, ... (one call of next() per k, in
 // that order).  FP64 steps by a complex rotation (error ~ steps x 1e-16);
@@ -66,16 +76,15 @@ struct Rot<double> {
 };
 template <>
 struct Rot<float> {
-  int k, dk, n;
-  float a;
+  int k, dk;
+  float an;   // a / n
   __device__ __forceinline__ void init(int k0, int dk_, int n_, double a_) {
     k = k0;
     dk = dk_;
-    n = n_;
-    a = (float)a_;
+    an = (float)(a_ / (double)n_);
   }
   __device__ __forceinline__ C2<float> next() {
-    const C2<float> r = expi_pi<float>(a * ((float)k / (float)n));
+    const C2<float> r = expi_pi<float>(an * (float)k);
     k += dk;
     return r;
   }
@@ -181,6 +190,23 @@ __device__ void dft_any(C2<T>* s, int N, int ring_class, const PlanDevT<T>& P, L
   __syncthreads();
 }
 
+// Geometry of ring i computed once per CTA (FP64 division and square root)
+// and shared with all its threads, with 1 / sin(theta).
+struct RingS {
+  Ring r;
+  double is;
+};
+__device__ __forceinline__ RingS ring_geom_cta(int nside, int i) {
+  __shared__ RingS sh;
+  __syncthreads();   // earlier readers of sh are done
+  if (threadIdx.x == 0) {
+    sh.r = ring_geom(nside, i);
+    sh.is = 1.0 / sh.r.s;
+  }
+  __syncthreads();
+  return sh;
+}
+
 __device__ __forceinline__ int ring_class_of(int nside, int i) {
   const int ip = i < 2 * nside ? i : 4 * nside - i;
   return ip < nside ? ip : 0;
@@ -190,7 +216,7 @@ __device__ __forceinline__ int ring_class_of(int nside, int i) {
 template <typename T>
 __device__ void ring_analysis_ring(const double* __restrict__ map, int nside, int lmax, double weight,
                                    C2<T>* __restrict__ F, int ldf, const PlanDevT<T>& P, int i, C2<T>* s) {
-  const Ring r = ring_geom(nside, i);
+  const Ring r = ring_geom_cta(nside, i).r;
   const int n = r.npix, N = n / 2;
   const double* x = map + r.first;
   dft_any<T>(s, N, ring_class_of(nside, i), P, [&](int j) { return cx<T>((T)x[2 * j], (T)x[2 * j + 1]); });
@@ -283,12 +309,13 @@ __device__ __forceinline__ C2<T> spec_of(const SynthArgsT<T>& a, int mode, int f
 template <typename T>
 __device__ void ring_synthesis_ring(const SynthArgsT<T>& a, int nside, int lmax, int mode, const PlanDevT<T>& P,
                                     int i, C2<T>* s, C2<T>* Xs) {
-  const Ring r = ring_geom(nside, i);
+  const RingS rs = ring_geom_cta(nside, i);
+  const Ring& r = rs.r;
   const int n = r.npix, N = n / 2;
   const int ring0 = i - 1;
   const bool shifted = r.phi0 != 0.0;
   RingFac<T> gf;
-  gf.isd = 1.0 / r.s;
+  gf.isd = rs.is;
   gf.is2d = gf.isd * gf.isd;
   gf.cd = r.z;
   gf.is = (T)gf.isd;
