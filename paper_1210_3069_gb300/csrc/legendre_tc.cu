@@ -210,7 +210,10 @@ __device__ __forceinline__ int find_class(const TcBatchDev& b, long long idx, lo
 }
 
 // ---------------------------------------------------------------------------
-// ring FFTs (FP32) of every plane of every class
+// ring FFTs (FP32) of every plane of every class; one ring per CTA at a time
+// (512 threads for the six-field synthesis, 256 for the analysis)
+
+constexpr int kRingThreads = 512;
 
 __global__ void k_tc_ring_analysis(TcBatchDev b) {
   extern __shared__ __align__(16) unsigned char smem_ra[];
@@ -225,7 +228,7 @@ __global__ void k_tc_ring_analysis(TcBatchDev b) {
   }
 }
 
-__global__ void k_tc_ring_synthesis(TcBatchDev b) {
+__global__ void __launch_bounds__(kRingThreads, 2) k_tc_ring_synthesis(TcBatchDev b) {
   extern __shared__ __align__(16) unsigned char smem_rs[];
   C2<float>* s = reinterpret_cast<C2<float>*>(smem_rs);
   for (long long it = blockIdx.x; it < b.n_ring; it += gridDim.x) {
@@ -852,8 +855,8 @@ int tc_run_stage(clc_ctx* ctx, const TcBatchDev& b, const TcItems& it, const TcL
     }
     default: {
       cudaFuncSetAttribute(k_tc_ring_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, it.fft_sy_smem);
-      const int g = grid_of(ctx, k_tc_ring_synthesis, 256, it.fft_sy_smem, b.n_ring, L.fft_ctas);
-      CLC_LAUNCH(ctx, "k_tc_ring_synthesis", k_tc_ring_synthesis, g, 256, it.fft_sy_smem, b);
+      const int g = grid_of(ctx, k_tc_ring_synthesis, kRingThreads, it.fft_sy_smem, b.n_ring, L.fft_ctas);
+      CLC_LAUNCH(ctx, "k_tc_ring_synthesis", k_tc_ring_synthesis, g, kRingThreads, it.fft_sy_smem, b);
       return launch_check(ctx, "k_tc_ring_synthesis");
     }
   }
