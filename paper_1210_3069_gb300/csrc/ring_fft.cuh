@@ -81,7 +81,7 @@ struct Rot<float> {
   __device__ __forceinline__ void init(int k0, int dk_, int n_, double a_) {
     k = k0;
     dk = dk_;
-    an = (float)(a_ / (double)n_);
+    an = (float)a_ / (float)n_;   // FP32: an FP64 division here would run on the slow FP64 pipe
   }
   __device__ __forceinline__ C2<float> next() {
     const C2<float> r = expi_pi<float>(an * (float)k);
@@ -185,7 +185,7 @@ __device__ void dft_any(C2<T>* s, int N, int ring_class, const PlanDevT<T>& P, L
   }
   __syncthreads();
   fft_pow2<T>(s, logM, P);
-  const T invM = (T)(1.0 / (double)M);
+  const T invM = (T)1 / (T)M;
   for (int k = threadIdx.x; k < N; k += blockDim.x) s[pidx<T>(k)] = (conj(s[pidx<T>(k)]) * invM) * conj(w[k]);
   __syncthreads();
 }
