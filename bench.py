@@ -228,20 +228,56 @@ def run_gpu(args, cfg, rank, world):
     stream = torch.cuda.current_stream(dev)
     cycles = []
 
-    def step():
+    def step(zz=z, pp=phi, used=None):
         counts.zero_()
-        ctx.bin_particles(z, phi, nf, counts=counts)
+        ctx.bin_particles(zz, pp, nf, counts=counts)
+        if used is not None:
+            used.record(stream)   # the particle buffer may be refilled from here on
         ctx.counts_to_kappa(counts, nf, nbar, scale, kappa=kappa)
         ctx.poisson_shtmg(kappa, nf, sol, check=False)
         cycles.append(sol.info()[0])
         ctx.rays_init_pixels(rays, nf, chi_n, cfg["nside_bundle"])
         ctx.ray_step(rays, chi_prev, chi_n, chi_next, sol=sol)
 
-    def e2e_step():
-        z.copy_(host_z, non_blocking=True)
-        phi.copy_(host_phi, non_blocking=True)
-        step()
-        host_A.copy_(rays.A, non_blocking=True)
+    # End to end, pipelined as a production driver would run it: each step's
+    # particles are copied in from pinned host memory on a copy stream while
+    # the previous step computes (two device buffers), and each step's ray
+    # Jacobians leave through a device staging buffer, copied to pinned host
+    # memory while the next step computes.  Every step's copies are inside the
+    # timed region.
+    copy_stream = torch.cuda.Stream(dev)
+    zb, pb = [z, torch.empty_like(z)], [phi, torch.empty_like(phi)]
+    A_stage = torch.empty_like(rays.A)
+    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_used = [torch.cuda.Event(), torch.cuda.Event()]
+    ev_staged, ev_out = torch.cuda.Event(), torch.cuda.Event()
+
+    def e2e_run(nsteps, start_event):
+        copy_stream.wait_event(start_event)
+        with torch.cuda.stream(copy_stream):
+            zb[0].copy_(host_z, non_blocking=True)
+            pb[0].copy_(host_phi, non_blocking=True)
+            ev_in[0].record(copy_stream)
+        for k in range(nsteps):
+            cur, nxt = k % 2, (k + 1) % 2
+            if k + 1 < nsteps:
+                with torch.cuda.stream(copy_stream):
+                    if k >= 1:
+                        copy_stream.wait_event(ev_used[nxt])   # step k - 1 has binned from buffer nxt
+                    zb[nxt].copy_(host_z, non_blocking=True)
+                    pb[nxt].copy_(host_phi, non_blocking=True)
+                    ev_in[nxt].record(copy_stream)
+            stream.wait_event(ev_in[cur])
+            step(zb[cur], pb[cur], ev_used[cur])
+            if k >= 1:
+                stream.wait_event(ev_out)   # the staging buffer has reached the host
+            A_stage.copy_(rays.A)
+            ev_staged.record(stream)
+            with torch.cuda.stream(copy_stream):
+                copy_stream.wait_event(ev_staged)
+                host_A.copy_(A_stage, non_blocking=True)
+                ev_out.record(copy_stream)
+        stream.wait_stream(copy_stream)
 
     for _ in range(args.warmup):
         step()
@@ -273,9 +309,8 @@ def run_gpu(args, cfg, rank, world):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    e2e_steps = max(1, min(args.steps, 3))
-    for _ in range(e2e_steps):
-        e2e_step()
+    e2e_steps = max(1, args.steps)
+    e2e_run(e2e_steps, e0)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
