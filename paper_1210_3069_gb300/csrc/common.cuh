@@ -442,6 +442,30 @@ __device__ __forceinline__ double interp_map_tab(const double* __restrict__ map,
   return v;
 }
 
+// FP32 <-> FP64 by moving bits on the integer pipe (the hardware conversions
+// run on the FP64 pipe, 1/64 of the FP32 rate on this GPU).
+// f2d_exact: exact for normal floats, infinities and NaN; zero and subnormal
+// floats give (signless) zero.
+__device__ __forceinline__ double f2d_exact(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xFFu;
+  if (e == 0) return 0.0;
+  const unsigned hi = (u & 0x80000000u) | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
+}
+// d2f_rn: round to nearest even, identical to (float)x; results that are
+// zero, subnormal or out of the float range go through the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7FFu) - 1023 + 127;
+  if (e <= 0 || e >= 255) return (float)x;
+  const unsigned m = (unsigned)((b >> 29) & 0x7FFFFFu);
+  const unsigned rem = (unsigned)(b & 0x1FFFFFFFu);
+  unsigned f = ((unsigned)(b >> 32) & 0x80000000u) | ((unsigned)e << 23) | m;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ++f;   // a mantissa carry steps the exponent
+  return __uint_as_float(f);
+}
+
 __device__ __forceinline__ void record_error(int* d_err, int code) {
   atomicCAS(d_err, 0, code);
 }

@@ -103,8 +103,8 @@ template <typename T>
 __device__ __forceinline__ T from_double(double v) { return (T)v; }
 template <>
 __device__ __forceinline__ float2 from_double<float2>(double v) {
-  const float h = (float)v;
-  return make_float2(h, (float)(v - (double)h));
+  const float h = d2f_rn(v);
+  return make_float2(h, d2f_rn(v - f2d_exact(h)));
 }
 
 __global__ void k_mg_rotations(int nb, int npatch, double* rot) {
@@ -251,7 +251,7 @@ __global__ void k_mg_setup_base_ff(int n, const int4* __restrict__ idx, const do
   float2 v = apply_plan_ff(psi_ff, psi, ns, ring_th, idx[pos], w, pos);
   if (k1 == 0 || k2 == 0 || k1 == n + 1 || k2 == n + 1) v = make_float2(2.f * v.x, 2.f * v.y);
   base_ff[pos] = v;
-  base[pos] = (double)v.x + (double)v.y;
+  base[pos] = f2d_exact(v.x) + f2d_exact(v.y);
 }
 
 // Mixed set-up, float-float: defect source f' = kappa - L base at the cells,
@@ -1034,7 +1034,7 @@ __global__ void k_combine_ff(double* __restrict__ base, const float2* __restrict
   const size_t side = n + 2;
   const size_t c = (size_t)b * side * side + (size_t)(i + 1) * side + (j + 1);
   const float2 v = e[(size_t)b * upatch(n) + uidx(n, i, j)];
-  base[c] += (double)v.x + (double)v.y;
+  base[c] += f2d_exact(v.x) + f2d_exact(v.y);
 }
 
 // final potential u = base + e (interior cells)

@@ -101,13 +101,12 @@ __device__ __forceinline__ int pidx(int i) { return i + (i >> fft_pad_shift<T>()
 // FP32 -> FP64 by moving the bits (exact for normal floats; zero and
 // subnormal floats give zero): keeps the output conversion off the FP64 pipe
 __device__ __forceinline__ double to_out(double v) { return v; }
-__device__ __forceinline__ double to_out(float v) {
-  const unsigned u = __float_as_uint(v);
-  const unsigned e = (u >> 23) & 0xFFu;
-  if (e == 0) return 0.0;
-  const unsigned hi = (u & 0x80000000u) | ((e == 0xFFu ? 0x7FFu : e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
-  return __hiloint2double((int)hi, (int)((u & 7u) << 29));
-}
+// FP64 map value in the arithmetic type (FP32: rounded on the integer pipe)
+template <typename T>
+__device__ __forceinline__ T to_in(double v) { return (T)v; }
+template <>
+__device__ __forceinline__ float to_in<float>(double v) { return d2f_rn(v); }
+__device__ __forceinline__ double to_out(float v) { return f2d_exact(v); }
 
 __device__ __forceinline__ int brev(int j, int logM) { return logM == 0 ? 0 : (int)(__brev((unsigned)j) >> (32 - logM)); }
 __device__ __forceinline__ bool is_pow2(int v) { return (v & (v - 1)) == 0; }
@@ -219,7 +218,7 @@ __device__ void ring_analysis_ring(const double* __restrict__ map, int nside, in
   const Ring r = ring_geom_cta(nside, i).r;
   const int n = r.npix, N = n / 2;
   const double* x = map + r.first;
-  dft_any<T>(s, N, ring_class_of(nside, i), P, [&](int j) { return cx<T>((T)x[2 * j], (T)x[2 * j + 1]); });
+  dft_any<T>(s, N, ring_class_of(nside, i), P, [&](int j) { return cx<T>(to_in<T>(x[2 * j]), to_in<T>(x[2 * j + 1])); });
   const bool shifted = r.phi0 != 0.0;
   const T w = (T)weight, half = (T)0.5;
   for (int m = threadIdx.x; m <= lmax; m += blockDim.x) {
