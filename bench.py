@@ -58,6 +58,15 @@ BATCH_WORKLOADS = {
     # one full class (21 planes with derivatives) at Nside 512: the profiling case of the batch kernels
     "sht_batch_nside512": dict(sizes=[(512, 1024)] * 21, seed=1210004, fp64_sample=1),
 }
+# adaptive Epanechnikov smoothing of the plane's particles (Sec. 3.2) at the
+# benchmark plane's size, sigma = 2.5 pixel scales
+SMOOTH_WORKLOADS = {
+    "smooth_particles_nside2048": dict(nside=2048, particles=50_000_000, sigma_pix=2.5, seed=1210002,
+                                       oracle_sample=16),
+    "smooth_particles_small": dict(nside=256, particles=1_000_000, sigma_pix=2.5, seed=1210002, oracle_sample=64),
+}
+SMOOTH_METRIC = "particles/s (Epanechnikov smoothing with exact mass conservation onto HEALPix)"
+
 BATCH_METRIC = "lens planes/s (batched mixed-precision SHT Poisson, Nside 512/1024/2048, lmax = 2 Nside)"
 
 # gradient of a galaxy-shear loss with respect to every plane's convergence
@@ -527,6 +536,105 @@ def adjoint_line(args, wl, r):
     }
 
 
+def run_smooth(args, wl):
+    """Particles per second of the smoothing step (zero the map, smooth every
+    particle, form kappa), and the oracle on a sample of the same particles."""
+    import paper_1210_3069_gb300 as clc
+    from oracle import smoothing as osm
+    clc.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(0)
+    nside, n = wl["nside"], wl["particles"]
+    npix = 12 * nside * nside
+    sigma = wl["sigma_pix"] * math.sqrt(4 * math.pi / npix)
+    z, phi = synthetic.lognormal_particles(n, wl["seed"], device=dev)
+    n = z.numel()   # Poisson-sampled: about the requested number
+    rho = torch.zeros(npix, dtype=torch.float64, device=dev)
+    kappa = torch.empty(npix, dtype=torch.float64, device=dev)
+    nbar = n / npix
+
+    def step(zz=z, pp=phi):
+        rho.zero_()
+        ctx.smooth_particles(zz, pp, nside, sigma, rho=rho)
+        ctx.density_to_kappa(rho, nside, nbar, 1.0, kappa=kappa)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile_query("k_smooth_particles")
+    ctx.profile(False)
+    mass_err = abs(float(rho.sum()) - n) / n
+    # end to end: particles in from pinned host memory, kappa out
+    hz, hp_ = z.cpu().pin_memory(), phi.cpu().pin_memory()
+    hk = torch.empty(npix, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        z.copy_(hz, non_blocking=True)
+        phi.copy_(hp_, non_blocking=True)
+        step()
+        hk.copy_(kappa, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    # the oracle on a sample of the particles (all-pixel brute force)
+    cpu = None
+    if not args.no_cpu_baseline:
+        k = wl["oracle_sample"]
+        zs, ps = z[:k].cpu(), phi[:k].cpu()
+        t0 = time.perf_counter()
+        osm.smooth_particles(nside, zs, ps, sigma)
+        secs = time.perf_counter() - t0
+        cpu = {"value": k / secs, "unit": "particles/s", "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"{k} particles of the same set, all-pixel oracle at Nside {nside}"}
+    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, clocks=clocks.summary(), n=n, npix=npix,
+                sigma=sigma, mass_err=mass_err, cpu=cpu)
+
+
+def smooth_line(args, wl, r):
+    peaks, peak_kind = load_peaks()
+    n = r["n"]
+    value = n * args.steps / (r["ms"] / 1e3)
+    # FP64 ALU work: about pi sigma^2 / Omega_pix pixels within each kernel,
+    # about 20 FP64 flops to test and weigh each (chord, rotation, asin^2
+    # series, weight), once; the deposit is FP64 atomics
+    per_particle = math.pi * wl["sigma_pix"] ** 2 * 20.0
+    launches, kms = r["prof"]
+    roof = None
+    if kms > 0:
+        ach = per_particle * n * launches / (kms / 1e3) / 1e12
+        roof = {"kernel": "k_smooth_particles", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (derived)"}
+    return {
+        "metric": SMOOTH_METRIC, "value": value, "unit": "particles/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nside": wl["nside"], "particles": n, "sigma_rad": r["sigma"],
+                   "sigma_pixel_scales": wl["sigma_pix"], "l2": "inputs larger than L2 (no flush)"},
+        "mass_conservation_rel_err": r["mass_err"],
+        "roofline": roof,
+        "e2e": {"value": n / (r["e2e_ms"] / 1e3), "unit": "particles/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 8 * r["npix"]},
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "cpu_baseline": r["cpu"],
+    }
+
+
 def batch_line(args, wl, r):
     peaks, peak_kind = load_peaks()
     sizes = wl["sizes"]
@@ -671,7 +779,8 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["fp64", "fp32", "mixed"],
                     help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
     ap.add_argument("--workload", default="shtmg_plane_nside2048",
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS)
+                    + sorted(SMOOTH_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload in ADJOINT_WORKLOADS:
@@ -682,6 +791,16 @@ def main():
             return
         wl = ADJOINT_WORKLOADS[args.workload]
         print(json.dumps(adjoint_line(args, wl, run_adjoint(args, wl))))
+        return
+    if args.workload in SMOOTH_WORKLOADS:
+        if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": args.impl, "metric": SMOOTH_METRIC,
+                                  "unavailable": "the smoothing workload runs on one GPU (its oracle sample is in "
+                                                 "the GPU line's cpu_baseline)"}))
+            return
+        wl = SMOOTH_WORKLOADS[args.workload]
+        print(json.dumps(smooth_line(args, wl, run_smooth(args, wl))))
         return
     if args.workload in BATCH_WORKLOADS:
         if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:

@@ -124,6 +124,24 @@ int clc_bin_particles(clc_ctx* ctx, const double* z, const double* phi, int64_t 
 int clc_counts_to_kappa(clc_ctx* ctx, const uint32_t* counts, int nside, double nbar,
                         double scale, double* kappa);
 
+/* Adaptive Epanechnikov smoothing of unit-mass particles (Sec. 3.2): each
+ * particle's mass is spread over the RING pixels whose centres lie at angular
+ * distance theta < sigma from it, in proportion to the kernel
+ * K(theta; sigma) ~ 1 - (theta / sigma)^2, the weights divided by their sum so
+ * that the mass is conserved exactly; a particle with no pixel centre within
+ * sigma puts its mass on its own pixel.  nside <= 8192.  sigma (radians, 0 < sigma <= 0.5) is
+ * one smoothing length for all particles, or sigma_each[n] (device, may be
+ * NULL) one per particle.  map (FP64[12 nside^2], particle number per pixel)
+ * is accumulated, not cleared; sums of FP64 atomic adds, so the last bits
+ * depend on their order.  n == 0 is a no-op. */
+int clc_smooth_particles(clc_ctx* ctx, const double* z, const double* phi, int64_t n, int nside,
+                         double sigma, const double* sigma_each, double* map);
+
+/* kappa[p] = scale * (rho[p] / nbar - 1) (Eq. lenspoisson) for a smoothed
+ * particle-number map rho, each operation rounded separately. */
+int clc_density_to_kappa(clc_ctx* ctx, const double* rho, int nside, double nbar, double scale,
+                         double* kappa);
+
 /* Coarse RING map = mean of the (nside_fine / nside_coarse)^2 NEST children of
  * every coarse pixel (children summed in NEST order): equal to binning the
  * same particles at nside_coarse. */

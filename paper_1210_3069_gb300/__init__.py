@@ -57,6 +57,8 @@ _SIGS = {
     "clc_bin_particles": (_i, [_p, _p, _p, _i64, _i, _i, _p]),
     "clc_counts_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
     "clc_degrade": (_i, [_p, _p, _i, _p, _i]),
+    "clc_smooth_particles": (_i, [_p, _p, _p, _i64, _i, _d, _p, _p]),
+    "clc_density_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
     "clc_set_table_budget": (_i, [_p, ctypes.c_size_t]),
     "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
     "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
@@ -191,6 +193,21 @@ class Context:
         if kappa is None:
             kappa = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)
         self._check(lib().clc_counts_to_kappa(self.h, _ptr(counts), nside, float(nbar), float(scale), _ptr(kappa)))
+        return kappa
+
+    def smooth_particles(self, z, phi, nside, sigma=0.0, sigma_each=None, rho=None):
+        """Epanechnikov-smoothed particle number per RING pixel (accumulated
+        into rho, a new zero map if None)."""
+        if rho is None:
+            rho = torch.zeros(12 * nside * nside, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_smooth_particles(self.h, _ptr(z), _ptr(phi), z.numel(), int(nside), float(sigma),
+                                               _ptr(sigma_each) if sigma_each is not None else None, _ptr(rho)))
+        return rho
+
+    def density_to_kappa(self, rho, nside, nbar, scale, kappa=None):
+        if kappa is None:
+            kappa = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)
+        self._check(lib().clc_density_to_kappa(self.h, _ptr(rho), int(nside), float(nbar), float(scale), _ptr(kappa)))
         return kappa
 
     def degrade(self, fine, nside_fine, nside_coarse, out=None):
