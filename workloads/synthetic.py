@@ -129,3 +129,33 @@ def galaxies(n, z_lo, z_hi, seed, device="cpu"):
     g = _gen(seed + 3, device)
     red = z_lo + (z_hi - z_lo) * torch.rand(n, generator=g, dtype=F64, device=device)
     return zz, pp, red
+
+
+def cored_lens_map(n, centre, b, s):
+    """Source-sphere directions of rays seen at unit vectors n [..., 3] through
+    an axisymmetric lens at unit vector `centre`: a ray at angle theta from the
+    centre is moved along its great circle to theta - alpha(theta), with the
+    cored isothermal deflection alpha = b (sqrt(theta^2 + s^2) - s) / theta
+    tapered by ((1 + cos theta) / 2)^2 so that the map stays smooth at the
+    antipode (one image for b / (2 s) < 1, three near the centre above).
+    Also returns alpha(theta) as a function for root finding."""
+    def alpha(th):
+        th = torch.as_tensor(th, dtype=F64)
+        a = b * (torch.sqrt(th * th + s * s) - s) / torch.where(th == 0, torch.ones_like(th), th)
+        a = torch.where(th == 0, torch.zeros_like(th), a)
+        return a * ((1.0 + torch.cos(th)) / 2.0) ** 2
+
+    c = torch.as_tensor(centre, dtype=F64, device=n.device)
+    ct = (n @ c).clamp(-1.0, 1.0)
+    th = torch.arccos(ct)
+    e = n - ct[..., None] * c
+    en = torch.linalg.vector_norm(e, dim=-1, keepdim=True)
+    e = e / torch.where(en > 0, en, torch.ones_like(en))
+    beta = th - alpha(th)
+    return torch.cos(beta)[..., None] * c + torch.sin(beta)[..., None] * e, alpha
+
+
+def random_jacobians(n, amp, seed, device="cpu"):
+    """[n, 2, 2] matrices I + amp * (standard normal entries)."""
+    g = _gen(seed, device)
+    return torch.eye(2, dtype=F64, device=device) + amp * torch.randn(n, 2, 2, generator=g, dtype=F64, device=device)
