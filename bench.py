@@ -67,6 +67,17 @@ SMOOTH_WORKLOADS = {
 }
 SMOOTH_METRIC = "particles/s (Epanechnikov smoothing with exact mass conservation onto HEALPix)"
 
+# grid search for the images of galaxies (Sec. 2.3) on the rays of the
+# benchmark plane: the plane is solved and its rays stepped once (set-up),
+# then the images of uniformly placed galaxies on the next sphere are found
+IMAGE_WORKLOADS = {
+    "image_search_nside2048": dict(plane="shtmg_plane_nside2048", galaxies=10_000_000, max_images=4,
+                                   seed=1210006, oracle_sample=32),
+    "image_search_small": dict(plane="shtmg_plane_nside512", galaxies=500_000, max_images=4, seed=1210006,
+                               oracle_sample=32),
+}
+IMAGE_METRIC = "galaxies/s (grid search for lensed images with transported Jacobians, rays on Nside 2048)"
+
 BATCH_METRIC = "lens planes/s (batched mixed-precision SHT Poisson, Nside 512/1024/2048, lmax = 2 Nside)"
 
 # gradient of a galaxy-shear loss with respect to every plane's convergence
@@ -606,6 +617,157 @@ def run_smooth(args, wl):
                 sigma=sigma, mass_err=mass_err, cpu=cpu)
 
 
+def run_images(args, wl):
+    """Galaxies per second of the image search on the rays of one solved
+    plane, and the oracle on a sample of the same galaxies."""
+    import paper_1210_3069_gb300 as clc
+    from oracle import healpix as ohp, images as oim
+    clc.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(0)
+    cfg = WORKLOADS[wl["plane"]]
+    nf = cfg["nside"]
+    npix = 12 * nf * nf
+    chi_prev, chi_n, chi_next, scale = plane_geometry()
+    P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
+                      nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=clc.MIXED)
+    z, phi = synthetic.lognormal_particles(cfg["particles"], cfg["seed"], device=dev)
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    ctx.bin_particles(z, phi, nf, counts=counts)
+    kappa = ctx.counts_to_kappa(counts, nf, z.numel() / npix, scale)
+    del z, phi, counts
+    sol = ctx.solution(nf, P)
+    ctx.poisson_shtmg(kappa, nf, sol, check=False)
+    rays = ctx.rays(npix)
+    ctx.rays_init_pixels(rays, nf, chi_n, cfg["nside_bundle"])
+    ctx.ray_step(rays, chi_prev, chi_n, chi_next, sol=sol)
+    del sol
+    M, K = wl["galaxies"], wl["max_images"]
+    gz, gp = synthetic.uniform_sphere(M, wl["seed"], device=dev)
+    sg = torch.sqrt((1 - gz) * (1 + gz))
+    g = torch.stack([sg * torch.cos(gp), sg * torch.sin(gp), gz]).contiguous()
+    del gz, gp, sg
+    torch.cuda.synchronize()
+
+    def step(gg=g):
+        return ctx.find_images(nf, rays.x, rays.A, gg, K)
+
+    for _ in range(args.warmup):
+        out = step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    prof = {k: ctx.profile_query(k) for k in ("k_find_images", "k_image_bounds")}
+    ctx.profile(False)
+    nimg = out[0]
+    hist = torch.bincount(nimg.clamp(max=3).long(), minlength=4).cpu().tolist()
+    # end to end: galaxies in from pinned host memory, every output back
+    hg = g.cpu().pin_memory()
+    host_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in out]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.copy_(hg, non_blocking=True)
+        o = step()
+        for h, t in zip(host_out, o):
+            h.copy_(t, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    d2h = sum(t.numel() * t.element_size() for t in out)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on a sample of the galaxies, each tested against the
+        # triangles of the pixels within (largest ray displacement + four
+        # pixel sizes) of it, the pixels found from a dense grid of points
+        k = wl["oracle_sample"]
+        x = rays.x.T.cpu()
+        A = rays.A.T.reshape(npix, 2, 2).cpu()
+        cen = ohp.pix2vec_ring(nf, torch.arange(npix))
+        xn = x / torch.linalg.vector_norm(x, dim=-1, keepdim=True)
+        dmax = float(torch.atan2(torch.linalg.vector_norm(torch.linalg.cross(xn, cen, dim=-1), dim=-1),
+                                 (xn * cen).sum(-1)).max())
+        del cen, xn
+        h = math.sqrt(4 * math.pi / npix)
+        gs = g[:, :k].T.cpu()
+        secs = 0.0
+        for m in range(k):
+            own = _pixels_near(nf, gs[m], dmax + 4 * h)
+            t0 = time.perf_counter()
+            oim.find_images(nf, x, A, gs[m:m + 1], K, owners=own)
+            secs += time.perf_counter() - t0
+        cpu = {"value": k / secs, "unit": "galaxies/s", "cores": torch.get_num_threads(), "kind": "oracle",
+               "sample": f"{k} galaxies of the same set, oracle on the triangles of the pixels within the largest "
+                         f"ray displacement ({dmax:.2e} rad) + 4 pixel sizes of each"}
+    return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, clocks=clocks.summary(), M=M, npix=npix,
+                hist=hist, h2d=g.numel() * 8, d2h=d2h, cpu=cpu, nside=nf)
+
+
+def _pixels_near(nside, g, radius):
+    """RING pixels hit by a grid of points (a quarter pixel apart) within
+    `radius` of the unit vector g."""
+    from oracle import healpix as ohp
+    g = g / torch.linalg.vector_norm(g)
+    h = math.sqrt(4 * math.pi / (12 * nside * nside))
+    n = int(math.ceil(radius / (0.25 * h)))
+    u = torch.linspace(-radius, radius, 2 * n + 1, dtype=torch.float64)
+    a = torch.linalg.cross(g, torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64))
+    a = a / torch.linalg.vector_norm(a)
+    b = torch.linalg.cross(g, a)
+    U, V = torch.meshgrid(u, u, indexing="ij")
+    r = torch.sqrt(U * U + V * V)
+    keep = r <= radius
+    U, V, r = U[keep], V[keep], r[keep]
+    d = (U[:, None] * a + V[:, None] * b) / torch.where(r > 0, r, 1.0)[:, None]
+    pts = torch.cos(r)[:, None] * g + torch.sin(r)[:, None] * d
+    phi = torch.remainder(torch.atan2(pts[:, 1], pts[:, 0]), 2 * math.pi)
+    return torch.unique(ohp.ang2pix_ring(nside, pts[:, 2].clamp(-1, 1), phi))
+
+
+def images_line(args, wl, r):
+    value = r["M"] * args.steps / (r["ms"] / 1e3)
+    n, kms = r["prof"]["k_find_images"]
+    roof = None
+    if kms > 0:
+        # HBM-bound model: per galaxy the source position in (24 B), the
+        # outputs out (4 + 56 B per slot), and the rays that decide and
+        # interpolate its images: the three vertices of its triangle (24 B
+        # each) and the eight interpolation rays (24 B position + 32 B matrix)
+        per_gal = 24 + 4 + 56 * wl["max_images"] + 3 * 24 + 8 * 56
+        pk = load_peaks()[0].get("hbm_gbs", 6800.0)
+        ach = per_gal * r["M"] * n / (kms / 1e3) / 1e9
+        roof = {"kernel": "k_find_images", "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                "frac": ach / pk, "traffic": None, "launches": n, "avg_launch_ms": kms / max(n, 1),
+                "peak_source": "HBM copy, measured (MEASURED_PEAKS.json hbm_gbs)"}
+    return {
+        "metric": IMAGE_METRIC, "value": value, "unit": "galaxies/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "nside_rays": r["nside"], "rays": r["npix"], "galaxies": r["M"],
+                   "max_images": wl["max_images"], "rays_from": wl["plane"] + " (one solved plane, one ray step)",
+                   "l2": "inputs larger than L2 (no flush)"},
+        "images_per_galaxy_hist": {"0": r["hist"][0], "1": r["hist"][1], "2": r["hist"][2], "3+": r["hist"][3]},
+        "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in r["prof"].items()},
+        "roofline": roof,
+        "e2e": {"value": r["M"] / (r["e2e_ms"] / 1e3), "unit": "galaxies/s", "h2d_bytes_per_step": r["h2d"],
+                "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"], "clocks": r["clocks"], "cpu_baseline": r["cpu"],
+    }
+
+
 def smooth_line(args, wl, r):
     peaks, peak_kind = load_peaks()
     n = r["n"]
@@ -780,7 +942,7 @@ def main():
                     help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
     ap.add_argument("--workload", default="shtmg_plane_nside2048",
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS)
-                    + sorted(SMOOTH_WORKLOADS))
+                    + sorted(SMOOTH_WORKLOADS) + sorted(IMAGE_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.workload in ADJOINT_WORKLOADS:
@@ -801,6 +963,16 @@ def main():
             return
         wl = SMOOTH_WORKLOADS[args.workload]
         print(json.dumps(smooth_line(args, wl, run_smooth(args, wl))))
+        return
+    if args.workload in IMAGE_WORKLOADS:
+        if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": args.impl, "metric": IMAGE_METRIC,
+                                  "unavailable": "the image-search workload runs on one GPU (its oracle sample is "
+                                                 "in the GPU line's cpu_baseline)"}))
+            return
+        wl = IMAGE_WORKLOADS[args.workload]
+        print(json.dumps(images_line(args, wl, run_images(args, wl))))
         return
     if args.workload in BATCH_WORKLOADS:
         if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:

@@ -290,6 +290,51 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
                         const double* chi_host, clc_rays* rays);
 
 /* ------------------------------------------------------------------------ */
+/* Galaxy images by grid search (Sec. 2.3; grid-search implementation, Sec. 3) */
+
+/* Images of ngal galaxies on one source sphere.  The rays must have been
+ * started at the RING pixel centres of nside (clc_rays_init_pixels, n =
+ * 12 nside^2) and traced to the galaxies' source sphere: x[3][n] their
+ * positions there (any common positive length) and A[4][n] their inverse
+ * magnification matrices in the (theta-hat, phi-hat) basis at x (device,
+ * the layout of clc_rays).  g[3][ngal] (device) are the galaxies' source
+ * positions as Cartesian vectors of any positive length.
+ *
+ * Triangles: between consecutive rings every pixel centre closes one
+ * triangle with its predecessor on its ring and the last centre of the
+ * neighbouring ring before it in longitude; ring 1 and the last ring close
+ * the caps with two triangles each (2 npix - 4 triangles, counter-clockwise
+ * seen from outside).  Triangle id 2 p + s belongs to centre p (s = 0: strip
+ * below p's ring, s = 1: strip above; the caps are ids 3, 7, 2 (npix - 3),
+ * 2 (npix - 1)).  A galaxy has one image per triangle whose rays' source
+ * positions contain it in the gnomonic projection at the galaxy (triple
+ * products det(g, x_i, x_j) of one sign, each edge's product evaluated once
+ * on its endpoints in increasing pixel order, all vertices in g's
+ * hemisphere); the image is the unit vector along sum_i lambda_i c_i, c_i
+ * the vertices' pixel centres and lambda the barycentric coordinates in
+ * that projection.  The matrix at the image is the ring-bilinear
+ * interpolation (clc_ray_step's map interpolation) of the rays' A, each
+ * parallel transported from the basis at its source position to the image.
+ *
+ * Outputs (device): nimg[ngal] the number of images found; for slot
+ * q < max_images (1..8) in increasing triangle id: tri[q][ngal] the
+ * triangle id (-1 if unused), img_z[q][ngal] = cos theta and
+ * img_phi[q][ngal] in [0, 2 pi) of the image (0 if unused), and
+ * A_img[4][q][ngal] (index (c * max_images + q) * ngal + m) the matrix at the
+ * image in the basis there (0 if unused).  A and A_img are both NULL to skip
+ * the matrices.  A galaxy vector of zero length or with a non-finite
+ * component has no image.  The search visits only pixels near each galaxy, with a
+ * radius taken from the largest displacement of a ray from its pixel centre
+ * and the largest triangle on the source sphere, and finds every triangle
+ * that contains the galaxy.  CLC_EINVAL before any search launch for bad
+ * arguments, non-finite ray positions, or rays so far from their pixels
+ * that the search would cover most of the sphere for many galaxies.  The
+ * call waits for a small device-to-host copy of that radius. */
+int clc_find_images(clc_ctx* ctx, int nside, const double* x, const double* A, int64_t ngal, const double* g,
+                    int max_images, int32_t* nimg, int64_t* tri, double* img_z, double* img_phi,
+                    double* A_img);
+
+/* ------------------------------------------------------------------------ */
 /* Differentiation: galaxy shears and their adjoint (Sec. 2.2, 3.2, App. D)   */
 
 /* Shears of ngal galaxies through nplanes pure-SHT planes: one ray per

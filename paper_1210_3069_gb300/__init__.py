@@ -59,6 +59,7 @@ _SIGS = {
     "clc_degrade": (_i, [_p, _p, _i, _p, _i]),
     "clc_smooth_particles": (_i, [_p, _p, _p, _i64, _i, _d, _p, _p]),
     "clc_density_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
+    "clc_find_images": (_i, [_p, _i, _p, _p, _i64, _p, _i, _p, _p, _p, _p, _p]),
     "clc_set_table_budget": (_i, [_p, ctypes.c_size_t]),
     "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
     "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
@@ -343,6 +344,24 @@ class Context:
         self._check(lib().clc_ray_step(self.h, sol.h if sol is not None else None,
                                        ctypes.byref(d) if d is not None else None, int(nside_maps),
                                        float(chi_prev), float(chi_n), float(chi_next), ctypes.byref(rays.struct())))
+
+    def find_images(self, nside, x, A, g, max_images=4, matrices=True):
+        """Images of galaxies at source positions g [3, M] from rays started at
+        the RING pixel centres of nside with source positions x [3, npix] and
+        matrices A [4, npix].  Returns (nimg [M] int32, tri [max_images, M]
+        int64, img_z, img_phi [max_images, M], A_img [4, max_images, M] or
+        None)."""
+        M = g.shape[-1]
+        dev = self.device
+        nimg = torch.empty(M, dtype=torch.int32, device=dev)
+        tri = torch.empty(max_images, M, dtype=torch.int64, device=dev)
+        iz = torch.empty(max_images, M, dtype=torch.float64, device=dev)
+        ip = torch.empty(max_images, M, dtype=torch.float64, device=dev)
+        Ai = torch.empty(4, max_images, M, dtype=torch.float64, device=dev) if matrices else None
+        self._check(lib().clc_find_images(self.h, int(nside), _ptr(x), _ptr(A) if matrices else None, int(M),
+                                          _ptr(g), int(max_images), _ptr(nimg), _ptr(tri), _ptr(iz), _ptr(ip),
+                                          _ptr(Ai)))
+        return nimg, tri, iz, ip, Ai
 
     def raytrace_planes(self, solver, params, kappa_planes, nside, chi, rays):
         n = len(kappa_planes)

@@ -59,14 +59,6 @@ __global__ void k_degrade(const double* __restrict__ fine, int nf, double* __res
 
 constexpr int kSmoothCache = 48;   // pixels of the first pass kept for the deposit
 
-// continuous ring coordinate of z (ring i at z_i gives i)
-__device__ __forceinline__ double ring_coord(int nside, double z) {
-  const double n = nside;
-  if (z > 2.0 / 3.0) return n * sqrt(3.0 * (1.0 - z));
-  if (z < -2.0 / 3.0) return 4.0 * n - n * sqrt(3.0 * (1.0 + z));
-  return n * (2.0 - 1.5 * z);
-}
-
 // theta^2 from the chord c^2 = |a - b|^2 of two unit vectors, 4 asin^2(c / 2):
 // the Taylor series of asin^2 through the c^12 term for c^2 <= 1/400 (first
 // omitted term below 1e-17 relative), else directly

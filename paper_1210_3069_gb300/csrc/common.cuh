@@ -317,6 +317,14 @@ __device__ __forceinline__ int pix2ring(int nside, int64_t p, int64_t* j) {
   return (int)(4 * n - i);
 }
 
+// continuous ring coordinate of z (ring i at z_i gives i)
+__device__ __forceinline__ double ring_coord(int nside, double z) {
+  const double n = nside;
+  if (z > 2.0 / 3.0) return n * sqrt(3.0 * (1.0 - z));
+  if (z < -2.0 / 3.0) return 4.0 * n - n * sqrt(3.0 * (1.0 + z));
+  return n * (2.0 - 1.5 * z);
+}
+
 // theta of ring i
 __device__ __forceinline__ double ring_theta(int nside, int i) {
   const Ring r = ring_geom(nside, i);

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "mg.cuh"
+#include "sphere.cuh"
 
 namespace clc {
 
@@ -42,13 +43,6 @@ __device__ __forceinline__ double atan_small(double t) {
   const double t2 = t * t;
   return t * (1.0 - t2 * ((1.0 / 3.0) - t2 * ((1.0 / 5.0) - t2 * ((1.0 / 7.0) - t2 * ((1.0 / 9.0) -
                                                                                     t2 * ((1.0 / 11.0) - t2 * (1.0 / 13.0)))))));
-}
-
-// Tangent basis (theta-hat, phi-hat) at the unit vector n.
-__device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
-  const double r2 = n[0] * n[0] + n[1] * n[1], ir = rsqrt(r2), rho = r2 * ir;
-  t[0] = n[2] * n[0] * ir; t[1] = n[2] * n[1] * ir; t[2] = -rho;
-  p[0] = -n[1] * ir; p[1] = n[0] * ir; p[2] = 0.0;
 }
 
 template <typename T>
