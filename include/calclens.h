@@ -318,10 +318,9 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
  *
  * Outputs (device): nimg[ngal] the number of images found; for slot
  * q < max_images (1..8) in increasing triangle id: tri[q][ngal] the
- * triangle id (-1 if unused), img_z[q][ngal] = cos theta and
- * img_phi[q][ngal] in [0, 2 pi) of the image (0 if unused), and
- * A_img[4][q][ngal] (index (c * max_images + q) * ngal + m) the matrix at the
- * image in the basis there (0 if unused).  A and A_img are both NULL to skip
+ * triangle id (-1 if unused), img[3][q][ngal] (index (c * max_images + q) *
+ * ngal + m) the image's unit vector (0 if unused), and A_img[4][q][ngal]
+ * (same indexing) the matrix at the image in the basis there (0 if unused).  A and A_img are both NULL to skip
  * the matrices.  A galaxy vector of zero length or with a non-finite
  * component has no image.  The search visits only pixels near each galaxy, with a
  * radius taken from the largest displacement of a ray from its pixel centre
@@ -331,8 +330,7 @@ int clc_raytrace_planes(clc_ctx* ctx, int solver, const clc_mg_params* mg,
  * that the search would cover most of the sphere for many galaxies.  The
  * call waits for a small device-to-host copy of that radius. */
 int clc_find_images(clc_ctx* ctx, int nside, const double* x, const double* A, int64_t ngal, const double* g,
-                    int max_images, int32_t* nimg, int64_t* tri, double* img_z, double* img_phi,
-                    double* A_img);
+                    int max_images, int32_t* nimg, int64_t* tri, double* img, double* A_img);
 
 /* ------------------------------------------------------------------------ */
 /* Differentiation: galaxy shears and their adjoint (Sec. 2.2, 3.2, App. D)   */

@@ -59,7 +59,7 @@ _SIGS = {
     "clc_degrade": (_i, [_p, _p, _i, _p, _i]),
     "clc_smooth_particles": (_i, [_p, _p, _p, _i64, _i, _d, _p, _p]),
     "clc_density_to_kappa": (_i, [_p, _p, _i, _d, _d, _p]),
-    "clc_find_images": (_i, [_p, _i, _p, _p, _i64, _p, _i, _p, _p, _p, _p, _p]),
+    "clc_find_images": (_i, [_p, _i, _p, _p, _i64, _p, _i, _p, _p, _p, _p]),
     "clc_set_table_budget": (_i, [_p, ctypes.c_size_t]),
     "clc_sht_analysis": (_i, [_p, _p, _i, _i, _p]),
     "clc_sht_synthesis": (_i, [_p, _p, _i, _i, _p]),
@@ -349,19 +349,17 @@ class Context:
         """Images of galaxies at source positions g [3, M] from rays started at
         the RING pixel centres of nside with source positions x [3, npix] and
         matrices A [4, npix].  Returns (nimg [M] int32, tri [max_images, M]
-        int64, img_z, img_phi [max_images, M], A_img [4, max_images, M] or
-        None)."""
+        int64, img [3, max_images, M] unit vectors, A_img [4, max_images, M]
+        or None)."""
         M = g.shape[-1]
         dev = self.device
         nimg = torch.empty(M, dtype=torch.int32, device=dev)
         tri = torch.empty(max_images, M, dtype=torch.int64, device=dev)
-        iz = torch.empty(max_images, M, dtype=torch.float64, device=dev)
-        ip = torch.empty(max_images, M, dtype=torch.float64, device=dev)
+        img = torch.empty(3, max_images, M, dtype=torch.float64, device=dev)
         Ai = torch.empty(4, max_images, M, dtype=torch.float64, device=dev) if matrices else None
         self._check(lib().clc_find_images(self.h, int(nside), _ptr(x), _ptr(A) if matrices else None, int(M),
-                                          _ptr(g), int(max_images), _ptr(nimg), _ptr(tri), _ptr(iz), _ptr(ip),
-                                          _ptr(Ai)))
-        return nimg, tri, iz, ip, Ai
+                                          _ptr(g), int(max_images), _ptr(nimg), _ptr(tri), _ptr(img), _ptr(Ai)))
+        return nimg, tri, img, Ai
 
     def raytrace_planes(self, solver, params, kappa_planes, nside, chi, rays):
         n = len(kappa_planes)

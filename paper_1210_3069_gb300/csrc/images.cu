@@ -205,8 +205,7 @@ __global__ void k_image_bounds(const double* __restrict__ x, int nside, int64_t 
 struct ImageOut {
   int32_t* nimg;
   int64_t* tri;
-  double* iz;
-  double* iphi;
+  double* img;   // [3][max_images][ngal]
   double* A;     // [4][max_images][ngal] or null
 };
 
@@ -224,8 +223,7 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
     for (int q = 0; q < max_images; ++q) {
       const size_t o = (size_t)q * ngal + m;
       out.tri[o] = -1;
-      out.iz[o] = 0.0;
-      out.iphi[o] = 0.0;
+      for (int c = 0; c < 3; ++c) out.img[((size_t)c * max_images + q) * ngal + m] = 0.0;
       if (out.A)
         for (int c = 0; c < 4; ++c) out.A[((size_t)c * max_images + q) * ngal + m] = 0.0;
     }
@@ -299,8 +297,7 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
     const size_t o = (size_t)q * ngal + m;
     if (q >= nfound) {
       out.tri[o] = -1;
-      out.iz[o] = 0.0;
-      out.iphi[o] = 0.0;
+      for (int c = 0; c < 3; ++c) out.img[((size_t)c * max_images + q) * ngal + m] = 0.0;
       if (out.A)
         for (int c = 0; c < 4; ++c) out.A[((size_t)c * max_images + q) * ngal + m] = 0.0;
       continue;
@@ -329,14 +326,13 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
     }
     double ni[3];
     normalize3(w3, ni);
+    out.tri[o] = id;
+    for (int c = 0; c < 3; ++c) out.img[((size_t)c * max_images + q) * ngal + m] = ni[c];
+    if (!out.A) continue;
+    // inverse magnification matrix at the image
     const double rho = sqrt(ni[0] * ni[0] + ni[1] * ni[1]);
     double ph = atan2(ni[1], ni[0]);
     if (ph < 0.0) ph += 2.0 * kPi;
-    out.tri[o] = id;
-    out.iz[o] = ni[2];
-    out.iphi[o] = ph;
-    if (!out.A) continue;
-    // inverse magnification matrix at the image
     const Interp8 w = interp_weights(nside, atan2(rho, ni[2]), ph);
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = 0; k < 8; ++k) {
@@ -363,15 +359,15 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
 using namespace clc;
 
 extern "C" int clc_find_images(clc_ctx* ctx, int nside, const double* x, const double* A, int64_t ngal,
-                               const double* g, int max_images, int32_t* nimg, int64_t* tri, double* img_z,
-                               double* img_phi, double* A_img) {
+                               const double* g, int max_images, int32_t* nimg, int64_t* tri, double* img,
+                               double* A_img) {
   if (!ctx) return CLC_EINVAL;
   if (!valid_nside(nside) || ngal < 0 || max_images < 1 || max_images > kMaxImages)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: bad nside, ngal or max_images (1..8)");
   if ((A == nullptr) != (A_img == nullptr))
     return set_err(ctx, CLC_EINVAL, "clc_find_images: A and A_img must both be given or both be NULL");
   if (ngal == 0) return CLC_OK;
-  if (!x || !g || !nimg || !tri || !img_z || !img_phi)
+  if (!x || !g || !nimg || !tri || !img)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: null pointer");
   cudaSetDevice(ctx->device);
   const int64_t npx = 12 * (int64_t)nside * nside;
@@ -401,7 +397,7 @@ extern "C" int clc_find_images(clc_ctx* ctx, int nside, const double* x, const d
   if (cand * (double)ngal > 5e10)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: rays too far from their pixels for the search (radius " +
                                         std::to_string(R) + " rad)");
-  ImageOut out{nimg, tri, img_z, img_phi, A_img};
+  ImageOut out{nimg, tri, img, A_img};
   const int threads = 128;
   const int64_t blocks = (ngal + threads - 1) / threads;
   if (blocks > 0x7fffffff) return set_err(ctx, CLC_EINVAL, "clc_find_images: too many galaxies");

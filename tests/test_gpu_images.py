@@ -62,18 +62,19 @@ def _gpu(c, nside, x, A, g, max_images, matrices=True):
     return [t.cpu() if t is not None else None for t in out]
 
 
+def _maxabs(t):
+    return float(t.abs().max()) if t.numel() else 0.0
+
+
 def _check(nside, x, A, g, max_images, got, matrices=True):
-    nimg, tri, iz, ip, Ai = got
+    nimg, tri, img, Ai = got
     wn, wt, wi, wA = im.find_images(nside, x, A, g, max_images)
     assert torch.equal(nimg.long(), wn)
     assert torch.equal(tri.T, wt)
     used = wt >= 0
-    sz = torch.sqrt((1 - iz.T) * (1 + iz.T))
-    v = torch.stack([sz * torch.cos(ip.T), sz * torch.sin(ip.T), iz.T], -1)
-    err = torch.linalg.vector_norm(v - wi, dim=-1)
-    assert float(err[used].max(initial=0.0)) < 1e-13
-    assert float(iz.T[~used].abs().max(initial=0.0)) == 0.0 and float(ip.T[~used].abs().max(initial=0.0)) == 0.0
-    assert bool(((ip >= 0) & (ip < 2 * math.pi)).all())
+    v = img.permute(2, 1, 0)
+    assert _maxabs(torch.linalg.vector_norm(v - wi, dim=-1)[used]) < 1e-13
+    assert _maxabs(v[~used]) == 0.0
     if matrices:
         ga = Ai.permute(2, 1, 0).reshape(g.shape[0], max_images, 2, 2)
         assert float((ga - wA).abs().max()) < 1e-12
@@ -100,11 +101,11 @@ def test_images_without_matrices_and_empty_call():
     A = synthetic.random_jacobians(x.shape[0], 0.1, 71)
     g = _galaxies(x, 100, 72)
     got = _gpu(c, nside, x, A, g, 3, matrices=False)
-    assert got[4] is None
+    assert got[3] is None
     _check(nside, x, A, g, 3, got, matrices=False)
     e = torch.empty(3, 0, dtype=F64, device="cuda")
-    nimg, tri, iz, ip, Ai = c.find_images(nside, x.T.contiguous().cuda(), A.reshape(-1, 4).T.contiguous().cuda(),
-                                          e, 2)
+    nimg, tri, img, Ai = c.find_images(nside, x.T.contiguous().cuda(), A.reshape(-1, 4).T.contiguous().cuda(),
+                                       e, 2)
     c.sync()
     assert nimg.numel() == 0
 
@@ -167,7 +168,7 @@ def test_full_size_weak_lens_sampled():
     A = synthetic.random_jacobians(npx, 0.05, 81)
     z, phi = synthetic.uniform_sphere(1_000_000, 82)
     g = torch.cat([hp.vec_from_zphi(z, phi), LENS + 0.01 * torch.randn(2000, 3, generator=torch.Generator().manual_seed(83), dtype=F64)])
-    nimg, tri, iz, ip, Ai = _gpu(c, nside, x, A, g, 2)
+    nimg, tri, img, Ai = _gpu(c, nside, x, A, g, 2)
     assert bool((nimg == 1).all())
     h = math.sqrt(4 * math.pi / npx)
     sample = torch.tensor([0, 1, 2, 3, 999_999, 1_000_000, 1_000_500, 1_001_999])
@@ -176,7 +177,5 @@ def test_full_size_weak_lens_sampled():
         own = _local_owners(nside, gm, 2e-3 + 6 * h)
         wn, wt, wi, wA = im.find_images(nside, x, A, g[m:m + 1], 2, owners=own)
         assert int(wn[0]) == int(nimg[m]) and torch.equal(wt[0], tri[:, m])
-        sz = math.sqrt((1 - float(iz[0, m])) * (1 + float(iz[0, m])))
-        v = torch.tensor([sz * math.cos(float(ip[0, m])), sz * math.sin(float(ip[0, m])), float(iz[0, m])], dtype=F64)
-        assert float(torch.linalg.vector_norm(v - wi[0, 0])) < 1e-13
+        assert float(torch.linalg.vector_norm(img[:, 0, m] - wi[0, 0])) < 1e-13
         assert float((Ai[:, 0, m].reshape(2, 2) - wA[0, 0]).abs().max()) < 1e-12
