@@ -34,11 +34,19 @@ def kappa_gamma(u_tt, u_pp, u_tp):
 
 
 def basis(n):
-    """Orthonormal tangent basis (theta-hat, phi-hat) at unit vectors n[..., 3]."""
+    """Orthonormal tangent basis (theta-hat, phi-hat) at unit vectors n[..., 3];
+    on a pole, where it is undefined, its limit along phi = 0."""
     x, y, z = n[..., 0], n[..., 1], n[..., 2]
     rho = torch.sqrt(x * x + y * y)
-    th = torch.stack([z * x / rho, z * y / rho, -rho], -1)
-    ph = torch.stack([-y / rho, x / rho, torch.zeros_like(x)], -1)
+    pole = rho == 0
+    r = torch.where(pole, torch.ones_like(rho), rho)
+    th = torch.stack([z * x / r, z * y / r, -rho], -1)
+    ph = torch.stack([-y / r, x / r, torch.zeros_like(x)], -1)
+    zero = torch.zeros_like(x)
+    th_pole = torch.stack([torch.where(z >= 0, torch.ones_like(z), -torch.ones_like(z)), zero, zero], -1)
+    ph_pole = torch.stack([zero, torch.ones_like(x), zero], -1)
+    th = torch.where(pole[..., None], th_pole, th)
+    ph = torch.where(pole[..., None], ph_pole, ph)
     return th, ph
 
 

@@ -7,9 +7,16 @@
 
 namespace clc {
 
-// Tangent basis (theta-hat, phi-hat) at the unit vector n.
+// Tangent basis (theta-hat, phi-hat) at the unit vector n; on a pole (where
+// it is undefined) its limit along phi = 0.
 __device__ __forceinline__ void tangent_basis(const double n[3], double t[3], double p[3]) {
-  const double r2 = n[0] * n[0] + n[1] * n[1], ir = rsqrt(r2), rho = r2 * ir;
+  const double r2 = n[0] * n[0] + n[1] * n[1];
+  if (r2 == 0.0) {
+    t[0] = n[2] >= 0.0 ? 1.0 : -1.0; t[1] = 0.0; t[2] = 0.0;
+    p[0] = 0.0; p[1] = 1.0; p[2] = 0.0;
+    return;
+  }
+  const double ir = rsqrt(r2), rho = r2 * ir;
   t[0] = n[2] * n[0] * ir; t[1] = n[2] * n[1] * ir; t[2] = -rho;
   p[0] = -n[1] * ir; p[1] = n[0] * ir; p[2] = 0.0;
 }

@@ -210,3 +210,12 @@ def test_matrix_interpolation_of_rotation_invariant_matrices():
     bi = interp.interpolate(nside, bb, th, ph)
     want = ai[:, None, None] * torch.eye(2, dtype=F64) + bi[:, None, None] * J
     assert torch.allclose(Aimg[:, 0], want, rtol=0, atol=1e-14)
+
+
+def test_basis_at_a_pole_is_the_limit_along_phi_zero():
+    from oracle import geometry
+    eps = 1e-9
+    for zs in (1.0, -1.0):
+        t0, p0 = geometry.basis(torch.tensor([[0.0, 0.0, zs]], dtype=F64))
+        t1, p1 = geometry.basis(torch.tensor([[math.sin(eps), 0.0, zs * math.cos(eps)]], dtype=F64))
+        assert torch.allclose(t0, t1, atol=2 * eps) and torch.allclose(p0, p1, atol=2 * eps)
