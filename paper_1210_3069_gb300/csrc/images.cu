@@ -364,9 +364,9 @@ extern "C" int clc_find_images(clc_ctx* ctx, int nside, const double* x, const d
   if (!ctx) return CLC_EINVAL;
   if (!valid_nside(nside) || ngal < 0 || max_images < 1 || max_images > kMaxImages)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: bad nside, ngal or max_images (1..8)");
+  if (ngal == 0) return CLC_OK;
   if ((A == nullptr) != (A_img == nullptr))
     return set_err(ctx, CLC_EINVAL, "clc_find_images: A and A_img must both be given or both be NULL");
-  if (ngal == 0) return CLC_OK;
   if (!x || !g || !nimg || !tri || !img)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: null pointer");
   cudaSetDevice(ctx->device);
