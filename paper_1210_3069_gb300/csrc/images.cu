@@ -393,7 +393,8 @@ extern "C" int clc_find_images(clc_ctx* ctx, int nside, const double* x, const d
   if (!(dm >= 0.0) || !(tm >= 0.0) || !std::isfinite(dm) || !std::isfinite(tm))
     return set_err(ctx, CLC_EINVAL, "clc_find_images: non-finite ray positions");
   const double R = std::fmin(dm + tm + 2 * kSearchMargin, kPi);
-  const double cand = 0.5 * (1.0 - std::cos(R)) * (double)npx + 8.0 * (4.0 * nside);
+  // pixels within R, plus the margin of a few pixels on each ring in range
+  const double cand = 0.5 * (1.0 - std::cos(R)) * (double)npx + 3.0 * (8.0 * R * nside / kPi + 3.0);
   if (cand * (double)ngal > 5e10)
     return set_err(ctx, CLC_EINVAL, "clc_find_images: rays too far from their pixels for the search (radius " +
                                         std::to_string(R) + " rad)");
