@@ -68,19 +68,16 @@ __device__ __forceinline__ int last_before(int k, const RingI& a, const RingI& b
 }
 
 // Vertices, counter-clockwise seen from outside, of triangle 2 p + s (s = 0:
-// the strip below p's ring, s = 1: the strip above); false for unused ids.
-__device__ __forceinline__ bool tri_vertices(int nside, int64_t p, int s, int64_t v[3]) {
-  const int64_t np = 12 * (int64_t)nside * nside;
-  int64_t kk;
-  const int r = pix2ring(nside, p, &kk);
-  const int k = (int)kk;
+// the strip below p's ring, s = 1: the strip above) for p at position k of
+// ring r; false for unused ids.
+__device__ __forceinline__ bool tri_vertices_rk(int nside, int64_t p, int r, int k, int s, int64_t v[3]) {
   if (s == 1 && r == 1) {
     if (p == 1) { v[0] = 0; v[1] = 1; v[2] = 2; return true; }
     if (p == 3) { v[0] = 2; v[1] = 3; v[2] = 0; return true; }
     return false;
   }
   if (s == 0 && r == 4 * nside - 1) {
-    const int64_t f = np - 4;
+    const int64_t f = 12 * (int64_t)nside * nside - 4;
     if (p == f + 1) { v[0] = f + 2; v[1] = f + 1; v[2] = f; return true; }
     if (p == f + 3) { v[0] = f; v[1] = f + 3; v[2] = f + 2; return true; }
     return false;
@@ -92,6 +89,12 @@ __device__ __forceinline__ bool tri_vertices(int nside, int64_t p, int s, int64_
   v[1] = s == 0 ? q : p;
   v[2] = s == 0 ? p : q;
   return true;
+}
+
+__device__ __forceinline__ bool tri_vertices(int nside, int64_t p, int s, int64_t v[3]) {
+  int64_t k;
+  const int r = pix2ring(nside, p, &k);
+  return tri_vertices_rk(nside, p, r, (int)k, s, v);
 }
 
 __device__ __forceinline__ void load3(const double* __restrict__ x, int64_t n, int64_t p, double o[3]) {
@@ -143,16 +146,16 @@ __device__ __forceinline__ void normalize3(const double a[3], double o[3]) {
   o[2] = a[2] * is;
 }
 
-// angle between unit vectors from their chord
-__device__ __forceinline__ double chord_angle(const double a[3], const double b[3]) {
+// squared chord between unit vectors, and the angle it spans
+__device__ __forceinline__ double chord2(const double a[3], const double b[3]) {
   const double dx = a[0] - b[0], dy = a[1] - b[1], dz = a[2] - b[2];
-  return 2.0 * asin(fmin(1.0, 0.5 * sqrt(dx * dx + dy * dy + dz * dz)));
+  return dx * dx + dy * dy + dz * dz;
 }
 
-// unit vector of the centre of RING pixel p
-__device__ __forceinline__ void centre_vec(int nside, int64_t p, double c[3]) {
-  int64_t k;
-  const int r = pix2ring(nside, p, &k);
+__device__ __forceinline__ double chord2_angle(double c2) { return 2.0 * asin(fmin(1.0, 0.5 * sqrt(c2))); }
+
+// unit vector of the centre of the pixel at position k of ring r
+__device__ __forceinline__ void centre_vec(int nside, int r, int64_t k, double c[3]) {
   const Ring g = ring_geom(nside, r);
   const int h = g.phi0 != 0.0 ? 1 : 0;
   double sn, cs;
@@ -162,32 +165,41 @@ __device__ __forceinline__ void centre_vec(int nside, int64_t p, double c[3]) {
   c[2] = g.z;
 }
 
+__device__ __forceinline__ void centre_vec(int nside, int64_t p, double c[3]) {
+  int64_t k;
+  const int r = pix2ring(nside, p, &k);
+  centre_vec(nside, r, k, c);
+}
+
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* a, double v) {
   atomicMax(a, (unsigned long long)__double_as_longlong(v));   // v >= 0: bit order = value order
 }
 
-// bounds[0] = D, bounds[1] = T (as the bits of non-negative doubles)
+// bounds[0], bounds[1]: the squared chords of D and T (as the bits of
+// non-negative doubles, whose integer order is their value order)
 __global__ void k_image_bounds(const double* __restrict__ x, int nside, int64_t npx,
                                unsigned long long* __restrict__ bounds) {
   double dmax = 0.0, tmax = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < npx; p += stride) {
+    int64_t k;
+    const int r = pix2ring(nside, p, &k);
     double xr[3], xn[3], c[3];
     load3(x, npx, p, xr);
     normalize3(xr, xn);
-    centre_vec(nside, p, c);
-    dmax = fmax(dmax, chord_angle(xn, c));
+    centre_vec(nside, r, k, c);
+    dmax = fmax(dmax, chord2(xn, c));
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
       int64_t v[3];
-      if (!tri_vertices(nside, p, s, v)) continue;
+      if (!tri_vertices_rk(nside, p, r, (int)k, s, v)) continue;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         if (v[i] == p) continue;
         double yr[3], yn[3];
         load3(x, npx, v[i], yr);
         normalize3(yr, yn);
-        tmax = fmax(tmax, chord_angle(xn, yn));
+        tmax = fmax(tmax, chord2(xn, yn));
       }
     }
   }
@@ -209,7 +221,7 @@ struct ImageOut {
   double* A;     // [4][max_images][ngal] or null
 };
 
-__global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ x, const double* __restrict__ Ar,
+__global__ void __launch_bounds__(128, 4) k_find_images(const double* __restrict__ x, const double* __restrict__ Ar,
                                                      int nside, int64_t npx, const double* __restrict__ gal,
                                                      int64_t ngal, const unsigned long long* __restrict__ bounds,
                                                      int max_images, ImageOut out) {
@@ -230,8 +242,8 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
     return;
   }
   normalize3(g, gn);
-  const double dmax = __longlong_as_double((long long)bounds[0]);
-  const double tmax = __longlong_as_double((long long)bounds[1]);
+  const double dmax = chord2_angle(__longlong_as_double((long long)bounds[0]));
+  const double tmax = chord2_angle(__longlong_as_double((long long)bounds[1]));
   const double tm = tmax + kSearchMargin;
   const double R = dmax + tm + kSearchMargin;
   // chord^2 limits (a 4 admits every point of the sphere)
@@ -271,13 +283,13 @@ __global__ void __launch_bounds__(128) k_find_images(const double* __restrict__ 
       double xr[3], xn[3];
       load3(x, npx, p, xr);
       normalize3(xr, xn);
-      const double dx = xn[0] - gn[0], dy = xn[1] - gn[1], dz = xn[2] - gn[2];
-      if (dx * dx + dy * dy + dz * dz > c2t) continue;
+      if (chord2(xn, gn) > c2t) continue;
+      const int jw = (int)(p - r.first);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         int64_t v[3];
         double d[3], gx[3];
-        if (!tri_vertices(nside, p, s, v) || !contains(x, npx, g, v, d, gx)) continue;
+        if (!tri_vertices_rk(nside, p, i, jw, s, v) || !contains(x, npx, g, v, d, gx)) continue;
         ++count;
         // keep the max_images smallest triangle ids, ascending
         const int64_t id = 2 * p + s;
@@ -387,11 +399,13 @@ extern "C" int clc_find_images(clc_ctx* ctx, int nside, const double* x, const d
   if (cuda_check(ctx, cudaMemcpyAsync(hb, bounds, sizeof(hb), cudaMemcpyDeviceToHost, ctx->stream), "bounds copy") ||
       cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "bounds sync"))
     return CLC_ECUDA;
-  double dm, tm;
-  memcpy(&dm, &hb[0], sizeof(double));
-  memcpy(&tm, &hb[1], sizeof(double));
-  if (!(dm >= 0.0) || !(tm >= 0.0) || !std::isfinite(dm) || !std::isfinite(tm))
+  double c2d, c2t;
+  memcpy(&c2d, &hb[0], sizeof(double));
+  memcpy(&c2t, &hb[1], sizeof(double));
+  if (!(c2d >= 0.0) || !(c2t >= 0.0) || !std::isfinite(c2d) || !std::isfinite(c2t))
     return set_err(ctx, CLC_EINVAL, "clc_find_images: non-finite ray positions");
+  const double dm = 2.0 * std::asin(std::fmin(1.0, 0.5 * std::sqrt(c2d)));
+  const double tm = 2.0 * std::asin(std::fmin(1.0, 0.5 * std::sqrt(c2t)));
   const double R = std::fmin(dm + tm + 2 * kSearchMargin, kPi);
   // pixels within R, plus the margin of a few pixels on each ring in range
   const double cand = 0.5 * (1.0 - std::cos(R)) * (double)npx + 3.0 * (8.0 * R * nside / kPi + 3.0);
