@@ -742,16 +742,19 @@ def images_line(args, wl, r):
     n, kms = r["prof"]["k_find_images"]
     roof = None
     if kms > 0:
-        # HBM-bound model: per galaxy the source position in (24 B), the
-        # outputs out (4 + 56 B per slot), and the rays that decide and
-        # interpolate its images: the three vertices of its triangle (24 B
-        # each) and the eight interpolation rays (24 B position + 32 B matrix)
-        per_gal = 24 + 4 + 56 * wl["max_images"] + 3 * 24 + 8 * 56
-        pk = load_peaks()[0].get("hbm_gbs", 6800.0)
-        ach = per_gal * r["M"] * n / (kms / 1e3) / 1e9
-        roof = {"kernel": "k_find_images", "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
-                "frac": ach / pk, "traffic": None, "launches": n, "avg_launch_ms": kms / max(n, 1),
-                "peak_source": "HBM copy, measured (MEASURED_PEAKS.json hbm_gbs)"}
+        # FP64-ALU-bound (ncu: FP64 pipe 83% busy, DRAM 3%).  Algorithmic FP64
+        # work per galaxy, what any search must do once the containing
+        # triangle is known: its three triple products and three hemisphere
+        # dots (57 flops), barycentric weights and the normalised image (35),
+        # the interpolation weights (20) and, for each of the four
+        # interpolation rays, normalisation, tangent basis, transport
+        # rotation, Q A Q^T and the weighted sum (106): about 540 flops
+        per_gal = 57 + 35 + 20 + 4 * 106
+        ach = per_gal * r["M"] * n / (kms / 1e3) / 1e12
+        roof = {"kernel": "k_find_images", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None, "launches": n,
+                "avg_launch_ms": kms / max(n, 1),
+                "peak_source": "FP64 FMA: 152 SMs x 2/clk x 2 flop x 2.07 GHz (derived)"}
     return {
         "metric": IMAGE_METRIC, "value": value, "unit": "galaxies/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
