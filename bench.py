@@ -223,6 +223,29 @@ def roofline(prof, models, peaks, peak_kind):
     return ents
 
 
+def plane_seed(cfg, rank):
+    """Seed of the synthetic plane of one rank: every rank solves its own
+    shell (independent problems, no data-path collective)."""
+    return cfg["seed"] + rank
+
+
+def max_over_ranks(value, device):
+    """The largest value over all ranks (a job's time is that of its slowest
+    rank); the value itself without a process group."""
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(world, units_per_rank, ms_max):
+    """Units per second of the whole job: every rank's units over the slowest
+    rank's time (weak scaling)."""
+    return world * units_per_rank / (ms_max / 1000.0)
+
+
 def run_gpu(args, cfg, rank, world):
     import paper_1210_3069_gb300 as clc
     clc.build()
@@ -236,7 +259,7 @@ def run_gpu(args, cfg, rank, world):
     P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
                       nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=prec)
     # seeded synthetic plane (a different shell per rank)
-    z, phi = synthetic.lognormal_particles(cfg["particles"], cfg["seed"] + rank, device=dev)
+    z, phi = synthetic.lognormal_particles(cfg["particles"], plane_seed(cfg, rank), device=dev)
     nbar = z.numel() / npix
     counts = torch.zeros(npix, dtype=torch.int32, device=dev)
     kappa = torch.empty(npix, dtype=torch.float64, device=dev)
@@ -321,10 +344,7 @@ def run_gpu(args, cfg, rank, world):
     prof = {k: ctx.profile_query(k) for k in KERNELS}
     ctx.profile(False)
     timed_cycles = cycles[-args.steps:]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t)
+    ms = max_over_ranks(ms, dev)
     # end to end through the public API with host buffers
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -333,11 +353,7 @@ def run_gpu(args, cfg, rank, world):
     e2e_run(e2e_steps, e0)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
     sol.close()
     return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, cycles=timed_cycles, clocks=clocks.summary(),
                 npix=npix, h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
@@ -1018,8 +1034,7 @@ def main():
             torch.distributed.destroy_process_group()
         return
     peaks, peak_kind = load_peaks()
-    planes = world * args.steps
-    value = planes / (r["ms"] / 1000.0)
+    value = whole_job_rate(world, args.steps, r["ms"])
     roof = roofline(r["prof"], kernel_models(cfg, args.precision, r["cycles"], args.steps), peaks, peak_kind)
     top = max(r["prof"].items(), key=lambda kv: kv[1][1])[0]
     line = {
@@ -1027,13 +1042,13 @@ def main():
         "ms_per_step": r["ms"] / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}[args.precision], "data": "synthetic",
         "config": config,
-        "rays_per_s": world * r["npix"] * args.steps / (r["ms"] / 1000.0),
+        "rays_per_s": whole_job_rate(world, r["npix"] * args.steps, r["ms"]),
         "mg_cycles": r["cycles"],
         "top_kernel": top,
         "roofline": roof[0] if roof else None,
         "roofline_all": roof,
         "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in r["prof"].items()},
-        "e2e": {"value": world / (r["e2e_ms"] / 1000.0), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
+        "e2e": {"value": whole_job_rate(world, 1, r["e2e_ms"]), "unit": UNIT, "h2d_bytes_per_step": r["h2d"],
                 "d2h_bytes_per_step": r["d2h"]},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
