@@ -160,7 +160,7 @@ def test_rays_sht_path_matches_oracle():
     assert rel_l2(rs.beta.T, st["beta"]) < TOL
     assert rel_l2(rs.A.T.reshape(-1, 2, 2), st["A"]) < TOL
     assert rel_l2(rs.Ap.T.reshape(-1, 2, 2), st["Ap"]) < TOL
-    # the driver entry point gives the same state
+    # the multi-plane entry point (clc_raytrace_planes) gives the same state
     rs2 = c.rays(p.numel())
     c.rays_init(rs2, z.cuda(), phi.cuda(), chi[0])
     c.raytrace_planes(clc.SOLVER_SHT, clc.mg_params(nside, lmax, 1), [k.cuda() for k in kap], nside, chi, rs2)
