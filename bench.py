@@ -199,8 +199,29 @@ def kernel_models(cfg, precision, cycles, nsteps):
     return out
 
 
-def roofline(prof, models, peaks, peak_kind):
-    """Roofline entries of the modelled kernels, largest total time first."""
+# DRAM bytes (read + write) of one V-cycle of the FP32 band kernels per
+# patch of 256^2 cells, over its five band levels (256 .. 16), from the ncu
+# capture of the Nside-512 plane (768 patches; every level's launch of the
+# first V-cycle).  Traffic grows with the number of patches, so a launch at
+# another patch count moves (this x patches / 5) bytes on average.
+BAND_DRAM_PER_PATCH_CYCLE = {
+    "k_prolong_smooth": (0.003 + 0.010 + 0.033 + 0.122 + 0.023 + 0.469 + 0.177) * 1e9 / 768,
+}
+
+
+def band_traffic(name, cfg, precision):
+    """Measured DRAM bytes per launch of a band kernel at this workload's
+    patch count (FP32 band kernels of 256-cell patches only), else None."""
+    per = BAND_DRAM_PER_PATCH_CYCLE.get(name)
+    if per is None or cfg["ncell"] != 256 or precision == "fp64":
+        return None
+    return per * 12 * cfg["nside_bundle"] ** 2 / 5
+
+
+def roofline(prof, models, peaks, peak_kind, traffic=None):
+    """Roofline entries of the modelled kernels, largest total time first;
+    traffic: {kernel: measured DRAM bytes per launch}."""
+    traffic = traffic or {}
     ents = []
     for name, (bound, amount, unit) in models.items():
         n, ms = prof.get(name, (0, 0.0))
@@ -217,7 +238,7 @@ def roofline(prof, models, peaks, peak_kind):
             ach = amount / (ms / 1e3) / 1e9
             pk = peaks.get("hbm_gbs", 6800.0)
             ents.append({"kernel": name, "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
-                         "frac": ach / pk, "traffic": None, "launches": n, "avg_launch_ms": ms / n,
+                         "frac": ach / pk, "traffic": traffic.get(name), "launches": n, "avg_launch_ms": ms / n,
                          "peak_source": f"HBM copy, {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"})
     ents.sort(key=lambda e: -e["avg_launch_ms"] * e["launches"])
     return ents
@@ -1035,7 +1056,8 @@ def main():
         return
     peaks, peak_kind = load_peaks()
     value = whole_job_rate(world, args.steps, r["ms"])
-    roof = roofline(r["prof"], kernel_models(cfg, args.precision, r["cycles"], args.steps), peaks, peak_kind)
+    roof = roofline(r["prof"], kernel_models(cfg, args.precision, r["cycles"], args.steps), peaks, peak_kind,
+                    traffic={k: band_traffic(k, cfg, args.precision) for k in BAND_DRAM_PER_PATCH_CYCLE})
     top = max(r["prof"].items(), key=lambda kv: kv[1][1])[0]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
