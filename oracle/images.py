@@ -5,7 +5,7 @@ search: triangles built from the rays' starting points on the image sphere
 map, vertex for vertex, to triangles of the same rays on the source sphere;
 every source-sphere triangle that contains the galaxy gives one image, at the
 position interpolated linearly over the triangle's image-sphere vertices.
-The implementation section on the grid search builds the triangles from the
+Sec. 3.3 (the grid-search implementation) builds the triangles from the
 HEALPix pixel centres, tests containment and interpolates with barycentric
 coordinates in the plane tangent to the sphere at the galaxy's source
 position, and obtains the inverse magnification matrix at the image from a

@@ -404,3 +404,22 @@ def fields_at(sol, nside_bundle, nvec, home):
     lookup = {int(b): k for k, b in enumerate(sol["bundles"].tolist())}
     idx = torch.tensor([lookup[int(b)] for b in home.tolist()], dtype=torch.long)
     return derivs_at(sol["partials"], sol["R"], sol["h"], idx, nvec)
+
+
+def partial_sky_kappa(kappa_fine, nside_fine, covered):
+    """Plane source of a light cone that covers only part of the sphere
+    (Sec. 3.4): outside the covered pixels (RING boolean mask) the matter is
+    set to the mean density, i.e. kappa = 0 there."""
+    kappa_fine = torch.as_tensor(kappa_fine)
+    return torch.where(torch.as_tensor(covered, dtype=torch.bool), kappa_fine, torch.zeros_like(kappa_fine))
+
+
+def domain_bundles(nside_bundle, centre, radius):
+    """NEST bundles of a circular domain of interest: those whose centres lie
+    within `radius` of the unit vector `centre`.  Partial-sky ray tracing
+    (Sec. 3.4) runs the SHT over the full sky and MG only on these bundles:
+    solve_plane(..., bundles=domain_bundles(...))."""
+    z, phi = hp.pix2ang_nest(nside_bundle, torch.arange(12 * nside_bundle * nside_bundle))
+    c = torch.as_tensor(centre, dtype=torch.float64)
+    d = torch.arccos((hp.vec_from_zphi(z, phi) @ c).clamp(-1.0, 1.0))
+    return torch.nonzero(d < radius).flatten()

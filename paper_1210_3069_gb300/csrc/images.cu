@@ -1,5 +1,5 @@
 // Grid search for lensed galaxy images (paper Sec. 2.3 and the grid-search
-// implementation of Sec. 3).  Rays start at the RING pixel centres; the
+// implementation, Sec. 3.3).  Rays start at the RING pixel centres; the
 // triangles joining centres of consecutive rings (every centre closes one
 // triangle with its predecessor on its ring and the last centre of the
 // neighbouring ring before it in longitude; two cap triangles at each pole)

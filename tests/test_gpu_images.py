@@ -1,5 +1,5 @@
 """GPU grid search for galaxy images (Sec. 2.3 and the grid-search
-implementation of Sec. 3) against the oracle, which tests every triangle:
+implementation, Sec. 3.3) against the oracle, which tests every triangle:
 image counts and triangle ids bit for bit (both sides take the containment
 decision with the same unfused FP64 triple products on identical inputs),
 image positions and transported matrices to rounding.  Undeflected, rotated,

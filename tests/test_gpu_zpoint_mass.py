@@ -1,5 +1,5 @@
-"""Point-mass tests of the SHT+MG Poisson solver (Sec. 4, point-mass tests;
-Fig. 4) on the GPU path: the measurement of `test_oracle_point_mass.py`
+"""Point-mass tests of the SHT+MG Poisson solver (Sec. 4.1,
+Fig. 2) on the GPU path: the measurement of `test_oracle_point_mass.py`
 (an Epanechnikov-smoothed unit mass, sigma = 3 pixels, normalised to unit
 mass; deflection and tangential shear 8 pixels to 0.25 rad from it against
 the Appendix A/E closed forms) through clc_poisson_shtmg in mixed precision

@@ -1,5 +1,5 @@
 """Pins of the grid-search oracle for galaxy images (paper Sec. 2.3 and the
-grid-search implementation of Sec. 3).
+grid-search implementation, Sec. 3.3).
 
 The triangulation is checked as a tiling of the sphere (count, orientation,
 solid angles summing to 4 pi, every edge shared by exactly two triangles);

@@ -1,5 +1,5 @@
-"""Point-mass tests of the SHT+MG Poisson solver (Sec. 4, point-mass tests;
-Fig. 4), on the oracle at a reduced scale.
+"""Point-mass tests of the SHT+MG Poisson solver (Sec. 4.1,
+Fig. 2), on the oracle at a reduced scale.
 
 A unit mass smoothed by the Epanechnikov kernel (Appendix E, sigma = 3
 pixels, sampled at the pixel centres and normalised to unit mass as the
