@@ -379,17 +379,20 @@ def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, 
 
 
 def solve_plane(kappa_fine, nside_fine, nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2,
-                tol=1e-10, max_cycles=60, fixed_cycles=None, bundles=None, coarsest=8):
+                tol=1e-10, max_cycles=60, fixed_cycles=None, bundles=None, coarsest=8, psi_sht=None):
     """The whole SHT+MG plane solve of Sec. 3.2 for the given bundles (all by
     default): degrade kappa to the SHT grid, SHT Poisson solve, patch set-up,
-    V-cycles on the correction to the SHT solution.  Returns dict with R, h,
-    u (interior [B, N, N]), partials, bundles, cycles, residual and psi_sht."""
+    V-cycles on the correction to the SHT solution.  A caller that already
+    holds the SHT potential of this kappa (psi_sht, RING map at nside_sht)
+    may pass it to skip the SHT step.  Returns dict with R, h, u (interior
+    [B, N, N]), partials, bundles, cycles, residual and psi_sht."""
     from . import binning, sht
     if bundles is None:
         bundles = torch.arange(12 * nside_bundle * nside_bundle)
     bundles = torch.as_tensor(bundles)
-    ks = binning.degrade_ring(kappa_fine, nside_fine, nside_sht)
-    psi_sht = sht.poisson_sht(ks, nside_sht, lmax, derivatives=False)["psi"]
+    if psi_sht is None:
+        ks = binning.degrade_ring(kappa_fine, nside_fine, nside_sht)
+        psi_sht = sht.poisson_sht(ks, nside_sht, lmax, derivatives=False)["psi"]
     R, h, u, f, ghosts = setup_patches(kappa_fine, nside_fine, psi_sht, nside_sht, nside_bundle, bundles,
                                        ncell=ncell, coarsest=coarsest)
     ui, cycles, rr = solve_correction(u, f, h, ncell, nu1=nu1, nu2=nu2, tol=tol, max_cycles=max_cycles,

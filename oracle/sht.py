@@ -170,6 +170,29 @@ def synthesis(alm, nside, lmax):
     return ring_inverse_fourier(nside, G, lmax)
 
 
+def synthesis_rings(alm, nside, lmax, rings):
+    """The synthesis of `synthesis` on the listed rings only (0-based ring
+    indices); every other pixel of the returned map is NaN, so a later use of
+    a pixel that was not synthesised shows up as NaN.  The same sums as the
+    full synthesis, restricted to fewer rings."""
+    rt = hp.ring_table(nside)
+    rings = torch.as_tensor(rings, dtype=torch.int64)
+    G = torch.zeros((rings.numel(), lmax + 1), dtype=C128)
+    for m, lam in legendre_columns(lmax, rt["z"][rings], rt["sin_theta"][rings]):
+        i0 = alm_index(lmax, m, m)
+        G[:, m] = lam.T.to(C128) @ alm[i0:i0 + lmax - m + 1]
+    f = torch.full((hp.npix(nside),), float("nan"), dtype=F64)
+    m = torch.arange(lmax + 1)
+    c = torch.where(m == 0, 1.0, 2.0).to(F64)
+    for k, r in enumerate(rings.tolist()):
+        n = int(rt["npix"][r])
+        first = int(rt["first"][r])
+        H = torch.zeros(n, dtype=C128)
+        H.index_add_(0, m % n, c * G[k] * torch.exp(1j * m.to(F64) * float(rt["phi0"][r])))
+        f[first:first + n] = (torch.fft.ifft(H) * n).real
+    return f
+
+
 def ell_of_index(lmax):
     ls = []
     for m in range(lmax + 1):

@@ -1,0 +1,175 @@
+"""GPU parity of the SHT+MG solver in the configuration the throughput is
+measured on (paper Sec. 3.2): 256-cell patches, so the FP32 band kernels of
+256 and 128 cells per side (eight and four 32-row bands per patch) run,
+hundreds to thousands of patches, CLC_MIXED (FP32 V-cycles refining an
+FP64-accurate residual) and CLC_FP32 as well as CLC_FP64.
+
+* Nside 512 / nside_sht 128 / lmax 256 / bundle Nside 8: 768 patches of 256^2
+  cells.  FP64 at a fixed cycle count equals the oracle on 16 sampled
+  bundles; CLC_MIXED and CLC_FP32 at the same cycle count reproduce the FP64
+  iterate on every patch to their arithmetic's level; CLC_MIXED converged to a
+  1e-10 relative residual equals the converged oracle on 16 bundles.
+* The Nside-2048 plane itself (5e7 lognormal particles, the seed and plane
+  scale of the throughput measurement, nside_sht 512, lmax 1024, 12288
+  patches): the converged CLC_MIXED fields at every pixel of four bundles
+  (north polar, two equatorial-face, south) equal the converged oracle's.
+"""
+import math
+
+import pytest
+import torch
+
+from oracle import binning, healpix as hp, interp, mg as omg, sht
+from tests.gpu_util import ctx, rel_l2
+from workloads import cosmology, synthetic
+
+pytestmark = pytest.mark.gpu
+KEYS = ("a_th", "a_ph", "u_tt", "u_pp", "u_tp")
+
+
+def _params(clc, ns, lmax, nb, ncell, prec, fixed=0, tol=1e-10):
+    return clc.mg_params(ns, lmax, nb, ncell=ncell, nu1=2, nu2=2, fixed_cycles=fixed, tol=tol, precision=prec,
+                         max_cycles=60)
+
+
+def _bundle_pixels(nf, nb, bundles):
+    """RING pixels of nf whose home bundle (NEST at nb) is in `bundles`, the
+    unit vectors of their centres and their home bundles."""
+    p = torch.arange(hp.npix(nf))
+    home = omg.home_bundle(nf, nb, hp.ring2nest(nf, p))
+    sel = torch.isin(home, torch.as_tensor(bundles))
+    return p[sel], hp.pix2vec_ring(nf, p[sel]), home[sel]
+
+
+@pytest.fixture(scope="module")
+def plane512():
+    nf = 512
+    z, phi = synthetic.lognormal_particles(3_000_000, 1210002)
+    kappa = binning.kappa_from_counts(binning.bin_counts(nf, z, phi), z.numel() / hp.npix(nf), 1.0)
+    return nf, kappa
+
+
+# 16 bundles of Nside 8: both polar caps, the belt, face corners and edges
+SAMPLE8 = [0, 15, 63, 64, 200, 255, 300, 383, 400, 511, 512, 600, 700, 703, 704, 767]
+
+
+def test_fp64_768_patches_fixed_cycles_match_oracle(plane512):
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, kappa = plane512
+    ns, lmax, nb, ncell, cyc = 128, 256, 8, 256, 3
+    sol = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.FP64, fixed=cyc))
+    got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
+    c.sync()
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, fixed_cycles=cyc, bundles=SAMPLE8)
+    pix, nv, home = _bundle_pixels(nf, nb, SAMPLE8)
+    want = omg.fields_at(ref, nb, nv, home)
+    for k in KEYS:
+        assert rel_l2(got[k].cpu()[pix], want[k]) < 1e-10, k
+    sol.close()
+
+
+@pytest.mark.parametrize("prec_name,tol", [("MIXED", 1e-6), ("FP32", 1e-4)])
+def test_float_band_kernels_reproduce_fp64_iterate(plane512, prec_name, tol):
+    """The same number of V-cycles on every one of the 768 patches: CLC_MIXED
+    (FP32 cycles on the float-float residual) and CLC_FP32 against CLC_FP64,
+    every field at every pixel."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, kappa = plane512
+    ns, lmax, nb, ncell, cyc = 128, 256, 8, 256, 4
+    kd = kappa.cuda()
+    s64 = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.FP64, fixed=cyc))
+    ref = c.poisson_shtmg(kd, nf, s64, derivatives=True)
+    c.sync()
+    s64.close()
+    sx = c.solution(nf, _params(clc, ns, lmax, nb, ncell, getattr(clc, prec_name), fixed=cyc))
+    got = c.poisson_shtmg(kd, nf, sx, derivatives=True)
+    c.sync()
+    assert sx.info()[0] == cyc
+    errs = {k: rel_l2(got[k], ref[k]) for k in KEYS}
+    print(prec_name, errs)
+    for k in KEYS:
+        assert errs[k] < tol, (k, errs)
+    sx.close()
+
+
+def test_mixed_768_patches_converged_matches_oracle(plane512):
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, kappa = plane512
+    ns, lmax, nb, ncell = 128, 256, 8, 256
+    sol = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.MIXED, tol=1e-10))
+    got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
+    c.sync()
+    cyc, res = sol.info()
+    assert res < 1e-10
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, fixed_cycles=cyc + 6, bundles=SAMPLE8)
+    pix, nv, home = _bundle_pixels(nf, nb, SAMPLE8)
+    want = omg.fields_at(ref, nb, nv, home)
+    errs = {k: rel_l2(got[k].cpu()[pix], want[k]) for k in KEYS}
+    print("mixed converged", cyc, res, errs)
+    for k in KEYS:
+        # both sides converged: the agreement is bounded by the GPU's 1e-10
+        # relative residual through the operator, not by 1e-10 itself
+        assert errs[k] < 1e-7, (k, errs)
+    sol.close()
+
+
+def _rings_touched(ns, nb, bundles, ncell):
+    """0-based rings of the nside_sht map that the patch set-up of these
+    bundles reads (every level's interpolation positions)."""
+    R = omg.rotation(nb, torch.as_tensor(bundles))
+    h = omg.patch_side(nb) / ncell
+    pix = []
+    for n in omg.level_sizes(ncell):
+        v = omg.to_global(R, omg.patch_vectors(n, h * (ncell // n)))
+        th, ph = omg.theta_phi(v)
+        idx, w = interp.interp_weights(ns, th.reshape(-1), ph.reshape(-1))
+        pix.append(idx.reshape(-1))
+    ring, _ = hp.pix2ring(ns, torch.unique(torch.cat(pix)))
+    return torch.unique(ring - 1)
+
+
+def test_nside2048_plane_sampled_bundles_match_oracle():
+    """The converged CLC_MIXED solve of the Nside-2048 plane of the throughput
+    measurement (12288 patches), every pixel of four bundles, against the
+    oracle run on those bundles only (same particles, same plane scale)."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, ns, lmax, nb, ncell = 2048, 512, 1024, 32, 256
+    pl = cosmology.lens_planes(40, 50.0)
+    scale = pl["scale"][20] * pl["growth"][20]
+    z, phi = synthetic.lognormal_particles(50_000_000, 1210002, device="cuda")
+    npx = hp.npix(nf)
+    nbar = z.numel() / npx
+    counts = c.bin_particles(z, phi, nf)
+    kappa = c.counts_to_kappa(counts, nf, nbar, scale)
+    sol = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.MIXED, tol=1e-10))
+    got = c.poisson_shtmg(kappa, nf, sol, derivatives=True)
+    c.sync()
+    cyc, res = sol.info()
+    assert res < 1e-10
+    bundles = [1023, 5 * 1024 + 500, 6 * 1024 + 37, 9 * 1024 + 700]
+    pix, nv, home = _bundle_pixels(nf, nb, bundles)
+    gsel = {k: got[k][pix.cuda()].cpu() for k in KEYS}
+    sol.close()
+    del got, counts
+    # the oracle side: binning of the same particles, the SHT on the rings the
+    # four patches read, V-cycles on the four patches
+    zc, pc = z.cpu(), phi.cpu()
+    del z, phi
+    kap_o = binning.kappa_from_counts(binning.bin_counts(nf, zc, pc), nbar, scale)
+    del zc, pc
+    assert torch.equal(kap_o, kappa.cpu())    # bit-exact binning (also tested on its own)
+    ks = binning.degrade_ring(kap_o, nf, ns)
+    plm = sht.poisson(sht.analysis(ks, ns, lmax), lmax)
+    psi = sht.synthesis_rings(plm, ns, lmax, _rings_touched(ns, nb, bundles, ncell))
+    ref = omg.solve_plane(kap_o, nf, ns, lmax, nb, ncell=ncell, fixed_cycles=cyc + 6, bundles=bundles,
+                          psi_sht=psi)
+    want = omg.fields_at(ref, nb, nv, home)
+    errs = {k: rel_l2(gsel[k], want[k]) for k in KEYS}
+    print("nside 2048 plane", cyc, res, errs)
+    for k in KEYS:
+        assert bool(torch.isfinite(want[k]).all())
+        assert errs[k] < 1e-7, (k, errs)

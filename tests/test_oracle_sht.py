@@ -122,6 +122,29 @@ def test_analysis_is_weighted_adjoint_of_synthesis():
     assert abs(float(lhs - rhs)) < 1e-11 * float(abs(lhs) + 1)
 
 
+def test_ring_restricted_synthesis_against_direct_sum():
+    """synthesis_rings on a few rings (polar cap, belt, last ring) equals the
+    direct sum of a_lm Y_lm (scipy) at those rings' pixel centres; every other
+    pixel is NaN."""
+    nside, L = 8, 12
+    g = torch.Generator().manual_seed(6)
+    alm = torch.randn(sht.nalm(L), dtype=torch.complex128, generator=g)
+    rings = [0, 5, 14, 30]
+    f = sht.synthesis_rings(alm, nside, L, rings)
+    ring, _ = hp.pix2ring(nside, torch.arange(hp.npix(nside)))
+    on = torch.isin(ring - 1, torch.tensor(rings))
+    z, phi = hp.pix2ang_ring(nside, torch.arange(hp.npix(nside))[on])
+    th = np.arccos(z.numpy())
+    want = np.zeros(th.shape)
+    for m in range(L + 1):
+        for l in range(m, L + 1):
+            y = sp.sph_harm_y(l, m, th, phi.numpy())
+            a = complex(alm[sht.alm_index(L, l, m)])
+            want += (a * y).real if m == 0 else 2.0 * (a * y).real
+    assert np.allclose(f[on].numpy(), want, rtol=0, atol=1e-12 * np.abs(want).max())
+    assert bool(torch.isnan(f[~on]).all())
+
+
 def test_iterated_analysis_recovers_band_limited_map():
     """Jacobi-iterated analysis a <- a + A(f - S a) converges to the exact
     coefficients of a band-limited map (L <= Nside / 2)."""
