@@ -43,7 +43,7 @@ def interp_weights(nside, theta, phi):
     rt = hp.ring_table(nside)
     th_r = ring_theta(nside)
     nr = th_r.numel()
-    theta = torch.as_tensor(theta, dtype=F64)
+    theta = torch.as_tensor(theta, dtype=F64).contiguous()
     phi = torch.as_tensor(phi, dtype=F64)
     # ring index r1 (0-based) with th_r[r1] <= theta < th_r[r1 + 1]; -1 above the first ring
     r1 = torch.searchsorted(th_r, theta, right=True) - 1

@@ -409,12 +409,21 @@ def fields_at(sol, nside_bundle, nvec, home):
     return derivs_at(sol["partials"], sol["R"], sol["h"], idx, nvec)
 
 
-def partial_sky_kappa(kappa_fine, nside_fine, covered):
+def partial_sky_kappa(density, covered, scale):
     """Plane source of a light cone that covers only part of the sphere
     (Sec. 3.4): outside the covered pixels (RING boolean mask) the matter is
-    set to the mean density, i.e. kappa = 0 there."""
-    kappa_fine = torch.as_tensor(kappa_fine)
-    return torch.where(torch.as_tensor(covered, dtype=torch.bool), kappa_fine, torch.zeros_like(kappa_fine))
+    at the mean density of the universe, so kappa = 0 there; inside,
+    kappa_p = scale * (density_p / nbar - 1) (Eq. lenspoisson) with density
+    the particle number per pixel (binned counts or a smoothed map) and nbar
+    the light cone's own mean over its covered pixels.  With that mean the
+    source integrates to zero over the sphere, the condition for a solution
+    of the Poisson equation on the closed sphere: the SHT step drops l = 0,
+    and the MG patches, which see the source itself, then solve the same
+    problem."""
+    d = torch.as_tensor(density).to(F64)
+    covered = torch.as_tensor(covered, dtype=torch.bool)
+    nbar = d[covered].sum() / covered.sum()
+    return torch.where(covered, scale * (d / nbar - 1.0), torch.zeros_like(d))
 
 
 def domain_bundles(nside_bundle, centre, radius):
