@@ -69,7 +69,8 @@ def test_fp64_768_patches_fixed_cycles_match_oracle(plane512):
     sol.close()
 
 
-@pytest.mark.parametrize("prec_name,tol", [("MIXED", 1e-6), ("FP32", 1e-4)])
+# measured on GB300: MIXED 2.5e-9, FP32 1.1e-6 (largest field, u_tt)
+@pytest.mark.parametrize("prec_name,tol", [("MIXED", 1e-8), ("FP32", 1e-5)])
 def test_float_band_kernels_reproduce_fp64_iterate(plane512, prec_name, tol):
     """The same number of V-cycles on every one of the 768 patches: CLC_MIXED
     (FP32 cycles on the float-float residual) and CLC_FP32 against CLC_FP64,
@@ -111,8 +112,9 @@ def test_mixed_768_patches_converged_matches_oracle(plane512):
     print("mixed converged", cyc, res, errs)
     for k in KEYS:
         # both sides converged: the agreement is bounded by the GPU's 1e-10
-        # relative residual through the operator, not by 1e-10 itself
-        assert errs[k] < 1e-7, (k, errs)
+        # relative residual through the operator (second derivatives see it
+        # almost undamped), not by 1e-10 itself; measured 8e-11 on GB300
+        assert errs[k] < 1e-8, (k, errs)
     sol.close()
 
 
@@ -172,4 +174,5 @@ def test_nside2048_plane_sampled_bundles_match_oracle():
     print("nside 2048 plane", cyc, res, errs)
     for k in KEYS:
         assert bool(torch.isfinite(want[k]).all())
-        assert errs[k] < 1e-7, (k, errs)
+        # as above; measured 1.2e-9 on GB300 (u_tt)
+        assert errs[k] < 1e-8, (k, errs)
