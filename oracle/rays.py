@@ -86,6 +86,17 @@ def step(state, lens, chi_prev, chi_n, chi_next):
             "A": transport(A_next, n, n_new), "Ap": transport(A, n, n_new)}
 
 
+def image_basis(A, n_source, n_image):
+    """A[M, 2, 2] carried from the tangent basis at the rays' positions on the
+    source sphere to the basis at their image positions (the directions in
+    which they were shot), by the transport of Appendix B along the geodesic
+    between the two.  The recursion keeps A in the basis at the ray's current
+    position; maps of the final shear over the image-plane grid (Sec. 5) are
+    taken in the basis at each image position, the frame in which the
+    relations C_l^E ~ C_l^kappa and C_l^B ~ C_l^omega hold."""
+    return transport(A, n_source, n_image)
+
+
 def trace(n0, chi, lenses, checkpoints=None):
     """Trace rays through planes 0 .. N-1 at distances chi[0 .. N-1] to the
     source sphere chi[N]; lenses[m](n) gives the plane-m lens fields.

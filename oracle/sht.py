@@ -235,6 +235,32 @@ def derivative_synthesis(psi_lm, nside, lmax):
     }
 
 
+def lens_fields_at(psi_lm, lmax, nvec):
+    """alpha and U (Appendix A conventions, (theta-hat, phi-hat) basis) of the
+    band-limited potential psi_lm at arbitrary unit vectors nvec[M, 3], by
+    direct synthesis of psi's partial derivatives there: the fields of the
+    pure-SHT solver (Sec. 3.2) without a map grid or an interpolation."""
+    from . import geometry
+    z = nvec[:, 2].contiguous()
+    s = torch.sqrt(nvec[:, 0] ** 2 + nvec[:, 1] ** 2)
+    ph = torch.atan2(nvec[:, 1], nvec[:, 0])
+    acc = {k: torch.zeros(z.shape, dtype=F64) for k in ("p_t", "p_p", "p_tt", "p_pp", "p_tp")}
+    for m, lam, dl, d2l in dtheta_columns(lmax, z, s):
+        i0 = alm_index(lmax, m, m)
+        a = psi_lm[i0:i0 + lmax - m + 1].to(C128)
+        e = torch.exp(1j * m * ph)
+        c = 1.0 if m == 0 else 2.0
+        g0 = (lam.T.to(C128) @ a) * e
+        g1 = (dl.T.to(C128) @ a) * e
+        g2 = (d2l.T.to(C128) @ a) * e
+        acc["p_t"] += c * g1.real
+        acc["p_tt"] += c * g2.real
+        acc["p_p"] += c * (1j * m * g0).real
+        acc["p_pp"] += c * (-(m * m) * g0).real
+        acc["p_tp"] += c * (1j * m * g1).real
+    return geometry.lens_fields_from_partials(acc["p_t"], acc["p_p"], acc["p_tt"], acc["p_pp"], acc["p_tp"], s, z)
+
+
 def pixel_sin_cos(nside):
     """sin theta and cos theta at every RING pixel centre."""
     rt = hp.ring_table(nside)

@@ -76,7 +76,8 @@ def cl(alm, lmax, alm2=None):
 def spectra_from_A(A, nside, lmax):
     """kappa, E, B and omega spectra from inverse magnification matrices
     A[Npix, 2, 2] on the RING pixel grid of the ray start positions
-    (Eq. invmagmat, Sec. 5)."""
+    (Eq. invmagmat, Sec. 5), each given in the tangent basis at its pixel
+    centre (rays.image_basis carries a traced A there)."""
     kappa = 1.0 - 0.5 * (A[:, 0, 0] + A[:, 1, 1])
     g1 = -0.5 * (A[:, 0, 0] - A[:, 1, 1])
     g2 = -0.5 * (A[:, 0, 1] + A[:, 1, 0])

@@ -86,6 +86,19 @@ def test_synthesis_and_derivatives_of_single_harmonic(l, m):
         assert np.allclose(d[k].numpy(), ref, atol=1e-12), k
     # the synthesis alone gives the same psi
     assert torch.allclose(sht.synthesis(alm, nside, L), d["psi"], atol=1e-13)
+    # the fields synthesised at arbitrary points (off the pixel grid, poles
+    # excluded) against the Appendix A formulas on the symbolic partials
+    g = torch.Generator().manual_seed(l * 10 + m)
+    zr = 1.8 * torch.rand(40, generator=g, dtype=F64) - 0.9
+    pr = 2 * math.pi * torch.rand(40, generator=g, dtype=F64)
+    sr = torch.sqrt((1 - zr) * (1 + zr))
+    nv = torch.stack([sr * torch.cos(pr), sr * torch.sin(pr), zr], -1)
+    got = sht.lens_fields_at(alm, L, nv)
+    ev = {k: torch.from_numpy(np.broadcast_to(sympy.lambdify((t, p), sympy.re(e), "numpy")(
+        np.arccos(zr.numpy()), pr.numpy()), zr.shape).copy()) for k, e in exprs.items()}
+    want = geometry.lens_fields_from_partials(ev["p_t"], ev["p_p"], ev["p_tt"], ev["p_pp"], ev["p_tp"], sr, zr)
+    for k in want:
+        assert torch.allclose(got[k], want[k], rtol=0, atol=1e-11), k
 
 
 def test_laplacian_eigen_relation():
