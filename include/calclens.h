@@ -387,11 +387,18 @@ int clc_eb_analysis(clc_ctx* ctx, const double* gamma1, const double* gamma2, in
  * (b = a if alm2 is NULL). */
 int clc_power_spectrum(clc_ctx* ctx, const double* alm, const double* alm2, int lmax, double* cl);
 /* From inverse magnification matrices A (SoA A[4][12 nside^2]: A_tt, A_tp,
- * A_pt, A_pp at the RING pixel centres where the rays started), the spectra
- * of kappa = 1 - (A_tt + A_pp)/2, of the E and B modes of
+ * A_pt, A_pp of the rays started at the RING pixel centres, ray k at pixel
+ * k), the spectra of kappa = 1 - (A_tt + A_pp)/2, of the E and B modes of
  * gamma = (-(A_tt - A_pp)/2, -(A_tp + A_pt)/2) and of omega = (A_tp - A_pt)/2
- * (Eq. invmagmat): cl_out[4][lmax + 1] in the order kappa, E, B, omega. */
-int clc_lensing_spectra(clc_ctx* ctx, const double* A, int nside, int lmax, double* cl_out);
+ * (Eq. invmagmat, Sec. 5): cl_out[4][lmax + 1] in the order kappa, E, B,
+ * omega.  The maps are taken in the basis at each ray's image position (its
+ * pixel centre).  x (device, SoA x[3][12 nside^2], nullable): the rays'
+ * positions on the source sphere, in whose tangent basis the ray recursion
+ * leaves A (clc_rays.x); each A is then first carried to its pixel centre by
+ * the transport of Appendix B.  x == NULL: A is already in the pixel basis.
+ * In the image basis C_l^E = s_l C_l^kappa and, at second order, C_l^B =
+ * s_l C_l^omega, s_l = (l+2)(l-1)/(l(l+1)). */
+int clc_lensing_spectra(clc_ctx* ctx, const double* x, const double* A, int nside, int lmax, double* cl_out);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics (no counterpart in the paper beyond its per-step wall timers) */

@@ -87,7 +87,7 @@ _SIGS = {
     "clc_gemm_f16x3": (_i, [_p, _p, _p, _p, _p, _i, _i, _i, _i, _p]),
     "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
     "clc_power_spectrum": (_i, [_p, _p, _p, _i, _p]),
-    "clc_lensing_spectra": (_i, [_p, _p, _i, _i, _p]),
+    "clc_lensing_spectra": (_i, [_p, _p, _p, _i, _i, _p]),
     "clc_profile": (_i, [_p, _i]),
     "clc_profile_query": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(_d)]),
     "clc_launch_count": (_i64, [_p]),
@@ -301,10 +301,12 @@ class Context:
         self._check(lib().clc_power_spectrum(self.h, _ptr(alm), _ptr(alm2), lmax, _ptr(cl)))
         return cl
 
-    def lensing_spectra(self, A, nside, lmax):
-        """dict of C_l for kappa, E, B, omega from A[4, 12 nside^2]."""
+    def lensing_spectra(self, A, nside, lmax, x=None):
+        """dict of C_l for kappa, E, B, omega from A[4, 12 nside^2] (rays from
+        the RING pixel centres); x[3, 12 nside^2]: the rays' source positions,
+        whose basis A is in (None: A is in the pixel basis)."""
         cl = torch.empty(4, lmax + 1, dtype=torch.float64, device=self.device)
-        self._check(lib().clc_lensing_spectra(self.h, _ptr(A), nside, lmax, _ptr(cl)))
+        self._check(lib().clc_lensing_spectra(self.h, _ptr(x), _ptr(A), nside, lmax, _ptr(cl)))
         return dict(zip(("kappa", "E", "B", "omega"), cl))
 
     # -- step 3 / 4 ---------------------------------------------------------

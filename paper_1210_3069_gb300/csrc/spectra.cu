@@ -16,6 +16,7 @@
 // takes the opposite one, which fixes the north/south combinations.
 #include "fft.cuh"
 #include "legendre.cuh"
+#include "sphere.cuh"
 
 int clc_sht_analysis(clc_ctx*, const double*, int, int, double*);
 
@@ -123,6 +124,38 @@ __global__ void k_decompose_A(const double* __restrict__ A, int64_t n, double* _
   }
 }
 
+// The same decomposition after carrying each ray's A from the tangent basis
+// at its source-sphere position x to the basis at its image position, the
+// centre of RING pixel k (Appendix B transport along the geodesic between
+// them).  One CTA per ring, like the ray initialisation: the ring geometry
+// once, longitudes by sincospi.  kappa and omega are invariant under the
+// rotation; the shear turns by twice its angle.
+__global__ void k_decompose_A_image(const double* __restrict__ x, const double* __restrict__ A, int nside, int64_t n,
+                                    double* __restrict__ out) {
+  const int i = blockIdx.x + 1;
+  const Ring r = ring_geom(nside, i);
+  const double inv = 1.0 / (double)r.npix;
+  const int shift = r.phi0 != 0.0 ? 1 : 0;
+  for (int j = threadIdx.x; j < r.npix; j += blockDim.x) {
+    const int64_t k = r.first + j;
+    double sp, cp;
+    sincospi((double)(2 * j + shift) * inv, &sp, &cp);
+    const double n0[3] = {r.s * cp, r.s * sp, r.z};
+    const double xv[3] = {x[k], x[n + k], x[2 * n + k]};
+    const double ix = rsqrt(dot3(xv, xv));
+    const double nx[3] = {xv[0] * ix, xv[1] * ix, xv[2] * ix};
+    double t[3], q[3], Q[4], Ai[4];
+    tangent_basis(nx, t, q);
+    transport_q(nx, t, n0, Q);
+    const double Ak[4] = {A[k], A[n + k], A[2 * n + k], A[3 * n + k]};
+    qaqt(Q, Ak, Ai);
+    out[k] = 1.0 - 0.5 * (Ai[0] + Ai[3]);
+    out[n + k] = -0.5 * (Ai[0] - Ai[3]);
+    out[2 * n + k] = -0.5 * (Ai[1] + Ai[2]);
+    out[3 * n + k] = 0.5 * (Ai[1] - Ai[2]);
+  }
+}
+
 int eb_analysis(clc_ctx* ctx, const double* g1, const double* g2, int nside, int lmax, double2* E, double2* B) {
   int rc;
   auto plan = get_fft_plan(ctx, nside, &rc);
@@ -167,7 +200,8 @@ extern "C" int clc_power_spectrum(clc_ctx* ctx, const double* alm, const double*
   return launch_check(ctx, "k_cl");
 }
 
-extern "C" int clc_lensing_spectra(clc_ctx* ctx, const double* A, int nside, int lmax, double* cl_out) {
+extern "C" int clc_lensing_spectra(clc_ctx* ctx, const double* x, const double* A, int nside, int lmax,
+                                   double* cl_out) {
   if (!ctx) return CLC_EINVAL;
   if (!valid_nside(nside) || nside > 4096 || lmax < 2 || lmax > 4 * nside || !A || !cl_out)
     return set_err(ctx, CLC_EINVAL, "clc_lensing_spectra: bad arguments");
@@ -178,7 +212,10 @@ extern "C" int clc_lensing_spectra(clc_ctx* ctx, const double* A, int nside, int
   if (!maps) return CLC_ENOMEM;
   double2* alm = (double2*)(maps + 4 * np);
   int rc;
-  CLC_LAUNCH(ctx, "k_decompose_A", k_decompose_A, 1024, 256, 0, A, np, maps);
+  if (x)
+    CLC_LAUNCH(ctx, "k_decompose_A", k_decompose_A_image, 4 * nside - 1, 256, 0, x, A, nside, np, maps);
+  else
+    CLC_LAUNCH(ctx, "k_decompose_A", k_decompose_A, 1024, 256, 0, A, np, maps);
   if ((rc = launch_check(ctx, "k_decompose_A"))) return rc;
   if ((rc = clc_sht_analysis(ctx, maps, nside, lmax, (double*)alm))) return rc;                    // kappa
   if ((rc = clc_sht_analysis(ctx, maps + 3 * np, nside, lmax, (double*)(alm + na)))) return rc;    // omega

@@ -169,6 +169,27 @@ def test_lensing_spectra_match_oracle():
         assert rel_l2(got[k], want[k]) < TOL, k
 
 
+def test_lensing_spectra_in_image_basis_match_oracle():
+    """A given in the basis at the rays' source-sphere positions x: the call
+    carries it to the pixel centres (Appendix B transport) before the
+    spectra, as the oracle's image_basis does."""
+    from oracle import rays as orays, spectra
+    c = ctx()
+    nside, lmax = 32, 64
+    g = torch.Generator().manual_seed(10)
+    npx = hp.npix(nside)
+    A = torch.eye(2, dtype=torch.float64).expand(npx, 2, 2) + \
+        0.01 * torch.randn(npx, 2, 2, dtype=torch.float64, generator=g)
+    n0 = hp.pix2vec_ring(nside, torch.arange(npx))
+    x = 700.0 * (n0 + 0.02 * torch.randn(npx, 3, dtype=torch.float64, generator=g))
+    nx = x / torch.linalg.vector_norm(x, dim=-1, keepdim=True)
+    got = c.lensing_spectra(A.reshape(-1, 4).T.contiguous().cuda(), nside, lmax, x=x.T.contiguous().cuda())
+    c.sync()
+    want = spectra.spectra_from_A(orays.image_basis(A, nx, n0), nside, lmax)
+    for k in ("kappa", "E", "B", "omega"):
+        assert rel_l2(got[k], want[k]) < TOL, k
+
+
 def test_fp64_sht_in_order_ranges_is_identical():
     """With the FP64 Legendre table limited to a fraction of its size the SHT
     runs over order ranges; every result is bit-identical to the whole-table
