@@ -141,3 +141,27 @@ def test_patch_derivatives_in_global_basis_match_sht():
     for k in ("a_th", "a_ph", "u_tt", "u_pp", "u_tp"):
         scale = float(ref[k].abs().max()) + 1e-3
         assert float((out[k] - ref[k]).abs().max()) < 2e-4 * scale, k
+
+
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_correction_form_gives_the_fas_iterates(cycles):
+    """V-cycles on the correction e = u - u_SHT with zero Dirichlet data
+    (solve_correction) give the same iterates as FAS V-cycles on u itself
+    from the SHT starting guess with the SHT ghosts (PatchSolver.solve): the
+    operator is linear, so the two differ only by rounding."""
+    from oracle import binning, healpix as hp
+    from workloads import synthetic
+    nf, ns, lmax, nb, n = 32, 8, 16, 2, 32
+    z, phi = synthetic.lognormal_particles(200_000, 7)
+    kappa = binning.kappa_from_counts(binning.bin_counts(nf, z, phi), z.numel() / hp.npix(nf), 1.0)
+    psi = sht.poisson_sht(binning.degrade_ring(kappa, nf, ns), ns, lmax, derivatives=False)["psi"]
+    R, h, u0, f, ghosts = mg.setup_patches(kappa, nf, psi, ns, nb, torch.arange(12 * nb * nb), ncell=n)
+    S = mg.PatchSolver(n, h, ghosts, nu1=2, nu2=2)
+    u = u0.clone()
+    S.solve(u, f, fixed_cycles=cycles)
+    ue, k, _ = mg.solve_correction(u0, f, h, n, nu1=2, nu2=2, fixed_cycles=cycles)
+    assert k == cycles
+    scale = float(u[:, 1:-1, 1:-1].abs().max())
+    assert float((ue - u[:, 1:-1, 1:-1]).abs().max()) < 1e-12 * scale
+    # and the correction made a difference (the comparison is not vacuous)
+    assert float((ue - u0[:, 1:-1, 1:-1]).abs().max()) > 1e-4 * scale
