@@ -74,7 +74,10 @@ typedef struct clc_mg_params {
   int max_cycles;   /* V-cycle cap when iterating to tol                     */
   int fixed_cycles; /* > 0: run exactly this many V-cycles, ignore tol       */
   double tol;       /* stop when max over patches ||f - L u||_2 / ||f||_2 < tol */
-  int precision;    /* CLC_FP64 (all FP64) or CLC_FP32 (FP32 fields, FP64 coarsest) */
+  int precision;    /* CLC_FP64: all FP64; CLC_FP32: FP32 V-cycles and residual
+                       (FP64 coarsest solve); CLC_MIXED: FP32 V-cycles refining a
+                       residual of FP64 accuracy (float-float), converging to the
+                       same tol as CLC_FP64 */
 } clc_mg_params;
 
 /* Ray state, structure of arrays of n rays (device FP64):
@@ -412,6 +415,13 @@ int clc_profile(clc_ctx* ctx, int enable);
 int clc_profile_query(clc_ctx* ctx, const char* name, int64_t* launches_host, double* total_ms_host);
 /* Number of kernels this context has launched since it was created. */
 int64_t clc_launch_count(const clc_ctx* ctx);
+/* Exercise the bounded-wait error path of the pipelined kernels: one CTA
+ * waits on an mbarrier that nothing completes and gives up after `polls`
+ * polls (1 .. 2^20), recording a timeout in the context's device error word
+ * exactly as the tensor-core and MG kernels do when a copy never lands.  The
+ * next clc_sync returns CLC_ETIMEOUT and clears the word; the context stays
+ * usable.  No copy or MMA is left in flight. */
+int clc_diag_bounded_wait(clc_ctx* ctx, int64_t polls);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free SHT analysis.  The paper has no counterpart: this entry   */

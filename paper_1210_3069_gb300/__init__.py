@@ -91,6 +91,7 @@ _SIGS = {
     "clc_profile": (_i, [_p, _i]),
     "clc_profile_query": (_i, [_p, ctypes.c_char_p, ctypes.POINTER(_i64), ctypes.POINTER(_d)]),
     "clc_launch_count": (_i64, [_p]),
+    "clc_diag_bounded_wait": (_i, [_p, _i64]),
 }
 
 
@@ -182,6 +183,11 @@ class Context:
 
     def launch_count(self):
         return int(lib().clc_launch_count(self.h))
+
+    def diag_bounded_wait(self, polls):
+        """Run the bounded mbarrier wait that nothing completes (the timeout
+        path of the pipelined kernels); the next sync raises CLC_ETIMEOUT."""
+        self._check(lib().clc_diag_bounded_wait(self.h, int(polls)))
 
     # -- step 1 -----------------------------------------------------------
     def bin_particles(self, z, phi, nside, ordering=RING, counts=None):
