@@ -91,6 +91,17 @@ ADJOINT_WORKLOADS = {
 ADJOINT_METRIC = "loss+gradient evaluations/s (galaxy shear through SHT planes, adjoint w.r.t. all kappa maps)"
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+# FP64 operations of one ray step on an SHT+MG plane (k_ray_step, patch
+# lookup included), counted operation by operation on the formulas of the
+# kernel (an FMA is 2, a square root, reciprocal square root or division 1,
+# the small-angle series of asin and of the rotation coefficients term by
+# term): unit vector and tangent basis 20; patch lookup 293 (rotation to
+# the patch frame 15, angles 39, bilinear blend of the 6 x 6 stencil block
+# 177 = cell fractions 4 + row/column blends 36 + first-derivative blends of
+# the six rows 66 + five blended partials 63 + scales 8, Appendix A 10, rotation to the
+# global basis 52); Eq. Atraj 29; Eq. betaprop 81; Eq. posprop 16; new
+# unit vector and basis 20; Appendix B transport 32 and two Q A Q^T 48.
+RAY_STEP_FLOPS_MG = 539
 KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
            "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",
@@ -196,6 +207,9 @@ def kernel_models(cfg, precision, cycles, nsteps):
         n0 = cfg["ncell"]
         nres = sum((c + 1) // 2 + 1 for c in cycles)
         out["k_resid_mixed"] = ("hbm", 32.0 * npatch * n0 * n0 * nres, "byte")
+    # the ray step: FP64-ALU bound (228 B of state per ray against ~540 FP64
+    # operations), one step of every ray per plane
+    out["k_ray_step"] = ("alu", float(RAY_STEP_FLOPS_MG) * 12 * cfg["nside"] ** 2 * nsteps, "flop")
     return out
 
 
@@ -292,16 +306,17 @@ def run_gpu(args, cfg, rank, world):
     stream = torch.cuda.current_stream(dev)
     cycles = []
 
-    def step(zz=z, pp=phi, used=None):
+    def step(zz=z, pp=phi, used=None, solution=None):
+        solution = sol if solution is None else solution
         counts.zero_()
         ctx.bin_particles(zz, pp, nf, counts=counts)
         if used is not None:
             used.record(stream)   # the particle buffer may be refilled from here on
         ctx.counts_to_kappa(counts, nf, nbar, scale, kappa=kappa)
-        ctx.poisson_shtmg(kappa, nf, sol, check=False)
-        cycles.append(sol.info()[0])
+        ctx.poisson_shtmg(kappa, nf, solution, check=False)
+        cycles.append(solution.info()[0])
         ctx.rays_init_pixels(rays, nf, chi_n, cfg["nside_bundle"])
-        ctx.ray_step(rays, chi_prev, chi_n, chi_next, sol=sol)
+        ctx.ray_step(rays, chi_prev, chi_n, chi_next, sol=solution)
 
     # End to end, pipelined as a production driver would run it: each step's
     # particles are copied in from pinned host memory on a copy stream while
@@ -375,9 +390,50 @@ def run_gpu(args, cfg, rank, world):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dev)
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_steps > 0:
+        fp64 = fp64_comparison(args, ctx, cfg, sol, step, kappa, clc, dev)
     sol.close()
     return dict(ms=ms, e2e_ms=e2e_ms, launches=launches, prof=prof, cycles=timed_cycles, clocks=clocks.summary(),
-                npix=npix, h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix)
+                npix=npix, h2d=2 * 8 * z.numel(), d2h=4 * 8 * npix, fp64=fp64)
+
+
+def fp64_comparison(args, ctx, cfg, sol, step, kappa, clc, dev):
+    """The same step with the plain FP64 solver on the same plane (the
+    metric's comparison): FP64 ms per step, and the relative L2 difference of
+    the five lens fields between the two solutions at a seeded sample of
+    pixels (both stop at the same relative residual)."""
+    nf = cfg["nside"]
+    npix = 12 * nf * nf
+    g = torch.Generator(device=dev)
+    g.manual_seed(cfg["seed"] + 17)
+    pix = torch.randint(0, npix, (1_000_000,), generator=g, device=dev)
+    mine = {k: v[pix] for k, v in ctx.poisson_shtmg(kappa, nf, sol, derivatives=True, check=False).items()}
+    torch.cuda.synchronize()
+    sol.close()
+    P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
+                      nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=clc.FP64)
+    s64 = ctx.solution(nf, P)
+    step(solution=s64)                     # warm-up
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.fp64_steps):
+        step(solution=s64)
+    ev1.record()
+    torch.cuda.synchronize()
+    ms64 = ev0.elapsed_time(ev1) / args.fp64_steps
+    cyc64 = s64.info()[0]
+    ref = ctx.poisson_shtmg(kappa, nf, s64, derivatives=True, check=False)
+    err = {}
+    for k, v in ref.items():
+        w = v[pix]
+        err[k] = float(torch.linalg.vector_norm(mine[k] - w) / torch.linalg.vector_norm(w))
+    s64.close()
+    return {"value": 1000.0 / ms64, "unit": UNIT, "ms_per_step": ms64, "steps": args.fp64_steps,
+            "mg_cycles": cyc64, "rel_l2_vs_fp64": err, "max_rel_l2_vs_fp64": max(err.values()),
+            "sample": "1e6 seeded pixels, alpha and U of both solutions (both stopped at the same relative "
+                      "residual tolerance)"}
 
 
 def batch_maps(ctx, sizes, seed, dev):
@@ -957,6 +1013,11 @@ def oracle_plane_estimate(cfg, sample_patches=4, sample_rays=20_000, sample_part
     return sum(parts.values()), parts
 
 
+# V-cycles the GPU path needs to reach the 1e-10 tolerance on the Nside-2048
+# plane (its line's mg_cycles); the reference arm runs the oracle at this count
+ORACLE_CYCLES = 10
+
+
 def cpu_baseline(cfg, cycles, seed=0, small=False):
     kw = dict(sample_patches=2, sample_rays=5_000, sample_particles=500_000, sht_mcols=8) if small else {}
     t0 = time.perf_counter()
@@ -984,6 +1045,8 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS)
                     + sorted(SMOOTH_WORKLOADS) + sorted(IMAGE_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed steps of the plain FP64 solver on the same plane after the main run (0: skip)")
     args = ap.parse_args()
     if args.workload in ADJOINT_WORKLOADS:
         if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
@@ -1033,17 +1096,27 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        steps = []
+        # the FP64 oracle on the GPU line's cpu_baseline sample, at the V-cycle
+        # count the GPU path needs on this plane; each step times one sample
+        # and extrapolates it to a whole plane
+        est, walls = [], []
         for s in range(args.warmup + args.steps):
             t = time.perf_counter()
-            cpu_baseline(cfg, cycles=12, seed=s, small=True)
-            steps.append(time.perf_counter() - t)
-        est = cpu_baseline(cfg, cycles=12, small=True)
-        line = {"metric": METRIC, "value": est["value"], "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": 1000.0 / est["value"], "higher_is_better": True,
+            e = cpu_baseline(cfg, cycles=ORACLE_CYCLES, seed=s)
+            if s >= args.warmup:
+                est.append(e)
+                walls.append(time.perf_counter() - t)
+        secs = statistics.median(e["seconds_per_plane"] for e in est)
+        parts = {k: round(statistics.median(e["parts_s"][k] for e in est), 3) for k in est[0]["parts_s"]}
+        value = 1.0 / secs
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1000.0 * secs, "extrapolated": True,
+                "sample_wall_ms_per_step": 1000.0 * statistics.median(walls), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-                "impl": "reference", "cpu_baseline": {k: est[k] for k in ("kind", "cores", "sample", "value", "unit")},
-                "e2e": {"value": est["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                "impl": "reference",
+                "cpu_baseline": {"kind": "oracle", "cores": est[0]["cores"], "sample": est[0]["sample"],
+                                 "value": value, "unit": UNIT, "parts_s": parts},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
 
@@ -1075,9 +1148,11 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
     }
+    if r.get("fp64"):
+        line["fp64"] = r["fp64"]
+        line["speedup_vs_fp64"] = value / (world * r["fp64"]["value"])
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(cfg, cycles=max(r["cycles"]) if r["cycles"] else 10)
-        line["cpu_baseline"].pop("parts_s", None)
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()

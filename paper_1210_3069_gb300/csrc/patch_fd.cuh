@@ -37,19 +37,6 @@ __device__ __forceinline__ int fd_stencil(int k, int n, int order, double w[5]) 
   return n - 5;
 }
 
-// atan(t) by the Gregory series through t^13 for |t| < 0.04 (first omitted
-// term below 1e-20 relative).
-__device__ __forceinline__ double atan_small(double t) {
-  const double t2 = t * t;
-  return t * (1.0 - t2 * ((1.0 / 3.0) - t2 * ((1.0 / 5.0) - t2 * ((1.0 / 7.0) - t2 * ((1.0 / 9.0) -
-                                                                                    t2 * ((1.0 / 11.0) - t2 * (1.0 / 13.0)))))));
-}
-
-template <typename T>
-__device__ __forceinline__ double uat(const T* u, int n, int i, int j) {
-  return (double)u[(size_t)(i + 1) * (n + 2) + (j + 1)];
-}
-
 // Bilinear blend of the stencils of cells k and k + 1 (weights 1 - f, f) as
 // one stencil on the six points first .. first + 5: w1 (first derivative),
 // w2 (second derivative), both x 12.  The second cell's stencil starts at
@@ -90,12 +77,36 @@ __device__ __forceinline__ int fd_blend(int k, int n, double f, double w1[6], do
   return first;
 }
 
+// asin(s) by its Maclaurin series through s^13 for |s| < 0.04 (first omitted
+// term below 1e-21 relative); coefficients (2k)! / (4^k (k!)^2 (2k + 1)).
+__device__ __forceinline__ double asin_small(double s) {
+  const double s2 = s * s;
+  return s * (1.0 + s2 * ((1.0 / 6.0) + s2 * ((3.0 / 40.0) + s2 * ((5.0 / 112.0) + s2 * ((35.0 / 1152.0) +
+              s2 * ((63.0 / 2816.0) + s2 * (231.0 / 13312.0)))))));
+}
+
+// Fourth-order central stencils x 12 (first, second derivative) at point
+// s + 2 of the 6-vector y: y_s - y_{s+4} + 8 (y_{s+3} - y_{s+1}) and
+// 16 (y_{s+1} + y_{s+3}) - 30 y_{s+2} - (y_s + y_{s+4}).
+__device__ __forceinline__ double c_d1(const double* y, int s) { return fma(8.0, y[s + 3] - y[s + 1], y[s] - y[s + 4]); }
+__device__ __forceinline__ double c_d2(const double* y, int s) {
+  return fma(-30.0, y[s + 2], fma(16.0, y[s + 1] + y[s + 3], -(y[s] + y[s + 4])));
+}
+// the blend (1 - f) D(k) + f D(k + 1) of two neighbouring cells' stencils
+__device__ __forceinline__ double blend_d1(const double* y, double f) { return fma(f, c_d1(y, 1) - c_d1(y, 0), c_d1(y, 0)); }
+__device__ __forceinline__ double blend_d2(const double* y, double f) { return fma(f, c_d2(y, 1) - c_d2(y, 0), c_d2(y, 0)); }
+
 // Lens fields at unit vector nv (tangent basis et, ep there) from patch
-// potential u (n x n cells of size h, ghost-ring layout), R the patch rotation.  The five partials of the four
-// cells around the point are blended bilinearly; since each partial is a
-// tensor-product stencil, the blend is one tensor-product stencil on a 6 x 6
-// block of cells.  The patch angles' sines and cosines come from the
-// components of the rotated unit vector.
+// potential u (n x n cells of size h, ghost-ring layout), R the patch
+// rotation.  The five partials of the four cells around the point are blended
+// bilinearly; each partial is a tensor-product stencil, so the blend is one
+// tensor-product stencil on the 6 x 6 block of cells ii - 2 .. ii + 3,
+// jj - 2 .. jj + 3.  Away from the patch edge (every ray in its home bundle's
+// patch) all stencils are central and the blend is applied as (1 - f) D_k +
+// f D_{k+1} with the integer stencils, on row and column blends read straight
+// from the block; within two cells of the edge the one-sided stencils are
+// blended into six-point weights (fd_blend).  The patch angles come from the
+// rotated unit vector: theta' - pi/2 = -asin(v_z), phi' = asin(v_y / rho).
 template <typename T>
 __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h, double inv_h, const double* R,
                                                     const double nv[3], const double et[3], const double ep[3],
@@ -105,84 +116,98 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   const double vy = R[3] * nv[0] + R[4] * nv[1] + R[5] * nv[2];
   const double vz = R[6] * nv[0] + R[7] * nv[1] + R[8] * nv[2];
   const double r2 = vx * vx + vy * vy, is = rsqrt(r2), rho = r2 * is;
-  // theta' - pi/2 = -atan(vz / rho) and phi' = atan(vy / vx): near the patch
-  // centre (theta', phi') = (pi/2, 0) both ratios are small
-  const double tz = vz * is, ty = vx > 0.0 ? vy / vx : 1.0;
-  const double dth = fabs(tz) < 0.04 ? -atan_small(tz) : atan2(rho, vz) - 0.5 * kPi;
-  const double php = fabs(ty) < 0.04 ? atan_small(ty) : atan2(vy, vx);
+  const double sp = vy * is, cp = vx * is;   // sin, cos of phi'
+  double dth, php;
+  if (fabs(vz) < 0.04 && fabs(sp) < 0.04 && vx > 0.0) {
+    dth = -asin_small(vz);
+    php = asin_small(sp);
+  } else {
+    dth = atan2(rho, vz) - 0.5 * kPi;
+    php = atan2(vy, vx);
+  }
   const double x = dth * inv_h + 0.5 * n - 0.5;
   const double y = php * inv_h + 0.5 * n - 0.5;
-  double i0 = floor(x), j0 = floor(y);
-  i0 = fmin(fmax(i0, 0.0), (double)(n - 2));
-  j0 = fmin(fmax(j0, 0.0), (double)(n - 2));
-  const double fx = x - i0, fy = y - j0;
-  const int ii = (int)i0, jj = (int)j0;
-  // blended stencils (rows: theta', columns: phi')
-  double A1[6], A2[6], B1[6], B2[6];
-  const int r0 = fd_blend(ii, n, fx, A1, A2);
-  const int c0 = fd_blend(jj, n, fy, B1, B2);
+  int ii = __double2int_rd(x), jj = __double2int_rd(y);
+  ii = min(max(ii, 0), n - 2);
+  jj = min(max(jj, 0), n - 2);
+  const double fx = x - (double)ii, fy = y - (double)jj;
   const size_t pitch = (size_t)n + 2;
-  const T* ub = u + (size_t)(r0 + 1) * pitch + (c0 + 1);
-  const int ci = jj - c0, ri = ii - r0;   // the bilinear cells inside the 6 x 6 block
-  double pt = 0, ptt = 0, ptp = 0, pp = 0, ppp = 0;
-  double rl[6] = {0, 0, 0, 0, 0, 0};      // rows ii, ii + 1 blended, per column
+  double pt, ptt, ptp, pp, ppp;
+  if (ii >= 2 && ii + 4 <= n && jj >= 2 && jj + 4 <= n) {
+    // central stencils: block rows / columns ii - 2 .. ii + 3, jj - 2 .. jj + 3
+    const T* ub = u + (size_t)(ii - 1) * pitch + (jj - 1);
+    double c[6], mix[6], r[6];
+    const double gy = 1.0 - fy, gx = 1.0 - fx;
 #pragma unroll
-  for (int a = 0; a < 6; ++a) {
-    const T* row = ub + (size_t)a * pitch;
-    double v[6];
+    for (int a = 0; a < 6; ++a) {
+      const T* row = ub + (size_t)a * pitch;
+      double v[6];
 #pragma unroll
-    for (int b = 0; b < 6; ++b) v[b] = (double)row[b];
-    // columns jj, jj + 1 blended in this row
-    double cl = 0.0, mix = 0.0;
+      for (int b = 0; b < 6; ++b) v[b] = (double)row[b];
+      c[a] = fma(fy, v[3], gy * v[2]);    // columns jj, jj + 1
+      mix[a] = blend_d1(v, fy);
+    }
+    const T* ra = ub + 2 * pitch;         // rows ii, ii + 1
+#pragma unroll
+    for (int b = 0; b < 6; ++b) r[b] = fma(fx, (double)ra[pitch + b], gx * (double)ra[b]);
+    pt = blend_d1(c, fx);
+    ptt = blend_d2(c, fx);
+    ptp = blend_d1(mix, fx);
+    pp = blend_d1(r, fy);
+    ppp = blend_d2(r, fy);
+  } else {
+    double A1[6], A2[6], B1[6], B2[6];
+    const int r0 = fd_blend(ii, n, fx, A1, A2);
+    const int c0 = fd_blend(jj, n, fy, B1, B2);
+    const T* ub = u + (size_t)(r0 + 1) * pitch + (c0 + 1);
+    const int ci = jj - c0, ri = ii - r0;   // the bilinear cells inside the 6 x 6 block
+    pt = ptt = ptp = pp = ppp = 0.0;
+    double rl[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      const T* row = ub + (size_t)a * pitch;
+      const double cl = (1.0 - fy) * (double)row[ci] + fy * (double)row[ci + 1];
+      double mix = 0.0;
+#pragma unroll
+      for (int b = 0; b < 6; ++b) mix += B1[b] * (double)row[b];
+      pt += A1[a] * cl;
+      ptt += A2[a] * cl;
+      ptp += A1[a] * mix;
+    }
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+      rl[b] = (1.0 - fx) * (double)ub[(size_t)ri * pitch + b] + fx * (double)ub[(size_t)(ri + 1) * pitch + b];
 #pragma unroll
     for (int b = 0; b < 6; ++b) {
-      if (b == ci) cl += (1.0 - fy) * v[b];
-      if (b == ci + 1) cl += fy * v[b];
-      mix += B1[b] * v[b];
+      pp += B1[b] * rl[b];
+      ppp += B2[b] * rl[b];
     }
-    pt += A1[a] * cl;
-    ptt += A2[a] * cl;
-    ptp += A1[a] * mix;
-    const double wr = (a == ri) ? 1.0 - fx : (a == ri + 1 ? fx : 0.0);
-#pragma unroll
-    for (int b = 0; b < 6; ++b) rl[b] += wr * v[b];
   }
-#pragma unroll
-  for (int b = 0; b < 6; ++b) {
-    pp += B1[b] * rl[b];
-    ppp += B2[b] * rl[b];
-  }
-  const double c1 = inv_h / 12.0, c2 = inv_h * inv_h / 12.0;
-  const double v0 = pt * c1, v1 = pp * c1, v2 = ptt * c2, v3 = ppp * c2, v4 = ptp * c1 * inv_h / 12.0;
+  const double c1 = inv_h * (1.0 / 12.0), c2 = c1 * inv_h;
+  const double v0 = pt * c1, v1 = pp * c1, v2 = ptt * c2, v3 = ppp * c2, v4 = ptp * (c1 * c1);
   // Appendix A in the patch basis at the point: sin(theta') = rho, cos(theta') = vz
-  // (the rotated vector is a unit vector), sin(phi') = vy / rho, cos(phi') = vx / rho
-  const double s = rho, co = vz;
+  const double co = vz;
   const double a_t = -v0, a_p = -v1 * is;
   const double u_tt = v2;
-  const double u_pp = v3 * is * is + co * is * v0;
-  const double u_tp = v4 * is - co * v1 * is * is;
-  // patch basis vectors at the point, mapped to global coordinates (R^T)
-  const double sp = vy * is, cp = vx * is;
-  const double tl[3] = {co * cp, co * sp, -s};
-  const double pl[3] = {-sp, cp, 0.0};
-  double tg[3], pg[3];
+  const double u_pp = (v3 * is + co * v0) * is;
+  const double u_tp = (v4 - co * v1 * is) * is;
+  // theta-hat' of the patch basis at the point, in global coordinates (R^T);
+  // both bases are right-handed at the same point, so the change of basis is
+  // the plane rotation [[q00, -q10], [q10, q00]]
+  const double tl[3] = {co * cp, co * sp, -rho};
+  double tg[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    tg[k] = R[k] * tl[0] + R[3 + k] * tl[1] + R[6 + k] * tl[2];
-    pg[k] = R[k] * pl[0] + R[3 + k] * pl[1] + R[6 + k] * pl[2];
-  }
+  for (int k = 0; k < 3; ++k) tg[k] = R[k] * tl[0] + R[3 + k] * tl[1] + R[6 + k] * tl[2];
   const double q00 = et[0] * tg[0] + et[1] * tg[1] + et[2] * tg[2];
-  const double q01 = et[0] * pg[0] + et[1] * pg[1] + et[2] * pg[2];
-  const double q10 = ep[0] * tg[0] + ep[1] * tg[1] + ep[2] * tg[2];
-  const double q11 = ep[0] * pg[0] + ep[1] * pg[1] + ep[2] * pg[2];
-  out[0] = q00 * a_t + q01 * a_p;
-  out[1] = q10 * a_t + q11 * a_p;
+  const double q10 = ep[0] * tg[0] + ep[1] * tg[1];
+  out[0] = q00 * a_t - q10 * a_p;
+  out[1] = q10 * a_t + q00 * a_p;
   // U_g = Q U Q^T
-  const double m00 = q00 * u_tt + q01 * u_tp, m01 = q00 * u_tp + q01 * u_pp;
-  const double m10 = q10 * u_tt + q11 * u_tp, m11 = q10 * u_tp + q11 * u_pp;
-  out[2] = m00 * q00 + m01 * q01;            // U_tt
-  out[3] = m10 * q10 + m11 * q11;            // U_pp
-  out[4] = m00 * q10 + m01 * q11;            // U_tp
+  const double m00 = q00 * u_tt - q10 * u_tp, m01 = q00 * u_tp - q10 * u_pp;
+  const double m10 = q10 * u_tt + q00 * u_tp, m11 = q10 * u_tp + q00 * u_pp;
+  out[2] = m00 * q00 - m01 * q10;            // U_tt
+  out[3] = m10 * q10 + m11 * q00;            // U_pp
+  out[4] = m00 * q10 + m01 * q00;            // U_tp
 }
 
 __device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], const double et[3],

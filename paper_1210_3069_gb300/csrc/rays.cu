@@ -112,18 +112,49 @@ struct StepCoef {
   double c, d, dchi2;
 };
 
-// sin and cos of an angle, by their Taylor series through x^9 and x^10 for
-// |x| < 2^-5 (first omitted terms below 1e-22 relative), else by sincos
-__device__ __forceinline__ void sincos_small(double x, double* s, double* c) {
-  if (fabs(x) < 0.03125) {
-    const double x2 = x * x;
-    *s = x * (1.0 - x2 * (1.0 / 6.0) * (1.0 - x2 * (1.0 / 20.0) * (1.0 - x2 * (1.0 / 42.0) * (1.0 - x2 * (1.0 / 72.0)))));
-    *c = 1.0 - x2 * 0.5 *
-                   (1.0 - x2 * (1.0 / 12.0) *
-                              (1.0 - x2 * (1.0 / 30.0) * (1.0 - x2 * (1.0 / 56.0) * (1.0 - x2 * (1.0 / 90.0)))));
+// Rotation of beta about the unit axis k = n x alpha / |alpha| by the angle
+// a = |alpha| (Eq. betaprop), written with the unnormalised axis kk = n x alpha
+// (|kk| = a, alpha being tangent at n):
+//   R beta = beta cos a + (kk x beta) sin(a) / a + kk (kk . beta)(1 - cos a) / a^2,
+// whose three coefficients are even functions of a: for a < 2^-5 their
+// Maclaurin series in a^2 (through a^8; first omitted terms below 1e-21),
+// so no square root or trigonometric call is needed; sincos beyond.
+__device__ __forceinline__ void rotate_by_deflection(const double be[3], const double kk[3], double a2, double bn[3]) {
+  double cs, sc, vc;
+  if (a2 < 0.0009765625) {
+    cs = 1.0 - a2 * (0.5 - a2 * ((1.0 / 24.0) - a2 * ((1.0 / 720.0) - a2 * (1.0 / 40320.0))));
+    sc = 1.0 - a2 * ((1.0 / 6.0) - a2 * ((1.0 / 120.0) - a2 * ((1.0 / 5040.0) - a2 * (1.0 / 362880.0))));
+    vc = 0.5 - a2 * ((1.0 / 24.0) - a2 * ((1.0 / 720.0) - a2 * ((1.0 / 40320.0) - a2 * (1.0 / 3628800.0))));
   } else {
-    sincos(x, s, c);
+    const double a = sqrt(a2);
+    double sn;
+    sincos(a, &sn, &cs);
+    sc = sn / a;
+    vc = (1.0 - cs) / a2;
   }
+  double kb[3];
+  cross3(kk, be, kb);
+  const double kd = dot3(kk, be) * vc;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) bn[i] = fma(be[i], cs, fma(kb[i], sc, kk[i] * kd));
+}
+
+// Transport matrix Q from the basis (t0, .) at n0 to the basis (t1, p1) at n1
+// (Appendix B).  The rotation taking n0 to n1 about n0 x n1 maps a vector v
+// orthogonal to n0 to v - ((n1 . v) / (1 + n0 . n1)) (n0 + n1); with
+// t1 . n1 = p1 . n1 = 0 the change of basis is the plane rotation
+// [[q0, -q1], [q1, q0]], q0 = t1 . t0 - (n1 . t0)(t1 . n0) / (1 + c),
+// q1 = p1 . t0 - (n1 . t0)(p1 . n0) / (1 + c).  (The same Q as transport_q,
+// without the normalised axis.)
+__device__ __forceinline__ void transport_q_closed(const double n0[3], const double t0[3], const double n1[3],
+                                                   const double t1[3], const double p1[3], double Q[4]) {
+  const double w = dot3(n1, t0) / (1.0 + dot3(n0, n1));
+  const double q0 = dot3(t1, t0) - w * dot3(t1, n0);
+  const double q1 = (p1[0] * t0[0] + p1[1] * t0[1]) - w * (p1[0] * n0[0] + p1[1] * n0[1]);
+  Q[0] = q0;
+  Q[1] = -q1;
+  Q[2] = q1;
+  Q[3] = q0;
 }
 
 template <bool kMG>
@@ -150,18 +181,10 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     An[2] = (1.0 - sc.c) * Ap[2] + sc.c * A[2] - sc.d * (U[2] * A[0] + U[3] * A[2]);
     An[3] = (1.0 - sc.c) * Ap[3] + sc.c * A[3] - sc.d * (U[2] * A[1] + U[3] * A[3]);
     // Eq. betaprop: rotate beta about n x alpha by |alpha|
-    const double av[3] = {L[0] * t[0] + L[1] * q[0], L[0] * t[1] + L[1] * q[1], L[0] * t[2] + L[1] * q[2]};
-    const double a2 = dot3(av, av);
-    double bn[3] = {be[0], be[1], be[2]};
-    if (a2 > 0.0) {
-      double kx[3];
-      cross3(nv, av, kx);
-      const double iam = rsqrt(a2), am = a2 * iam;
-      const double kk[3] = {kx[0] * iam, kx[1] * iam, kx[2] * iam};
-      double sn, cs;
-      sincos_small(am, &sn, &cs);
-      rodrigues(be, kk, cs, sn, bn);
-    }
+    const double av[3] = {L[0] * t[0] + L[1] * q[0], L[0] * t[1] + L[1] * q[1], L[0] * t[2]};
+    double kk[3], bn[3];
+    cross3(nv, av, kk);
+    rotate_by_deflection(be, kk, dot3(av, av), bn);
     // Eq. posprop: lambda > 0 root, rationalised
     const double xb = dot3(x, bn);
     const double lam = sc.dchi2 / (xb + sqrt(xb * xb + sc.dchi2));
@@ -171,8 +194,9 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     const double ix1 = rsqrt(dot3(x1, x1));
     const double n1[3] = {x1[0] * ix1, x1[1] * ix1, x1[2] * ix1};
     // Appendix B: transport A^(n+1) and A^(n) to the basis at the new point
-    double Q[4], Ao[4], Apo[4];
-    transport_q(nv, t, n1, Q);
+    double t1[3], p1[3], Q[4], Ao[4], Apo[4];
+    tangent_basis(n1, t1, p1);
+    transport_q_closed(nv, t, n1, t1, p1, Q);
     qaqt(Q, An, Ao);
     qaqt(Q, A, Apo);
 #pragma unroll
