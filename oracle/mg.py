@@ -363,7 +363,7 @@ def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, 
 
     def ratio():
         r = fd - S.ops[0].apply(e)
-        return float((torch.sqrt((r * r).sum((1, 2))) / fn).max())
+        return float((torch.sqrt((r * r).sum((1, 2))) / fn).max().detach())
     k = 0
     rr = ratio()
     if fixed_cycles is not None:

@@ -196,3 +196,38 @@ def galaxy_shear(kappas, nside, lmax, chi, gz, gphi, gchi):
         g2 = g2 + torch.where(sel, a2, torch.zeros_like(a2))
     del hp
     return torch.stack([g1, g2])
+
+
+def galaxy_shear_mg(kappas, nside_fine, nside_sht, lmax, nside_bundle, ncell, chi, gz, gphi, gchi, cycles=20,
+                    nu1=2, nu2=2):
+    """galaxy_shear with the SHT+MG solver of Sec. 3.2 on every plane: the
+    plane's potential from solve_plane (`cycles` V-cycles, enough to converge
+    to rounding), each galaxy's ray looked up in the patch of the bundle that
+    contains its starting direction (rays keep their bundle, Sec. 3.1) with
+    the fourth-order finite differences and rotation of Appendix A.
+    Differentiable with respect to kappas (torch autograd through the SHT,
+    the interpolations, the V-cycles and the lookup)."""
+    from . import healpix as hp
+    from . import mg
+    chi = [float(c) for c in chi]
+    N = len(kappas)
+    s = torch.sqrt((1 - gz) * (1 + gz))
+    n0 = torch.stack([s * torch.cos(gphi), s * torch.sin(gphi), gz], -1)
+    home = hp.ang2pix_nest(nside_bundle, gz, gphi)
+    bins = galaxy_bins(chi, gchi)
+    st = init_rays(n0, chi[0])
+    g1 = torch.zeros(gz.shape, dtype=F64)
+    g2 = torch.zeros(gz.shape, dtype=F64)
+    for m in range(N):
+        sol = mg.solve_plane(kappas[m], nside_fine, nside_sht, lmax, nside_bundle, ncell=ncell, nu1=nu1, nu2=nu2,
+                             fixed_cycles=cycles)
+        chi_prev = chi[m - 1] if m > 0 else 0.0
+        st = step(st, lambda n, sol=sol: mg.fields_at(sol, nside_bundle, n, home), chi_prev, chi[m], chi[m + 1])
+        sel = bins == m
+        Ag = galaxy_interp(st["Ap"], st["A"], torch.full_like(gchi, chi[m]), torch.full_like(gchi, chi[m + 1]),
+                           torch.where(sel, gchi, torch.full_like(gchi, chi[m + 1])))
+        _, a1, a2, _ = decompose(Ag)
+        g1 = g1 + torch.where(sel, a1, torch.zeros_like(a1))
+        g2 = g2 + torch.where(sel, a2, torch.zeros_like(a2))
+    return torch.stack([g1, g2])
+
