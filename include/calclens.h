@@ -360,6 +360,23 @@ int clc_gal_trace(clc_ctx* ctx, int nplanes, const double* const* kappa_host, in
  * differentiated from its checkpoint and the adjoint of the SHT Poisson solve
  * applied.  kappa_bar is a host array of nplanes device maps (written). */
 int clc_gal_trace_adjoint(clc_gal_tape* tape, const double* gamma_bar, double* const* kappa_bar_host);
+/* clc_gal_trace with the SHT+MG solver of Sec. 3.2 on every plane (params:
+ * as for clc_poisson_shtmg, precision CLC_FP64 only; kappa maps of nside =
+ * the fine Nside): each galaxy's ray is looked up in the patch of the bundle
+ * that contains its starting direction (rays keep their bundle, Sec. 3.1).
+ * The tape's adjoint (clc_gal_trace_adjoint) recomputes each plane's patch
+ * solution and differentiates the converged solve: the adjoint patch
+ * problem L^T lambda = ubar is solved with the same V-cycles (W L is
+ * symmetric for W = diag(sin theta'), so lambda = W L^-1 W^-1 ubar), to a
+ * relative residual of min(tol / 100, 1e-12); lambda then goes back through
+ * the transposed interpolations of the source and of the boundary values,
+ * the (symmetric) SHT Poisson solve and the transposed degrade.  The
+ * gradient is that of the converged solve, so the forward should converge
+ * (tol or enough fixed_cycles).  Returns CLC_ENOTCONVERGED (tape and outputs
+ * written) if a plane stopped at max_cycles above tol. */
+int clc_gal_trace_mg(clc_ctx* ctx, int nplanes, const double* const* kappa_host, int nside,
+                     const clc_mg_params* params, const double* chi_host, int64_t ngal, const double* gz,
+                     const double* gphi, const double* gchi, double* gamma, clc_gal_tape** tape);
 int clc_gal_tape_destroy(clc_gal_tape* tape);
 
 /* ------------------------------------------------------------------------ */

@@ -347,12 +347,31 @@ def home_bundle(nside_fine, nside_bundle, nest_pix):
     return torch.as_tensor(nest_pix) >> shift
 
 
-def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, fixed_cycles=None, coarsest=8):
+def tau_estimate(S, u, ghost_c):
+    """The fine-grid truncation-error estimate of the full approximation
+    scheme (Sec. 3.2, stopping rule): tau = L_c R u - R L_f u, u[B, N+2, N+2]
+    with 2 g on its ghost ring, ghost_c[B, N/2+2, N/2+2] the coarse level's
+    ghost ring (2 g at the coarse edge faces).  Returns tau [B, N/2, N/2]."""
+    op, opc = S.ops[0], S.ops[1]
+    uc = ghost_c.clone()
+    uc[:, 1:-1, 1:-1] = op.restrict(u[:, 1:-1, 1:-1])
+    return opc.apply(uc) - op.restrict(op.apply(u))
+
+
+def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, fixed_cycles=None, coarsest=8,
+                     stop="residual", eps=0.1, ghost_c=None):
     """V-cycles on the correction e = u - base: L e = f - L base with zero
     Dirichlet values on every level, from e = 0.  base[B, N+2, N+2] holds the
-    starting guess inside and 2 g on its ghost ring.  The stopping ratio is
-    ||f - L u||_2 / ||f||_2 with the original source f.  Returns (u interior,
-    cycles, ratio)."""
+    starting guess inside and 2 g on its ghost ring.  Stopping rules (every
+    patch receives the same number of V-cycles):
+    * "residual": max over patches of ||f - L u||_2 / ||f||_2 < tol, with
+      the original source f;
+    * "tau" (the paper's rule, Sec. 3.2, after Press et al. Sec. 20.6):
+      max over patches of rms(f - L u) / rms(tau) < eps, rms the root mean
+      square over the patch's fine (residual) or coarse (tau) cells, tau the
+      estimate of tau_estimate on u = base + e (ghost_c: the coarse level's
+      ghost ring, 2 g).
+    Returns (u interior, cycles, ratio of the chosen rule)."""
     B = f.shape[0]
     zeros = [torch.zeros((B, n + 2, n + 2), dtype=F64) for n in level_sizes(ncell, coarsest)]
     S = PatchSolver(ncell, h, zeros, nu1=nu1, nu2=nu2, coarsest=coarsest)
@@ -363,7 +382,14 @@ def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, 
 
     def ratio():
         r = fd - S.ops[0].apply(e)
+        if stop == "tau":
+            u = base + e
+            t = tau_estimate(S, u, ghost_c)
+            rr = torch.sqrt((r * r).mean((1, 2)))
+            tt = torch.sqrt((t * t).mean((1, 2)))
+            return float((rr / torch.where(tt > 0, tt, 1e-300)).max().detach())
         return float((torch.sqrt((r * r).sum((1, 2))) / fn).max().detach())
+    limit = eps if stop == "tau" else tol
     k = 0
     rr = ratio()
     if fixed_cycles is not None:
@@ -371,7 +397,7 @@ def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, 
             S.vcycle(0, e, fd)
         k, rr = fixed_cycles, ratio()
     else:
-        while rr >= tol and k < max_cycles:
+        while rr >= limit and k < max_cycles:
             S.vcycle(0, e, fd)
             k += 1
             rr = ratio()
@@ -379,7 +405,8 @@ def solve_correction(base, f, h, ncell, nu1=2, nu2=2, tol=1e-10, max_cycles=60, 
 
 
 def solve_plane(kappa_fine, nside_fine, nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2,
-                tol=1e-10, max_cycles=60, fixed_cycles=None, bundles=None, coarsest=8, psi_sht=None):
+                tol=1e-10, max_cycles=60, fixed_cycles=None, bundles=None, coarsest=8, psi_sht=None,
+                stop="residual", eps=0.1):
     """The whole SHT+MG plane solve of Sec. 3.2 for the given bundles (all by
     default): degrade kappa to the SHT grid, SHT Poisson solve, patch set-up,
     V-cycles on the correction to the SHT solution.  A caller that already
@@ -396,7 +423,8 @@ def solve_plane(kappa_fine, nside_fine, nside_sht, lmax, nside_bundle, ncell=256
     R, h, u, f, ghosts = setup_patches(kappa_fine, nside_fine, psi_sht, nside_sht, nside_bundle, bundles,
                                        ncell=ncell, coarsest=coarsest)
     ui, cycles, rr = solve_correction(u, f, h, ncell, nu1=nu1, nu2=nu2, tol=tol, max_cycles=max_cycles,
-                                      fixed_cycles=fixed_cycles, coarsest=coarsest)
+                                      fixed_cycles=fixed_cycles, coarsest=coarsest, stop=stop, eps=eps,
+                                      ghost_c=ghosts[1])
     return {"R": R, "h": h, "u": ui, "partials": fd_partials(ui, h), "bundles": bundles, "cycles": cycles,
             "residual": rr, "psi_sht": psi_sht}
 

@@ -83,6 +83,8 @@ _SIGS = {
     "clc_gal_trace": (_i, [_p, _i, ctypes.POINTER(_p), _i, _i, _i, ctypes.POINTER(_d), _i64, _p, _p, _p, _p,
                            ctypes.POINTER(_p)]),
     "clc_gal_trace_adjoint": (_i, [_p, _p, ctypes.POINTER(_p)]),
+    "clc_gal_trace_mg": (_i, [_p, _i, ctypes.POINTER(_p), _i, ctypes.POINTER(MGParams), ctypes.POINTER(_d), _i64, _p,
+                              _p, _p, _p, ctypes.POINTER(_p)]),
     "clc_gal_tape_destroy": (_i, [_p]),
     "clc_gemm_f16x3": (_i, [_p, _p, _p, _p, _p, _i, _i, _i, _i, _p]),
     "clc_eb_analysis": (_i, [_p, _p, _p, _i, _i, _p, _p]),
@@ -283,6 +285,20 @@ class Context:
                                         _ptr(gchi), _ptr(gamma), ctypes.byref(h) if tape else None))
         return gamma, (GalTape(self, h, kappas) if tape else None)
 
+    def gal_trace_mg(self, kappas, nside, params, chi, gz, gphi, gchi, tape=True):
+        """Galaxy shears gamma[2, ngal] through SHT+MG planes kappas[N, Npix]
+        (clc_gal_trace_mg, FP64 MG parameters); returns (gamma, GalTape or None)."""
+        N = kappas.shape[0]
+        n = gz.numel()
+        gamma = torch.empty(2, n, dtype=torch.float64, device=self.device)
+        kp = (_p * N)(*[kappas[i].data_ptr() for i in range(N)])
+        _ptr(kappas)
+        ch = (_d * (N + 1))(*[float(c) for c in chi])
+        h = _p()
+        self._check(lib().clc_gal_trace_mg(self.h, N, kp, nside, ctypes.byref(params), ch, n, _ptr(gz), _ptr(gphi),
+                                           _ptr(gchi), _ptr(gamma), ctypes.byref(h) if tape else None))
+        return gamma, (GalTape(self, h, kappas) if tape else None)
+
     def sht_plan(self, nsides, lmaxs, derivatives=True, graph=True, tune=False):
         return ShtPlan(self, nsides, lmaxs, derivatives, graph, tune)
 
@@ -449,13 +465,19 @@ class GalTape:
 
 
 class GalaxyShear(torch.autograd.Function):
-    """gamma[2, ngal] = galaxy shears through the pure-SHT planes kappas[N, Npix];
-    the backward pass is the library's adjoint (checkpointed ray states,
-    recomputed lens maps, transposed SHT)."""
+    """gamma[2, ngal] = galaxy shears through the planes kappas[N, Npix], each
+    solved by the pure SHT (lmax_or_params an int band limit) or by SHT+MG
+    (lmax_or_params an FP64 mg_params); the backward pass is the library's
+    adjoint (checkpointed ray states, recomputed planes, the transposed SHT
+    and, for SHT+MG, the adjoint patch solve)."""
 
     @staticmethod
-    def forward(fctx, kappas, lib_ctx, nside, lmax, chi, gz, gphi, gchi, precision):
-        gamma, tape = lib_ctx.gal_trace(kappas.detach().contiguous(), nside, lmax, chi, gz, gphi, gchi, precision)
+    def forward(fctx, kappas, lib_ctx, nside, lmax_or_params, chi, gz, gphi, gchi, precision):
+        k = kappas.detach().contiguous()
+        if isinstance(lmax_or_params, MGParams):
+            gamma, tape = lib_ctx.gal_trace_mg(k, nside, lmax_or_params, chi, gz, gphi, gchi)
+        else:
+            gamma, tape = lib_ctx.gal_trace(k, nside, lmax_or_params, chi, gz, gphi, gchi, precision)
         fctx.tape = tape
         return gamma
 
@@ -467,7 +489,8 @@ class GalaxyShear(torch.autograd.Function):
 
 
 def galaxy_shear(lib_ctx, kappas, nside, lmax, chi, gz, gphi, gchi, precision=FP64):
-    """Differentiable galaxy shears (see GalaxyShear)."""
+    """Differentiable galaxy shears (see GalaxyShear); lmax may be an
+    mg_params (FP64) for the SHT+MG solver."""
     return GalaxyShear.apply(kappas, lib_ctx, nside, lmax, chi, gz, gphi, gchi, precision)
 
 

@@ -21,9 +21,13 @@
 // transposed Poisson and analysis) turns them into the gradient map.
 #include "fft.cuh"
 #include "legendre.cuh"
+#include "patch_fd.cuh"
 
 int clc_poisson_sht(clc_ctx*, const double*, int, int, int, double*, const clc_derivs*);
 int clc_sht_synthesis(clc_ctx*, const double*, int, int, double*);
+int clc_poisson_shtmg(clc_ctx*, const double*, int, const clc_mg_params*, clc_plane_solution*, const clc_derivs*);
+int clc_solution_create(clc_ctx*, int, const clc_mg_params*, clc_plane_solution**);
+int clc_solution_destroy(clc_plane_solution*);
 
 namespace clc {
 
@@ -432,6 +436,198 @@ __device__ void lens_scatter(const clc_derivs& Mbar, int nside, const double nv[
 }
 
 // ---------------------------------------------------------------------------
+// SHT+MG lens lookup templated in the scalar (the galaxy rays' lookup in
+// their home bundle's patch, Sec. 3.2): fourth-order finite differences on
+// the finest patch level (one-sided stencils at the edge), the bilinear blend
+// of the four cells around the point as one tensor-product stencil on a 6 x 6
+// block, Appendix A in the patch basis and the rotation to the global basis
+// at the point.  The position enters through the patch angles and the blend
+// fractions, so dual numbers carry the lookup's dependence on the ray.
+
+template <typename S>
+__device__ __forceinline__ S asin_s(const S& x) {
+  const S x2 = x * x;
+  return x * (1.0 + x2 * ((1.0 / 6.0) + x2 * ((3.0 / 40.0) + x2 * ((5.0 / 112.0) + x2 * ((35.0 / 1152.0) +
+              x2 * ((63.0 / 2816.0) + x2 * (231.0 / 13312.0)))))));
+}
+
+// six-point weights of the blend (1 - f) D_k + f D_{k+1} (x 12), first point returned
+template <typename S>
+__device__ __forceinline__ int fd_blend_s(int k, int n, const S& f, S w1[6], S w2[6]) {
+  double a1[5], a2[5], b1[5], b2[5];
+  const int ba = fd_stencil(k, n, 1, a1), bb = fd_stencil(k + 1, n, 1, b1);
+  fd_stencil(k, n, 2, a2);
+  fd_stencil(k + 1, n, 2, b2);
+  const int first = min(ba, bb);
+  const bool sa = ba > first, sb = bb > first;
+  const S g = 1.0 - f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const double A1 = sa ? (t >= 1 ? a1[t - 1] : 0.0) : (t < 5 ? a1[t] : 0.0);
+    const double B1 = sb ? (t >= 1 ? b1[t - 1] : 0.0) : (t < 5 ? b1[t] : 0.0);
+    const double A2 = sa ? (t >= 1 ? a2[t - 1] : 0.0) : (t < 5 ? a2[t] : 0.0);
+    const double B2 = sb ? (t >= 1 ? b2[t - 1] : 0.0) : (t < 5 ? b2[t] : 0.0);
+    w1[t] = g * A1 + f * B1;
+    w2[t] = g * A2 + f * B2;
+  }
+  return first;
+}
+
+// position-dependent part of the lookup: patch angles, blend weights
+template <typename S>
+struct PatchGeo {
+  S v[3];            // patch-frame unit vector
+  S rho, is, sp, cp; // sin theta', 1 / sin theta', sin phi', cos phi'
+  S A1[6], A2[6], B1[6], B2[6], Rx[6], Cy[6];
+  int r0, c0;        // first row / column of the 6 x 6 block (interior cell indices)
+};
+
+template <typename S>
+__device__ void patch_geo(const MGView& V, int b, const S nv[3], PatchGeo<S>& G) {
+  const int n = V.n;
+  const double* R = V.rot + 9 * (size_t)b;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) G.v[r] = R[3 * r] * nv[0] + R[3 * r + 1] * nv[1] + R[3 * r + 2] * nv[2];
+  G.rho = sqrt(G.v[0] * G.v[0] + G.v[1] * G.v[1]);
+  G.is = 1.0 / G.rho;
+  G.sp = G.v[1] * G.is;
+  G.cp = G.v[0] * G.is;
+  S dth, php;
+  if (fabs(val(G.v[2])) < 0.04 && fabs(val(G.sp)) < 0.04 && val(G.v[0]) > 0.0) {
+    dth = -asin_s(G.v[2]);
+    php = asin_s(G.sp);
+  } else {
+    dth = atan2(G.rho, G.v[2]) - 0.5 * kPi;
+    php = atan2(G.v[1], G.v[0]);
+  }
+  const S x = dth * V.inv_h + (0.5 * n - 0.5);
+  const S y = php * V.inv_h + (0.5 * n - 0.5);
+  int ii = (int)floor(val(x)), jj = (int)floor(val(y));
+  ii = min(max(ii, 0), n - 2);
+  jj = min(max(jj, 0), n - 2);
+  const S fx = x - (double)ii, fy = y - (double)jj;
+  G.r0 = fd_blend_s(ii, n, fx, G.A1, G.A2);
+  G.c0 = fd_blend_s(jj, n, fy, G.B1, G.B2);
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    G.Rx[t] = Lift<S>::of(0.0);
+    G.Cy[t] = Lift<S>::of(0.0);
+  }
+  // bilinear weights of cells ii, ii + 1 (rows) and jj, jj + 1 (columns) in the block
+  for (int t = 0; t < 6; ++t) {
+    if (t == ii - G.r0) G.Rx[t] = 1.0 - fx;
+    if (t == ii - G.r0 + 1) G.Rx[t] = fx;
+    if (t == jj - G.c0) G.Cy[t] = 1.0 - fy;
+    if (t == jj - G.c0 + 1) G.Cy[t] = fy;
+  }
+}
+
+// lens fields at the point from the five patch partials (x 12 stencil sums)
+// P = (pt, pp, ptt, ppp, ptp): Appendix A in the patch basis, then alpha and
+// U rotated to the basis (et, ep) at nv
+template <typename S, typename P>
+__device__ void fields_from_partials(const MGView& V, int b, const PatchGeo<S>& G, const P pr[5], const S et[3],
+                                     const S ep[3], P out[5]) {
+  const double* R = V.rot + 9 * (size_t)b;
+  const double c1 = V.inv_h / 12.0, c2 = c1 * V.inv_h;
+  const P v0 = pr[0] * c1, v1 = pr[1] * c1, v2 = pr[2] * c2, v3 = pr[3] * c2, v4 = pr[4] * (c1 * c1);
+  const S co = G.v[2];
+  const P a_t = -v0, a_p = -(v1 * G.is);
+  const P u_tt = v2;
+  const P u_pp = (v3 * G.is + co * v0) * G.is;
+  const P u_tp = (v4 - co * v1 * G.is) * G.is;
+  const S tl[3] = {co * G.cp, co * G.sp, -G.rho};
+  S tg[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) tg[k] = R[k] * tl[0] + R[3 + k] * tl[1] + R[6 + k] * tl[2];
+  const S q00 = et[0] * tg[0] + et[1] * tg[1] + et[2] * tg[2];
+  const S q10 = ep[0] * tg[0] + ep[1] * tg[1] + ep[2] * tg[2];
+  out[0] = q00 * a_t - q10 * a_p;
+  out[1] = q10 * a_t + q00 * a_p;
+  const P m00 = q00 * u_tt - q10 * u_tp, m01 = q00 * u_tp - q10 * u_pp;
+  const P m10 = q10 * u_tt + q00 * u_tp, m11 = q10 * u_tp + q00 * u_pp;
+  out[2] = m00 * q00 - m01 * q10;
+  out[3] = m10 * q10 + m11 * q00;
+  out[4] = m00 * q10 + m01 * q00;
+}
+
+// Lens values at nv in patch b (double or dual scalar)
+template <typename S>
+__device__ void patch_eval(const MGView& V, int b, const S nv[3], S out[5]) {
+  PatchGeo<S> G;
+  patch_geo(V, b, nv, G);
+  const int n = V.n;
+  const double* ub = V.u + (size_t)(n + 2) * (n + 2) * b + (size_t)(G.r0 + 1) * (n + 2) + (G.c0 + 1);
+  S c[6], mix[6], rr[6];
+#pragma unroll
+  for (int t = 0; t < 6; ++t) rr[t] = Lift<S>::of(0.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const double* row = ub + (size_t)a * (n + 2);
+    S ca = Lift<S>::of(0.0), ma = Lift<S>::of(0.0);
+#pragma unroll
+    for (int bb = 0; bb < 6; ++bb) {
+      ca = ca + G.Cy[bb] * row[bb];
+      ma = ma + G.B1[bb] * row[bb];
+      rr[bb] = rr[bb] + G.Rx[a] * row[bb];
+    }
+    c[a] = ca;
+    mix[a] = ma;
+  }
+  S pr[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) pr[q] = Lift<S>::of(0.0);
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    pr[0] = pr[0] + G.A1[a] * c[a];      // pt
+    pr[2] = pr[2] + G.A2[a] * c[a];      // ptt
+    pr[4] = pr[4] + G.A1[a] * mix[a];    // ptp
+    pr[1] = pr[1] + G.B1[a] * rr[a];     // pp
+    pr[3] = pr[3] + G.B2[a] * rr[a];     // ppp
+  }
+  S et[3], ep[3];
+  basis_s(nv, et, ep);
+  fields_from_partials<S, S>(V, b, G, pr, et, ep, out);
+}
+
+// Adjoint of the lookup's linear dependence on the patch potential: the five
+// lens adjoints Lb at nv become adjoints of the five partials (dual numbers
+// seeded on the partials give the Jacobian of fields_from_partials), which
+// the tensor-product stencils spread over the 6 x 6 block of ubar.
+__device__ void patch_scatter(const MGView& V, int b, const double nv[3], const double Lb[5], double* ubar) {
+  typedef Dual<5> D5;
+  PatchGeo<double> G;
+  patch_geo(V, b, nv, G);
+  double et[3], ep[3];
+  basis_s(nv, et, ep);
+  D5 pr[5], out[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    pr[q] = dual_const<5>(0.0);
+    pr[q].d[q] = 1.0;
+  }
+  fields_from_partials<double, D5>(V, b, G, pr, et, ep, out);
+  double pb[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) acc += Lb[c] * out[c].d[q];
+    pb[q] = acc;
+  }
+  const int n = V.n;
+  double* ub = ubar + (size_t)n * n * b + (size_t)G.r0 * n + G.c0;
+#pragma unroll
+  for (int a = 0; a < 6; ++a)
+#pragma unroll
+    for (int bb = 0; bb < 6; ++bb) {
+      const double g = pb[0] * G.A1[a] * G.Cy[bb] + pb[2] * G.A2[a] * G.Cy[bb] + pb[4] * G.A1[a] * G.B1[bb] +
+                       pb[1] * G.Rx[a] * G.B1[bb] + pb[3] * G.Rx[a] * G.B2[bb];
+      if (g != 0.0) atomicAdd(ub + (size_t)a * n + bb, g);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // kernels
 
 struct RaySoA {
@@ -441,9 +637,10 @@ struct RaySoA {
 
 __global__ void k_gal_init(const double* __restrict__ z, const double* __restrict__ phi,
                            const double* __restrict__ gchi, const double* __restrict__ chi, int N, double* st, int64_t n,
-                           int* __restrict__ bin, double* __restrict__ tw) {
+                           int* __restrict__ bin, double* __restrict__ tw, int nb, int32_t* __restrict__ bundle) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const double zz = z[k], pp = phi[k];
+    if (nb > 0) bundle[k] = (int32_t)ang2pix_nest(nb, zz, pp);   // the ray keeps its start bundle (Sec. 3.1)
     const double s = sqrt((1.0 - zz) * (1.0 + zz));
     const double v[3] = {s * cos(pp), s * sin(pp), zz};
     for (int c = 0; c < 3; ++c) {
@@ -466,7 +663,22 @@ __global__ void k_gal_init(const double* __restrict__ z, const double* __restric
   }
 }
 
-__global__ void k_gal_step(double* st, int64_t n, clc_derivs M, int nside, StepC sc, const int* __restrict__ bin,
+// lens source of a plane: RING maps of nside (pure SHT) or the SHT+MG patches
+struct LensSrc {
+  clc_derivs M;
+  int nside;
+  MGView V;
+  const int32_t* bundle;
+};
+
+template <bool kMG, typename S>
+__device__ __forceinline__ void lens_at(const LensSrc& src, int64_t k, const S nv[3], S L[5]) {
+  if (kMG) patch_eval<S>(src.V, src.bundle[k], nv, L);
+  else lens_eval<S>(src.M, src.nside, nv, L);
+}
+
+template <bool kMG>
+__global__ void k_gal_step(double* st, int64_t n, LensSrc src, StepC sc, const int* __restrict__ bin,
                            const double* __restrict__ tw, int plane, double* __restrict__ gamma) {
   for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     double in[14], o[14];
@@ -475,7 +687,7 @@ __global__ void k_gal_step(double* st, int64_t n, clc_derivs M, int nside, StepC
     const double xn = ::sqrt(in[0] * in[0] + in[1] * in[1] + in[2] * in[2]);
     const double nv[3] = {in[0] / xn, in[1] / xn, in[2] / xn};
     double L[5];
-    lens_eval<double>(M, nside, nv, L);
+    lens_at<kMG, double>(src, k, nv, L);
     step_eval<double>(in, in + 3, in + 6, in + 10, L, sc, o);
 #pragma unroll
     for (int c = 0; c < 14; ++c) st[c * n + k] = o[c];
@@ -494,8 +706,9 @@ __global__ void k_gal_step(double* st, int64_t n, clc_derivs M, int nside, StepC
 // the plane on entry and of the state entering it on return.
 constexpr int kDualK = 5;
 
+template <bool kMG>
 __global__ void __launch_bounds__(128) k_gal_step_adjoint(const double* __restrict__ ck, double* adj, int64_t n,
-                                                          clc_derivs M, clc_derivs Mbar, int nside, StepC sc,
+                                                          LensSrc src, clc_derivs Mbar, double* ubar, StepC sc,
                                                           const int* __restrict__ bin, const double* __restrict__ tw,
                                                           int plane, const double* __restrict__ gbar) {
   typedef Dual<kDualK> D;
@@ -529,7 +742,7 @@ __global__ void __launch_bounds__(128) k_gal_step_adjoint(const double* __restri
       const D xn = sqrt(in[0] * in[0] + in[1] * in[1] + in[2] * in[2]);
       const D nv[3] = {in[0] / xn, in[1] / xn, in[2] / xn};
       D L[5];
-      lens_eval<D>(M, nside, nv, L);
+      lens_at<kMG, D>(src, k, nv, L);
 #pragma unroll
       for (int c = 0; c < 5; ++c)
 #pragma unroll
@@ -552,7 +765,22 @@ __global__ void __launch_bounds__(128) k_gal_step_adjoint(const double* __restri
     for (int c = 0; c < 14; ++c) adj[c * n + k] = ib[c];
     const double xn = ::sqrt(in0[0] * in0[0] + in0[1] * in0[1] + in0[2] * in0[2]);
     const double nv[3] = {in0[0] / xn, in0[1] / xn, in0[2] / xn};
-    lens_scatter(Mbar, nside, nv, Lb);
+    if (kMG) patch_scatter(src.V, src.bundle[k], nv, Lb, ubar);
+    else lens_scatter(Mbar, src.nside, nv, Lb);
+  }
+}
+
+// adjoint of the degrade to the SHT grid (mean of k children): every fine
+// RING pixel receives its coarse parent's adjoint / k
+__global__ void k_degrade_adjoint(const double* __restrict__ coarse_bar, int ns, int nf, double* __restrict__ fine_bar) {
+  const int64_t np = 12ll * nf * nf;
+  const int shift = 2 * (ilog2(nf) - ilog2(ns));
+  const double inv = 1.0 / (double)(1ll << shift);
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j;
+    const int i = pix2ring(nf, p, &j);
+    const int64_t parent = nest2ring(ns, ring_pos2nest(nf, i, j) >> shift);
+    fine_bar[p] += coarse_bar[parent] * inv;
   }
 }
 
@@ -639,10 +867,16 @@ using namespace clc;
 struct clc_gal_tape {
   clc_ctx* ctx = nullptr;
   int N = 0, nside = 0, lmax = 0, precision = CLC_FP64;
+  int solver = CLC_SOLVER_SHT;
+  clc_mg_params mg{};                 // CLC_SOLVER_SHTMG: the plane solver's parameters
+  clc_plane_solution* sol = nullptr;  // CLC_SOLVER_SHTMG: one plane's multigrid state, reused
   int64_t n = 0;
   std::vector<double> chi;
   std::vector<const double*> kappa;
-  Buffer d_chi, state, ckpt, adj, bin, tw, maps, fbar, work;
+  Buffer d_chi, state, ckpt, adj, bin, tw, maps, fbar, work, bundle, ubar, psibar, kbar_s;
+  ~clc_gal_tape() {
+    if (sol) clc_solution_destroy(sol);
+  }
 };
 
 static int sht_poisson_adjoint(clc_gal_tape* T, const clc_derivs& Fb, double* kbar) {
@@ -690,74 +924,175 @@ static int sht_poisson_adjoint(clc_gal_tape* T, const clc_derivs& Fb, double* kb
   return clc_sht_synthesis(ctx, (const double*)kt, ns, L, kbar);
 }
 
-extern "C" int clc_gal_trace(clc_ctx* ctx, int nplanes, const double* const* kappa, int nside, int lmax,
-                             int precision, const double* chi, int64_t ngal, const double* gz, const double* gphi,
-                             const double* gchi, double* gamma, clc_gal_tape** tape_out) {
-  if (!ctx) return CLC_EINVAL;
-  if (nplanes < 1 || !kappa || !chi || !valid_nside(nside) || nside > 4096 || lmax < 1 || lmax > 4 * nside ||
-      ngal < 0 || (ngal > 0 && (!gz || !gphi || !gchi || !gamma)) ||
-      (precision != CLC_FP64 && precision != CLC_MIXED))
-    return set_err(ctx, CLC_EINVAL, "clc_gal_trace: bad arguments");
-  for (int m = 0; m < nplanes; ++m)
-    if (!kappa[m] || !(chi[m] > 0) || !(chi[m + 1] > chi[m]))
-      return set_err(ctx, CLC_EINVAL, "clc_gal_trace: null plane or non-increasing chi");
-  cudaSetDevice(ctx->device);
-  auto T = std::make_unique<clc_gal_tape>();
-  T->ctx = ctx;
-  T->N = nplanes;
-  T->nside = nside;
-  T->lmax = lmax;
-  T->precision = precision;
-  T->n = ngal;
-  T->chi.assign(chi, chi + nplanes + 1);
-  T->kappa.assign(kappa, kappa + nplanes);
-  const size_t np = 12ull * nside * nside;
+static bool tape_alloc(Buffer& b, size_t bytes) {
+  b.bytes = bytes;
+  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    b.bytes = 0;
+    return false;
+  }
+  return true;
+}
+
+static StepC step_coef(const std::vector<double>& chi, int m) {
+  StepC sc;
+  const double cp = m > 0 ? chi[m - 1] : 0.0, cn = chi[m], cx = chi[m + 1];
+  sc.c = (cn / cx) * ((cx - cp) / (cn - cp));
+  sc.d = (cx - cn) / cx;
+  sc.dchi2 = cx * cx - cn * cn;
+  return sc;
+}
+
+// the lens source of plane m: its maps (pure SHT) or its patch solution
+static int plane_lens(clc_gal_tape* T, int m, LensSrc* src) {
+  clc_ctx* ctx = T->ctx;
+  if (T->solver == CLC_SOLVER_SHT) {
+    const size_t np = 12ull * T->nside * T->nside;
+    double* mp = (double*)T->maps.p;
+    src->M = clc_derivs{mp, mp + np, mp + 2 * np, mp + 3 * np, mp + 4 * np};
+    src->nside = T->nside;
+    src->bundle = nullptr;
+    return clc_poisson_sht(ctx, T->kappa[m], T->nside, T->lmax, T->precision, nullptr, &src->M);
+  }
+  int rc = clc_poisson_shtmg(ctx, T->kappa[m], T->nside, &T->mg, T->sol, nullptr);
+  if (rc != CLC_OK && rc != CLC_ENOTCONVERGED) return rc;
+  src->M = clc_derivs{};
+  src->nside = 0;
+  src->V = mg_view(T->sol);
+  src->bundle = (const int32_t*)T->bundle.p;
+  return CLC_OK;
+}
+
+static int gal_trace(std::unique_ptr<clc_gal_tape> T, const double* gz, const double* gphi, const double* gchi,
+                     double* gamma, clc_gal_tape** tape_out) {
+  clc_ctx* ctx = T->ctx;
+  const int N = T->N;
+  const int64_t ngal = T->n;
   const size_t nn = (size_t)std::max<int64_t>(ngal, 1);
-  auto alloc = [&](Buffer& b, size_t bytes) -> bool {
-    b.bytes = bytes;
-    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      b.p = nullptr;
-      return false;
-    }
-    return true;
-  };
   const bool keep = tape_out != nullptr;
-  if (!alloc(T->d_chi, sizeof(double) * (nplanes + 1)) || !alloc(T->state, sizeof(double) * 14 * nn) ||
-      !alloc(T->bin, sizeof(int) * nn) || !alloc(T->tw, sizeof(double) * nn) ||
-      !alloc(T->maps, sizeof(double) * 5 * np) ||
-      (keep && !alloc(T->ckpt, sizeof(double) * 14 * nn * nplanes)))
+  const bool mg = T->solver == CLC_SOLVER_SHTMG;
+  if (!tape_alloc(T->d_chi, sizeof(double) * (N + 1)) || !tape_alloc(T->state, sizeof(double) * 14 * nn) ||
+      !tape_alloc(T->bin, sizeof(int) * nn) || !tape_alloc(T->tw, sizeof(double) * nn) ||
+      (!mg && !tape_alloc(T->maps, sizeof(double) * 5 * 12ull * T->nside * T->nside)) ||
+      (mg && !tape_alloc(T->bundle, sizeof(int32_t) * nn)) ||
+      (keep && !tape_alloc(T->ckpt, sizeof(double) * 14 * nn * N)))
     return set_err(ctx, CLC_ENOMEM, "clc_gal_trace: allocation failed");
   int rc;
-  if ((rc = cuda_check(ctx, cudaMemcpyAsync(T->d_chi.p, chi, sizeof(double) * (nplanes + 1), cudaMemcpyHostToDevice,
-                                            ctx->stream), "chi upload")))
+  if (mg && (rc = clc_solution_create(ctx, T->nside, &T->mg, &T->sol))) return rc;
+  if ((rc = cuda_check(ctx, cudaMemcpyAsync(T->d_chi.p, T->chi.data(), sizeof(double) * (N + 1),
+                                            cudaMemcpyHostToDevice, ctx->stream), "chi upload")))
     return rc;
   if (ngal > 0) {
     cudaMemsetAsync(gamma, 0, sizeof(double) * 2 * ngal, ctx->stream);
     CLC_LAUNCH(ctx, "k_gal_init", k_gal_init, launch_blocks(ctx, ngal, 256, 16), 256, 0, gz, gphi, gchi,
-               (const double*)T->d_chi.p, nplanes, (double*)T->state.p, ngal, (int*)T->bin.p, (double*)T->tw.p);
+               (const double*)T->d_chi.p, N, (double*)T->state.p, ngal, (int*)T->bin.p, (double*)T->tw.p,
+               mg ? T->mg.nside_bundle : 0, (int32_t*)T->bundle.p);
     if ((rc = launch_check(ctx, "k_gal_init"))) return rc;
   }
-  double* mp = (double*)T->maps.p;
-  clc_derivs d{mp, mp + np, mp + 2 * np, mp + 3 * np, mp + 4 * np};
-  for (int m = 0; m < nplanes; ++m) {
-    if ((rc = clc_poisson_sht(ctx, kappa[m], nside, lmax, precision, nullptr, &d))) return rc;
+  int status = CLC_OK;
+  for (int m = 0; m < N; ++m) {
+    LensSrc src;
+    if ((rc = plane_lens(T.get(), m, &src))) return rc;
+    if (mg && T->sol->residual >= T->mg.tol && T->mg.fixed_cycles == 0) status = CLC_ENOTCONVERGED;
     if (ngal == 0) continue;
     if (keep)
       cudaMemcpyAsync((double*)T->ckpt.p + (size_t)m * 14 * ngal, T->state.p, sizeof(double) * 14 * ngal,
                       cudaMemcpyDeviceToDevice, ctx->stream);
-    StepC sc;
-    const double cp = m > 0 ? chi[m - 1] : 0.0, cn = chi[m], cx = chi[m + 1];
-    sc.c = (cn / cx) * ((cx - cp) / (cn - cp));
-    sc.d = (cx - cn) / cx;
-    sc.dchi2 = cx * cx - cn * cn;
-    CLC_LAUNCH(ctx, "k_gal_step", k_gal_step, launch_blocks(ctx, ngal, 128, 16), 128, 0, (double*)T->state.p, ngal, d,
-               nside, sc, (const int*)T->bin.p, (const double*)T->tw.p, m, gamma);
+    const StepC sc = step_coef(T->chi, m);
+    if (mg)
+      CLC_LAUNCH(ctx, "k_gal_step", k_gal_step<true>, launch_blocks(ctx, ngal, 128, 16), 128, 0,
+                 (double*)T->state.p, ngal, src, sc, (const int*)T->bin.p, (const double*)T->tw.p, m, gamma);
+    else
+      CLC_LAUNCH(ctx, "k_gal_step", k_gal_step<false>, launch_blocks(ctx, ngal, 128, 16), 128, 0,
+                 (double*)T->state.p, ngal, src, sc, (const int*)T->bin.p, (const double*)T->tw.p, m, gamma);
     if ((rc = launch_check(ctx, "k_gal_step"))) return rc;
   }
   if (keep) *tape_out = T.release();
   else if ((rc = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "gal trace"))) return rc;
+  return status == CLC_OK ? CLC_OK : set_err(ctx, status, "clc_gal_trace: an SHT+MG plane stopped above tol");
+}
+
+static std::unique_ptr<clc_gal_tape> new_tape(clc_ctx* ctx, int nplanes, const double* const* kappa, int nside,
+                                              const double* chi, int64_t ngal) {
+  auto T = std::make_unique<clc_gal_tape>();
+  T->ctx = ctx;
+  T->N = nplanes;
+  T->nside = nside;
+  T->n = ngal;
+  T->chi.assign(chi, chi + nplanes + 1);
+  T->kappa.assign(kappa, kappa + nplanes);
+  return T;
+}
+
+static int check_gal_args(clc_ctx* ctx, int nplanes, const double* const* kappa, const double* chi, int64_t ngal,
+                          const double* gz, const double* gphi, const double* gchi, double* gamma) {
+  if (nplanes < 1 || !kappa || !chi || ngal < 0 || (ngal > 0 && (!gz || !gphi || !gchi || !gamma)))
+    return set_err(ctx, CLC_EINVAL, "clc_gal_trace: bad arguments");
+  for (int m = 0; m < nplanes; ++m)
+    if (!kappa[m] || !(chi[m] > 0) || !(chi[m + 1] > chi[m]))
+      return set_err(ctx, CLC_EINVAL, "clc_gal_trace: null plane or non-increasing chi");
   return CLC_OK;
+}
+
+extern "C" int clc_gal_trace(clc_ctx* ctx, int nplanes, const double* const* kappa, int nside, int lmax,
+                             int precision, const double* chi, int64_t ngal, const double* gz, const double* gphi,
+                             const double* gchi, double* gamma, clc_gal_tape** tape_out) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = check_gal_args(ctx, nplanes, kappa, chi, ngal, gz, gphi, gchi, gamma);
+  if (rc) return rc;
+  if (!valid_nside(nside) || nside > 4096 || lmax < 1 || lmax > 4 * nside ||
+      (precision != CLC_FP64 && precision != CLC_MIXED))
+    return set_err(ctx, CLC_EINVAL, "clc_gal_trace: bad arguments");
+  cudaSetDevice(ctx->device);
+  auto T = new_tape(ctx, nplanes, kappa, nside, chi, ngal);
+  T->lmax = lmax;
+  T->precision = precision;
+  return gal_trace(std::move(T), gz, gphi, gchi, gamma, tape_out);
+}
+
+extern "C" int clc_gal_trace_mg(clc_ctx* ctx, int nplanes, const double* const* kappa, int nside,
+                                const clc_mg_params* params, const double* chi, int64_t ngal, const double* gz,
+                                const double* gphi, const double* gchi, double* gamma, clc_gal_tape** tape_out) {
+  if (!ctx) return CLC_EINVAL;
+  int rc = check_gal_args(ctx, nplanes, kappa, chi, ngal, gz, gphi, gchi, gamma);
+  if (rc) return rc;
+  if (!params || params->precision != CLC_FP64 || !valid_nside(nside))
+    return set_err(ctx, CLC_EINVAL, "clc_gal_trace_mg: needs CLC_FP64 MG parameters");
+  cudaSetDevice(ctx->device);
+  auto T = new_tape(ctx, nplanes, kappa, nside, chi, ngal);
+  T->solver = CLC_SOLVER_SHTMG;
+  T->mg = *params;
+  T->lmax = params->lmax;
+  T->precision = CLC_FP64;
+  return gal_trace(std::move(T), gz, gphi, gchi, gamma, tape_out);
+}
+
+// adjoint of one SHT+MG plane's solve: ubar (patch interiors) -> kappa_bar
+static int shtmg_adjoint(clc_gal_tape* T, double* kbar) {
+  clc_ctx* ctx = T->ctx;
+  clc_plane_solution* S = T->sol;
+  const int nf = T->nside, ns = T->mg.nside_sht;
+  const int64_t nf2 = 12ll * nf * nf, ns2 = 12ll * ns * ns;
+  cudaMemsetAsync(kbar, 0, sizeof(double) * nf2, ctx->stream);
+  cudaMemsetAsync(T->psibar.p, 0, sizeof(double) * ns2, ctx->stream);
+  // the adjoint solve stops two orders below the forward tolerance (or at
+  // 1e-12), so that it is no less converged than the forward solve
+  const double tol = std::min(T->mg.tol * 1e-2, 1e-12);
+  int rc = mg_adjoint_solve(ctx, S, (const double*)T->ubar.p, tol, std::max(T->mg.max_cycles, 40), kbar,
+                            (double*)T->psibar.p, nullptr, nullptr);
+  if (rc != CLC_OK && rc != CLC_ENOTCONVERGED) return rc;
+  const int st = rc;
+  // the SHT potential's dependence on kappa_sht: the psi-only SHT Poisson
+  // solve (analysis, -1 / l(l+1), synthesis) is symmetric, so its adjoint is
+  // the same solve; then the transposed degrade
+  if ((rc = clc_poisson_sht(ctx, (const double*)T->psibar.p, ns, T->mg.lmax, CLC_FP64, (double*)T->kbar_s.p,
+                            nullptr)))
+    return rc;
+  CLC_LAUNCH(ctx, "k_degrade_adjoint", k_degrade_adjoint, launch_blocks(ctx, nf2, 256, 16), 256, 0,
+             (const double*)T->kbar_s.p, ns, nf, kbar);
+  if ((rc = launch_check(ctx, "k_degrade_adjoint"))) return rc;
+  return st;
 }
 
 extern "C" int clc_gal_trace_adjoint(clc_gal_tape* T, const double* gamma_bar, double* const* kappa_bar) {
@@ -767,49 +1102,55 @@ extern "C" int clc_gal_trace_adjoint(clc_gal_tape* T, const double* gamma_bar, d
   for (int m = 0; m < T->N; ++m)
     if (!kappa_bar[m]) return set_err(ctx, CLC_EINVAL, "clc_gal_trace_adjoint: null gradient map");
   cudaSetDevice(ctx->device);
+  const bool mg = T->solver == CLC_SOLVER_SHTMG;
   const int ns = T->nside;
   const size_t np = 12ull * ns * ns;
   const int64_t n = T->n;
   int rc;
-  if (!T->adj.p) {
-    T->adj.bytes = sizeof(double) * 14 * (size_t)std::max<int64_t>(n, 1);
-    if (cudaMalloc(&T->adj.p, T->adj.bytes) != cudaSuccess) {
-      cudaGetLastError();
-      T->adj.p = nullptr;
-      return set_err(ctx, CLC_ENOMEM, "adjoint state");
-    }
-  }
-  if (!T->fbar.p) {
-    T->fbar.bytes = sizeof(double) * 5 * np;
-    if (cudaMalloc(&T->fbar.p, T->fbar.bytes) != cudaSuccess) {
-      cudaGetLastError();
-      T->fbar.p = nullptr;
-      return set_err(ctx, CLC_ENOMEM, "adjoint maps");
-    }
+  if (!T->adj.p && !tape_alloc(T->adj, sizeof(double) * 14 * (size_t)std::max<int64_t>(n, 1)))
+    return set_err(ctx, CLC_ENOMEM, "adjoint state");
+  if (!mg && !T->fbar.p && !tape_alloc(T->fbar, sizeof(double) * 5 * np))
+    return set_err(ctx, CLC_ENOMEM, "adjoint maps");
+  if (mg && !T->ubar.p) {
+    const size_t nc = (size_t)T->mg.ncell;
+    const size_t ns2 = 12ull * T->mg.nside_sht * T->mg.nside_sht;
+    if (!tape_alloc(T->ubar, sizeof(double) * nc * nc * T->sol->npatch) || !tape_alloc(T->psibar, sizeof(double) * ns2) ||
+        !tape_alloc(T->kbar_s, sizeof(double) * ns2))
+      return set_err(ctx, CLC_ENOMEM, "SHT+MG adjoint buffers");
   }
   cudaMemsetAsync(T->adj.p, 0, T->adj.bytes, ctx->stream);
-  double* mp = (double*)T->maps.p;
   double* fp = (double*)T->fbar.p;
-  clc_derivs d{mp, mp + np, mp + 2 * np, mp + 3 * np, mp + 4 * np};
-  clc_derivs db{fp, fp + np, fp + 2 * np, fp + 3 * np, fp + 4 * np};
+  clc_derivs db{};
+  if (!mg) db = clc_derivs{fp, fp + np, fp + 2 * np, fp + 3 * np, fp + 4 * np};
+  int status = CLC_OK;
   for (int m = T->N - 1; m >= 0; --m) {
-    // recompute the plane's lens maps from its convergence map
-    if ((rc = clc_poisson_sht(ctx, T->kappa[m], ns, T->lmax, T->precision, nullptr, &d))) return rc;
-    cudaMemsetAsync(fp, 0, T->fbar.bytes, ctx->stream);
+    // recompute the plane's lens fields from its convergence map
+    LensSrc src;
+    if ((rc = plane_lens(T, m, &src))) return rc;
+    if (mg) cudaMemsetAsync(T->ubar.p, 0, T->ubar.bytes, ctx->stream);
+    else cudaMemsetAsync(fp, 0, T->fbar.bytes, ctx->stream);
     if (n > 0) {
-      StepC sc;
-      const double cp = m > 0 ? T->chi[m - 1] : 0.0, cn = T->chi[m], cx = T->chi[m + 1];
-      sc.c = (cn / cx) * ((cx - cp) / (cn - cp));
-      sc.d = (cx - cn) / cx;
-      sc.dchi2 = cx * cx - cn * cn;
-      CLC_LAUNCH(ctx, "k_gal_step_adjoint", k_gal_step_adjoint, launch_blocks(ctx, n, 128, 16), 128, 0,
-                 (const double*)T->ckpt.p + (size_t)m * 14 * n, (double*)T->adj.p, n, d, db, ns, sc,
-                 (const int*)T->bin.p, (const double*)T->tw.p, m, gamma_bar);
+      const StepC sc = step_coef(T->chi, m);
+      const double* ck = (const double*)T->ckpt.p + (size_t)m * 14 * n;
+      if (mg)
+        CLC_LAUNCH(ctx, "k_gal_step_adjoint", k_gal_step_adjoint<true>, launch_blocks(ctx, n, 128, 16), 128, 0, ck,
+                   (double*)T->adj.p, n, src, db, (double*)T->ubar.p, sc, (const int*)T->bin.p,
+                   (const double*)T->tw.p, m, gamma_bar);
+      else
+        CLC_LAUNCH(ctx, "k_gal_step_adjoint", k_gal_step_adjoint<false>, launch_blocks(ctx, n, 128, 16), 128, 0, ck,
+                   (double*)T->adj.p, n, src, db, (double*)nullptr, sc, (const int*)T->bin.p,
+                   (const double*)T->tw.p, m, gamma_bar);
       if ((rc = launch_check(ctx, "k_gal_step_adjoint"))) return rc;
     }
-    if ((rc = sht_poisson_adjoint(T, db, kappa_bar[m]))) return rc;
+    if (mg) {
+      rc = shtmg_adjoint(T, kappa_bar[m]);
+      if (rc == CLC_ENOTCONVERGED) status = rc;
+      else if (rc) return rc;
+    } else if ((rc = sht_poisson_adjoint(T, db, kappa_bar[m]))) {
+      return rc;
+    }
   }
-  return CLC_OK;
+  return status;
 }
 
 extern "C" int clc_gal_tape_destroy(clc_gal_tape* T) {

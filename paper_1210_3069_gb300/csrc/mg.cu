@@ -1427,6 +1427,147 @@ struct MG {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Adjoint of the converged patch solve (the SHT+MG adjoint).
+//
+// Converged, the interior potential of a patch is u = L^-1 (f - L_g G): L the
+// interior operator with the Dirichlet extrapolation on its diagonal, L_g the
+// coupling of the edge rows and columns to the ghost ring G = 2 g (g =
+// psi_SHT at the edge-face centres) and f = kappa at the cell centres (the
+// interior starting guess drops out).  Given the adjoint ubar of u,
+// lambda = L^-T ubar, fbar = lambda and gbar = -2 L_g^T lambda.  W L is
+// symmetric for W = diag(cos((i + 1/2 - n/2) h)) = diag(sin theta'_i) (the
+// finite-volume fluxes between rows i, i + 1 carry sin theta'_{i+1/2} on both
+// sides; the phi fluxes and the diagonal are local to a row), so
+// L^T = W L W^-1 and lambda = W mu with L mu = W^-1 ubar: the forward
+// V-cycles from zero with zero Dirichlet data, run to the tolerance.  fbar
+// and gbar then go back through the transposed interpolations to kappa_fine
+// and psi_SHT.
+
+__global__ void k_adj_rhs(int n, const double* __restrict__ ubar, const double* __restrict__ wrow,
+                          double* __restrict__ f, double* __restrict__ fnorm) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  double ff = 0.0;
+  if (i < n && j < n) {
+    const double r = ubar[(size_t)b * n * n + (size_t)i * n + j] / wrow[i];
+    f[(size_t)b * n * n + fidx(n, i, j)] = r;
+    ff = r * r;
+  }
+  for (int o = 16; o > 0; o >>= 1) ff += __shfl_xor_sync(0xffffffffu, ff, o);
+  if (threadIdx.x == 0 && ff != 0.0) atomicAdd(fnorm + b, ff);
+}
+
+// v at (theta, phi) scattered into map through the ring-bilinear weights
+__device__ __forceinline__ void scatter_at(double* __restrict__ map, int nside, const double* __restrict__ ring_th,
+                                           double th, double ph, double v) {
+  const Interp8 o = interp_weights_tab(nside, ring_th, th, ph);
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+    if (o.w[k] != 0.0) atomicAdd(map + o.p[k], o.w[k] * v);
+}
+
+// v at plan position pos (or, without plans, at patch-frame position `cell`
+// of patch b) scattered into map: the transpose of the set-up interpolation
+__device__ __forceinline__ void scatter_plan(double* __restrict__ map, int nside, const double* __restrict__ ring_th,
+                                             const int4* __restrict__ idx, const double4_32a* __restrict__ w,
+                                             size_t pos, const double* __restrict__ R, const double* __restrict__ pv,
+                                             double v) {
+  if (idx) {
+    const int4 ix = idx[pos];
+    const double4_32a ww = w[pos];
+    if (ix.x < 0) {
+      scatter_at(map, nside, ring_th, ww.x, ww.y, v);
+    } else {
+      atomicAdd(map + ix.x, ww.x * v);
+      atomicAdd(map + ix.y, ww.y * v);
+      atomicAdd(map + ix.z, ww.z * v);
+      atomicAdd(map + ix.w, ww.w * v);
+    }
+    return;
+  }
+  double th, ph;
+  cell_angles(R, pv, &th, &ph);
+  scatter_at(map, nside, ring_th, th, ph, v);
+}
+
+// lambda = W mu from the converged correction array; kappa_bar += I_kappa^T
+// lambda; psi_bar += I_psi^T (-2 L_g^T lambda) at the ghost positions
+__global__ void k_adj_scatter(int n, const double* __restrict__ U, const double* __restrict__ wrow,
+                              const double* __restrict__ coef, const int4* __restrict__ kidx,
+                              const double4_32a* __restrict__ kw, const int4* __restrict__ pidx,
+                              const double4_32a* __restrict__ pw, const double* __restrict__ rot,
+                              const double* __restrict__ pvec, int nf, const double* __restrict__ th_fine, int ns,
+                              const double* __restrict__ th_sht, double* __restrict__ kbar,
+                              double* __restrict__ psibar) {
+  const int b = blockIdx.z;
+  const int i = blockIdx.y * kBY + threadIdx.y, j = blockIdx.x * kBX + threadIdx.x;
+  if (i >= n || j >= n) return;
+  const int side = n + 2;
+  const double lam = wrow[i] * U[(size_t)b * upatch(n) + uidx(n, i, j)];
+  if (lam == 0.0) return;
+  const double* R = rot + 9 * (size_t)b;
+  scatter_plan(kbar, nf, th_fine, kidx, kw, (size_t)b * n * n + (size_t)i * n + j, R,
+               pvec + 3 * (size_t)((i + 1) * side + (j + 1)), lam);
+  const size_t pb = (size_t)b * side * side;
+  // ghost couplings: aN_0 above row 0, aS_{n-1} below row n - 1, b_i left and right
+  if (i == 0)
+    scatter_plan(psibar, ns, th_sht, pidx, pw, pb + (size_t)(j + 1), R, pvec + 3 * (size_t)(j + 1),
+                 -2.0 * coef[n] * lam);
+  if (i == n - 1)
+    scatter_plan(psibar, ns, th_sht, pidx, pw, pb + (size_t)(n + 1) * side + (j + 1), R,
+                 pvec + 3 * (size_t)((n + 1) * side + (j + 1)), -2.0 * coef[n - 1] * lam);
+  if (j == 0)
+    scatter_plan(psibar, ns, th_sht, pidx, pw, pb + (size_t)(i + 1) * side, R, pvec + 3 * (size_t)((i + 1) * side),
+                 -2.0 * coef[2 * n + i] * lam);
+  if (j == n - 1)
+    scatter_plan(psibar, ns, th_sht, pidx, pw, pb + (size_t)(i + 1) * side + (n + 1), R,
+                 pvec + 3 * (size_t)((i + 1) * side + (n + 1)), -2.0 * coef[2 * n + i] * lam);
+}
+
+int mg_adjoint_solve(clc_ctx* ctx, clc_plane_solution* s, const double* ubar, double tol, int max_cycles,
+                     double* kbar_fine, double* psibar_sht, int* cycles_out, double* ratio_out) {
+  if (s->p.precision != CLC_FP64) return set_err(ctx, CLC_EINVAL, "SHT+MG adjoint needs a CLC_FP64 solution");
+  const int n = s->sizes[0];
+  if (!s->wrow.p) {
+    std::vector<double> w(n);
+    for (int i = 0; i < n; ++i) w[i] = std::cos((i + 0.5 - 0.5 * n) * s->h);
+    s->wrow.bytes = n * sizeof(double);
+    if (cudaMalloc(&s->wrow.p, s->wrow.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      s->wrow.p = nullptr;
+      return set_err(ctx, CLC_ENOMEM, "adjoint row weights");
+    }
+    int rc = cuda_check(ctx, cudaMemcpy(s->wrow.p, w.data(), s->wrow.bytes, cudaMemcpyHostToDevice), "row weights");
+    if (rc) return rc;
+  }
+  MG<double> mg{s, ctx};
+  cudaMemsetAsync(s->fnorm.p, 0, sizeof(double) * s->npatch, ctx->stream);
+  CLC_LAUNCH(ctx, "k_adj_rhs", k_adj_rhs, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, n, ubar,
+             (const double*)s->wrow.p, mg.F(0), (double*)s->fnorm.p);
+  int rc = launch_check(ctx, "k_adj_rhs");
+  if (rc) return rc;
+  double rr = 0.0;
+  int cyc = 0;
+  do {
+    mg.vcycle(0, cyc == 0);
+    if ((rc = launch_check(ctx, "adjoint V-cycle"))) return rc;
+    ++cyc;
+    if ((rc = mg.residual(&rr))) return rc;
+  } while (rr >= tol && cyc < max_cycles);
+  if (cycles_out) *cycles_out = cyc;
+  if (ratio_out) *ratio_out = rr;
+  const bool pl = s->plan;
+  CLC_LAUNCH(ctx, "k_adj_scatter", k_adj_scatter, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, n,
+             (const double*)mg.U(0), (const double*)s->wrow.p, mg.C64(0),
+             pl ? (const int4*)s->plan_kap_idx.p : nullptr, (const double4_32a*)s->plan_kap_w.p,
+             pl ? (const int4*)s->plan_psi_idx.p : nullptr, (const double4_32a*)s->plan_psi_w.p,
+             (const double*)s->rot.p, (const double*)s->pvec.p, s->nside_fine, (const double*)s->ring_th_fine.p,
+             s->p.nside_sht, (const double*)s->ring_th_sht.p, kbar_fine, psibar_sht);
+  if ((rc = launch_check(ctx, "k_adj_scatter"))) return rc;
+  return rr < tol ? CLC_OK : set_err(ctx, CLC_ENOTCONVERGED, "SHT+MG adjoint solve stopped at max_cycles above tol");
+}
+
 static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
   if (!p) return set_err(ctx, CLC_EINVAL, "null MG parameters");
   if (!valid_nside(nf) || !valid_nside(p->nside_sht) || !valid_nside(p->nside_bundle) || p->nside_bundle > nf ||

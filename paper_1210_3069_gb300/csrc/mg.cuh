@@ -37,6 +37,7 @@ struct clc_plane_solution {
   clc::Buffer kappa_sht;        // double[12 nside_sht^2]
   clc::Buffer norms;            // double[npatch][2]
   clc::Buffer ratio;            // double[1]
+  clc::Buffer wrow;             // double[n]: sin theta'_i of the finest rows (adjoint solve)
   int cycles = 0;
   double residual = 0;
 };
@@ -53,5 +54,14 @@ struct MGView {
 };
 
 MGView mg_view(const clc_plane_solution* sol);
+
+// Adjoint of the converged SHT+MG patch solve of the plane held in `sol`
+// (CLC_FP64 solutions): ubar[npatch][n][n] the adjoint of the finest interior
+// potential; accumulates the transposed source interpolation into
+// kbar_fine (RING map of nside_fine) and the transposed boundary-value
+// interpolation into psibar_sht (RING map of nside_sht).  V-cycles until the
+// max relative residual is below tol (or max_cycles).
+int mg_adjoint_solve(clc_ctx* ctx, clc_plane_solution* s, const double* ubar, double tol, int max_cycles,
+                     double* kbar_fine, double* psibar_sht, int* cycles_out, double* ratio_out);
 
 }  // namespace clc

@@ -73,8 +73,8 @@ def test_mg_adjoint_matches_oracle_gradient(nf, ns, lmax, nb, ncell):
     for e in errs:
         # the oracle differentiates its 20 V-cycles, the GPU solves the
         # adjoint patch problem to 1e-12: both are the converged solve's
-        # gradient up to the iteration's residual
-        assert e < 1e-9, errs
+        # gradient up to the iteration's residual (measured 1.2e-11 on GB300)
+        assert e < 1e-10, errs
 
 
 def test_mg_adjoint_matches_finite_differences():
@@ -95,7 +95,7 @@ def test_mg_adjoint_matches_finite_differences():
     L0.backward()
     grad = kg.grad
     h = 1e-6
-    fd_floor = 1e-15 * float(L0) * (2 * gz.numel()) ** 0.5 / (2 * h)
+    fd_floor = 1e-15 * float(L0.detach()) * (2 * gz.numel()) ** 0.5 / (2 * h)
     gen = torch.Generator().manual_seed(3)
     for m in range(kappas.shape[0]):
         gmax = float(grad[m].abs().max())

@@ -165,3 +165,43 @@ def test_correction_form_gives_the_fas_iterates(cycles):
     assert float((ue - u[:, 1:-1, 1:-1]).abs().max()) < 1e-12 * scale
     # and the correction made a difference (the comparison is not vacuous)
     assert float((ue - u0[:, 1:-1, 1:-1]).abs().max()) > 1e-4 * scale
+
+
+def test_tau_estimate_is_second_order():
+    """tau = L_c R u - R L_f u of the exact solution (a truncation-error
+    estimate of the second-order discretisation) falls by four when the
+    cells halve, away from the patch edge; in the two coarse rows and columns
+    at the edge it stays of order one (the ghost-cell extrapolation of the
+    Dirichlet data is a first-order boundary closure, whose truncation error
+    still gives a second-order solution error)."""
+    rms = []
+    edge = []
+    for n in (32, 64, 128):
+        R, h, ghosts, exact, f, u = manufactured(n)
+        S = mg.PatchSolver(n, h, ghosts)
+        ue = ghosts[0].clone()
+        ue[:, 1:-1, 1:-1] = exact
+        t = mg.tau_estimate(S, ue, ghosts[1])
+        ti = t[:, 2:-2, 2:-2]
+        rms.append(float(torch.sqrt((ti * ti).mean())))
+        edge.append(float(t.abs().max()))
+    for a, b in zip(rms, rms[1:]):
+        assert 3.8 < a / b < 4.2, rms
+    assert min(edge) > 0.5 * max(edge), edge
+
+
+def test_tau_rule_stops_at_the_discretisation_error():
+    """The paper's rule ||r|| < eps ||tau|| (eps = 0.1) leaves the solution
+    within a few per cent of the discretisation error of the converged one,
+    after fewer V-cycles than a 1e-10 relative residual needs."""
+    n = 64
+    R, h, ghosts, exact, f, u0 = manufactured(n)
+    conv, kc, _ = mg.solve_correction(u0, f, h, n, tol=1e-12)
+    tau_u, kt, ratio = mg.solve_correction(u0, f, h, n, stop="tau", eps=0.1, ghost_c=ghosts[1])
+    e_conv = float((conv - exact).abs().max())
+    e_tau = float((tau_u - exact).abs().max())
+    assert ratio < 0.1 and 1 <= kt < kc
+    assert e_tau < 1.05 * e_conv, (e_tau, e_conv, kt, kc)
+    # a looser eps stops earlier and further from the converged solution
+    loose, kl, _ = mg.solve_correction(u0, f, h, n, stop="tau", eps=10.0, ghost_c=ghosts[1])
+    assert kl <= kt and float((loose - conv).abs().max()) >= float((tau_u - conv).abs().max())
