@@ -292,7 +292,8 @@ def run_gpu(args, cfg, rank, world):
     chi_prev, chi_n, chi_next, scale = plane_geometry()
     prec = {"fp32": clc.FP32, "fp64": clc.FP64, "mixed": clc.MIXED}[args.precision]
     P = clc.mg_params(cfg["nside_sht"], cfg["lmax"], cfg["nside_bundle"], ncell=cfg["ncell"], nu1=cfg["nu1"],
-                      nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=prec)
+                      nu2=cfg["nu2"], max_cycles=cfg["max_cycles"], tol=cfg["tol"], precision=prec,
+                      refine_cycles=args.refine_cycles)
     # seeded synthetic plane (a different shell per rank)
     z, phi = synthetic.lognormal_particles(cfg["particles"], plane_seed(cfg, rank), device=dev)
     nbar = z.numel() / npix
@@ -1045,6 +1046,8 @@ def main():
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS)
                     + sorted(SMOOTH_WORKLOADS) + sorted(IMAGE_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--refine-cycles", type=int, default=0,
+                    help="mixed precision: FP32 V-cycles per float-float residual refinement (0: the library's 2)")
     ap.add_argument("--fp64-steps", type=int, default=3,
                     help="timed steps of the plain FP64 solver on the same plane after the main run (0: skip)")
     args = ap.parse_args()
@@ -1091,6 +1094,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     config = {"workload": args.workload, **{k: v for k, v in cfg.items() if k != "seed"},
               "rays": 12 * cfg["nside"] ** 2, "precision": args.precision,
+              "refine_cycles": args.refine_cycles or 2,
               "l2": "inputs larger than L2 (no flush)", "planes_per_rank_per_step": 1}
 
     if args.impl == "reference":

@@ -73,12 +73,24 @@ typedef struct clc_mg_params {
   int nu1, nu2;     /* red-black Gauss-Seidel sweeps before / after the coarse step, 0..8, sum >= 1 */
   int max_cycles;   /* V-cycle cap when iterating to tol                     */
   int fixed_cycles; /* > 0: run exactly this many V-cycles, ignore tol       */
-  double tol;       /* stop when max over patches ||f - L u||_2 / ||f||_2 < tol */
+  double tol;       /* CLC_STOP_RESIDUAL: stop when max over patches ||f - L u||_2 / ||f||_2 < tol */
   int precision;    /* CLC_FP64: all FP64; CLC_FP32: FP32 V-cycles and residual
                        (FP64 coarsest solve); CLC_MIXED: FP32 V-cycles refining a
                        residual of FP64 accuracy (float-float), converging to the
                        same tol as CLC_FP64 */
+  int stop_rule;    /* CLC_STOP_RESIDUAL (0, the rule above) or CLC_STOP_TAU (1):
+                       the paper's rule (Sec. 3.2), stop when max over patches of
+                       rms(f - L u) / rms(tau) < eps, tau = L_c R u - R L_f u the
+                       truncation-error estimate on the next coarser level (R the
+                       area-weighted restriction, the coarse ghost ring holding
+                       2 psi_SHT at the coarse edge faces), rms over the patch's
+                       fine and coarse cells */
+  double eps;       /* CLC_STOP_TAU: the fraction (the paper uses 0.1 and 0.01) */
+  int refine_cycles;/* CLC_MIXED: FP32 V-cycles between two float-float residual
+                       refinements (0 = 2); with CLC_STOP_* checked after each */
 } clc_mg_params;
+
+enum { CLC_STOP_RESIDUAL = 0, CLC_STOP_TAU = 1 };
 
 /* Ray state, structure of arrays of n rays (device FP64):
  * x[3][n] Cartesian position, beta[3][n] propagation direction,

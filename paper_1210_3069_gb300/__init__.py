@@ -22,6 +22,7 @@ RING, NEST = 0, 1
 FP64, FP32, MIXED = 0, 1, 2
 PLAN_GRAPH, PLAN_TUNE = 1, 2
 SOLVER_SHT, SOLVER_SHTMG = 0, 1
+STOP_RESIDUAL, STOP_TAU = 0, 1
 
 _p = ctypes.c_void_p
 _i = ctypes.c_int
@@ -41,7 +42,8 @@ class Derivs(ctypes.Structure):
 
 class MGParams(ctypes.Structure):
     _fields_ = [("nside_sht", _i), ("lmax", _i), ("nside_bundle", _i), ("ncell", _i), ("nu1", _i), ("nu2", _i),
-                ("max_cycles", _i), ("fixed_cycles", _i), ("tol", _d), ("precision", _i)]
+                ("max_cycles", _i), ("fixed_cycles", _i), ("tol", _d), ("precision", _i), ("stop_rule", _i),
+                ("eps", _d), ("refine_cycles", _i)]
 
 
 class Rays(ctypes.Structure):
@@ -543,5 +545,6 @@ class ShtPlan:
 
 
 def mg_params(nside_sht, lmax, nside_bundle, ncell=256, nu1=2, nu2=2, max_cycles=60, fixed_cycles=0, tol=1e-10,
-              precision=FP64):
-    return MGParams(nside_sht, lmax, nside_bundle, ncell, nu1, nu2, max_cycles, fixed_cycles, tol, precision)
+              precision=FP64, stop_rule=STOP_RESIDUAL, eps=0.1, refine_cycles=0):
+    return MGParams(nside_sht, lmax, nside_bundle, ncell, nu1, nu2, max_cycles, fixed_cycles, tol, precision,
+                    stop_rule, eps, refine_cycles)

@@ -1170,6 +1170,103 @@ static LevelCoef level_coef(int n, double h) {
 
 static dim3 grid3(int nx, int ny, int npatch) { return dim3((nx + kBX - 1) / kBX, (ny + kBY - 1) / kBY, npatch); }
 
+// ---------------------------------------------------------------------------
+// The paper's stopping rule (Sec. 3.2): ||r|| < eps ||tau||, tau = L_c R u -
+// R L_f u the truncation-error estimate of the full approximation scheme on
+// the next coarser level, u = base + e with its Dirichlet ghost ring.
+
+// 2 psi_SHT at the centres of the coarse level's edge faces (the coarse
+// ghost ring), per patch [top J, bottom J, left I, right I] x nc
+__global__ void k_mg_coarse_ghosts(int nc, double hc, const double* __restrict__ rot, const double* __restrict__ psi,
+                                   int ns, const double* __restrict__ ring_th, double* __restrict__ gc) {
+  const int b = blockIdx.y;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * nc) return;
+  const int side = t / nc, k = t % nc;
+  const double edge = 0.5 * nc * hc, cen = (k + 0.5 - 0.5 * nc) * hc;
+  double dth, dph;   // theta' - pi/2 and phi' of the face centre
+  if (side == 0) { dth = -edge; dph = cen; }
+  else if (side == 1) { dth = edge; dph = cen; }
+  else if (side == 2) { dth = cen; dph = -edge; }
+  else { dth = cen; dph = edge; }
+  // theta' = pi/2 + dth: sin theta' = cos dth, cos theta' = -sin dth
+  double sd, cd, sp, cp;
+  sincos(dth, &sd, &cd);
+  sincos(dph, &sp, &cp);
+  const double v[3] = {cd * cp, cd * sp, -sd};
+  double th, ph;
+  cell_angles(rot + 9 * (size_t)b, v, &th, &ph);
+  gc[(size_t)b * 4 * nc + t] = 2.0 * interp_map_tab(psi, ns, ring_th, th, ph);
+}
+
+template <typename E>
+__device__ __forceinline__ double e_at(const E* e, size_t k) { return (double)e[k]; }
+template <>
+__device__ __forceinline__ double e_at<float2>(const float2* e, size_t k) {
+  const float2 v = e[k];
+  return f2d_exact(v.x) + f2d_exact(v.y);
+}
+
+// ||tau||^2 per patch over the coarse cells
+template <typename E>
+__global__ void k_tau_norm(int n, const double* __restrict__ base, const E* __restrict__ e,
+                           const double* __restrict__ cf, const double* __restrict__ df,
+                           const double* __restrict__ cc, const double* __restrict__ dc,
+                           const double* __restrict__ rd, const double* __restrict__ gc, double* __restrict__ tau2) {
+  const int b = blockIdx.z;
+  const int nc = n / 2, side = n + 2;
+  const int I = blockIdx.y * kBY + threadIdx.y, J = blockIdx.x * kBX + threadIdx.x;
+  double tt = 0.0;
+  if (I < nc && J < nc) {
+    const double* B = base + (size_t)b * side * side;
+    const E* Eb = e + (size_t)b * upatch(n);
+    // fine u at -1 <= i, j <= n (the correction's ghost ring is zero)
+    auto u = [&](int i, int j) -> double { return B[(size_t)(i + 1) * side + (j + 1)] + e_at(Eb, uidx(n, i, j)); };
+    auto Ru = [&](int Ic, int Jc) -> double {
+      if (Ic < 0) return gc[(size_t)b * 4 * nc + Jc];
+      if (Ic >= nc) return gc[(size_t)b * 4 * nc + nc + Jc];
+      if (Jc < 0) return gc[(size_t)b * 4 * nc + 2 * nc + Ic];
+      if (Jc >= nc) return gc[(size_t)b * 4 * nc + 3 * nc + Ic];
+      const int i = 2 * Ic, j = 2 * Jc;
+      return (cf[3 * n + i] * (u(i, j) + u(i, j + 1)) + cf[3 * n + i + 1] * (u(i + 1, j) + u(i + 1, j + 1))) * rd[Ic];
+    };
+    auto Lf = [&](int i, int j) -> double {
+      return cf[i] * u(i + 1, j) + cf[n + i] * u(i - 1, j) + cf[2 * n + i] * (u(i, j + 1) + u(i, j - 1)) -
+             df[(size_t)i * n + j] * u(i, j);
+    };
+    const double Lc = cc[I] * Ru(I + 1, J) + cc[nc + I] * Ru(I - 1, J) + cc[2 * nc + I] * (Ru(I, J + 1) + Ru(I, J - 1)) -
+                      dc[(size_t)I * nc + J] * Ru(I, J);
+    const int i = 2 * I, j = 2 * J;
+    const double RL = (cf[3 * n + i] * (Lf(i, j) + Lf(i, j + 1)) + cf[3 * n + i + 1] * (Lf(i + 1, j) + Lf(i + 1, j + 1))) *
+                      rd[I];
+    const double t = Lc - RL;
+    tt = t * t;
+  }
+  for (int o = 16; o > 0; o >>= 1) tt += __shfl_xor_sync(0xffffffffu, tt, o);
+  if (threadIdx.x == 0 && tt != 0.0) atomicAdd(tau2 + b, tt);
+}
+
+// max over patches of rms(r) / rms(tau) = sqrt(rr / tau2) / 2 (n^2 fine
+// cells against (n/2)^2 coarse ones)
+__global__ void k_max_ratio_tau(const double* __restrict__ rr, const double* __restrict__ t2, int npatch,
+                                double* __restrict__ out) {
+  double mx = 0.0;
+  for (int b = threadIdx.x; b < npatch; b += blockDim.x) {
+    const double r = rr[b], t = t2[b];
+    const double q = t > 0.0 ? 0.5 * sqrt(r / t) : (r > 0.0 ? HUGE_VAL : 0.0);
+    mx = fmax(mx, q);
+  }
+  __shared__ double s[32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    mx = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (threadIdx.x == 0) out[0] = mx;
+  }
+}
+
 template <typename T>
 struct MG {
   clc_plane_solution* s;
@@ -1271,13 +1368,34 @@ struct MG {
     prolong_smooth(l);
   }
 
-  int residual(double* ratio_host) {
+  // the paper's rule applies when asked for and when there is a coarser level
+  bool tau_rule() const { return s->p.stop_rule == CLC_STOP_TAU && s->nlev > 1; }
+
+  // ratio of the stopping rule into s->ratio from the per-patch residual
+  // norms in s->norms: ||r|| / ||f|| (relative residual) or rms(r) / rms(tau)
+  // with tau from u = base + e
+  template <typename E>
+  void stop_ratio(const E* e, bool tau) {
+    const int n = s->sizes[0];
+    if (!tau) {
+      CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
+                 s->npatch, (double*)s->ratio.p);
+      return;
+    }
+    cudaMemsetAsync(s->tau2.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    CLC_LAUNCH(ctx, "k_tau_norm", k_tau_norm<E>, grid3(n / 2, n / 2, s->npatch), dim3(kBX, kBY), 0, n,
+               (const double*)s->base.p, e, C64(0), G64(0), C64(1), G64(1), (const double*)s->rden[0].p,
+               (const double*)s->gc.p, (double*)s->tau2.p);
+    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio_tau, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->tau2.p,
+               s->npatch, (double*)s->ratio.p);
+  }
+
+  int residual(double* ratio_host, bool tau = false) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
     CLC_LAUNCH(ctx, "k_resnorm", k_resnorm<T>, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, U(0), F(0), C64(0), G64(0), n,
                (double*)s->norms.p);
-    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
-               s->npatch, (double*)s->ratio.p);
+    stop_ratio<T>(U(0), tau);
     int rc = launch_check(ctx, "MG residual");
     if (rc) return rc;
     rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -1289,6 +1407,12 @@ struct MG {
   // base (SHT solution + edge values), defect source f' = kappa - L base,
   // ||kappa||^2 per patch, and a zero starting correction
   int setup(const double* kappa_fine) {
+    if (tau_rule()) {
+      const int nc = s->sizes[1];
+      CLC_LAUNCH(ctx, "k_mg_coarse_ghosts", k_mg_coarse_ghosts, dim3((4 * nc + 127) / 128, s->npatch), 128, 0, nc,
+                 2.0 * s->h, (const double*)s->rot.p, (const double*)s->psi_sht.p, s->p.nside_sht,
+                 (const double*)s->ring_th_sht.p, (double*)s->gc.p);
+    }
     if (mixed && s->plan) return setup_ff(kappa_fine);
     if (mixed) return setup_t<float2>(kappa_fine, (float2*)s->fd64.p);
     return setup_t<T>(kappa_fine, F(0));
@@ -1354,8 +1478,7 @@ struct MG {
     CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_ff, grid, dim3(kBX, kBY), 0, e_old, d, (const float2*)s->fd64.p,
                (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, n, e_new, (float*)s->f[0].p,
                (double*)s->norms.p);
-    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
-               s->npatch, (double*)s->ratio.p);
+    stop_ratio<float2>(e_new, tau_rule());
     int rc = launch_check(ctx, "MG mixed residual");
     if (rc) return rc;
     rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
@@ -1374,10 +1497,13 @@ struct MG {
     float2* nxt = (float2*)s->e64b.p;
     if ((rc = residual_mixed(cur, nullptr, nxt, &rr))) return rc;
     std::swap(cur, nxt);
-    while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= s->p.tol && s->cycles < s->p.max_cycles)) {
-      // two FP32 V-cycles on L d = r (the second continues from the first)
-      // per FP64 refinement: the FP64 residual is the ALU-bound part
-      const int inner = (fixed ? s->p.fixed_cycles - s->cycles : s->p.max_cycles - s->cycles) >= 2 ? 2 : 1;
+    const double limit = tau_rule() ? s->p.eps : s->p.tol;
+    const int per = s->p.refine_cycles > 0 ? s->p.refine_cycles : 2;
+    while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= limit && s->cycles < s->p.max_cycles)) {
+      // `per` FP32 V-cycles on L d = r (each continuing from the last) per
+      // refinement of the FP64-accurate residual, the bandwidth-heavy part
+      const int left = fixed ? s->p.fixed_cycles - s->cycles : s->p.max_cycles - s->cycles;
+      const int inner = left < per ? left : per;
       for (int k = 0; k < inner; ++k) vcycle(0, k == 0);   // d starts at zero in each refinement
       s->cycles += inner - 1;
       if ((rc = launch_check(ctx, "mixed V-cycle"))) return rc;
@@ -1389,7 +1515,7 @@ struct MG {
     CLC_LAUNCH(ctx, "k_combine", k_combine_ff, grid3(n, n, s->npatch), dim3(kBX, kBY), 0, (double*)s->base.p,
                (const float2*)cur, n);
     if ((rc = launch_check(ctx, "MG combine"))) return rc;
-    if (!fixed && rr >= s->p.tol) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
+    if (!fixed && rr >= limit) return set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
     return CLC_OK;
   }
 
@@ -1404,22 +1530,24 @@ struct MG {
     double rr = 0.0;
     s->cycles = 0;
     int st = CLC_OK;
+    const bool tau = tau_rule();
+    const double limit = tau ? s->p.eps : s->p.tol;
     if (s->p.fixed_cycles > 0) {
       for (int k = 0; k < s->p.fixed_cycles; ++k) {
         vcycle(0, false);
         if ((rc = launch_check(ctx, "V-cycle"))) return rc;
       }
       s->cycles = s->p.fixed_cycles;
-      if ((rc = residual(&rr))) return rc;
+      if ((rc = residual(&rr, tau))) return rc;
     } else {
-      if ((rc = residual(&rr))) return rc;
-      while (rr >= s->p.tol && s->cycles < s->p.max_cycles) {
+      if ((rc = residual(&rr, tau))) return rc;
+      while (rr >= limit && s->cycles < s->p.max_cycles) {
         vcycle(0, false);
         if ((rc = launch_check(ctx, "V-cycle"))) return rc;
         ++s->cycles;
-        if ((rc = residual(&rr))) return rc;
+        if ((rc = residual(&rr, tau))) return rc;
       }
-      if (rr >= s->p.tol) st = set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
+      if (rr >= limit) st = set_err(ctx, CLC_ENOTCONVERGED, "MG stopped at max_cycles above tol");
     }
     s->residual = rr;
     if ((rc = finish())) return rc;
@@ -1581,6 +1709,9 @@ static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
     return set_err(ctx, CLC_EINVAL, "MG: need 0 <= nu1, nu2 <= 8, nu1 + nu2 >= 1 and cycle counts >= 0");
   if (p->precision != CLC_FP64 && p->precision != CLC_FP32 && p->precision != CLC_MIXED)
     return set_err(ctx, CLC_EINVAL, "MG: bad precision");
+  if ((p->stop_rule != CLC_STOP_RESIDUAL && p->stop_rule != CLC_STOP_TAU) ||
+      (p->stop_rule == CLC_STOP_TAU && !(p->eps > 0.0)) || p->refine_cycles < 0 || p->refine_cycles > 16)
+    return set_err(ctx, CLC_EINVAL, "MG: bad stopping rule, eps or refine_cycles");
   return CLC_OK;
 }
 
@@ -1703,6 +1834,8 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   const int nc = s->sizes.back();
   const size_t ns2 = 12ull * p->nside_sht * p->nside_sht;
   ok = ok && alloc(s->rot, 9 * sizeof(double) * s->npatch) && alloc(s->coarse_inv, sizeof(double) * nc * nc * nc * nc) &&
+       alloc(s->tau2, sizeof(double) * s->npatch) &&
+       alloc(s->gc, sizeof(double) * s->npatch * 4 * (s->nlev > 1 ? s->sizes[1] : 1)) &&
        alloc(s->psi_sht, sizeof(double) * ns2) && alloc(s->kappa_sht, sizeof(double) * ns2) &&
        alloc(s->norms, sizeof(double) * s->npatch) && alloc(s->ratio, sizeof(double));
   if (!ok) {

@@ -38,6 +38,8 @@ struct clc_plane_solution {
   clc::Buffer norms;            // double[npatch][2]
   clc::Buffer ratio;            // double[1]
   clc::Buffer wrow;             // double[n]: sin theta'_i of the finest rows (adjoint solve)
+  clc::Buffer gc;               // double[npatch][4][n/2]: 2 psi_SHT at the coarse edge faces (tau rule)
+  clc::Buffer tau2;             // double[npatch]: ||tau||^2 over the coarse cells (tau rule)
   int cycles = 0;
   double residual = 0;
 };

@@ -176,3 +176,26 @@ def test_nside2048_plane_sampled_bundles_match_oracle():
         assert bool(torch.isfinite(want[k]).all())
         # as above; measured 1.2e-9 on GB300 (u_tt)
         assert errs[k] < 1e-8, (k, errs)
+
+
+def test_mixed_square_block_kernels_reproduce_fp64_iterate():
+    """Patches wider than a row band (512 cells) run the square-block
+    kernels on the finest level: CLC_MIXED against CLC_FP64 at the same
+    cycle count, as for the band kernels."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, ns, lmax, nb, ncell, cyc = 128, 32, 64, 2, 512, 4
+    z, phi = synthetic.lognormal_particles(1_000_000, 1210002)
+    kappa = binning.kappa_from_counts(binning.bin_counts(nf, z, phi), z.numel() / hp.npix(nf), 1.0).cuda()
+    s64 = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.FP64, fixed=cyc))
+    ref = c.poisson_shtmg(kappa, nf, s64, derivatives=True)
+    c.sync()
+    s64.close()
+    sx = c.solution(nf, _params(clc, ns, lmax, nb, ncell, clc.MIXED, fixed=cyc))
+    got = c.poisson_shtmg(kappa, nf, sx, derivatives=True)
+    c.sync()
+    errs = {k: rel_l2(got[k], ref[k]) for k in KEYS}
+    print("mixed square blocks", errs)
+    for k in KEYS:
+        assert errs[k] < 1e-8, (k, errs)
+    sx.close()

@@ -227,3 +227,49 @@ def test_invalid_mg_parameters():
         c.solution(64, _params(clc, 16, 32, 4, 48))       # ncell not a power of two
     with pytest.raises(clc.CalclensError):
         c.solution(64, _params(clc, 16, 32, 4, 32, nu1=9))  # more sweeps than the block halo allows
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.01])
+def test_tau_stopping_rule_matches_oracle(eps):
+    """The paper's rule ||r|| < eps ||tau|| (Sec. 3.2) in FP64: the GPU stops
+    after the same number of V-cycles as the oracle, with the same fields."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, ns, lmax, nb, ncell = 64, 16, 32, 4, 32
+    kappa = _kappa(nf, 25)
+    P = clc.mg_params(ns, lmax, nb, ncell=ncell, stop_rule=clc.STOP_TAU, eps=eps, precision=clc.FP64)
+    sol = c.solution(nf, P)
+    got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
+    c.sync()
+    cyc, ratio = sol.info()
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, stop="tau", eps=eps)
+    assert cyc == ref["cycles"] and ratio < eps
+    assert abs(ratio - ref["residual"]) <= 1e-8 * ref["residual"]
+    home, nv = _pixel_home(nf, nb)
+    want = omg.fields_at(ref, nb, nv, home)
+    for k in KEYS:
+        assert rel_l2(got[k], want[k]) < TOL, k
+    sol.close()
+
+
+def test_tau_stopping_rule_mixed_precision():
+    """CLC_MIXED with the tau rule checked after every V-cycle
+    (refine_cycles = 1): the same cycle count as the FP64 oracle and its
+    fields at that count to the mixed path's level."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf, ns, lmax, nb, ncell = 64, 16, 32, 4, 64
+    kappa = _kappa(nf, 26)
+    P = clc.mg_params(ns, lmax, nb, ncell=ncell, stop_rule=clc.STOP_TAU, eps=0.1, precision=clc.MIXED,
+                      refine_cycles=1)
+    sol = c.solution(nf, P)
+    got = c.poisson_shtmg(kappa.cuda(), nf, sol, derivatives=True)
+    c.sync()
+    cyc, ratio = sol.info()
+    ref = omg.solve_plane(kappa, nf, ns, lmax, nb, ncell=ncell, stop="tau", eps=0.1)
+    assert cyc == ref["cycles"] and ratio < 0.1
+    home, nv = _pixel_home(nf, nb)
+    want = omg.fields_at(ref, nb, nv, home)
+    for k in KEYS:
+        assert rel_l2(got[k], want[k]) < 1e-7, k
+    sol.close()

@@ -69,3 +69,61 @@ def test_point_mass_errors_on_the_gpu_path():
         bias, rms, mx = fine[name]
         assert abs(bias) < 2e-3 and rms < 1e-2 and mx < 5e-2, (name, fine[name])
         assert coarse[name][1] > 1.5 * rms, (name, coarse[name], fine[name])
+
+
+def test_point_mass_trends_at_nside2048():
+    """The Sec. 4.1 / Fig. 2 measurements at the throughput configuration's
+    scale: a smoothed unit mass on the Nside-2048 sphere solved by SHT+MG on
+    every patch (mixed precision), deflection and tangential shear against the
+    closed forms.  Trends: a finer SHT grid (nside_sht 1024 against 512)
+    lowers the errors; larger bundles (Nside 16 with 512-cell patches against
+    Nside 32 with 256, the same MG cell) move the errors outwards; the paper's
+    stopping rule with eps = 0.1 and 0.01 stops after a few V-cycles at the
+    converged solution's errors."""
+    import paper_1210_3069_gb300 as clc
+    c = ctx()
+    nf = 2048
+    kappa, cen, c0, d, sig, h = smoothed_point_mass(nf, seed=1)
+    idx = torch.nonzero((d > 8 * h) & (d < 0.25)).flatten()
+    kd = kappa.cuda()
+    idx_d = idx.cuda()
+
+    def run(ns, lmax, nb, ncell, **kw):
+        sol = c.solution(nf, clc.mg_params(ns, lmax, nb, ncell=ncell, precision=clc.MIXED, **kw))
+        got = c.poisson_shtmg(kd, nf, sol, derivatives=True)
+        c.sync()
+        cyc = sol.info()[0]
+        sol.close()
+        sel = {k: v[idx_d].cpu() for k, v in got.items()}
+        # point_mass_errors indexes full maps: hand it maps that hold the selected values
+        maps = {}
+        for k, v in sel.items():
+            m = torch.zeros(d.numel(), dtype=F64)
+            m[idx] = v
+            maps[k] = m
+        out = point_mass_errors(maps, cen, c0, d, sig, h)
+        a_ref = torch.from_numpy(ep_alpha_gamma(d[idx].numpy(), sig)[0])
+        t, q = geometry.basis(cen[idx])
+        er = cen[idx] * (cen[idx] @ c0)[:, None] - c0
+        er = er / torch.linalg.vector_norm(er, dim=-1, keepdim=True)
+        a_r = ((sel["a_th"][:, None] * t + sel["a_ph"][:, None] * q) * er).sum(-1)
+        e2 = ((a_r - a_ref) / a_ref.abs()) ** 2
+        out["centroid"] = float((e2 * d[idx]).sum() / e2.sum())
+        out["cycles"] = cyc
+        return out
+
+    base = run(512, 1024, 32, 256)
+    fine_sht = run(1024, 2048, 32, 256)
+    big = run(512, 1024, 16, 512)
+    e1 = run(512, 1024, 32, 256, stop_rule=clc.STOP_TAU, eps=0.1, refine_cycles=1)
+    e2 = run(512, 1024, 32, 256, stop_rule=clc.STOP_TAU, eps=0.01, refine_cycles=1)
+    for tag, r in (("base", base), ("sht1024", fine_sht), ("nb16", big), ("eps0.1", e1), ("eps0.01", e2)):
+        print("point mass Nside 2048", tag, r)
+    for name in ("alpha", "gamma_t"):
+        bias, rms, mx = base[name]
+        assert abs(bias) < 2e-3 and rms < 1e-2 and mx < 5e-2, (name, base[name])
+        assert fine_sht[name][1] < base[name][1] / 1.5, (name, fine_sht[name], base[name])
+        assert abs(e1[name][1] - base[name][1]) < 0.02 * base[name][1], (name, e1[name], base[name])
+        assert abs(e2[name][1] - base[name][1]) <= abs(e1[name][1] - base[name][1]) + 1e-12, name
+    assert e1["cycles"] <= e2["cycles"] < base["cycles"]
+    assert big["centroid"] > 1.3 * base["centroid"], (big["centroid"], base["centroid"])
