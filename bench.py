@@ -90,6 +90,17 @@ ADJOINT_WORKLOADS = {
 }
 ADJOINT_METRIC = "loss+gradient evaluations/s (galaxy shear through SHT planes, adjoint w.r.t. all kappa maps)"
 
+# multiple-plane ray tracing through a light cone of SHT+MG planes: every ray
+# of the Nside grid traced through all planes (one step = one traversal), then
+# the kappa, E, B and omega spectra of the final Jacobians in the image basis
+LIGHTCONE_WORKLOADS = {
+    "lightcone_nside2048": dict(nplanes=40, dchi=50.0, particles=20_000_000, nside=2048, nside_sht=512, lmax=1024,
+                                nside_bundle=32, ncell=256, tol=1e-10, seed=1210003, spectra_lmax=1024),
+    "lightcone_small": dict(nplanes=8, dchi=50.0, particles=2_000_000, nside=256, nside_sht=64, lmax=128,
+                            nside_bundle=8, ncell=128, tol=1e-10, seed=1210003, spectra_lmax=256),
+}
+LIGHTCONE_METRIC = "rays/s (full traversal of the light cone's SHT+MG planes, rays on every pixel centre)"
+
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
 # FP64 operations of one ray step on an SHT+MG plane (k_ray_step, patch
 # lookup included), counted operation by operation on the formulas of the
@@ -953,6 +964,106 @@ def batch_line(args, wl, r):
     }
 
 
+def run_lightcone(args, wl):
+    """40 shells of 50 Mpc/h (flat LCDM, Om = 0.25), each a seeded lognormal
+    plane scaled by the linear growth factor and Poisson-sampled to
+    `particles`; one timed step traces every ray of the Nside grid through all
+    planes (binning, kappa, SHT+MG solve, ray step per plane) and takes the
+    spectra of the final Jacobians (carried to the image basis)."""
+    import paper_1210_3069_gb300 as clc
+    clc.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ctx = clc.Context(0)
+    N, nf = wl["nplanes"], wl["nside"]
+    npix = 12 * nf * nf
+    pl = cosmology.lens_planes(N, wl["dchi"])
+    chi = pl["chi"]
+    parts = [synthetic.lognormal_particles(wl["particles"], wl["seed"] + m, device=dev, growth=pl["growth"][m])
+             for m in range(N)]
+    prec = {"fp32": clc.FP32, "fp64": clc.FP64, "mixed": clc.MIXED}[args.precision]
+    P = clc.mg_params(wl["nside_sht"], wl["lmax"], wl["nside_bundle"], ncell=wl["ncell"], tol=wl["tol"],
+                      precision=prec)
+    sol = ctx.solution(nf, P)
+    rays = ctx.rays(npix)
+    counts = torch.zeros(npix, dtype=torch.int32, device=dev)
+    kappa = torch.empty(npix, dtype=torch.float64, device=dev)
+    cycles = []
+
+    def traverse():
+        ctx.rays_init_pixels(rays, nf, chi[0], wl["nside_bundle"])
+        for m in range(N):
+            z, phi = parts[m]
+            counts.zero_()
+            ctx.bin_particles(z, phi, nf, counts=counts)
+            ctx.counts_to_kappa(counts, nf, z.numel() / npix, pl["scale"][m], kappa=kappa)
+            ctx.poisson_shtmg(kappa, nf, sol, check=False)
+            cycles.append(sol.info()[0])
+            ctx.ray_step(rays, chi[m - 1] if m else 0.0, chi[m], chi[m + 1], sol=sol)
+        return ctx.lensing_spectra(rays.A, nf, wl["spectra_lmax"], x=rays.x)
+
+    for _ in range(max(1, args.warmup)):
+        traverse()
+    torch.cuda.synchronize()
+    cycles.clear()
+    launches0 = ctx.launch_count()
+    ctx.profile(True)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clocks:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            cl = traverse()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    prof = {k: ctx.profile_query(k) for k in KERNELS}
+    ctx.profile(False)
+    sol.close()
+    return dict(ms=ms, launches=launches, clocks=clocks.summary(), cycles=cycles, cl={k: v.cpu() for k, v in cl.items()},
+                prof=prof, npix=npix)
+
+
+def lightcone_line(args, wl, r):
+    nf, N = wl["nside"], wl["nplanes"]
+    ms_step = r["ms"] / args.steps
+    cl = r["cl"]
+    L = wl["spectra_lmax"]
+    l = torch.arange(L + 1, dtype=torch.float64)
+    s_l = torch.where(l >= 2, (l + 2) * (l - 1) / torch.where(l > 0, l * (l + 1), torch.ones_like(l)),
+                      torch.zeros_like(l))
+    bands = []
+    lo = 8
+    while lo < L:
+        hi = min(4 * lo, L + 1)
+        sel = (l >= lo) & (l < hi)
+        bands.append({"l": [lo, hi - 1],
+                      "E_over_s_kappa": float(cl["E"][sel].sum() / (s_l[sel] * cl["kappa"][sel]).sum()),
+                      "B_over_s_omega": float(cl["B"][sel].sum() / (s_l[sel] * cl["omega"][sel]).sum()),
+                      "B_over_E": float(cl["B"][sel].sum() / cl["E"][sel].sum())})
+        lo = hi
+    return {
+        "metric": LIGHTCONE_METRIC, "value": r["npix"] / (ms_step / 1000.0), "unit": "rays/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "fp32": "f32", "mixed": "f32+f64"}[args.precision],
+        "data": "synthetic",
+        "config": {"workload": args.workload, **{k: v for k, v in wl.items() if k != "seed"}, "rays": r["npix"],
+                   "precision": args.precision, "l2": "inputs larger than L2 (no flush)"},
+        "ray_plane_steps_per_s": r["npix"] * N / (ms_step / 1000.0),
+        "planes_per_s": N / (ms_step / 1000.0),
+        "mg_cycles": sorted(set(r["cycles"])),
+        "spectra_bands": bands,
+        "stage_ms_per_step": {k: round(v[1] / args.steps, 3) for k, v in r["prof"].items()},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "e2e": None,
+        "e2e_note": "the light cone's particles (16 B each, all planes) stay resident; the default workload's line "
+                    "carries the end-to-end number",
+    }
+
+
 # ---------------------------------------------------------------------------
 # the FP64 oracle on a bounded sample of the same workload
 
@@ -1044,7 +1155,7 @@ def main():
                     help="MG arithmetic: fp64, fp32, or mixed (FP32 V-cycles on an FP64 residual equation)")
     ap.add_argument("--workload", default="shtmg_plane_nside2048",
                     choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS)
-                    + sorted(SMOOTH_WORKLOADS) + sorted(IMAGE_WORKLOADS))
+                    + sorted(SMOOTH_WORKLOADS) + sorted(IMAGE_WORKLOADS) + sorted(LIGHTCONE_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--refine-cycles", type=int, default=0,
                     help="mixed precision: FP32 V-cycles per float-float residual refinement (0: the library's 2)")
@@ -1059,6 +1170,16 @@ def main():
             return
         wl = ADJOINT_WORKLOADS[args.workload]
         print(json.dumps(adjoint_line(args, wl, run_adjoint(args, wl))))
+        return
+    if args.workload in LIGHTCONE_WORKLOADS:
+        if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:
+            if int(os.environ.get("RANK", "0")) == 0:
+                print(json.dumps({"impl": args.impl, "metric": LIGHTCONE_METRIC,
+                                  "unavailable": "the light-cone workload runs on one GPU; the oracle's per-plane "
+                                                 "cost is in the default workload's cpu_baseline"}))
+            return
+        wl = LIGHTCONE_WORKLOADS[args.workload]
+        print(json.dumps(lightcone_line(args, wl, run_lightcone(args, wl))))
         return
     if args.workload in SMOOTH_WORKLOADS:
         if args.impl == "reference" or int(os.environ.get("WORLD_SIZE", "1")) > 1:

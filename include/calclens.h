@@ -157,6 +157,15 @@ int clc_smooth_particles(clc_ctx* ctx, const double* z, const double* phi, int64
 int clc_density_to_kappa(clc_ctx* ctx, const double* rho, int nside, double nbar, double scale,
                          double* kappa);
 
+/* Partial-sky source (Sec. 3.4): for a light cone that covers only the RING
+ * pixels with covered[p] != 0 (uint8 mask), kappa[p] = scale * (counts[p] /
+ * nbar - 1) on covered pixels with nbar = (particles in covered pixels) /
+ * (number of covered pixels), the light cone's own mean density, and 0 (matter
+ * at the mean density) elsewhere, so that kappa has no monopole.  Integer
+ * sums, then the operations of clc_counts_to_kappa: reproducible bit for bit. */
+int clc_counts_to_kappa_masked(clc_ctx* ctx, const uint32_t* counts, const uint8_t* covered, int nside,
+                               double scale, double* kappa);
+
 /* Coarse RING map = mean of the (nside_fine / nside_coarse)^2 NEST children of
  * every coarse pixel (children summed in NEST order): equal to binning the
  * same particles at nside_coarse. */
@@ -242,6 +251,17 @@ int clc_sht_plan_destroy(clc_sht_plan* plan);
 int clc_solution_create(clc_ctx* ctx, int nside_fine, const clc_mg_params* params,
                         clc_plane_solution** sol);
 int clc_solution_destroy(clc_plane_solution* sol);
+/* Partial sky (Sec. 3.4): the SHT still runs over the full sky, but MG
+ * patches exist only for the nbundles distinct NEST bundles listed in
+ * bundles_host (each < 12 nside_bundle^2), so memory and time scale with the
+ * domain.  Lookups (clc_poisson_shtmg outputs, clc_lens_derivs, clc_ray_step,
+ * galaxy traces) of points whose bundle has no patch return zero lens fields
+ * (matter at the mean density does not deflect) and are counted. */
+int clc_solution_create_domain(clc_ctx* ctx, int nside_fine, const clc_mg_params* params, const int32_t* bundles_host,
+                               int nbundles, clc_plane_solution** sol);
+/* Number of patches of the solution and the lookups outside its domain since
+ * its last solve (0 on the full sky); waits for the context's stream. */
+int clc_solution_domain(const clc_plane_solution* sol, int* npatch_host, int64_t* outside_host);
 /* V-cycles run and final max residual ratio of the last solve into sol. */
 int clc_solution_info(const clc_plane_solution* sol, int* cycles_host, double* residual_host);
 

@@ -70,6 +70,10 @@ _SIGS = {
                                    ctypes.POINTER(Derivs)]),
     "clc_solution_create": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(_p)]),
     "clc_solution_destroy": (_i, [_p]),
+    "clc_solution_create_domain": (_i, [_p, _i, ctypes.POINTER(MGParams), ctypes.POINTER(ctypes.c_int32), _i,
+                                        ctypes.POINTER(_p)]),
+    "clc_solution_domain": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_i64)]),
+    "clc_counts_to_kappa_masked": (_i, [_p, _p, _p, _i, _d, _p]),
     "clc_solution_info": (_i, [_p, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "clc_poisson_shtmg": (_i, [_p, _p, _i, ctypes.POINTER(MGParams), _p, ctypes.POINTER(Derivs)]),
     "clc_lens_derivs": (_i, [_p, _p, _p, _p, _p, _i64, ctypes.POINTER(Derivs)]),
@@ -206,6 +210,17 @@ class Context:
         self._check(lib().clc_counts_to_kappa(self.h, _ptr(counts), nside, float(nbar), float(scale), _ptr(kappa)))
         return kappa
 
+    def counts_to_kappa_masked(self, counts, covered, nside, scale, kappa=None):
+        """Partial-sky source: kappa from the counts of the covered pixels
+        (covered: uint8/bool map), 0 elsewhere, with the covered region's own
+        mean density."""
+        if kappa is None:
+            kappa = torch.empty(12 * nside * nside, dtype=torch.float64, device=self.device)
+        cov = covered.to(torch.uint8).contiguous()
+        self._check(lib().clc_counts_to_kappa_masked(self.h, _ptr(counts), _ptr(cov), nside, float(scale),
+                                                     _ptr(kappa)))
+        return kappa
+
     def smooth_particles(self, z, phi, nside, sigma=0.0, sigma_each=None, rho=None):
         """Epanechnikov-smoothed particle number per RING pixel (accumulated
         into rho, a new zero map if None)."""
@@ -334,8 +349,10 @@ class Context:
         return dict(zip(("kappa", "E", "B", "omega"), cl))
 
     # -- step 3 / 4 ---------------------------------------------------------
-    def solution(self, nside_fine, params):
-        return Solution(self, nside_fine, params)
+    def solution(self, nside_fine, params, domain=None):
+        """A plane's multigrid state; domain: NEST bundle indices of a partial
+        sky (None: every bundle)."""
+        return Solution(self, nside_fine, params, domain)
 
     def poisson_shtmg(self, kappa_fine, nside_fine, sol, derivatives=False, check=True):
         npx = 12 * nside_fine * nside_fine
@@ -398,13 +415,26 @@ class Context:
 class Solution:
     """Multigrid state of one plane (clc_plane_solution)."""
 
-    def __init__(self, ctx, nside_fine, params):
+    def __init__(self, ctx, nside_fine, params, domain=None):
         self.ctx = ctx
         self.params = params
         self.nside_fine = nside_fine
         h = ctypes.c_void_p()
-        ctx._check(lib().clc_solution_create(ctx.h, nside_fine, ctypes.byref(params), ctypes.byref(h)))
+        if domain is None:
+            ctx._check(lib().clc_solution_create(ctx.h, nside_fine, ctypes.byref(params), ctypes.byref(h)))
+        else:
+            d = [int(b) for b in domain]
+            arr = (ctypes.c_int32 * len(d))(*d)
+            ctx._check(lib().clc_solution_create_domain(ctx.h, nside_fine, ctypes.byref(params), arr, len(d),
+                                                        ctypes.byref(h)))
         self.h = h
+
+    def domain(self):
+        """(number of patches, lookups outside the domain since the last solve)."""
+        n = _i()
+        o = _i64()
+        self.ctx._check(lib().clc_solution_domain(self.h, ctypes.byref(n), ctypes.byref(o)))
+        return n.value, o.value
 
     def info(self):
         c = ctypes.c_int()

@@ -551,7 +551,7 @@ __device__ void fields_from_partials(const MGView& V, int b, const PatchGeo<S>& 
   out[4] = m00 * q10 + m01 * q00;
 }
 
-// Lens values at nv in patch b (double or dual scalar)
+// Lens values at nv in patch slot b (double or dual scalar)
 template <typename S>
 __device__ void patch_eval(const MGView& V, int b, const S nv[3], S out[5]) {
   PatchGeo<S> G;
@@ -673,8 +673,17 @@ struct LensSrc {
 
 template <bool kMG, typename S>
 __device__ __forceinline__ void lens_at(const LensSrc& src, int64_t k, const S nv[3], S L[5]) {
-  if (kMG) patch_eval<S>(src.V, src.bundle[k], nv, L);
-  else lens_eval<S>(src.M, src.nside, nv, L);
+  if (kMG) {
+    const int slot = mg_slot(src.V, src.bundle[k]);
+    if (slot >= 0) {
+      patch_eval<S>(src.V, slot, nv, L);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 5; ++c) L[c] = Lift<S>::of(0.0);   // outside a partial sky's domain
+    }
+  } else {
+    lens_eval<S>(src.M, src.nside, nv, L);
+  }
 }
 
 template <bool kMG>
@@ -765,8 +774,12 @@ __global__ void __launch_bounds__(128) k_gal_step_adjoint(const double* __restri
     for (int c = 0; c < 14; ++c) adj[c * n + k] = ib[c];
     const double xn = ::sqrt(in0[0] * in0[0] + in0[1] * in0[1] + in0[2] * in0[2]);
     const double nv[3] = {in0[0] / xn, in0[1] / xn, in0[2] / xn};
-    if (kMG) patch_scatter(src.V, src.bundle[k], nv, Lb, ubar);
-    else lens_scatter(Mbar, src.nside, nv, Lb);
+    if (kMG) {
+      const int slot = src.V.slot ? src.V.slot[src.bundle[k]] : src.bundle[k];
+      if (slot >= 0) patch_scatter(src.V, slot, nv, Lb, ubar);
+    } else {
+      lens_scatter(Mbar, src.nside, nv, Lb);
+    }
   }
 }
 

@@ -25,6 +25,38 @@ __global__ void k_counts_to_kappa(const uint32_t* __restrict__ counts, int64_t n
   }
 }
 
+// Partial-sky source (Sec. 3.4): particle count and pixel count of the
+// covered region (exact integer sums), then nbar = their ratio and
+// kappa = scale (counts / nbar - 1) on covered pixels, 0 (mean density)
+// elsewhere.
+__global__ void k_masked_sums(const uint32_t* __restrict__ counts, const uint8_t* __restrict__ covered, int64_t npix,
+                              unsigned long long* __restrict__ sums) {
+  unsigned long long c = 0, m = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride)
+    if (covered[i]) {
+      c += counts[i];
+      ++m;
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    m += __shfl_xor_sync(0xffffffffu, m, o);
+  }
+  if ((threadIdx.x & 31) == 0 && (c || m)) {
+    atomicAdd(sums, c);
+    atomicAdd(sums + 1, m);
+  }
+}
+
+__global__ void k_counts_to_kappa_masked(const uint32_t* __restrict__ counts, const uint8_t* __restrict__ covered,
+                                         int64_t npix, const unsigned long long* __restrict__ sums, double scale,
+                                         double* __restrict__ kappa) {
+  const double nbar = __ddiv_rn((double)sums[0], (double)sums[1]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride)
+    kappa[i] = covered[i] ? __dmul_rn(scale, __dsub_rn(__ddiv_rn((double)counts[i], nbar), 1.0)) : 0.0;
+}
+
 // Coarse pixel P (RING) = mean of its NEST children at nside_fine.  The coarse
 // pixel's NEST index comes from its centre (pix2ang followed by ang2pix_nest,
 // which returns the pixel itself: centres lie far from pixel edges).
@@ -200,6 +232,22 @@ extern "C" int clc_counts_to_kappa(clc_ctx* ctx, const uint32_t* counts, int nsi
   const int64_t npix = 12ll * nside * nside;
   CLC_LAUNCH(ctx, "k_counts_to_kappa", k_counts_to_kappa, grid_for(ctx, npix, 256), 256, 0, counts, npix, nbar, scale, kappa);
   return launch_check(ctx, "k_counts_to_kappa");
+}
+
+extern "C" int clc_counts_to_kappa_masked(clc_ctx* ctx, const uint32_t* counts, const uint8_t* covered, int nside,
+                                          double scale, double* kappa) {
+  if (!ctx) return CLC_EINVAL;
+  if (!valid_nside(nside)) return set_err(ctx, CLC_EINVAL, "clc_counts_to_kappa_masked: bad nside");
+  if (!counts || !covered || !kappa) return set_err(ctx, CLC_EINVAL, "clc_counts_to_kappa_masked: null pointer");
+  cudaSetDevice(ctx->device);
+  const int64_t npix = 12ll * nside * nside;
+  unsigned long long* sums = (unsigned long long*)scratch(ctx, 7, 2 * sizeof(unsigned long long));
+  if (!sums) return CLC_ENOMEM;
+  cudaMemsetAsync(sums, 0, 2 * sizeof(unsigned long long), ctx->stream);
+  CLC_LAUNCH(ctx, "k_masked_sums", k_masked_sums, grid_for(ctx, npix, 256), 256, 0, counts, covered, npix, sums);
+  CLC_LAUNCH(ctx, "k_counts_to_kappa", k_counts_to_kappa_masked, grid_for(ctx, npix, 256), 256, 0, counts, covered,
+             npix, (const unsigned long long*)sums, scale, kappa);
+  return launch_check(ctx, "k_counts_to_kappa_masked");
 }
 
 extern "C" int clc_degrade(clc_ctx* ctx, const double* fine, int nf, double* coarse, int ns) {

@@ -33,6 +33,8 @@ MGView mg_view(const clc_plane_solution* sol) {
   v.inv_h = 1.0 / sol->h;
   v.rot = (const double*)sol->rot.p;
   v.u = (const double*)sol->base.p;
+  v.slot = sol->partial ? (const int32_t*)sol->bundle_slot.p : nullptr;
+  v.outside = sol->partial ? (unsigned long long*)sol->outside.p : nullptr;
   return v;
 }
 
@@ -107,9 +109,10 @@ __device__ __forceinline__ float2 from_double<float2>(double v) {
   return make_float2(h, d2f_rn(v - f2d_exact(h)));
 }
 
-__global__ void k_mg_rotations(int nb, int npatch, double* rot) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= npatch) return;
+__global__ void k_mg_rotations(int nb, int npatch, const int32_t* __restrict__ slot_bundle, double* rot) {
+  const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot >= npatch) return;
+  const int b = slot_bundle ? slot_bundle[slot] : slot;
   const int64_t rp = nest2ring(nb, b);
   int64_t j;
   const int i = pix2ring(nb, rp, &j);
@@ -117,7 +120,7 @@ __global__ void k_mg_rotations(int nb, int npatch, double* rot) {
   const double phi = r.phi0 + (2.0 * kPi) * (double)j / (double)r.npix;
   const double z = r.z, s = sqrt((1.0 - z) * (1.0 + z));
   const double cp = cos(phi), sp = sin(phi);
-  double* R = rot + 9 * (size_t)b;
+  double* R = rot + 9 * (size_t)slot;
   R[0] = s * cp; R[1] = s * sp; R[2] = z;
   R[3] = -sp;    R[4] = cp;     R[5] = 0.0;
   R[6] = -z * cp; R[7] = -z * sp; R[8] = s;
@@ -1719,17 +1722,31 @@ static int check_params(clc_ctx* ctx, int nf, const clc_mg_params* p) {
 
 using namespace clc;
 
-extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, clc_plane_solution** out) {
+static int solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, const int32_t* domain, int ndomain,
+                           clc_plane_solution** out) {
   if (!ctx || !out) return CLC_EINVAL;
   *out = nullptr;
   int rc = check_params(ctx, nf, p);
   if (rc) return rc;
+  const int nbund = 12 * p->nside_bundle * p->nside_bundle;
+  std::vector<int32_t> bslot;
+  if (domain) {
+    if (ndomain < 1 || ndomain > nbund) return set_err(ctx, CLC_EINVAL, "solution domain: 1 .. 12 nside_bundle^2 bundles");
+    bslot.assign(nbund, -1);
+    for (int k = 0; k < ndomain; ++k) {
+      const int b = domain[k];
+      if (b < 0 || b >= nbund || bslot[b] >= 0)
+        return set_err(ctx, CLC_EINVAL, "solution domain: bundles must be distinct NEST indices below 12 nside_bundle^2");
+      bslot[b] = k;
+    }
+  }
   cudaSetDevice(ctx->device);
   auto* s = new clc_plane_solution();
   s->ctx = ctx;
   s->nside_fine = nf;
   s->p = *p;
-  s->npatch = 12 * p->nside_bundle * p->nside_bundle;
+  s->partial = domain != nullptr;
+  s->npatch = domain ? ndomain : nbund;
   s->h = 4.0 * std::sqrt(kPi / 3.0) / p->nside_bundle / p->ncell;
   for (int n = p->ncell;; n /= 2) {
     s->sizes.push_back(n);
@@ -1833,6 +1850,15 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   }
   const int nc = s->sizes.back();
   const size_t ns2 = 12ull * p->nside_sht * p->nside_sht;
+  if (ok && s->partial) {
+    ok = alloc(s->slot_bundle, sizeof(int32_t) * s->npatch) && alloc(s->bundle_slot, sizeof(int32_t) * nbund) &&
+         alloc(s->outside, sizeof(unsigned long long));
+    if (ok) {
+      cudaMemcpy(s->slot_bundle.p, domain, sizeof(int32_t) * s->npatch, cudaMemcpyHostToDevice);
+      cudaMemcpy(s->bundle_slot.p, bslot.data(), sizeof(int32_t) * nbund, cudaMemcpyHostToDevice);
+      cudaMemset(s->outside.p, 0, sizeof(unsigned long long));
+    }
+  }
   ok = ok && alloc(s->rot, 9 * sizeof(double) * s->npatch) && alloc(s->coarse_inv, sizeof(double) * nc * nc * nc * nc) &&
        alloc(s->tau2, sizeof(double) * s->npatch) &&
        alloc(s->gc, sizeof(double) * s->npatch * 4 * (s->nlev > 1 ? s->sizes[1] : 1)) &&
@@ -1864,7 +1890,7 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
     cudaMemcpy(s->coarse_inv.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
   CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch,
-             (double*)s->rot.p);
+             s->partial ? (const int32_t*)s->slot_bundle.p : nullptr, (double*)s->rot.p);
   // interpolation plans, if they fit with 4 GiB to spare
   {
     const size_t pr = (size_t)s->npatch * (n0 + 2) * (n0 + 2), pk = (size_t)s->npatch * n0 * n0;
@@ -1898,6 +1924,33 @@ extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p,
   return CLC_OK;
 }
 
+extern "C" int clc_solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, clc_plane_solution** out) {
+  return solution_create(ctx, nf, p, nullptr, 0, out);
+}
+
+extern "C" int clc_solution_create_domain(clc_ctx* ctx, int nf, const clc_mg_params* p, const int32_t* bundles_host,
+                                          int nbundles, clc_plane_solution** out) {
+  if (!bundles_host) return ctx ? set_err(ctx, CLC_EINVAL, "clc_solution_create_domain: null bundle list") : CLC_EINVAL;
+  return solution_create(ctx, nf, p, bundles_host, nbundles, out);
+}
+
+extern "C" int clc_solution_domain(const clc_plane_solution* s, int* npatch_host, int64_t* outside_host) {
+  if (!s || !s->ctx) return CLC_EINVAL;
+  if (npatch_host) *npatch_host = s->npatch;
+  if (outside_host) {
+    *outside_host = 0;
+    if (s->partial) {
+      unsigned long long v = 0;
+      int rc = cuda_check(s->ctx, cudaStreamSynchronize(s->ctx->stream), "domain sync");
+      if (rc) return rc;
+      rc = cuda_check(s->ctx, cudaMemcpy(&v, s->outside.p, sizeof(v), cudaMemcpyDeviceToHost), "outside count");
+      if (rc) return rc;
+      *outside_host = (int64_t)v;
+    }
+  }
+  return CLC_OK;
+}
+
 extern "C" int clc_solution_destroy(clc_plane_solution* s) {
   if (!s) return CLC_EINVAL;
   if (s->ctx) cudaStreamSynchronize(s->ctx->stream);
@@ -1923,6 +1976,7 @@ extern "C" int clc_poisson_shtmg(clc_ctx* ctx, const double* kappa_fine, int nf,
     return set_err(ctx, CLC_EINVAL, "clc_poisson_shtmg: solution was created for other parameters");
   cudaSetDevice(ctx->device);
   s->p = *p;
+  if (s->partial) cudaMemsetAsync(s->outside.p, 0, sizeof(unsigned long long), ctx->stream);
   // global SHT step on kappa binned at the SHT resolution
   if ((rc = clc_degrade(ctx, kappa_fine, nf, (double*)s->kappa_sht.p, p->nside_sht))) return rc;
   if ((rc = clc_poisson_sht(ctx, (const double*)s->kappa_sht.p, p->nside_sht, p->lmax, CLC_FP64,

@@ -39,6 +39,11 @@ struct clc_plane_solution {
   clc::Buffer ratio;            // double[1]
   clc::Buffer wrow;             // double[n]: sin theta'_i of the finest rows (adjoint solve)
   clc::Buffer gc;               // double[npatch][4][n/2]: 2 psi_SHT at the coarse edge faces (tau rule)
+  // partial sky (Sec. 3.4): patches only for a domain's bundles
+  bool partial = false;
+  clc::Buffer slot_bundle;      // int32[npatch]: NEST bundle of each patch slot
+  clc::Buffer bundle_slot;      // int32[12 nside_bundle^2]: slot of each bundle, -1 outside the domain
+  clc::Buffer outside;          // uint64: lookups outside the domain since the last solve
   clc::Buffer tau2;             // double[npatch]: ||tau||^2 over the coarse cells (tau rule)
   int cycles = 0;
   double residual = 0;
@@ -53,6 +58,8 @@ struct MGView {
   double inv_h;    // 1 / h
   const double* rot;
   const double* u; // finest level potential u = u_SHT + e (ghost-ring layout)
+  const int32_t* slot;           // bundle -> patch slot (NULL: slot = bundle); -1 outside the domain
+  unsigned long long* outside;   // lookups of bundles outside the domain (partial sky)
 };
 
 MGView mg_view(const clc_plane_solution* sol);

@@ -210,10 +210,27 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   out[4] = m00 * q10 + m01 * q00;            // U_tp
 }
 
+// Patch slot of bundle b: the bundle itself on the full sky, the domain's
+// slot map on a partial sky (-1: the bundle has no patch; the lookup is
+// counted and gives zero fields, the lens action of matter at the mean
+// density, Sec. 3.4).
+__device__ __forceinline__ int mg_slot(const MGView& V, int b) {
+  if (!V.slot) return b;
+  const int s = V.slot[b];
+  if (s < 0 && V.outside) atomicAdd(V.outside, 1ull);
+  return s;
+}
+
 __device__ __forceinline__ void patch_lens_fields(const MGView& V, int b, const double nv[3], const double et[3],
                                                   const double ep[3], double out[5]) {
+  const int s = mg_slot(V, b);
+  if (s < 0) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) out[k] = 0.0;
+    return;
+  }
   const size_t stride = (size_t)(V.n + 2) * (V.n + 2);
-  patch_lens_fields_t(V.u + stride * b, V.n, V.h, V.inv_h, V.rot + 9 * (size_t)b, nv, et, ep, out);
+  patch_lens_fields_t(V.u + stride * s, V.n, V.h, V.inv_h, V.rot + 9 * (size_t)s, nv, et, ep, out);
 }
 
 }  // namespace clc
