@@ -275,6 +275,15 @@ def plane_seed(cfg, rank):
     return cfg["seed"] + rank
 
 
+def bundle_range(nside_bundle, rank, world):
+    """Contiguous NEST bundle range [lo, hi) of one rank when one plane's MG
+    patches and rays are split over ranks (Sec. 3.1: bundles are the unit of
+    work, NEST order keeps each range compact on the sphere): the 12 N_b^2
+    bundles in near-equal consecutive shares."""
+    nb = 12 * nside_bundle * nside_bundle
+    return nb * rank // world, nb * (rank + 1) // world
+
+
 def max_over_ranks(value, device):
     """The largest value over all ranks (a job's time is that of its slowest
     rank); the value itself without a process group."""
