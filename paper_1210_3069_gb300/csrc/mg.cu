@@ -78,6 +78,14 @@ __device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
   return ff_fast_sum(p, e);
 }
 
+// Float-float sum with one two-sum (the low words added directly): its error
+// stays below about 2^-47 (|a| + |b|), the precision the residual needs,
+// whose terms it sums (a residual is accurate only relative to its terms).
+__device__ __forceinline__ float2 ff_add_lite(float2 a, float2 b) {
+  const float2 s = ff_two_sum(a.x, b.x);
+  return ff_fast_sum(s.x, s.y + (a.y + b.y));
+}
+
 // Position of cell (i, j) in a patch's source array (n x n cells, n even):
 // the red cells ((i + j) even) first, then the black ones, each colour row by
 // row, so that a colour's sweep reads its sources contiguously.
@@ -1029,6 +1037,83 @@ __global__ void k_resid_ff(const float2* __restrict__ e_old, const float* __rest
   if (threadIdx.x == 0 && rr != 0.f) atomicAdd(norms + b, (double)rr);
 }
 
+// The same residual with each thread walking kWalk rows of one column pair
+// (2k, 2k + 1): every e + d is formed once, kept for the rows above and
+// below in registers, and handed to the horizontal neighbours by warp
+// shuffles; the sums use ff_add_lite.
+constexpr int kWalk = 16;
+
+__global__ void __launch_bounds__(kBX * kBY) k_resid_ff_walk(const float2* __restrict__ e_old,
+                                                              const float* __restrict__ d,
+                                                              const float2* __restrict__ fd,
+                                                              const float2* __restrict__ coef,
+                                                              const float2* __restrict__ diag, int n,
+                                                              float2* __restrict__ e_new, float* __restrict__ r32,
+                                                              double* __restrict__ norms) {
+  const int b = blockIdx.z, nh = n >> 1;
+  const int k = blockIdx.x * kBX + threadIdx.x;
+  const int lane = threadIdx.x;
+  const bool live = k < nh;
+  const size_t pb = (size_t)b * upatch(n), pl = uplane_of(n), P = upitch(n);
+  const float2* E = e_old + pb;
+  const float* D = d ? d + pb : nullptr;
+  auto ld = [&](int i, int col, int entry) -> float2 {   // e + d at colour `col`, row i, entry
+    const size_t o = (size_t)col * pl + (size_t)(i + 1 + kUHalo) * P + entry;
+    float2 v = E[o];
+    if (D) v = ff_add_f(v, D[o]);
+    return v;
+  };
+  const int i0 = (blockIdx.y * kBY + threadIdx.y) * kWalk;
+  if (i0 >= n) return;   // whole warps: every lane of the warp has the same rows
+  const int i1 = min(n, i0 + kWalk);
+  // cells (i, 2k) and (i, 2k + 1): entry k + 1 of colours i & 1 and (i + 1) & 1
+  float2 pa{0.f, 0.f}, pbv{0.f, 0.f}, ca{0.f, 0.f}, cbv{0.f, 0.f};
+  if (live) {
+    pa = ld(i0 - 1, (i0 - 1) & 1, k + 1);
+    pbv = ld(i0 - 1, i0 & 1, k + 1);
+    ca = ld(i0, i0 & 1, k + 1);
+    cbv = ld(i0, (i0 + 1) & 1, k + 1);
+  }
+  float rr = 0.f;
+  for (int i = i0; i < i1; ++i) {
+    float2 sa{0.f, 0.f}, sb{0.f, 0.f};
+    if (live) {
+      sa = ld(i + 1, (i + 1) & 1, k + 1);
+      sb = ld(i + 1, i & 1, k + 1);
+    }
+    // horizontal neighbours (i, 2k - 1) = lane - 1's second cell, (i, 2k + 2) = lane + 1's first
+    float2 w, e;
+    w.x = __shfl_up_sync(0xffffffffu, cbv.x, 1);
+    w.y = __shfl_up_sync(0xffffffffu, cbv.y, 1);
+    e.x = __shfl_down_sync(0xffffffffu, ca.x, 1);
+    e.y = __shfl_down_sync(0xffffffffu, ca.y, 1);
+    if (live) {
+      if (lane == 0) w = ld(i, (i + 1) & 1, k);          // entry k: column 2k - 1 (0 at the ghost ring)
+      if (lane == kBX - 1 || k == nh - 1) e = ld(i, i & 1, k + 2);
+      const float2 cS = coef[i], cN = coef[n + i], cB = coef[2 * n + i];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = 2 * k + h;
+        const float2 eC = h ? cbv : ca, eS = h ? sb : sa, eN = h ? pbv : pa;
+        const float2 eE = h ? e : cbv, eW = h ? ca : w;
+        const float2 nb = ff_add_lite(ff_add_lite(ff_mul(cS, eS), ff_mul(cN, eN)),
+                                      ff_add_lite(ff_mul(cB, ff_add_lite(eE, eW)), ff_neg(ff_mul(diag[i * n + j], eC))));
+        const size_t pos = (size_t)b * n * n + fidx(n, i, j);
+        const float2 r = ff_add_lite(fd[pos], ff_neg(nb));
+        r32[pos] = r.x + r.y;
+        e_new[pb + (size_t)((i + h) & 1) * pl + (size_t)(i + 1 + kUHalo) * P + (k + 1)] = eC;
+        rr = fmaf(r.x, r.x, rr);
+      }
+    }
+    pa = ca;
+    pbv = cbv;
+    ca = sa;
+    cbv = sb;
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  if (lane == 0 && rr != 0.f) atomicAdd(norms + b, (double)rr);
+}
+
 // final potential u = base + e for a float-float correction
 __global__ void k_combine_ff(double* __restrict__ base, const float2* __restrict__ e, int n) {
   const int b = blockIdx.z;
@@ -1477,8 +1562,8 @@ struct MG {
   int residual_mixed(const float2* e_old, const float* d, float2* e_new, double* ratio_host) {
     const int n = s->sizes[0];
     cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
-    const dim3 grid((n / 2 + kBX - 1) / kBX, (n + kBY * kRows - 1) / (kBY * kRows), s->npatch);
-    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_ff, grid, dim3(kBX, kBY), 0, e_old, d, (const float2*)s->fd64.p,
+    const dim3 grid((n / 2 + kBX - 1) / kBX, (n + kBY * kWalk - 1) / (kBY * kWalk), s->npatch);
+    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_ff_walk, grid, dim3(kBX, kBY), 0, e_old, d, (const float2*)s->fd64.p,
                (const float2*)s->coef_ff.p, (const float2*)s->diag_ff.p, n, e_new, (float*)s->f[0].p,
                (double*)s->norms.p);
     stop_ratio<float2>(e_new, tau_rule());

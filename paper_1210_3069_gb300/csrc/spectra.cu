@@ -27,33 +27,82 @@ __device__ __forceinline__ double eps_lm(int l, int m) {
   return sqrt(((double)l * l - (double)m * m) / (4.0 * l * l - 1.0));
 }
 
-// block (l-block, m): warp per l, lanes over the northern rings
+// block (l-block, m): warp per l (8 l per warp), lanes over the northern
+// rings, taken in chunks of kEbChunk rings staged in shared memory (the
+// ring sums of each l accumulate across chunks in registers)
+constexpr int kEbChunk = 1024;
+
 __global__ void k_legendre_eb(int nside, int lmax, int R, const long long* __restrict__ off,
                               const double* __restrict__ tab, const double2* __restrict__ F1,
                               const double2* __restrict__ F2, int ldf, double2* __restrict__ E,
                               double2* __restrict__ B) {
-  extern __shared__ double2 V[];  // [4][R]: F1 even/odd, F2 even/odd
+  extern __shared__ double2 V[];  // [4][kEbChunk]: F1 even/odd, F2 even/odd
   const int m = blockIdx.y;
   const int l0 = m + blockIdx.x * 64;
   if (l0 > lmax) return;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    const int i = r + 1;
-    const bool eq = i == 2 * nside;
-    const double2 a = F1[(size_t)m * ldf + i - 1], c = F2[(size_t)m * ldf + i - 1];
-    double2 as = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
-    if (!eq) {
-      as = F1[(size_t)m * ldf + 4 * nside - i - 1];
-      cs = F2[(size_t)m * ldf + 4 * nside - i - 1];
-    }
-    V[r] = make_double2(a.x + as.x, a.y + as.y);
-    V[R + r] = make_double2(a.x - as.x, a.y - as.y);
-    V[2 * R + r] = make_double2(c.x + cs.x, c.y + cs.y);
-    V[3 * R + r] = make_double2(c.x - cs.x, c.y - cs.y);
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const double* col = tab + off[m];
-  for (int l = l0 + warp; l <= lmax && l < l0 + 64; l += 8) {
+  double acc[8][4];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.0;
+  for (int c0 = 0; c0 < R; c0 += kEbChunk) {
+    const int cn = min(kEbChunk, R - c0);
+    __syncthreads();   // the previous chunk is consumed
+    for (int rr = threadIdx.x; rr < cn; rr += blockDim.x) {
+      const int i = c0 + rr + 1;
+      const bool eq = i == 2 * nside;
+      const double2 a = F1[(size_t)m * ldf + i - 1], c = F2[(size_t)m * ldf + i - 1];
+      double2 as = make_double2(0.0, 0.0), cs = make_double2(0.0, 0.0);
+      if (!eq) {
+        as = F1[(size_t)m * ldf + 4 * nside - i - 1];
+        cs = F2[(size_t)m * ldf + 4 * nside - i - 1];
+      }
+      V[rr] = make_double2(a.x + as.x, a.y + as.y);
+      V[kEbChunk + rr] = make_double2(a.x - as.x, a.y - as.y);
+      V[2 * kEbChunk + rr] = make_double2(c.x + cs.x, c.y + cs.y);
+      V[3 * kEbChunk + rr] = make_double2(c.x - cs.x, c.y - cs.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int l = l0 + warp + 8 * k;
+      if (l > lmax || l < 2) continue;
+      const double* row = col + (size_t)(l - m) * R;
+      const double* rowp = row + R;                              // l + 1 (table holds lmax + 1)
+      const double* rowm = l > m ? row - R : nullptr;            // l - 1
+      const double e1 = (double)l * eps_lm(l + 1, m), e0 = (l + 1.0) * eps_lm(l, m);
+      const double ll1 = (double)l * (l + 1.0), m2 = 2.0 * m * m, m_2 = 2.0 * m;
+      const int p = (l + m) & 1;
+      const double2* VA1 = V + (p ? kEbChunk : 0);          // F1 with A's parity
+      const double2* VB1 = V + (p ? 0 : kEbChunk);          // F1 with B's parity
+      const double2* VA2 = V + 2 * kEbChunk + (p ? kEbChunk : 0);
+      const double2* VB2 = V + 2 * kEbChunk + (p ? 0 : kEbChunk);
+      double ex = 0, ey = 0, bx = 0, by = 0;
+      for (int rr = lane; rr < cn; rr += 32) {
+        const int r = c0 + rr;
+        const Ring g = ring_geom(nside, r + 1);
+        const double is = 1.0 / g.s, cot = g.z * is;
+        const double lam = row[r];
+        const double dl = (e1 * rowp[r] - (rowm ? e0 * rowm[r] : 0.0)) * is;
+        const double A = -2.0 * cot * dl - (ll1 - m2 * is * is) * lam;
+        const double Bf = m_2 * is * (dl - cot * lam);
+        const double2 a1 = VA1[rr], b1 = VB1[rr], a2 = VA2[rr], b2 = VB2[rr];
+        // E += A F1 - i B F2 ; B += A F2 + i B F1
+        ex += A * a1.x + Bf * b2.y;
+        ey += A * a1.y - Bf * b2.x;
+        bx += A * a2.x - Bf * b1.y;
+        by += A * a2.y + Bf * b1.x;
+      }
+      acc[k][0] += ex;
+      acc[k][1] += ey;
+      acc[k][2] += bx;
+      acc[k][3] += by;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int l = l0 + warp + 8 * k;
+    if (l > lmax || l >= l0 + 64) continue;
     const size_t li = alm_idx(lmax, l, m);
     if (l < 2) {
       if (lane == 0) {
@@ -62,31 +111,7 @@ __global__ void k_legendre_eb(int nside, int lmax, int R, const long long* __res
       }
       continue;
     }
-    const double* row = col + (size_t)(l - m) * R;
-    const double* rowp = row + R;                              // l + 1 (table holds lmax + 1)
-    const double* rowm = l > m ? row - R : nullptr;            // l - 1
-    const double e1 = (double)l * eps_lm(l + 1, m), e0 = (l + 1.0) * eps_lm(l, m);
-    const double ll1 = (double)l * (l + 1.0), m2 = 2.0 * m * m, m_2 = 2.0 * m;
-    const int p = (l + m) & 1;
-    const double2* VA1 = V + (p ? R : 0);          // F1 with A's parity
-    const double2* VB1 = V + (p ? 0 : R);          // F1 with B's parity
-    const double2* VA2 = V + 2 * R + (p ? R : 0);
-    const double2* VB2 = V + 2 * R + (p ? 0 : R);
-    double ex = 0, ey = 0, bx = 0, by = 0;
-    for (int r = lane; r < R; r += 32) {
-      const Ring g = ring_geom(nside, r + 1);
-      const double is = 1.0 / g.s, cot = g.z * is;
-      const double lam = row[r];
-      const double dl = (e1 * rowp[r] - (rowm ? e0 * rowm[r] : 0.0)) * is;
-      const double A = -2.0 * cot * dl - (ll1 - m2 * is * is) * lam;
-      const double Bf = m_2 * is * (dl - cot * lam);
-      const double2 a1 = VA1[r], b1 = VB1[r], a2 = VA2[r], b2 = VB2[r];
-      // E += A F1 - i B F2 ; B += A F2 + i B F1
-      ex += A * a1.x + Bf * b2.y;
-      ey += A * a1.y - Bf * b2.x;
-      bx += A * a2.x - Bf * b1.y;
-      by += A * a2.y + Bf * b1.x;
-    }
+    double ex = acc[k][0], ey = acc[k][1], bx = acc[k][2], by = acc[k][3];
     for (int o = 16; o > 0; o >>= 1) {
       ex += __shfl_xor_sync(0xffffffffu, ex, o);
       ey += __shfl_xor_sync(0xffffffffu, ey, o);
@@ -170,7 +195,7 @@ int eb_analysis(clc_ctx* ctx, const double* g1, const double* g2, int nside, int
   if ((rc = ring_analysis(ctx, *plan, g1, lmax, w, F, ldf))) return rc;
   if ((rc = ring_analysis(ctx, *plan, g2, lmax, w, F2, ldf))) return rc;
   dim3 grid((lmax + 1 + 63) / 64, lmax + 1);
-  const int smem = 4 * T->R * (int)sizeof(double2);
+  const int smem = 4 * kEbChunk * (int)sizeof(double2);
   cudaFuncSetAttribute(k_legendre_eb, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   CLC_LAUNCH(ctx, "k_legendre_eb", k_legendre_eb, grid, 256, smem, nside, lmax, T->R, (const long long*)T->offsets.p,
              (const double*)T->data.p, F, F2, ldf, E, B);
