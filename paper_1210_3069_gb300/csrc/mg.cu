@@ -987,60 +987,10 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
 // pipe), r rounded to FP32 as the next V-cycle's source, ||r||^2 per patch.
 // e is kept in the layout of the correction arrays (colour-split rows).  A
 // thread takes the cells (i, 2k) and (i, 2k + 1), which sit at the same
-// entry of the two colour rows of row i, and kRows rows of that column pair;
-// every load and store of a warp is then contiguous.
-constexpr int kRows = 4;
-
-__global__ void k_resid_ff(const float2* __restrict__ e_old, const float* __restrict__ d,
-                           const float2* __restrict__ fd, const float2* __restrict__ coef,
-                           const float2* __restrict__ diag, int n, float2* __restrict__ e_new,
-                           float* __restrict__ r32, double* __restrict__ norms) {
-  const int b = blockIdx.z, nh = n >> 1;
-  const int k = blockIdx.x * kBX + threadIdx.x;
-  const size_t pb = (size_t)b * upatch(n), pl = uplane_of(n), P = upitch(n);
-  const float2* E = e_old + pb;
-  const float* D = d ? d + pb : nullptr;
-  float rr = 0.f;
-  auto ld = [&](size_t o) -> float2 {
-    float2 v = E[o];
-    if (D) v = ff_add_f(v, D[o]);
-    return v;
-  };
-#pragma unroll
-  for (int kr = 0; kr < kRows; ++kr) {
-    const int i = (blockIdx.y * kRows + kr) * kBY + threadIdx.y;
-    if (i < n && k < nh) {
-      const size_t o = (size_t)(i + 1 + kUHalo) * P + k + 1;
-      const size_t ca = (size_t)(i & 1) * pl + o, cb = (size_t)((i + 1) & 1) * pl + o;   // (i, 2k), (i, 2k + 1)
-      const float2 eA = ld(ca), eB = ld(cb);
-      const float2 eW = ld(cb - 1), eE = ld(ca + 1);     // (i, 2k - 1), (i, 2k + 2)
-      const float2 nA = ld(cb - P), nB = ld(ca - P);     // row i - 1
-      const float2 sA = ld(cb + P), sB = ld(ca + P);     // row i + 1
-      const float2 cS = coef[i], cN = coef[n + i], cb2 = coef[2 * n + i];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * k + h;
-        const float2 eC = h ? eB : eA, eS = h ? sB : sA, eN = h ? nB : nA;
-        const float2 eEh = h ? eE : eB, eWh = h ? eA : eW;
-        // L e = aS eS + aN eN + b (eE + eW) - diag eC
-        const float2 nb = ff_add(ff_add(ff_mul(cS, eS), ff_mul(cN, eN)),
-                                 ff_add(ff_mul(cb2, ff_add(eEh, eWh)), ff_neg(ff_mul(diag[i * n + j], eC))));
-        const size_t pos = (size_t)b * n * n + fidx(n, i, j);
-        const float2 r = ff_add(fd[pos], ff_neg(nb));
-        r32[pos] = r.x + r.y;
-        e_new[pb + (h ? cb : ca)] = eC;
-        rr = fmaf(r.x, r.x, rr);
-      }
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
-  if (threadIdx.x == 0 && rr != 0.f) atomicAdd(norms + b, (double)rr);
-}
-
-// The same residual with each thread walking kWalk rows of one column pair
-// (2k, 2k + 1): every e + d is formed once, kept for the rows above and
-// below in registers, and handed to the horizontal neighbours by warp
-// shuffles; the sums use ff_add_lite.
+// entry of the two colour rows of row i, and walks kWalk rows of that column
+// pair: every e + d is formed once, kept for the rows above and below in
+// registers, and handed to the horizontal neighbours by warp shuffles; the
+// sums use ff_add_lite.  Every load and store of a warp is contiguous.
 constexpr int kWalk = 16;
 
 __global__ void __launch_bounds__(kBX * kBY) k_resid_ff_walk(const float2* __restrict__ e_old,
