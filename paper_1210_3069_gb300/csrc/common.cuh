@@ -42,6 +42,10 @@ struct clc_ctx {
   int* d_err = nullptr;  // device error word
   // launch accounting and optional per-kernel CUDA-event timing
   long long launches = 0;
+  // first launch error not yet reported (taken right after each launch, so a
+  // later runtime call that returns it cannot lose it)
+  cudaError_t launch_err = cudaSuccess;
+  const char* launch_err_kernel = nullptr;
   bool prof = false;
   std::map<std::string, std::vector<std::pair<cudaEvent_t, cudaEvent_t>>> prof_ev;
   std::vector<cudaEvent_t> ev_pool;
@@ -83,10 +87,18 @@ struct LaunchScope {
   }
 };
 
+inline void note_launch(clc_ctx* ctx, cudaError_t e, const char* name) {
+  if (e != cudaSuccess && ctx->launch_err == cudaSuccess) {
+    ctx->launch_err = e;
+    ctx->launch_err_kernel = name;
+  }
+}
+
 #define CLC_LAUNCH(ctx, name, kern, g, b, s, ...)                    \
   do {                                                               \
     ::clc::LaunchScope _clc_ls((ctx), (name));                       \
     kern<<<(g), (b), (s), (ctx)->stream>>>(__VA_ARGS__);             \
+    ::clc::note_launch((ctx), cudaGetLastError(), (name));           \
   } while (0)
 int cuda_check(clc_ctx* ctx, cudaError_t e, const char* what);
 // Grow scratch buffer `slot` to at least `bytes`; returns nullptr on failure

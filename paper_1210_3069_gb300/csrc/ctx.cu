@@ -17,7 +17,16 @@ int cuda_check(clc_ctx* ctx, cudaError_t e, const char* what) {
   return set_err(ctx, CLC_ECUDA, m);
 }
 
-int launch_check(clc_ctx* ctx, const char* what) { return cuda_check(ctx, cudaGetLastError(), what); }
+int launch_check(clc_ctx* ctx, const char* what) {
+  if (ctx->launch_err != cudaSuccess) {
+    const cudaError_t e = ctx->launch_err;
+    const std::string m = std::string(what) + " (" + ctx->launch_err_kernel + ")";
+    ctx->launch_err = cudaSuccess;
+    cudaGetLastError();
+    return cuda_check(ctx, e, m.c_str());
+  }
+  return cuda_check(ctx, cudaGetLastError(), what);
+}
 
 cudaEvent_t pool_event(clc_ctx* ctx) {
   if (!ctx->ev_pool.empty()) {

@@ -923,118 +923,124 @@ __global__ void __launch_bounds__(kBandThreads) k_band_prolong_smooth(
 // Register-resident form of the two fused band kernels (FP32, nu = 2, patches
 // of 128 and 256 cells a side).  A CTA still owns a band of BR rows of one
 // patch with its halo rows (the region), but the region lives in registers:
-// the region is cut into an upper and a lower half of H rows, and thread
-// (half, q) holds the columns 4q .. 4q + 3 of the H rows of its half as two
+// the region's rows are cut into NV parts of H rows, and thread (part v,
+// quad q) holds the columns 4q .. 4q + 3 of the H rows of its part as two
 // pairs, A = (4q, 4q + 2) and B = (4q + 1, 4q + 3).  A pair's two cells have
 // one colour and share their row's coefficients, so a half-sweep relaxes both
 // with packed two-wide FP32 instructions (correctly rounded per lane, the
-// same bits as the scalar ones).  Vertical neighbours are the thread's own
+// same values as the scalar ones).  Vertical neighbours are the thread's own
 // registers; the column beyond the quad comes from the adjacent lane by a
-// warp shuffle; the warps' outer columns and the two rows where the halves
-// meet pass through shared memory.
+// warp shuffle; the warps' outer columns and the rows where the parts meet
+// pass through shared memory.
 //
-// Every region row inside the patch is relaxed in every half-sweep (rows
-// beyond the patch keep their zeros): a row next to the region's edge reads
-// zeros beyond it, and the error this introduces moves in by one row per
-// half-sweep, so after 2 nu half-sweeps the band rows (and, with the halo of
-// the pre-smoothing kernel, one row beyond them) hold exactly what sweeping
-// the whole patch gives.  The arithmetic per cell is that of band_half_sweep,
-// operation for operation, and the residual and prolongation formulas are
-// those of the shared-memory kernels, so both give the same bits.  The
-// sources of the region's rows arrive in shared memory by one bulk copy per
-// colour while the threads load their cells.
+// Every region row is relaxed in every half-sweep.  Rows beyond the patch
+// have zero coefficients and zero sources, so they keep the value zero; a
+// row next to the region's edge reads zeros beyond it, and the error this
+// introduces moves in by one row per half-sweep, so after 2 nu half-sweeps
+// the band rows (and, with the halo of the pre-smoothing kernel, one row
+// beyond them) hold exactly what sweeping the whole patch gives.  The
+// arithmetic per cell is that of band_half_sweep, operation for operation,
+// and the residual and prolongation formulas are those of the shared-memory
+// kernels, so both give the same values.  The sources of the region's rows
+// arrive in shared memory by one bulk copy per colour while the threads load
+// their cells.
 //
-// Shared exchange slots, per half: eL slot w holds the column 4q of lane 0 of
-// warp w (slot NWH: zeros, the ghost column beyond the patch), oR slot w + 1
-// the column 4q + 3 of lane 31 (slot 0: zeros); VA / VB [half][q] hold the
-// pairs of the half's row next to the other half.  A half-sweep of one colour
-// reads only the other colour's cells and publishes the cells it relaxes; in
-// one row these are different slots (the A and B pairs, the even and the odd
-// outer column), so the reads and writes of a half-sweep never meet and one
-// barrier per half-sweep orders them.
+// Shared exchange slots: per part, eL slot w holds the column 4q of lane 0 of
+// warp w (slot NWH: zeros, the ghost column beyond the patch) and oR slot
+// w + 1 the column 4q + 3 of lane 31 (slot 0: zeros); TA / TB [v] hold the
+// pairs of part v's first row, BA / BB [v + 1] those of its last row (slot
+// NV of T and slot 0 of B: zeros beyond the region).  A half-sweep of one
+// colour reads only the other colour's cells and publishes the cells it
+// relaxes; in one row these are different slots (the A and B pairs, the even
+// and the odd outer column), so the reads and writes of a half-sweep never
+// meet and one barrier per half-sweep orders them.
 
-template <int N, int HALO>
+template <int N, int HALO, int NV>
 struct QBand {
   static constexpr int NH = N / 2;                  // source entries per colour row
-  static constexpr int NQ = N / 4;                  // column quads = threads per half
-  static constexpr int NWH = NQ / 32;               // warps per half
+  static constexpr int NQ = N / 4;                  // column quads = threads per part
+  static constexpr int NWH = NQ / 32;               // warps per part
   static constexpr int BR = kBandRows;              // band rows
-  static constexpr int W = BR + 2 * HALO, H = W / 2;   // region rows, rows per half
+  static constexpr int W = BR + 2 * HALO, H = W / NV;   // region rows, rows per part
+  static constexpr int NT = NQ * NV;                // threads
   static constexpr int NC = N / 2, Wc = W / 2 + 2, Pc = upitch(NC);   // coarse rows / pitch (prolongation)
   static constexpr size_t f_bytes = (size_t)2 * W * NH * sizeof(float);
   static constexpr size_t e_bytes = (size_t)2 * Wc * Pc * sizeof(float);
-  static_assert(NQ % 32 == 0 && W % 2 == 0, "quad band geometry");
+  static_assert(NQ % 32 == 0 && H * NV == W && H % 2 == 0 && H >= 2, "quad band geometry");
 };
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
 
-// Per region row r, four float4 at rq[4 r]:
-// (aS, aS, aN, aN), (b, b, 1/d, 1/d), (1/d_edge, 1/d, 1/d, 1/d_edge), (d, d_edge, area, 0)
-// with d the diagonal of an interior cell, d_edge that of a first or last cell.
-template <int W>
-__device__ __forceinline__ void q_stage_rows(float4* rq, int gi0, int n, const float* __restrict__ coef,
-                                             const float* __restrict__ invd, const float* __restrict__ diag) {
-  for (int r = threadIdx.x; r < W; r += blockDim.x) {
-    const int gi = gi0 + r;
-    float4 z = make_float4(0.f, 0.f, 0.f, 0.f), p0 = z, p1 = z, p2 = z, p3 = z;
-    if (gi >= 0 && gi < n) {
-      const size_t row = (size_t)gi * n;
-      const float aS = coef[gi], aN = coef[n + gi], bh = coef[2 * n + gi], id = invd[row + 1], ide = invd[row];
-      p0 = make_float4(aS, aS, aN, aN);
-      p1 = make_float4(bh, bh, id, id);
-      p2 = make_float4(ide, id, id, ide);
-      p3 = make_float4(diag[row + 1], diag[row], coef[3 * n + gi], 0.f);
-    }
-    rq[4 * r] = p0;
-    rq[4 * r + 1] = p1;
-    rq[4 * r + 2] = p2;
-    rq[4 * r + 3] = p3;
-  }
-}
-
-// bulk copy of the sources of the region's rows in the patch, colour planes
-// [2][W][NH] (rows beyond the patch are not copied and their results unused);
-// the barrier also expects `extra` bytes that the caller's thread 0 copies next
-template <int N, int W>
-__device__ __forceinline__ void q_issue_f(float* Fs, uint64_t* bar, const float* __restrict__ Fb, int gi0,
-                                          uint32_t extra = 0) {
-  constexpr int NH = N / 2;
-  if (threadIdx.x == 0) {
-    umma::mbar_init(bar, 1);
-    umma::fence_mbar_init();
-    const int fa = max(gi0, 0), fb = min(gi0 + W, N);
-    const uint32_t bytes = (uint32_t)((fb - fa) * NH * sizeof(float));
-    umma::mbar_arrive_expect_tx(bar, 2 * bytes + extra);
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-      umma::bulk_g2s(Fs + (c * W + fa - gi0) * NH, Fb + ((size_t)c * N + fa) * NH, bytes, bar);
-  }
-}
-
-// The state of one thread and its exchange slots.
-template <int N, int HALO>
-struct QState {
-  using G = QBand<N, HALO>;
-  float2 A[G::H], B[G::H];
-};
-
-template <int N, int HALO>
+template <int N, int HALO, int NV>
 struct QShared {
-  using G = QBand<N, HALO>;
+  using G = QBand<N, HALO, NV>;
+  // per region row r, four float4 at rq[4 r]: (aS, aS, aN, aN), (b, b, 1/d, 1/d),
+  // (1/d_edge, 1/d, 1/d, 1/d_edge), (d, d_edge, area, 0), with d the diagonal
+  // of an interior cell, d_edge that of a first or last cell (zeros beyond the patch)
   float4 rq[4 * G::W];
-  float eL[2][G::NWH + 1][G::H], oR[2][G::NWH + 1][G::H];
-  float2 VA[2][G::NQ], VB[2][G::NQ];
+  float eL[NV][G::NWH + 1][G::H], oR[NV][G::NWH + 1][G::H];
+  float2 TA[NV + 1][G::NQ], TB[NV + 1][G::NQ], BA[NV + 1][G::NQ], BB[NV + 1][G::NQ];
   uint64_t bar;
 };
 
+template <int N, int HALO, int NV>
+struct QState {
+  using G = QBand<N, HALO, NV>;
+  float2 A[G::H], B[G::H];
+};
+
+// Stage the row coefficients; bulk copy the sources of the region's rows in
+// the patch, colour planes [2][W][NH], and zero those of rows beyond it; the
+// barrier also expects `extra` bytes that the caller's thread 0 copies next.
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void q_begin(QShared<N, HALO, NV>& X, float* Fs, const float* __restrict__ Fb, int gi0,
+                                        const float* __restrict__ coef, const float* __restrict__ invd,
+                                        const float* __restrict__ diag, uint32_t extra) {
+  using G = QBand<N, HALO, NV>;
+  const int fa = max(gi0, 0), fb = min(gi0 + G::W, N);
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&X.bar, 1);
+    umma::fence_mbar_init();
+    const uint32_t bytes = (uint32_t)((fb - fa) * G::NH * sizeof(float));
+    umma::mbar_arrive_expect_tx(&X.bar, 2 * bytes + extra);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      umma::bulk_g2s(Fs + (c * G::W + fa - gi0) * G::NH, Fb + ((size_t)c * N + fa) * G::NH, bytes, &X.bar);
+  }
+  for (int r = threadIdx.x; r < G::W; r += blockDim.x) {
+    const int gi = gi0 + r;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f), p0 = z, p1 = z, p2 = z, p3 = z;
+    if (gi >= 0 && gi < N) {
+      const size_t row = (size_t)gi * N;
+      const float aS = coef[gi], aN = coef[N + gi], bh = coef[2 * N + gi], id = invd[row + 1], ide = invd[row];
+      p0 = make_float4(aS, aS, aN, aN);
+      p1 = make_float4(bh, bh, id, id);
+      p2 = make_float4(ide, id, id, ide);
+      p3 = make_float4(diag[row + 1], diag[row], coef[3 * N + gi], 0.f);
+    }
+    X.rq[4 * r] = p0;
+    X.rq[4 * r + 1] = p1;
+    X.rq[4 * r + 2] = p2;
+    X.rq[4 * r + 3] = p3;
+  }
+  // rows beyond the patch (edge bands only): zero sources
+  const int nlo = fa - gi0, nhi = gi0 + G::W - fb;
+  for (int e = threadIdx.x; e < (nlo + nhi) * G::NH; e += blockDim.x) {
+    const int rr = e / G::NH, k = e - rr * G::NH;
+    const int r = rr < nlo ? rr : fb - gi0 + (rr - nlo);
+    Fs[r * G::NH + k] = 0.f;
+    Fs[(G::W + r) * G::NH + k] = 0.f;
+  }
+}
+
 // load the thread's cells (rows beyond the patch are the zero rows of the layout)
-template <int N, int HALO, int V>
-__device__ __forceinline__ void q_load(QState<N, HALO>& S, const float* __restrict__ Ub, int gi0, int q) {
-  using G = QBand<N, HALO>;
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void q_load(QState<N, HALO, NV>& S, const float* __restrict__ Ub, int g0, int q) {
+  using G = QBand<N, HALO, NV>;
 #pragma unroll
   for (int r = 0; r < G::H; ++r) {
-    const int gi = gi0 + V * G::H + r;
+    const int gi = g0 + r;
     if (Ub) {
       S.A[r] = f2(Ub[uidx(N, gi, 4 * q)], Ub[uidx(N, gi, 4 * q + 2)]);
       S.B[r] = f2(Ub[uidx(N, gi, 4 * q + 1)], Ub[uidx(N, gi, 4 * q + 3)]);
@@ -1045,96 +1051,106 @@ __device__ __forceinline__ void q_load(QState<N, HALO>& S, const float* __restri
 }
 
 // publish every exchange value of the thread (before the first half-sweep)
-template <int N, int HALO, int V>
-__device__ __forceinline__ void q_publish_all(const QState<N, HALO>& S, QShared<N, HALO>& X, int q) {
-  using G = QBand<N, HALO>;
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void q_publish_all(const QState<N, HALO, NV>& S, QShared<N, HALO, NV>& X, int v, int q) {
+  using G = QBand<N, HALO, NV>;
   const int lane = threadIdx.x & 31, wh = q >> 5;
   if (lane == 0) {
 #pragma unroll
-    for (int r = 0; r < G::H; ++r) X.eL[V][wh][r] = S.A[r].x;
+    for (int r = 0; r < G::H; ++r) X.eL[v][wh][r] = S.A[r].x;
   }
   if (lane == 31) {
 #pragma unroll
-    for (int r = 0; r < G::H; ++r) X.oR[V][wh + 1][r] = S.B[r].y;
+    for (int r = 0; r < G::H; ++r) X.oR[v][wh + 1][r] = S.B[r].y;
   }
-  const int rb = V == 0 ? G::H - 1 : 0;
-  X.VA[V][q] = S.A[rb];
-  X.VB[V][q] = S.B[rb];
-  if (q < G::H) {
-    X.eL[V][G::NWH][q] = 0.f;
-    X.oR[V][0][q] = 0.f;
+  X.TA[v][q] = S.A[0];
+  X.TB[v][q] = S.B[0];
+  X.BA[v + 1][q] = S.A[G::H - 1];
+  X.BB[v + 1][q] = S.B[G::H - 1];
+  if (v == 0) {
+    X.TA[NV][q] = X.TB[NV][q] = X.BA[0][q] = X.BB[0][q] = f2(0.f, 0.f);
+    if (q < G::H) {
+      for (int u = 0; u < NV; ++u) {
+        X.eL[u][G::NWH][q] = 0.f;
+        X.oR[u][0][q] = 0.f;
+      }
+    }
   }
 }
 
-// One half-sweep of colour C over the thread's rows.
-template <int N, int HALO, int V, int C>
-__device__ __forceinline__ void q_half_sweep(QState<N, HALO>& S, QShared<N, HALO>& X, const float* __restrict__ Fs,
-                                             int gi0, int q, int offA, int offB) {
-  using G = QBand<N, HALO>;
-  const int lane = threadIdx.x & 31, wh = q >> 5;
+// One half-sweep of colour C over the thread's rows; rb = v H, the part's
+// first region row (even, so the colour of column 4q in row r is (r + HALO) & 1).
+template <int N, int HALO, int NV, int C>
+__device__ __forceinline__ void q_half_sweep(QState<N, HALO, NV>& S, QShared<N, HALO, NV>& X,
+                                             const float* __restrict__ Fs, int v, int q, int offA, int offB) {
+  using G = QBand<N, HALO, NV>;
+  const int lane = threadIdx.x & 31, wh = q >> 5, rb = v * G::H;
+  const float* Fr = Fs + (C * G::W + rb) * G::NH + 2 * q;
+  const float4* R = X.rq + 4 * rb;
+  const float* eLv = &X.eL[v][0][0];
+  const float* oRv = &X.oR[v][0][0];
 #pragma unroll
   for (int r = 0; r < G::H; ++r) {
-    const int rg = V * G::H + r;                     // region row
-    const bool halo_row = rg < HALO || rg >= HALO + G::BR;
-    const bool in = !halo_row || (unsigned)(gi0 + rg) < (unsigned)N;
-    const float4 p0 = X.rq[4 * rg], p1 = X.rq[4 * rg + 1];
-    const float2 F = *reinterpret_cast<const float2*>(Fs + (C * G::W + rg) * G::NH + 2 * q);
-    const char* rqb = reinterpret_cast<const char*>(X.rq + 4 * rg);
-    if (((rg + HALO) & 1) == C) {
+    const float4 p0 = R[4 * r], p1 = R[4 * r + 1];
+    const float2 F = *reinterpret_cast<const float2*>(Fr + r * G::NH);
+    const char* rqb = reinterpret_cast<const char*>(R + 4 * r);
+    if (((r + HALO) & 1) == C) {
       // A = columns 4q, 4q + 2: west 4q - 1 (lane q - 1) and 4q + 1, east 4q + 1 and 4q + 3
       float w = __shfl_up_sync(0xffffffffu, S.B[r].y, 1);
-      if (lane == 0) w = X.oR[V][wh][r];
-      const float2 nN = r > 0 ? S.A[r - 1] : (V == 1 ? X.VA[0][q] : f2(0.f, 0.f));
-      const float2 nS = r + 1 < G::H ? S.A[r + 1] : (V == 0 ? X.VA[1][q] : f2(0.f, 0.f));
+      if (lane == 0) w = oRv[wh * G::H + r];
+      const float2 nN = r > 0 ? S.A[r - 1] : X.BA[v][q];
+      const float2 nS = r + 1 < G::H ? S.A[r + 1] : X.TA[v + 1][q];
       const float2 id = *reinterpret_cast<const float2*>(rqb + offA);
       const float2 s = __fadd2_rn(S.B[r], f2(w, S.B[r].x));
-      const float2 v = __ffma2_rn(f2(p1.x, p1.y), s, __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, neg2(F))));
-      const float2 u = __fmul2_rn(v, id);
-      if (in) S.A[r] = u;
-      if (lane == 0) X.eL[V][wh][r] = S.A[r].x;
-      if ((V == 0 && r == G::H - 1) || (V == 1 && r == 0)) X.VA[V][q] = S.A[r];
+      const float2 t = __ffma2_rn(f2(p1.x, p1.y), s, __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, neg2(F))));
+      S.A[r] = __fmul2_rn(t, id);
+      if (lane == 0) X.eL[v][wh][r] = S.A[r].x;
+      if (r == 0) X.TA[v][q] = S.A[r];
+      if (r == G::H - 1) X.BA[v + 1][q] = S.A[r];
     } else {
       // B = columns 4q + 1, 4q + 3: west 4q and 4q + 2, east 4q + 2 and 4q + 4 (lane q + 1)
       float e = __shfl_down_sync(0xffffffffu, S.A[r].x, 1);
-      if (lane == 31) e = X.eL[V][wh + 1][r];
-      const float2 nN = r > 0 ? S.B[r - 1] : (V == 1 ? X.VB[0][q] : f2(0.f, 0.f));
-      const float2 nS = r + 1 < G::H ? S.B[r + 1] : (V == 0 ? X.VB[1][q] : f2(0.f, 0.f));
+      if (lane == 31) e = eLv[(wh + 1) * G::H + r];
+      const float2 nN = r > 0 ? S.B[r - 1] : X.BB[v][q];
+      const float2 nS = r + 1 < G::H ? S.B[r + 1] : X.TB[v + 1][q];
       const float2 id = *reinterpret_cast<const float2*>(rqb + offB);
       const float2 s = __fadd2_rn(S.A[r], f2(S.A[r].y, e));
-      const float2 v = __ffma2_rn(f2(p1.x, p1.y), s, __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, neg2(F))));
-      const float2 u = __fmul2_rn(v, id);
-      if (in) S.B[r] = u;
-      if (lane == 31) X.oR[V][wh + 1][r] = S.B[r].y;
-      if ((V == 0 && r == G::H - 1) || (V == 1 && r == 0)) X.VB[V][q] = S.B[r];
+      const float2 t = __ffma2_rn(f2(p1.x, p1.y), s, __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, neg2(F))));
+      S.B[r] = __fmul2_rn(t, id);
+      if (lane == 31) X.oR[v][wh + 1][r] = S.B[r].y;
+      if (r == 0) X.TB[v][q] = S.B[r];
+      if (r == G::H - 1) X.BB[v + 1][q] = S.B[r];
     }
   }
 }
 
 // the four half-sweeps of nu = 2 (red, black, red, black), each closed by a
 // barrier; the sweep loop stays rolled to keep the code in the instruction cache
-template <int N, int HALO, int V>
-__device__ __forceinline__ void q_sweeps(QState<N, HALO>& S, QShared<N, HALO>& X, const float* __restrict__ Fs,
-                                         int gi0, int q) {
-  using G = QBand<N, HALO>;
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void q_sweeps(QState<N, HALO, NV>& S, QShared<N, HALO, NV>& X, const float* __restrict__ Fs,
+                                         int v, int q) {
+  using G = QBand<N, HALO, NV>;
   // byte offsets of the thread's inverse diagonals in a row's rq block:
   // (1/d_edge, 1/d) for the first quad's A pair, (1/d, 1/d_edge) for the last quad's B pair
   const int offA = q == 0 ? 32 : 24, offB = q == G::NQ - 1 ? 40 : 24;
 #pragma unroll 1
   for (int it = 0; it < 2; ++it) {
-    q_half_sweep<N, HALO, V, 0>(S, X, Fs, gi0, q, offA, offB);
+    q_half_sweep<N, HALO, NV, 0>(S, X, Fs, v, q, offA, offB);
     __syncthreads();
-    q_half_sweep<N, HALO, V, 1>(S, X, Fs, gi0, q, offA, offB);
+    q_half_sweep<N, HALO, NV, 1>(S, X, Fs, v, q, offA, offB);
     __syncthreads();
   }
 }
 
-template <int N, int HALO, int V>
-__device__ __forceinline__ void q_store(const QState<N, HALO>& S, float* __restrict__ Ub, int gi0, int q) {
-  using G = QBand<N, HALO>;
+// store the band rows among the thread's rows
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void q_store(const QState<N, HALO, NV>& S, float* __restrict__ Ub, int gi0, int v, int q) {
+  using G = QBand<N, HALO, NV>;
+  const int rb = v * G::H;
 #pragma unroll
   for (int r = 0; r < G::H; ++r) {
-    const int rg = V * G::H + r;
-    if (rg < HALO || rg >= HALO + G::BR) continue;   // compile-time: band rows only
+    const int rg = rb + r;
+    if (rg < HALO || rg >= HALO + G::BR) continue;
     const int gi = gi0 + rg;
     Ub[uidx(N, gi, 4 * q)] = S.A[r].x;
     Ub[uidx(N, gi, 4 * q + 1)] = S.B[r].x;
@@ -1143,52 +1159,69 @@ __device__ __forceinline__ void q_store(const QState<N, HALO>& S, float* __restr
   }
 }
 
-// Pre-smoothing (from zero when u_in is null) and restriction of the band.
-template <int N, int V>
-__device__ __forceinline__ void q_smooth_restrict_half(QShared<N, 5>& X, const float* __restrict__ Fs,
-                                                       const float* __restrict__ Ub_in, float* __restrict__ Ub_out,
-                                                       const float* __restrict__ rden, float* __restrict__ fcb,
-                                                       int gi0, int q, int* d_err) {
-  using G = QBand<N, 5>;
-  constexpr int HALO = 5, NC = G::NC;
-  const int lane = threadIdx.x & 31, wh = q >> 5;
-  QState<N, HALO> S;
-  q_load<N, HALO, V>(S, Ub_in, gi0, q);   // while the sources arrive
-  q_publish_all<N, HALO, V>(S, X, q);
+template <int N, int NV>
+__global__ void __launch_bounds__(QBand<N, 5, NV>::NT) k_reg_smooth_restrict(
+    const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
+    const float* __restrict__ coef, const float* __restrict__ invd, const float* __restrict__ diag,
+    const float* __restrict__ rden, float* __restrict__ fc, int* d_err) {
+  constexpr int HALO = 5;
+  using G = QBand<N, HALO, NV>;
+  extern __shared__ __align__(128) unsigned char smem_rsr[];
+  float* Fs = reinterpret_cast<float*>(smem_rsr);
+  __shared__ QShared<N, HALO, NV> X;
+  const size_t b = blockIdx.z;
+  const int gi0 = blockIdx.x * G::BR - HALO;
+  const int v = threadIdx.x / G::NQ, q = threadIdx.x % G::NQ, lane = threadIdx.x & 31, wh = q >> 5;
+  const int rb = v * G::H;
+  q_begin<N, HALO, NV>(X, Fs, f + b * N * N, gi0, coef, invd, diag, 0);
+  QState<N, HALO, NV> S;
+  q_load<N, HALO, NV>(S, u_in ? u_in + b * upatch(N) : nullptr, gi0 + rb, q);   // while the sources arrive
+  q_publish_all<N, HALO, NV>(S, X, v, q);
   if (!band_wait(&X.bar, d_err)) return;
-  q_sweeps<N, HALO, V>(S, X, Fs, gi0, q);
-  q_store<N, HALO, V>(S, Ub_out, gi0, q);
-  // Restriction of the band's rows: coarse cells (I, 2q) and (I, 2q + 1) from
-  // their red children (2I, 4q), (2I + 1, 4q + 1) and (2I, 4q + 2),
-  // (2I + 1, 4q + 3) (the black residuals vanish after the last, black,
-  // half-sweep, which also published the black values read here).
-  // r = f - (aS uS + aN uN + b (uE + uW) - diag u), weighted by the areas.
+  q_sweeps<N, HALO, NV>(S, X, Fs, v, q);
+  q_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, q);
+  // Residual of the red cells of the band rows among the thread's rows (the
+  // black residuals vanish after the last, black, half-sweep, which also
+  // published the black values read here), r = 0 + (f - (aS uS + aN uN +
+  // b (uE + uW) - diag u)), written over the red source it used.
 #pragma unroll
-  for (int r0 = 0; r0 < G::H; ++r0) {
-    const int rg = V * G::H + r0;
-    if (rg < HALO || rg >= HALO + G::BR || ((rg - HALO) & 1)) continue;   // compile-time: first row of a pair
-    const int I = (gi0 + rg) >> 1;
-    const float4 a0q = X.rq[4 * rg], a1q = X.rq[4 * rg + 1], a3q = X.rq[4 * rg + 3];
-    const float4 b0q = X.rq[4 * rg + 4], b1q = X.rq[4 * rg + 5], b3q = X.rq[4 * rg + 7];
-    float w = __shfl_up_sync(0xffffffffu, S.B[r0].y, 1);
-    if (lane == 0) w = X.oR[V][wh][r0];
-    float e = __shfl_down_sync(0xffffffffu, S.A[r0 + 1].x, 1);
-    if (lane == 31) e = X.eL[V][wh + 1][r0 + 1];
-    const float2 a0 = S.A[r0], a1 = S.B[r0], b0 = S.A[r0 + 1], b1 = S.B[r0 + 1];
-    const float2 n0 = r0 > 0 ? S.A[r0 - 1] : X.VA[0][q];
-    const float2 s1 = r0 + 2 < G::H ? S.B[r0 + 2] : X.VB[1][q];
-    const float2 d0 = f2(q == 0 ? a3q.y : a3q.x, a3q.x), d1 = f2(b3q.x, q == G::NQ - 1 ? b3q.y : b3q.x);
-    const float2 nb0 = __ffma2_rn(f2(a1q.x, a1q.y), __fadd2_rn(a1, f2(w, a1.x)),
-                                  __ffma2_rn(f2(a0q.z, a0q.w), n0, __ffma2_rn(f2(a0q.x, a0q.y), b0, __fmul2_rn(neg2(d0), a0))));
-    const float2 nb1 = __ffma2_rn(f2(b1q.x, b1q.y), __fadd2_rn(b0, f2(b0.y, e)),
-                                  __ffma2_rn(f2(b0q.z, b0q.w), a1, __ffma2_rn(f2(b0q.x, b0q.y), s1, __fmul2_rn(neg2(d1), b1))));
-    const float2 F0 = *reinterpret_cast<const float2*>(Fs + rg * G::NH + 2 * q);         // red sources
-    const float2 F1 = *reinterpret_cast<const float2*>(Fs + (rg + 1) * G::NH + 2 * q);
-    const float2 z = f2(0.f, 0.f);
-    const float2 rs0 = __fadd2_rn(z, __fadd2_rn(F0, neg2(nb0)));
-    const float2 rs1 = __fadd2_rn(z, __fadd2_rn(F1, neg2(nb1)));
-    float2 nr = __ffma2_rn(f2(a3q.z, a3q.z), rs0, z);
-    nr = __ffma2_rn(f2(b3q.z, b3q.z), rs1, nr);
+  for (int r = 0; r < G::H; ++r) {
+    const int rg = rb + r;
+    if (rg < HALO || rg >= HALO + G::BR) continue;
+    const float4 p0 = X.rq[4 * rg], p1 = X.rq[4 * rg + 1], p3 = X.rq[4 * rg + 3];
+    float2* Fr = reinterpret_cast<float2*>(Fs + rg * G::NH + 2 * q);
+    float2 nb;
+    if (((r + HALO) & 1) == 0) {   // red pair A (row of even gi)
+      float w = __shfl_up_sync(0xffffffffu, S.B[r].y, 1);
+      if (lane == 0) w = X.oR[v][wh][r];
+      const float2 nN = r > 0 ? S.A[r - 1] : X.BA[v][q];
+      const float2 nS = r + 1 < G::H ? S.A[r + 1] : X.TA[v + 1][q];
+      const float2 d = f2(q == 0 ? p3.y : p3.x, p3.x);
+      nb = __ffma2_rn(f2(p1.x, p1.y), __fadd2_rn(S.B[r], f2(w, S.B[r].x)),
+                      __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, __fmul2_rn(neg2(d), S.A[r]))));
+    } else {                        // red pair B (row of odd gi)
+      float e = __shfl_down_sync(0xffffffffu, S.A[r].x, 1);
+      if (lane == 31) e = X.eL[v][wh + 1][r];
+      const float2 nN = r > 0 ? S.B[r - 1] : X.BB[v][q];
+      const float2 nS = r + 1 < G::H ? S.B[r + 1] : X.TB[v + 1][q];
+      const float2 d = f2(p3.x, q == G::NQ - 1 ? p3.y : p3.x);
+      nb = __ffma2_rn(f2(p1.x, p1.y), __fadd2_rn(S.A[r], f2(S.A[r].y, e)),
+                      __ffma2_rn(f2(p0.z, p0.w), nN, __ffma2_rn(f2(p0.x, p0.y), nS, __fmul2_rn(neg2(d), S.B[r]))));
+    }
+    *Fr = __fadd2_rn(f2(0.f, 0.f), __fadd2_rn(*Fr, neg2(nb)));
+  }
+  __syncthreads();
+  // Restriction: coarse cells (I, 2q), (I, 2q + 1) from the red residuals of
+  // rows 2I and 2I + 1 weighted by their areas, in that order, times rden(I).
+  constexpr int NC = G::NC;
+  float* fcb = fc + b * NC * NC;
+  for (int Il = v; Il < G::BR / 2; Il += NV) {
+    const int rg = HALO + 2 * Il, I = (gi0 + rg) >> 1;
+    const float a0 = X.rq[4 * rg + 3].z, a1 = X.rq[4 * rg + 7].z;
+    const float2 rs0 = *reinterpret_cast<const float2*>(Fs + rg * G::NH + 2 * q);
+    const float2 rs1 = *reinterpret_cast<const float2*>(Fs + (rg + 1) * G::NH + 2 * q);
+    float2 nr = __ffma2_rn(f2(a0, a0), rs0, f2(0.f, 0.f));
+    nr = __ffma2_rn(f2(a1, a1), rs1, nr);
     const float rd = rden[I];
     const float2 out = __fmul2_rn(nr, f2(rd, rd));
     fcb[fidx(NC, I, 2 * q)] = out.x;
@@ -1196,115 +1229,70 @@ __device__ __forceinline__ void q_smooth_restrict_half(QShared<N, 5>& X, const f
   }
 }
 
-template <int N>
-__global__ void __launch_bounds__(N / 2, 768 / N) k_reg_smooth_restrict(const float* __restrict__ u_in,
-                                                                  float* __restrict__ u_out,
-                                                                  const float* __restrict__ f,
-                                                                  const float* __restrict__ coef,
-                                                                  const float* __restrict__ invd,
-                                                                  const float* __restrict__ diag,
-                                                                  const float* __restrict__ rden,
-                                                                  float* __restrict__ fc, int* d_err) {
-  using G = QBand<N, 5>;
-  extern __shared__ __align__(128) unsigned char smem_rsr[];
-  float* Fs = reinterpret_cast<float*>(smem_rsr);
-  __shared__ QShared<N, 5> X;
-  const size_t b = blockIdx.z;
-  const int gi0 = blockIdx.x * G::BR - 5;
-  q_issue_f<N, G::W>(Fs, &X.bar, f + b * N * N, gi0);
-  q_stage_rows<G::W>(X.rq, gi0, N, coef, invd, diag);
-  const int q = threadIdx.x % G::NQ;
-  const float* ui = u_in ? u_in + b * upatch(N) : nullptr;
-  float* uo = u_out + b * upatch(N);
-  float* fcb = fc + b * G::NC * G::NC;
-  // the halves run their own code (warp-uniform branch); every barrier is reached by all threads
-  if (threadIdx.x < G::NQ) q_smooth_restrict_half<N, 0>(X, Fs, ui, uo, rden, fcb, gi0, q, d_err);
-  else q_smooth_restrict_half<N, 1>(X, Fs, ui, uo, rden, fcb, gi0, q, d_err);
-}
-
-// Prolongation of the coarse correction onto the region and post-smoothing.
-template <int N, int V>
-__device__ __forceinline__ void q_prolong_smooth_half(QShared<N, 4>& X, const float* __restrict__ Fs,
-                                                      const float* __restrict__ E, const float* __restrict__ Ub_in,
-                                                      float* __restrict__ Ub_out, int gi0, int q, int* d_err) {
-  using G = QBand<N, 4>;
-  constexpr int HALO = 4, Pc = G::Pc, Wc = G::Wc;
-  QState<N, HALO> S;
-  q_load<N, HALO, V>(S, Ub_in, gi0, q);   // while the sources and the coarse rows arrive
-  if (!band_wait(&X.bar, d_err)) return;
-  // u += P(e_c) on the black cells of the region rows in the patch (the red
-  // ones are overwritten by the first half-sweep before anything reads them):
-  // in row gi the black cells are the A pair for odd gi, the B pair for even
-  // gi; fine row gi takes coarse rows I = gi / 2 and I -+ 1 (gi0 is even).
-  // E holds coarse rows gi0 / 2 - 1 .. in the correction layout: coarse cell
-  // (I, J) at entry J / 2 + 1 of colour plane (I + J) & 1.  Rows and columns
-  // beyond the coarse patch (zeros) are read only where the edge formula
-  // takes the injected value instead.
-  const float2 nine = f2(9.f, 9.f), three = f2(3.f, 3.f), sixteenth = f2(0.0625f, 0.0625f);
-#pragma unroll
-  for (int r = 0; r < G::H; ++r) {
-    const int rg = V * G::H + r, gi = gi0 + rg;
-    const bool halo_row = rg < HALO || rg >= HALO + G::BR;
-    const bool in = !halo_row || (unsigned)gi < (unsigned)N;
-    const bool rowedge = gi == 0 || gi == N - 1;
-    const int a = (rg >> 1) + 1, da = (rg & 1) ? a + 1 : a - 1;
-    // plane of coarse column 2q in coarse row I: the parity of I (= parity of a + gi0 / 2 - 1)
-    const int pa = (a + (gi0 >> 1) + 1) & 1, pd = pa ^ 1;
-    const float* Ea0 = E + (pa * Wc + a) * Pc + q;        // coarse columns 2q - 2 + 2j (entry q + j)
-    const float* Ea1 = E + ((pa ^ 1) * Wc + a) * Pc + q;  // coarse columns 2q - 1 + 2j
-    const float* Ed0 = E + (pd * Wc + da) * Pc + q;       // row I -+ 1: column 2q has the other plane
-    const float* Ed1 = E + ((pd ^ 1) * Wc + da) * Pc + q;
-    const float2 e11 = f2(Ea0[1], Ea1[1]), d11 = f2(Ed0[1], Ed1[1]);   // columns 2q, 2q + 1
-    if (rg & 1) {   // odd row: A = coarse columns 2q, 2q + 1, outer neighbours 2q - 1, 2q
-      const float2 c = __fmul2_rn(__ffma2_rn(nine, e11, __ffma2_rn(three, __fadd2_rn(d11, f2(Ea1[0], Ea0[1])), f2(Ed1[0], Ed0[1]))),
-                                  sixteenth);
-      const float2 cc = f2((rowedge || q == 0) ? e11.x : c.x, rowedge ? e11.y : c.y);
-      if (in) S.A[r] = __fadd2_rn(S.A[r], cc);
-    } else {        // even row: B = coarse columns 2q, 2q + 1, outer neighbours 2q + 1, 2q + 2
-      const float2 c = __fmul2_rn(__ffma2_rn(nine, e11, __ffma2_rn(three, __fadd2_rn(d11, f2(Ea1[1], Ea0[2])), f2(Ed1[1], Ed0[2]))),
-                                  sixteenth);
-      const float2 cc = f2(rowedge ? e11.x : c.x, (rowedge || q == G::NQ - 1) ? e11.y : c.y);
-      if (in) S.B[r] = __fadd2_rn(S.B[r], cc);
-    }
-  }
-  q_publish_all<N, HALO, V>(S, X, q);
-  __syncthreads();
-  q_sweeps<N, HALO, V>(S, X, Fs, gi0, q);
-  q_store<N, HALO, V>(S, Ub_out, gi0, q);
-}
-
-template <int N>
-__global__ void __launch_bounds__(N / 2, 768 / N) k_reg_prolong_smooth(const float* __restrict__ u_in,
-                                                                 float* __restrict__ u_out,
-                                                                 const float* __restrict__ f,
-                                                                 const float* __restrict__ coef,
-                                                                 const float* __restrict__ invd,
-                                                                 const float* __restrict__ diag,
-                                                                 const float* __restrict__ uc, int* d_err) {
-  using G = QBand<N, 4>;
+template <int N, int NV>
+__global__ void __launch_bounds__(QBand<N, 4, NV>::NT) k_reg_prolong_smooth(
+    const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
+    const float* __restrict__ coef, const float* __restrict__ invd, const float* __restrict__ diag,
+    const float* __restrict__ uc, int* d_err) {
+  constexpr int HALO = 4;
+  using G = QBand<N, HALO, NV>;
   constexpr int NC = G::NC, Wc = G::Wc, Pc = G::Pc;
   extern __shared__ __align__(128) unsigned char smem_rps[];
   float* Fs = reinterpret_cast<float*>(smem_rps);
   float* E = Fs + 2 * G::W * G::NH;
-  __shared__ QShared<N, 4> X;
+  __shared__ QShared<N, HALO, NV> X;
   const size_t b = blockIdx.z;
-  const int gi0 = blockIdx.x * G::BR - 4;
+  const int gi0 = blockIdx.x * G::BR - HALO;
+  const int v = threadIdx.x / G::NQ, q = threadIdx.x % G::NQ;
+  const int rb = v * G::H;
   // with the sources, the coarse correction's rows gi0 / 2 - 1 .. + Wc - 1 of
   // both colour planes (rows beyond the coarse patch are zero rows of the layout)
-  const uint32_t bytes = (uint32_t)(Wc * Pc * sizeof(float));
-  q_issue_f<N, G::W>(Fs, &X.bar, f + b * N * N, gi0, 2 * bytes);
+  const uint32_t cbytes = (uint32_t)(Wc * Pc * sizeof(float));
+  q_begin<N, HALO, NV>(X, Fs, f + b * N * N, gi0, coef, invd, diag, 2 * cbytes);
   if (threadIdx.x == 0) {
     const float* Cc = uc + b * upatch(NC) + (size_t)((gi0 >> 1) - 1 + 1 + kUHalo) * Pc;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) umma::bulk_g2s(E + c * Wc * Pc, Cc + c * uplane_of(NC), bytes, &X.bar);
+    for (int c = 0; c < 2; ++c) umma::bulk_g2s(E + c * Wc * Pc, Cc + c * uplane_of(NC), cbytes, &X.bar);
   }
-  q_stage_rows<G::W>(X.rq, gi0, N, coef, invd, diag);
-  const int q = threadIdx.x % G::NQ;
-  const float* ui = u_in + b * upatch(N);
-  float* uo = u_out + b * upatch(N);
-  // the halves run their own code (warp-uniform branch); every barrier is reached by all threads
-  if (threadIdx.x < G::NQ) q_prolong_smooth_half<N, 0>(X, Fs, E, ui, uo, gi0, q, d_err);
-  else q_prolong_smooth_half<N, 1>(X, Fs, E, ui, uo, gi0, q, d_err);
+  QState<N, HALO, NV> S;
+  q_load<N, HALO, NV>(S, u_in + b * upatch(N), gi0 + rb, q);   // while the sources and the coarse rows arrive
+  if (!band_wait(&X.bar, d_err)) return;
+  // u += P(e_c) on the black cells of the thread's rows (the red ones are
+  // overwritten by the first half-sweep before anything reads them): in row
+  // gi the black cells are the A pair for odd gi, the B pair for even gi;
+  // fine row gi takes coarse rows I = gi / 2 and I -+ 1 (gi0 is even).  E
+  // holds coarse rows gi0 / 2 - 1 .. in the correction layout: coarse cell
+  // (I, J) at entry J / 2 + 1 of colour plane (I + J) & 1.  Rows and columns
+  // beyond the coarse patch hold zeros, read only where the patch's edge cells
+  // take the injected value instead; rows beyond the patch stay zero.
+  const float2 nine = f2(9.f, 9.f), three = f2(3.f, 3.f), sixteenth = f2(0.0625f, 0.0625f);
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const int rg = rb + r, gi = gi0 + rg;
+    if ((unsigned)gi >= (unsigned)N) continue;
+    const bool rowedge = gi == 0 || gi == N - 1;
+    const int a = (rg >> 1) + 1, da = (r & 1) ? a + 1 : a - 1;
+    // plane of coarse column 2q in coarse row I = gi0 / 2 - 1 + a: the parity of I
+    const int pa = (a + (gi0 >> 1) + 1) & 1, pd = pa ^ 1;
+    const float* Ea0 = E + (pa * Wc + a) * Pc + q;        // even coarse columns 2q - 2 + 2j (entry q + j)
+    const float* Ea1 = E + ((pa ^ 1) * Wc + a) * Pc + q;  // odd coarse columns 2q - 1 + 2j
+    const float* Ed0 = E + (pd * Wc + da) * Pc + q;       // row I -+ 1: even columns in the other plane
+    const float* Ed1 = E + ((pd ^ 1) * Wc + da) * Pc + q;
+    const float2 e11 = f2(Ea0[1], Ea1[1]), d11 = f2(Ed0[1], Ed1[1]);   // columns 2q, 2q + 1
+    if (r & 1) {   // odd row: A = coarse columns 2q, 2q + 1, outer neighbours 2q - 1, 2q
+      const float2 c = __fmul2_rn(__ffma2_rn(nine, e11, __ffma2_rn(three, __fadd2_rn(d11, f2(Ea1[0], Ea0[1])), f2(Ed1[0], Ed0[1]))),
+                                  sixteenth);
+      S.A[r] = __fadd2_rn(S.A[r], f2((rowedge || q == 0) ? e11.x : c.x, rowedge ? e11.y : c.y));
+    } else {       // even row: B = coarse columns 2q, 2q + 1, outer neighbours 2q + 1, 2q + 2
+      const float2 c = __fmul2_rn(__ffma2_rn(nine, e11, __ffma2_rn(three, __fadd2_rn(d11, f2(Ea1[1], Ea0[2])), f2(Ed1[1], Ed0[2]))),
+                                  sixteenth);
+      S.B[r] = __fadd2_rn(S.B[r], f2(rowedge ? e11.x : c.x, (rowedge || q == G::NQ - 1) ? e11.y : c.y));
+    }
+  }
+  q_publish_all<N, HALO, NV>(S, X, v, q);
+  __syncthreads();
+  q_sweeps<N, HALO, NV>(S, X, Fs, v, q);
+  q_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, q);
 }
 
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
@@ -1735,22 +1723,26 @@ struct MG {
   // the residual to level l + 1: row bands for patches of 16 .. kBandMaxN
   // cells a side, square blocks beyond
   // register-resident band kernels: FP32, two sweeps, 128 or 256 cells a side
+  static constexpr int kRegPartsSR = 3, kRegPartsPS = 2;   // row parts of the two kernels' regions
   template <int N>
   void reg_smooth_restrict(int l, bool zero) {
-    using QB = QBand<N, 5>;
-    CLC_LAUNCH(ctx, "k_smooth_restrict", k_reg_smooth_restrict<N>, dim3(N / QB::BR, 1, s->npatch), dim3(N / 2),
-               QB::f_bytes, zero ? nullptr : (const float*)U(l), (float*)U2(l), (const float*)F(l),
+    using QB = QBand<N, 5, kRegPartsSR>;
+    // static plus dynamic shared memory goes beyond 48 KB: opt in
+    cudaFuncSetAttribute(k_reg_smooth_restrict<N, kRegPartsSR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)QB::f_bytes);
+    CLC_LAUNCH(ctx, "k_smooth_restrict", (k_reg_smooth_restrict<N, kRegPartsSR>), dim3(N / QB::BR, 1, s->npatch),
+               dim3(QB::NT), QB::f_bytes, zero ? nullptr : (const float*)U(l), (float*)U2(l), (const float*)F(l),
                (const float*)C(l), (const float*)D(l), (const float*)G(l), (const float*)RD(l), (float*)F(l + 1),
                ctx->d_err);
   }
   template <int N>
   void reg_prolong_smooth(int l) {
-    using QB = QBand<N, 4>;
+    using QB = QBand<N, 4, kRegPartsPS>;
     constexpr size_t smb = QB::f_bytes + QB::e_bytes;
-    if (smb > 48 * 1024) cudaFuncSetAttribute(k_reg_prolong_smooth<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-    CLC_LAUNCH(ctx, "k_prolong_smooth", k_reg_prolong_smooth<N>, dim3(N / QB::BR, 1, s->npatch), dim3(N / 2), smb,
-               (const float*)U2(l), (float*)U(l), (const float*)F(l), (const float*)C(l), (const float*)D(l),
-               (const float*)G(l), (const float*)U(l + 1), ctx->d_err);
+    cudaFuncSetAttribute(k_reg_prolong_smooth<N, kRegPartsPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    CLC_LAUNCH(ctx, "k_prolong_smooth", (k_reg_prolong_smooth<N, kRegPartsPS>), dim3(N / QB::BR, 1, s->npatch),
+               dim3(QB::NT), smb, (const float*)U2(l), (float*)U(l), (const float*)F(l), (const float*)C(l),
+               (const float*)D(l), (const float*)G(l), (const float*)U(l + 1), ctx->d_err);
   }
   bool use_reg(int n, int nu) const { return kF32 && nu == 2 && (n == 128 || n == 256); }
 

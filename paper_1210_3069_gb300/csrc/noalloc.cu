@@ -12,6 +12,7 @@
 // during stream capture), code embedded in a framework whose caching
 // allocator owns all device memory, or services that must not grow their
 // footprint after start-up.
+#include <atomic>
 #include "common.cuh"
 
 namespace clc {
@@ -140,17 +141,17 @@ using namespace clc;
 // Device address of the scratch array, looked up once per device (the first
 // call on a device does it; make that first call before any stream capture).
 static double2* noalloc_scratch(int device) {
-  static double2* addr[64] = {nullptr};
+  static std::atomic<double2*> addr[64];   // concurrent first calls store the same address
   if (device < 0 || device >= 64) return nullptr;
-  if (!addr[device]) {
-    double2* p = nullptr;
-    if (cudaGetSymbolAddress((void**)&p, g_noalloc_ring_fourier) != cudaSuccess) {
+  double2* a = addr[device].load(std::memory_order_acquire);
+  if (!a) {
+    if (cudaGetSymbolAddress((void**)&a, g_noalloc_ring_fourier) != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
-    addr[device] = p;
+    addr[device].store(a, std::memory_order_release);
   }
-  return addr[device];
+  return a;
 }
 
 extern "C" int clc_sht_analysis_noalloc(const double* map, int nside, int lmax, double* alm, void* cuda_stream) {
@@ -163,7 +164,10 @@ extern "C" int clc_sht_analysis_noalloc(const double* map, int nside, int lmax, 
   if (!F) return CLC_ECUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const double w = 4.0 * kPi / (12.0 * (double)nside * nside);
+  // an error left by earlier work on this thread stays with its owner
+  if (cudaPeekAtLastError() != cudaSuccess) return CLC_ECUDA;
   k_ring_dft_noalloc<<<4 * nside - 1, 128, 0, st>>>(map, nside, lmax, w, F);
+  if (cudaGetLastError() != cudaSuccess) return CLC_ECUDA;
   k_legendre_analysis_noalloc<<<lmax + 1, 256, 0, st>>>(nside, lmax, F, (double2*)alm);
   return cudaGetLastError() == cudaSuccess ? CLC_OK : CLC_ECUDA;
 }

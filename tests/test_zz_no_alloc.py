@@ -52,3 +52,22 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     assert f(p, 8, 33, q, None) == 1           # lmax above 4 nside
     assert f(p, 48, 10, q, None) == 1          # nside not a power of two
     assert f(None, 8, 10, q, None) == 1
+
+
+@pytest.mark.parametrize("nside", [1, 2, 4, 8])
+def test_noalloc_analysis_at_the_smallest_nsides(nside):
+    """A single ring-group of pixels per face (nside 1) up to nside 8, lmax
+    3 nside - 1: the few-ring grids where the polar and equatorial ring
+    lengths differ most."""
+    c = ctx()
+    f = _noalloc()
+    lmax = 3 * nside - 1
+    g = torch.Generator().manual_seed(100 + nside)
+    m = torch.randn(12 * nside * nside, dtype=torch.float64, generator=g).cuda()
+    ref = c.sht_analysis(m, nside, lmax)
+    out = torch.full_like(ref, float("nan"))
+    stream = torch.cuda.current_stream().cuda_stream
+    assert f(ctypes.c_void_p(m.data_ptr()), nside, lmax, ctypes.c_void_p(out.data_ptr()),
+             ctypes.c_void_p(stream)) == 0
+    torch.cuda.synchronize()
+    assert rel_l2(out, ref) < 1e-10, (nside, lmax)
