@@ -106,13 +106,15 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop
 # lookup included), counted operation by operation on the formulas of the
 # kernel (an FMA is 2, a square root, reciprocal square root or division 1,
 # the small-angle series of asin and of the rotation coefficients term by
-# term): unit vector and tangent basis 20; patch lookup 293 (rotation to
-# the patch frame 15, angles 39, bilinear blend of the 6 x 6 stencil block
-# 177 = cell fractions 4 + row/column blends 36 + first-derivative blends of
-# the six rows 66 + five blended partials 63 + scales 8, Appendix A 10, rotation to the
-# global basis 52); Eq. Atraj 29; Eq. betaprop 81; Eq. posprop 16; new
-# unit vector and basis 20; Appendix B transport 32 and two Q A Q^T 48.
-RAY_STEP_FLOPS_MG = 539
+# term): unit vector x / chi_n 3 and tangent basis 11; patch lookup 301
+# (rotation to the patch frame 15, angles 39, bilinear blend of the 6 x 6
+# stencil block 189 = cell fractions 4 + row/column blends 36 + the two
+# sets of six blended first-derivative weights 12 + first-derivative sums of
+# the six rows 66 + five blended partials 63 + scales 8, Appendix A 10,
+# rotation to the global basis 48); Eq. Atraj 29; Eq. betaprop 81; Eq.
+# posprop 15; new unit vector and basis 14; Appendix B transport 32 and two
+# Q A Q^T as rotations of the traceless parts 41.
+RAY_STEP_FLOPS_MG = 527
 KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
            "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",

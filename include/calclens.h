@@ -310,7 +310,10 @@ int clc_rays_init_pixels(clc_ctx* ctx, int nside, double chi0, int nside_bundle,
  * nside_maps (sol == NULL; ring-bilinear interpolation of alpha as a tangent
  * 3-vector and U as a tangent 3x3 tensor).  chi_prev is the previous plane
  * (0 for the first plane).  Eq. Atraj, Eq. betaprop, Eq. posprop and the
- * parallel transport of Appendix B. */
+ * parallel transport of Appendix B.  The rays must lie on the sphere of
+ * radius chi_n, as clc_rays_init / clc_rays_init_pixels at chi_n and the
+ * previous clc_ray_step to chi_n leave them: a ray's direction is taken as
+ * x / chi_n. */
 int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const clc_derivs* maps,
                  int nside_maps, double chi_prev, double chi_n, double chi_next, clc_rays* rays);
 

@@ -94,6 +94,22 @@ __device__ __forceinline__ double c_d2(const double* y, int s) {
 }
 // the blend (1 - f) D(k) + f D(k + 1) of two neighbouring cells' stencils
 __device__ __forceinline__ double blend_d1(const double* y, double f) { return fma(f, c_d1(y, 1) - c_d1(y, 0), c_d1(y, 0)); }
+// The six weights of blend_d1 over y[0 .. 5] (g = 1 - f): g D + f D shifted
+// by one point, D = (1, -8, 0, 8, -1), for sums taken several times with one f
+__device__ __forceinline__ void d1_weights(double f, double g, double w[6]) {
+  w[0] = g;
+  w[1] = fma(-8.0, g, f);
+  w[2] = -8.0 * f;
+  w[3] = 8.0 * g;
+  w[4] = fma(8.0, f, -g);
+  w[5] = -f;
+}
+__device__ __forceinline__ double dot6(const double w[6], const double* y) {
+  double s = w[0] * y[0];
+#pragma unroll
+  for (int b = 1; b < 6; ++b) s = fma(w[b], y[b], s);
+  return s;
+}
 __device__ __forceinline__ double blend_d2(const double* y, double f) { return fma(f, c_d2(y, 1) - c_d2(y, 0), c_d2(y, 0)); }
 
 // Lens fields at unit vector nv (tangent basis et, ep there) from patch
@@ -136,8 +152,10 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   if (ii >= 2 && ii + 4 <= n && jj >= 2 && jj + 4 <= n) {
     // central stencils: block rows / columns ii - 2 .. ii + 3, jj - 2 .. jj + 3
     const T* ub = u + (size_t)(ii - 1) * pitch + (jj - 1);
-    double c[6], mix[6], r[6];
+    double c[6], mix[6], r[6], wx[6], wy[6];
     const double gy = 1.0 - fy, gx = 1.0 - fx;
+    d1_weights(fx, gx, wx);
+    d1_weights(fy, gy, wy);
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
       const T* row = ub + (size_t)a * pitch;
@@ -145,15 +163,15 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
 #pragma unroll
       for (int b = 0; b < 6; ++b) v[b] = (double)row[b];
       c[a] = fma(fy, v[3], gy * v[2]);    // columns jj, jj + 1
-      mix[a] = blend_d1(v, fy);
+      mix[a] = dot6(wy, v);
     }
     const T* ra = ub + 2 * pitch;         // rows ii, ii + 1
 #pragma unroll
     for (int b = 0; b < 6; ++b) r[b] = fma(fx, (double)ra[pitch + b], gx * (double)ra[b]);
-    pt = blend_d1(c, fx);
+    pt = dot6(wx, c);
     ptt = blend_d2(c, fx);
-    ptp = blend_d1(mix, fx);
-    pp = blend_d1(r, fy);
+    ptp = dot6(wx, mix);
+    pp = dot6(wy, r);
     ppp = blend_d2(r, fy);
   } else {
     double A1[6], A2[6], B1[6], B2[6];
@@ -202,12 +220,14 @@ __device__ __forceinline__ void patch_lens_fields_t(const T* u, int n, double h,
   const double q10 = ep[0] * tg[0] + ep[1] * tg[1];
   out[0] = q00 * a_t - q10 * a_p;
   out[1] = q10 * a_t + q00 * a_p;
-  // U_g = Q U Q^T
-  const double m00 = q00 * u_tt - q10 * u_tp, m01 = q00 * u_tp - q10 * u_pp;
-  const double m10 = q10 * u_tt + q00 * u_tp, m11 = q10 * u_tp + q00 * u_pp;
-  out[2] = m00 * q00 - m01 * q10;            // U_tt
-  out[3] = m10 * q10 + m11 * q00;            // U_pp
-  out[4] = m00 * q10 + m01 * q00;            // U_tp
+  // U_g = Q U Q^T: the trace is kept and the traceless part
+  // ((u_tt - u_pp) / 2, u_tp) turns by twice the angle of Q
+  const double cq = fma(q00, q00, -q10 * q10), sq = 2.0 * q00 * q10;
+  const double hs = 0.5 * (u_tt + u_pp), hd = 0.5 * (u_tt - u_pp);
+  const double e2 = fma(cq, hd, -sq * u_tp);
+  out[2] = hs + e2;                          // U_tt
+  out[3] = hs - e2;                          // U_pp
+  out[4] = fma(sq, hd, cq * u_tp);           // U_tp
 }
 
 // Patch slot of bundle b: the bundle itself on the full sky, the domain's

@@ -110,6 +110,7 @@ __device__ void map_lens_fields(const clc_derivs& M, int nside, const double nv[
 
 struct StepCoef {
   double c, d, dchi2;
+  double ichi_n, ichi_next;   // 1 / chi_n, 1 / chi_next
 };
 
 // Rotation of beta about the unit axis k = n x alpha / |alpha| by the angle
@@ -157,6 +158,19 @@ __device__ __forceinline__ void transport_q_closed(const double n0[3], const dou
   Q[3] = q0;
 }
 
+// o = Q A Q^T for the plane rotation Q = [[q0, -q1], [q1, q0]]: the parts
+// (a00 + a11, a10 - a01) of A are kept and (a00 - a11, a01 + a10) turn by
+// twice the angle of Q
+__device__ __forceinline__ void rotate_2x2(double q0, double q1, const double A[4], double o[4]) {
+  const double c2 = 0.5 * fma(q0, q0, -q1 * q1), s2 = q0 * q1;   // halves of cos, sin of twice the angle
+  const double sm = A[0] + A[3], sk = A[2] - A[1], df = A[0] - A[3], sy = A[1] + A[2];
+  const double e = fma(c2, df, -s2 * sy), f = fma(s2, df, c2 * sy);
+  o[0] = fma(0.5, sm, e);
+  o[3] = fma(0.5, sm, -e);
+  o[1] = fma(-0.5, sk, f);
+  o[2] = fma(0.5, sk, f);
+}
+
 template <bool kMG>
 __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, StepCoef sc) {
   const int64_t n = R.n;
@@ -166,8 +180,9 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     for (int c = 0; c < 3; ++c) { x[c] = R.x[c * n + k]; be[c] = R.beta[c * n + k]; }
 #pragma unroll
     for (int c = 0; c < 4; ++c) { A[c] = R.A[c * n + k]; Ap[c] = R.Ap[c * n + k]; }
-    const double ixn = rsqrt(dot3(x, x));
-    const double nv[3] = {x[0] * ixn, x[1] * ixn, x[2] * ixn};
+    // the ray is on the sphere of radius chi_n (where the previous step or the
+    // initialisation put it): its direction is x / chi_n
+    const double nv[3] = {x[0] * sc.ichi_n, x[1] * sc.ichi_n, x[2] * sc.ichi_n};
     double t[3], q[3];
     tangent_basis(nv, t, q);
     double L[5];
@@ -185,20 +200,21 @@ __global__ void k_ray_step(RayPtrs R, MGView V, clc_derivs M, int nside_maps, St
     double kk[3], bn[3];
     cross3(nv, av, kk);
     rotate_by_deflection(be, kk, dot3(av, av), bn);
-    // Eq. posprop: lambda > 0 root, rationalised
+    // Eq. posprop: the root lambda > 0 of |x + lambda beta|^2 = chi_next^2
+    // (beta is nearly radial, x . beta close to chi_n, so the difference of
+    // the two terms keeps all but log2(chi_n / (chi_next - chi_n)) bits)
     const double xb = dot3(x, bn);
-    const double lam = sc.dchi2 / (xb + sqrt(xb * xb + sc.dchi2));
+    const double lam = sqrt(fma(xb, xb, sc.dchi2)) - xb;
     double x1[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x1[c] = x[c] + lam * bn[c];
-    const double ix1 = rsqrt(dot3(x1, x1));
-    const double n1[3] = {x1[0] * ix1, x1[1] * ix1, x1[2] * ix1};
+    for (int c = 0; c < 3; ++c) x1[c] = fma(lam, bn[c], x[c]);
+    const double n1[3] = {x1[0] * sc.ichi_next, x1[1] * sc.ichi_next, x1[2] * sc.ichi_next};
     // Appendix B: transport A^(n+1) and A^(n) to the basis at the new point
     double t1[3], p1[3], Q[4], Ao[4], Apo[4];
     tangent_basis(n1, t1, p1);
     transport_q_closed(nv, t, n1, t1, p1, Q);
-    qaqt(Q, An, Ao);
-    qaqt(Q, A, Apo);
+    rotate_2x2(Q[0], Q[2], An, Ao);
+    rotate_2x2(Q[0], Q[2], A, Apo);
 #pragma unroll
     for (int c = 0; c < 3; ++c) { R.x[c * n + k] = x1[c]; R.beta[c * n + k] = bn[c]; }
 #pragma unroll
@@ -268,7 +284,9 @@ extern "C" int clc_ray_step(clc_ctx* ctx, const clc_plane_solution* sol, const c
   StepCoef sc;
   sc.c = (chi_n / chi_next) * ((chi_next - chi_prev) / (chi_n - chi_prev));
   sc.d = (chi_next - chi_n) / chi_next;
-  sc.dchi2 = chi_next * chi_next - chi_n * chi_n;
+  sc.dchi2 = (chi_next - chi_n) * (chi_next + chi_n);
+  sc.ichi_n = 1.0 / chi_n;
+  sc.ichi_next = 1.0 / chi_next;
   clc_derivs M{};
   if (maps) M = *maps;
   if (sol) {
