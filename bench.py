@@ -232,7 +232,7 @@ def kernel_models(cfg, precision, cycles, nsteps):
 # first V-cycle).  Traffic grows with the number of patches, so a launch at
 # another patch count moves (this x patches / 5) bytes on average.
 BAND_DRAM_PER_PATCH_CYCLE = {
-    "k_prolong_smooth": (0.003 + 0.010 + 0.033 + 0.122 + 0.023 + 0.469 + 0.177) * 1e9 / 768,
+    "k_prolong_smooth": (0.0034 + 0.0097 + 0.0329 + 0.1283 + 0.0182 + 0.4880 + 0.1711) * 1e9 / 768,
 }
 
 
