@@ -198,7 +198,8 @@ def kernel_models(cfg, precision, cycles, nsteps):
     multiply), 10 per cell for the restricted residual and 7 for the
     prolongation.  The FP64
     residual of the mixed path (float-float on the FP32 pipe): 32 bytes per
-    fine cell per refinement (one refinement per two V-cycles, plus the first)."""
+    fine cell per refinement (one refinement per two V-cycles), and 12 for
+    the first residual of a solve (e = 0: the defect in, the FP32 source out)."""
     npatch = 12 * cfg["nside_bundle"] ** 2
     cells_cycle = 0
     n = cfg["ncell"]
@@ -216,10 +217,11 @@ def kernel_models(cfg, precision, cycles, nsteps):
         out["k_smooth_restrict"] = ("hbm", 9.0 * cells_cycle * ncyc + 4.0 * cells0 * (ncyc - nzero), "byte")
         out["k_prolong_smooth"] = ("hbm", 13.0 * cells_cycle * ncyc, "byte")
     if precision == "mixed":
-        # float-float residual: e (8 B) and d (4 B) in, source (8 B) in, e (8 B) and r (4 B) out per fine cell
+        # float-float residual: e (8 B) and d (4 B) in, source (8 B) in, e (8 B) and r (4 B) out per fine
+        # cell; the first of a solve reads the source (8 B) and writes r (4 B)
         n0 = cfg["ncell"]
-        nres = sum((c + 1) // 2 + 1 for c in cycles)
-        out["k_resid_mixed"] = ("hbm", 32.0 * npatch * n0 * n0 * nres, "byte")
+        nref = sum((c + 1) // 2 for c in cycles)
+        out["k_resid_mixed"] = ("hbm", (32.0 * nref + 12.0 * len(cycles)) * npatch * n0 * n0, "byte")
     # the ray step: FP64-ALU bound (228 B of state per ray against ~540 FP64
     # operations), one step of every ray per plane
     out["k_ray_step"] = ("alu", float(RAY_STEP_FLOPS_MG) * 12 * cfg["nside"] ** 2 * nsteps, "flop")

@@ -1440,6 +1440,35 @@ __global__ void __launch_bounds__(kBX * kBY) k_resid_ff_walk(const float2* __res
   if (lane == 0 && rr != 0.f) atomicAdd(norms + b, (double)rr);
 }
 
+// First residual of a mixed solve, where e = 0: r = f' (the float-float
+// defect; with the operator's terms all zero the walk above returns its
+// renormalised sum), the FP32 source fl(hi + lo) and ||r||^2 per patch,
+// without the stencil: f' and the source are the patches' contiguous arrays
+// (same cell order), read and written as one stream.  e stays zero.
+constexpr int kFirstThreads = 256, kFirstPer = 16;   // cells per thread and block pass
+__global__ void __launch_bounds__(kFirstThreads) k_resid_first_ff(const float2* __restrict__ fd, int nn,
+                                                                  float* __restrict__ r32,
+                                                                  double* __restrict__ norms) {
+  const int b = blockIdx.y;
+  const size_t pb = (size_t)b * nn;
+  float rr = 0.f;
+  for (int i = blockIdx.x * kFirstThreads + threadIdx.x; i < nn; i += gridDim.x * kFirstThreads) {
+    const float2 f = fd[pb + i];
+    const float r = f.x + f.y;
+    r32[pb + i] = r;
+    rr = fmaf(r, r, rr);
+  }
+  for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(0xffffffffu, rr, o);
+  __shared__ float part[kFirstThreads / 32];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = rr;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kFirstThreads / 32; ++w) t += part[w];
+    if (t != 0.f) atomicAdd(norms + b, (double)t);
+  }
+}
+
 // final potential u = base + e for a float-float correction
 __global__ void k_combine_ff(double* __restrict__ base, const float2* __restrict__ e, int n) {
   const int b = blockIdx.z;
@@ -1917,6 +1946,22 @@ struct MG {
     return launch_check(ctx, "MG setup");
   }
 
+  // CLC_MIXED, before the first V-cycle (e = 0): r = f'
+  int residual_first(const float2* e_zero, double* ratio_host) {
+    const int n = s->sizes[0], nn = n * n;
+    cudaMemsetAsync(s->norms.p, 0, sizeof(double) * s->npatch, ctx->stream);
+    const dim3 grid((nn + kFirstThreads * kFirstPer - 1) / (kFirstThreads * kFirstPer), s->npatch);
+    CLC_LAUNCH(ctx, "k_resid_mixed", k_resid_first_ff, grid, kFirstThreads, 0, (const float2*)s->fd64.p, nn,
+               (float*)s->f[0].p, (double*)s->norms.p);
+    stop_ratio<float2>(e_zero, tau_rule());
+    int rc = launch_check(ctx, "MG mixed residual");
+    if (rc) return rc;
+    rc = cuda_check(ctx, cudaMemcpyAsync(ratio_host, s->ratio.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+                    "residual copy");
+    if (rc) return rc;
+    return cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "residual sync");
+  }
+
   // CLC_MIXED: r = f' - L e in float-float (also the next FP32 source), FP32
   // V-cycle on L d = r from d = 0, e += d; u = base + e at the end
   int residual_mixed(const float2* e_old, const float* d, float2* e_new, double* ratio_host) {
@@ -1943,8 +1988,7 @@ struct MG {
     const bool fixed = s->p.fixed_cycles > 0;
     float2* cur = (float2*)s->e64.p;
     float2* nxt = (float2*)s->e64b.p;
-    if ((rc = residual_mixed(cur, nullptr, nxt, &rr))) return rc;
-    std::swap(cur, nxt);
+    if ((rc = residual_first(cur, &rr))) return rc;   // cur: zero since the set-up
     const double limit = tau_rule() ? s->p.eps : s->p.tol;
     const int per = s->p.refine_cycles > 0 ? s->p.refine_cycles : 2;
     while (fixed ? s->cycles < s->p.fixed_cycles : (rr >= limit && s->cycles < s->p.max_cycles)) {
