@@ -115,7 +115,7 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop
 # posprop 15; new unit vector and basis 14; Appendix B transport 32 and two
 # Q A Q^T as rotations of the traceless parts 41.
 RAY_STEP_FLOPS_MG = 527
-KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
+KERNELS = ("k_smooth_restrict", "k_prolong_smooth", "k_sub_vcycle", "k_coarse_solve", "k_resnorm", "k_resid_mixed",
            "k_combine", "k_mg_setup_base", "k_mg_setup_defect", "k_ray_step", "k_bin",
            "k_legendre_analysis", "k_legendre_synthesis", "k_ring_analysis", "k_ring_synthesis", "k_poisson_rhs",
            "k_degrade", "k_rays_init", "k_counts_to_kappa", "k_max_ratio", "k_split_ff")
@@ -203,7 +203,7 @@ def kernel_models(cfg, precision, cycles, nsteps):
     npatch = 12 * cfg["nside_bundle"] ** 2
     cells_cycle = 0
     n = cfg["ncell"]
-    while n > 8:
+    while n > band_floor(cfg):
         cells_cycle += npatch * n * n
         n //= 2
     cells0 = npatch * cfg["ncell"] ** 2
@@ -228,13 +228,19 @@ def kernel_models(cfg, precision, cycles, nsteps):
     return out
 
 
+def band_floor(cfg):
+    """Largest level size NOT run by the band kernels: the levels of 32 cells
+    and below (down to the 8 x 8 coarsest) run in one k_sub_vcycle launch."""
+    return 32 if cfg["ncell"] >= 16 and cfg["nu1"] >= 1 else 8
+
+
 # DRAM bytes (read + write) of one V-cycle of the FP32 band kernels per
-# patch of 256^2 cells, over its five band levels (256 .. 16), from the ncu
+# patch of 256^2 cells, over its three band levels (256 .. 64), from the ncu
 # capture of the Nside-512 plane (768 patches; every level's launch of the
 # first V-cycle).  Traffic grows with the number of patches, so a launch at
-# another patch count moves (this x patches / 5) bytes on average.
+# another patch count moves (this x patches / 3) bytes on average.
 BAND_DRAM_PER_PATCH_CYCLE = {
-    "k_prolong_smooth": (0.0034 + 0.0097 + 0.0329 + 0.1283 + 0.0182 + 0.4880 + 0.1711) * 1e9 / 768,
+    "k_prolong_smooth": (0.0329 + 0.1283 + 0.0182 + 0.4880 + 0.1711) * 1e9 / 768,
 }
 
 
@@ -244,7 +250,7 @@ def band_traffic(name, cfg, precision):
     per = BAND_DRAM_PER_PATCH_CYCLE.get(name)
     if per is None or cfg["ncell"] != 256 or precision == "fp64":
         return None
-    return per * 12 * cfg["nside_bundle"] ** 2 / 5
+    return per * 12 * cfg["nside_bundle"] ** 2 / 3
 
 
 def roofline(prof, models, peaks, peak_kind, traffic=None):

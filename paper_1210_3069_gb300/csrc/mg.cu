@@ -1295,6 +1295,233 @@ __global__ void __launch_bounds__(QBand<N, 4, NV>::NT) k_reg_prolong_smooth(
   q_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, q);
 }
 
+// ---------------------------------------------------------------------------
+// The coarse end of a V-cycle in one launch: the levels of at most kSubMax
+// cells a side, from a level's pre-smoothing down to the exact solve of the
+// 8 x 8 coarsest level and back up through every prolongation and
+// post-smoothing, one CTA per patch with every level's correction, source
+// and row coefficients in shared memory.  The separate band kernels spend
+// most of their time on launch and memory latency at these sizes; here only
+// the top level's source (in) and correction (out) cross HBM.  Each sweep,
+// restriction and prolongation is that of the band kernels, operation for
+// operation.  The coarsest solve is the dense inverse applied in FP64 for
+// FP64 V-cycles and in FP32 for the FP32 ones (four lanes per row, partial
+// sums added by shuffles; its rounding is that of the FP32 cycle around it).
+// Corrections are dense (n + 2)^2 arrays with a zero ghost ring, sources
+// dense n^2.  (At 64 cells a side the whole-patch arrays leave room for too
+// few CTAs per SM: that level stays with the band kernels.)
+constexpr int kSubMax = 32, kSubThreads = 256, kSubCoarse = 8;
+
+template <typename T>
+struct SubLev {
+  const T* coef;   // [4 n]: aS, aN, b, area per row
+  const T* invd;   // [n n]: 1 / diagonal (column 0: edge cells, 1: interior)
+  const T* diag;
+  const T* rden;   // [n / 2]
+};
+
+template <typename T>
+struct SubArgs {
+  SubLev<T> lev[4];     // levels n0, n0 / 2, .. down to 16 (the 8 x 8 level needs none)
+  int nu1, nu2;
+  const double* minv;   // the 8 x 8 level's dense inverse [64][64]
+  const float* minv32;  // the same in FP32
+};
+
+// row coefficients of a level in shared memory: aS, aN, b, area, 1/d (edge,
+// interior), d (edge, interior) per row, rden per coarse row
+template <typename T, int N>
+struct SubRows {
+  T aS[N], aN[N], bh[N], area[N], ide[N], idi[N], dge[N], dgi[N], rden[N / 2];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void sub_stage_rows(SubRows<T, N>& R, const SubLev<T>& L) {
+  for (int i = threadIdx.x; i < N; i += kSubThreads) {
+    R.aS[i] = L.coef[i];
+    R.aN[i] = L.coef[N + i];
+    R.bh[i] = L.coef[2 * N + i];
+    R.area[i] = L.coef[3 * N + i];
+    R.ide[i] = L.invd[i * N];
+    R.idi[i] = L.invd[i * N + 1];
+    R.dge[i] = L.diag[i * N];
+    R.dgi[i] = L.diag[i * N + 1];
+    if (i < N / 2) R.rden[i] = L.rden[i];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void sub_half_sweep(T* __restrict__ u, const T* __restrict__ f, const SubRows<T, N>& R,
+                                               int colour) {
+  constexpr int P = N + 2, NH = N / 2, CELLS = N * NH;
+#pragma unroll
+  for (int t0 = 0; t0 < CELLS; t0 += kSubThreads) {
+    const int t = t0 + threadIdx.x;
+    if (CELLS % kSubThreads != 0 && t >= CELLS) break;
+    const int i = t / NH, j = 2 * (t % NH) + ((i + colour) & 1);
+    T* c = u + (i + 1) * P + (j + 1);
+    const T id = (j == 0 || j == N - 1) ? R.ide[i] : R.idi[i];
+    const T v = fma(R.bh[i], c[1] + c[-1], fma(R.aN[i], c[-P], fma(R.aS[i], c[P], -f[i * N + j])));
+    *c = v * id;
+  }
+  __syncthreads();
+}
+
+// red-child residuals of level N restricted into the level N / 2 source
+template <typename T, int N>
+__device__ __forceinline__ void sub_restrict(const T* __restrict__ u, const T* __restrict__ f,
+                                             const SubRows<T, N>& R, T* __restrict__ fc) {
+  constexpr int P = N + 2, NC = N / 2;
+#pragma unroll
+  for (int t0 = 0; t0 < NC * NC; t0 += kSubThreads) {
+    const int t = t0 + threadIdx.x;
+    if ((NC * NC) % kSubThreads != 0 && t >= NC * NC) break;
+    const int I = t / NC, J = t % NC, i0 = 2 * I, i1 = i0 + 1;
+    const T* r0 = u + (i0 + 1) * P + (2 * J + 1);   // (2I, 2J)
+    const T* r1 = r0 + P;                           // (2I + 1, 2J)
+    const T a0 = r0[0], a1 = r0[1], w = r0[-1], n0v = r0[-P], b0 = r1[0], b1 = r1[1], e = r1[2], s1 = r1[P + 1];
+    const T d0 = J == 0 ? R.dge[i0] : R.dgi[i0];
+    const T d1 = J == NC - 1 ? R.dge[i1] : R.dgi[i1];
+    const T nb0 = fma(R.bh[i0], a1 + w, fma(R.aN[i0], n0v, fma(R.aS[i0], b0, -d0 * a0)));
+    const T nb1 = fma(R.bh[i1], e + b0, fma(R.aN[i1], a1, fma(R.aS[i1], s1, -d1 * b1)));
+    T rs0 = 0, rs1 = 0;
+    rs0 += f[i0 * N + 2 * J] - nb0;
+    rs1 += f[i1 * N + 2 * J + 1] - nb1;
+    T nr = 0;
+    nr = fma(R.area[i0], rs0, nr);
+    nr = fma(R.area[i1], rs1, nr);
+    fc[I * NC + J] = nr * R.rden[I];
+  }
+  __syncthreads();
+}
+
+// u += P(e_c) on the black cells of level N (every cell without post-smoothing)
+template <typename T, int N>
+__device__ __forceinline__ void sub_prolong(T* __restrict__ u, const T* __restrict__ E, bool black_only) {
+  constexpr int P = N + 2, NC = N / 2, Pc = NC + 2;
+#pragma unroll
+  for (int t0 = 0; t0 < N * N; t0 += kSubThreads) {
+    const int t = t0 + threadIdx.x;
+    if ((N * N) % kSubThreads != 0 && t >= N * N) break;
+    const int i = t / N, j = t % N;
+    if (black_only && !((i + j) & 1)) continue;
+    const int I = i >> 1, Id = (i & 1) ? I + 1 : I - 1, J = j >> 1;
+    const bool rowedge = i == 0 || i == N - 1;
+    const T* Ea = E + (I + 1) * Pc + (J + 1);
+    const T* Ed = E + (Id + 1) * Pc + (J + 1);
+    const T e11 = Ea[0], d11 = Ed[0];
+    T c;
+    if (!(j & 1)) c = (rowedge || J == 0) ? e11 : fma((T)9, e11, fma((T)3, d11 + Ea[-1], Ed[-1])) * (T)0.0625;
+    else c = (rowedge || J == NC - 1) ? e11 : fma((T)9, e11, fma((T)3, d11 + Ea[1], Ed[1])) * (T)0.0625;
+    u[(i + 1) * P + (j + 1)] += c;
+  }
+  __syncthreads();
+}
+
+template <typename T, int N>
+struct SubLevel {
+  T u[(N + 2) * (N + 2)];
+  T f[N * N];
+  SubRows<T, N> R;
+};
+
+// shared memory of the levels N .. 16 and the 8 x 8 level
+template <typename T, int N>
+struct SubStack {
+  SubLevel<T, N> top;
+  SubStack<T, N / 2> rest;
+};
+template <typename T>
+struct SubStack<T, kSubCoarse> {
+  T u[(kSubCoarse + 2) * (kSubCoarse + 2)];
+  T f[kSubCoarse * kSubCoarse];
+  double rhs[kSubCoarse * kSubCoarse];
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void sub_zero(SubStack<T, N>& S) {
+  if constexpr (N == kSubCoarse) {
+    for (int t = threadIdx.x; t < (N + 2) * (N + 2); t += kSubThreads) S.u[t] = (T)0;
+  } else {
+    for (int t = threadIdx.x; t < (N + 2) * (N + 2); t += kSubThreads) S.top.u[t] = (T)0;
+    sub_zero<T, N / 2>(S.rest);
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void sub_stage(SubStack<T, N>& S, const SubArgs<T>& a, int k) {
+  if constexpr (N != kSubCoarse) {
+    sub_stage_rows<T, N>(S.top.R, a.lev[k]);
+    sub_stage<T, N / 2>(S.rest, a, k + 1);
+  }
+}
+
+// one V-cycle from level N on the source already in S.top.f (coarser levels from zero)
+template <typename T, int N>
+__device__ __forceinline__ void sub_cycle(SubStack<T, N>& S, const SubArgs<T>& a) {
+  if constexpr (N == kSubCoarse) {
+    constexpr int nn = N * N;
+    if constexpr (sizeof(T) == 4) {
+      static_assert(kSubThreads == 4 * nn, "four lanes per row of the coarsest inverse");
+      const int t = threadIdx.x >> 2, part = threadIdx.x & 3;
+      const float* m = a.minv32 + (size_t)t * nn + part * (nn / 4);
+      const T* fv = S.f + part * (nn / 4);
+      float acc = 0.f;
+#pragma unroll
+      for (int q = 0; q < nn / 4; ++q) acc = fmaf(m[q], fv[q], acc);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (part == 0) S.u[(t / N + 1) * (N + 2) + (t % N + 1)] = acc;
+    } else {
+      for (int t = threadIdx.x; t < nn; t += kSubThreads) S.rhs[t] = (double)S.f[t];
+      __syncthreads();
+      for (int t = threadIdx.x; t < nn; t += kSubThreads) {
+        double acc = 0.0;
+        for (int q = 0; q < nn; ++q) acc += a.minv[(size_t)t * nn + q] * S.rhs[q];
+        S.u[(t / N + 1) * (N + 2) + (t % N + 1)] = (T)acc;
+      }
+    }
+    __syncthreads();
+  } else {
+    auto& L = S.top;
+    for (int s = 0; s < a.nu1; ++s) {
+      sub_half_sweep<T, N>(L.u, L.f, L.R, 0);
+      sub_half_sweep<T, N>(L.u, L.f, L.R, 1);
+    }
+    if constexpr (N / 2 == kSubCoarse) sub_restrict<T, N>(L.u, L.f, L.R, S.rest.f);
+    else sub_restrict<T, N>(L.u, L.f, L.R, S.rest.top.f);
+    sub_cycle<T, N / 2>(S.rest, a);
+    if constexpr (N / 2 == kSubCoarse) sub_prolong<T, N>(L.u, S.rest.u, a.nu2 > 0);
+    else sub_prolong<T, N>(L.u, S.rest.top.u, a.nu2 > 0);
+    for (int s = 0; s < a.nu2; ++s) {
+      sub_half_sweep<T, N>(L.u, L.f, L.R, 0);
+      sub_half_sweep<T, N>(L.u, L.f, L.R, 1);
+    }
+  }
+}
+
+template <typename T, int N0>
+__global__ void __launch_bounds__(kSubThreads) k_sub_vcycle(T* __restrict__ ug, const T* __restrict__ fg, int zero,
+                                                            SubArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_sub[];
+  SubStack<T, N0>& S = *reinterpret_cast<SubStack<T, N0>*>(smem_sub);
+  const size_t b = blockIdx.x;
+  sub_zero<T, N0>(S);
+  sub_stage<T, N0>(S, a, 0);
+  __syncthreads();
+  for (int t = threadIdx.x; t < N0 * N0; t += kSubThreads) {
+    const int i = t / N0, j = t % N0;
+    S.top.f[t] = fg[b * N0 * N0 + fidx(N0, i, j)];
+    if (!zero) S.top.u[(i + 1) * (N0 + 2) + (j + 1)] = ug[b * upatch(N0) + uidx(N0, i, j)];
+  }
+  __syncthreads();
+  sub_cycle<T, N0>(S, a);
+  for (int t = threadIdx.x; t < N0 * N0; t += kSubThreads) {
+    const int i = t / N0, j = t % N0;
+    ug[b * upatch(N0) + uidx(N0, i, j)] = S.top.u[(i + 1) * (N0 + 2) + (j + 1)];
+  }
+}
+
 // Exact solve of the coarsest level (nc^2 <= 256 unknowns), one CTA per patch:
 // u = Minv (f - ghost contributions), in FP64.
 template <typename T>
@@ -1833,8 +2060,39 @@ struct MG {
   // operator the coarse equation of the full approximation scheme, written
   // for e_c = u_c - R u, is L_c e_c = R (f - L u) from e_c = 0: the same
   // iterates with no restricted copy of u and no coarse source update.
+  // the levels from l down in one launch (k_sub_vcycle) when they are small
+  // enough: 16 or 32 cells a side, halving to the 8 x 8 coarsest level
+  bool use_sub(int l) {
+    const int n = s->sizes[l];
+    return (n == 16 || n == kSubMax) && s->sizes[s->nlev - 1] == kSubCoarse && s->p.nu1 >= 1 &&
+           sub_bytes(n) <= smem_cap();
+  }
+  static size_t sub_bytes(int n) { return n == 32 ? sizeof(SubStack<T, 32>) : sizeof(SubStack<T, 16>); }
+  template <int N0>
+  void sub_launch(int l, bool zero, const SubArgs<T>& a) {
+    const size_t smb = sizeof(SubStack<T, N0>);
+    cudaFuncSetAttribute(k_sub_vcycle<T, N0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    CLC_LAUNCH(ctx, "k_sub_vcycle", (k_sub_vcycle<T, N0>), s->npatch, kSubThreads, smb, U(l), (const T*)F(l),
+               zero ? 1 : 0, a);
+  }
+  void sub_vcycle(int l, bool zero) {
+    SubArgs<T> a{};
+    a.nu1 = s->p.nu1;
+    a.nu2 = s->p.nu2;
+    for (int k = 0; l + k < s->nlev - 1 && k < 4; ++k)
+      a.lev[k] = SubLev<T>{(const T*)C(l + k), (const T*)D(l + k), (const T*)G(l + k), (const T*)RD(l + k)};
+    a.minv = (const double*)s->coarse_inv.p;
+    a.minv32 = (const float*)s->coarse_inv32.p;
+    if (s->sizes[l] == 32) sub_launch<32>(l, zero, a);
+    else sub_launch<16>(l, zero, a);
+  }
+
   void vcycle(int l, bool zero) {
     const int n = s->sizes[l];
+    if (use_sub(l)) {
+      sub_vcycle(l, zero);
+      return;
+    }
     if (l == s->nlev - 1) {
       CLC_LAUNCH(ctx, "k_coarse_solve", k_coarse_solve<T>, s->npatch, 64, n * n * sizeof(double), U(l), F(l), C64(l),
                  (const double*)s->coarse_inv.p, n);
@@ -2349,6 +2607,7 @@ static int solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, const i
     }
   }
   ok = ok && alloc(s->rot, 9 * sizeof(double) * s->npatch) && alloc(s->coarse_inv, sizeof(double) * nc * nc * nc * nc) &&
+       alloc(s->coarse_inv32, sizeof(float) * nc * nc * nc * nc) &&
        alloc(s->tau2, sizeof(double) * s->npatch) &&
        alloc(s->gc, sizeof(double) * s->npatch * 4 * (s->nlev > 1 ? s->sizes[1] : 1)) &&
        alloc(s->psi_sht, sizeof(double) * ns2) && alloc(s->kappa_sht, sizeof(double) * ns2) &&
@@ -2377,6 +2636,8 @@ static int solution_create(clc_ctx* ctx, int nf, const clc_mg_params* p, const i
       return set_err(ctx, CLC_ECUDA, "coarsest MG operator is singular");
     }
     cudaMemcpy(s->coarse_inv.p, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> A32(A.begin(), A.end());
+    cudaMemcpy(s->coarse_inv32.p, A32.data(), A32.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   CLC_LAUNCH(ctx, "k_mg_rotations", k_mg_rotations, (s->npatch + 127) / 128, 128, 0, p->nside_bundle, s->npatch,
              s->partial ? (const int32_t*)s->slot_bundle.p : nullptr, (double*)s->rot.p);

@@ -33,6 +33,7 @@ struct clc_plane_solution {
   clc::Buffer coef_ff, diag_ff; // CLC_MIXED: finest-level operator coefficients as float-float pairs
   clc::Buffer rot;              // double[npatch][9]: R_b (global -> patch frame)
   clc::Buffer coarse_inv;       // double[nc^2][nc^2]
+  clc::Buffer coarse_inv32;     // the same in FP32 (the FP32 V-cycles' coarsest solve)
   clc::Buffer psi_sht;          // double[12 nside_sht^2]
   clc::Buffer kappa_sht;        // double[12 nside_sht^2]
   clc::Buffer norms;            // double[npatch][2]
