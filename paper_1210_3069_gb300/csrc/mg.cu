@@ -1159,12 +1159,16 @@ __device__ __forceinline__ void q_store(const QState<N, HALO, NV>& S, float* __r
   }
 }
 
+// halo rows of the pre-smoothing kernel's region: 2 nu, plus one for the
+// restriction's stencil (more only to make the region split evenly)
+constexpr int kSRHalo = 5;
+
 template <int N, int NV>
-__global__ void __launch_bounds__(QBand<N, 5, NV>::NT) k_reg_smooth_restrict(
+__global__ void __launch_bounds__(QBand<N, kSRHalo, NV>::NT) k_reg_smooth_restrict(
     const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
     const float* __restrict__ coef, const float* __restrict__ invd, const float* __restrict__ diag,
     const float* __restrict__ rden, float* __restrict__ fc, int* d_err) {
-  constexpr int HALO = 5;
+  constexpr int HALO = kSRHalo;
   using G = QBand<N, HALO, NV>;
   extern __shared__ __align__(128) unsigned char smem_rsr[];
   float* Fs = reinterpret_cast<float*>(smem_rsr);
@@ -1982,7 +1986,7 @@ struct MG {
   static constexpr int kRegPartsSR = 3, kRegPartsPS = 2;   // row parts of the two kernels' regions
   template <int N>
   void reg_smooth_restrict(int l, bool zero) {
-    using QB = QBand<N, 5, kRegPartsSR>;
+    using QB = QBand<N, kSRHalo, kRegPartsSR>;
     // static plus dynamic shared memory goes beyond 48 KB: opt in
     cudaFuncSetAttribute(k_reg_smooth_restrict<N, kRegPartsSR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)QB::f_bytes);
