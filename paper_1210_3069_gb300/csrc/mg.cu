@@ -248,7 +248,7 @@ __device__ __forceinline__ float2 apply_plan_ff(const float2* __restrict__ map_f
 // Mixed set-up, float-float: base = psi_SHT interpolated (2 psi_SHT on the
 // ghost ring), kept both as float-float pairs and as their FP64 sum.
 // Rows per thread of the defect set-up (independent kappa gathers in flight).
-constexpr int kSetupRows = 4;
+constexpr int kSetupRows = 8;
 
 __global__ void k_mg_setup_base_ff(int n, const int4* __restrict__ idx, const double4_32a* __restrict__ w,
                                    const float2* __restrict__ psi_ff, const double* __restrict__ psi, int ns,

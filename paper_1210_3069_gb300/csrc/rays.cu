@@ -41,7 +41,10 @@ __global__ void k_rays_init(const double* __restrict__ z, const double* __restri
 
 // rays at every RING pixel centre of nside: one CTA per ring, so the ring
 // geometry is computed once; longitudes by sincospi of (2 j + shift) / npix
-// and bundles by the integer RING -> NEST conversion
+// for the first quarter of the ring (the other three are the same angles
+// plus pi / 2, pi, 3 pi / 2: their cosines and sines are the first quarter's
+// swapped and negated, exactly) and bundles by the integer RING -> NEST
+// conversion
 __global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
   const int64_t n = R.n;
   const int i = blockIdx.x + 1;
@@ -49,18 +52,26 @@ __global__ void k_rays_init_pixels(int nside, double chi0, int nb, RayPtrs R) {
   const double inv = 1.0 / (double)r.npix;
   const int shift = r.phi0 != 0.0 ? 1 : 0;
   const int bshift = nb > 0 ? 2 * (ilog2(nside) - ilog2(nb)) : 0;
-  for (int j = threadIdx.x; j < r.npix; j += blockDim.x) {
-    const int64_t k = r.first + j;
+  const int quarter = r.npix / 4;
+  for (int j = threadIdx.x; j < quarter; j += blockDim.x) {
     double sp, cp;
     sincospi((double)(2 * j + shift) * inv, &sp, &cp);
-    const double v[3] = {r.s * cp, r.s * sp, r.z};
-    for (int c = 0; c < 3; ++c) {
-      R.x[c * n + k] = chi0 * v[c];
-      R.beta[c * n + k] = v[c];
+#pragma unroll
+    for (int qd = 0; qd < 4; ++qd) {
+      // (cos, sin) of the angle plus qd pi / 2
+      const double c = qd == 0 ? cp : qd == 1 ? -sp : qd == 2 ? -cp : sp;
+      const double sn = qd == 0 ? sp : qd == 1 ? cp : qd == 2 ? -sp : -cp;
+      const int jj = j + qd * quarter;
+      const int64_t k = r.first + jj;
+      const double v[3] = {r.s * c, r.s * sn, r.z};
+      for (int d = 0; d < 3; ++d) {
+        R.x[d * n + k] = chi0 * v[d];
+        R.beta[d * n + k] = v[d];
+      }
+      R.A[k] = 1.0; R.A[n + k] = 0.0; R.A[2 * n + k] = 0.0; R.A[3 * n + k] = 1.0;
+      R.Ap[k] = 1.0; R.Ap[n + k] = 0.0; R.Ap[2 * n + k] = 0.0; R.Ap[3 * n + k] = 1.0;
+      if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)(ring_pos2nest(nside, i, jj) >> bshift);
     }
-    R.A[k] = 1.0; R.A[n + k] = 0.0; R.A[2 * n + k] = 0.0; R.A[3 * n + k] = 1.0;
-    R.Ap[k] = 1.0; R.Ap[n + k] = 0.0; R.Ap[2 * n + k] = 0.0; R.Ap[3 * n + k] = 1.0;
-    if (nb > 0 && R.bundle) ((int32_t*)R.bundle)[k] = (int32_t)(ring_pos2nest(nside, i, j) >> bshift);
   }
 }
 
