@@ -54,14 +54,13 @@ def test_noalloc_rejects_sizes_beyond_its_maximum():
     assert f(None, 8, 10, q, None) == 1
 
 
-@pytest.mark.parametrize("nside", [1, 2, 4, 8])
-def test_noalloc_analysis_at_the_smallest_nsides(nside):
-    """A single ring-group of pixels per face (nside 1) up to nside 8, lmax
-    3 nside - 1: the few-ring grids where the polar and equatorial ring
-    lengths differ most."""
+@pytest.mark.parametrize("nside,lmax", [(1, 2), (1, 4), (2, 5), (2, 8), (4, 11), (4, 16), (8, 23), (8, 32)])
+def test_noalloc_analysis_at_the_smallest_nsides(nside, lmax):
+    """A single ring-group of pixels per face (nside 1) up to nside 8, at
+    lmax 3 nside - 1 and at the entry point's limit 4 nside: the few-ring
+    grids where the polar and equatorial ring lengths differ most."""
     c = ctx()
     f = _noalloc()
-    lmax = 3 * nside - 1
     g = torch.Generator().manual_seed(100 + nside)
     m = torch.randn(12 * nside * nside, dtype=torch.float64, generator=g).cuda()
     ref = c.sht_analysis(m, nside, lmax)
