@@ -967,6 +967,7 @@ struct QBand {
   static constexpr size_t f_bytes = (size_t)2 * W * NH * sizeof(float);
   static constexpr size_t e_bytes = (size_t)2 * Wc * Pc * sizeof(float);
   static_assert(NQ % 32 == 0 && H * NV == W && H % 2 == 0 && H >= 2, "quad band geometry");
+  static_assert(NT % 32 == 0, "whole warps: the shuffles name every lane");
 };
 
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
@@ -1297,6 +1298,339 @@ __global__ void __launch_bounds__(QBand<N, 4, NV>::NT) k_reg_prolong_smooth(
   __syncthreads();
   q_sweeps<N, HALO, NV>(S, X, Fs, v, q);
   q_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, q);
+}
+
+// ---------------------------------------------------------------------------
+// Eight columns per thread (256-cell patches): the same register-resident
+// band kernels with thread (part v, octet o) holding the columns 8o .. 8o + 7
+// of its part's rows as four same-colour pairs, A0 = (8o, 8o + 2),
+// A1 = (8o + 4, 8o + 6), B0 = (8o + 1, 8o + 3), B1 = (8o + 5, 8o + 7).  A
+// row is one warp, so the horizontal neighbours beyond the octet come by
+// shuffle alone and the patch's ghost columns are zeros at the row's first
+// and last lane; the sources of a pair of pairs arrive as one 16-byte
+// shared-memory load.  Operation for operation the arithmetic of the
+// four-column kernels.
+
+template <int N, int HALO, int NV>
+struct OBand {
+  static constexpr int NH = N / 2;                  // source entries per colour row
+  static constexpr int NO = N / 8;                  // octets = threads per part
+  static constexpr int BR = kBandRows;
+  static constexpr int W = BR + 2 * HALO, H = W / NV;
+  static constexpr int NT = NO * NV;
+  static constexpr int WID = 32;                    // shuffle width
+  static constexpr int NC = N / 2, Wc = W / 2 + 2, Pc = upitch(NC);
+  static constexpr size_t f_bytes = (size_t)2 * W * NH * sizeof(float);
+  static constexpr size_t e_bytes = (size_t)2 * Wc * Pc * sizeof(float);
+  static_assert(NO == 32, "a part row is one warp");
+  static_assert(NT % 32 == 0, "whole warps: the shuffles name every lane");
+  static_assert(H * NV == W && H % 2 == 0, "octet band geometry");
+};
+
+template <int N, int HALO, int NV>
+struct OShared {
+  using G = OBand<N, HALO, NV>;
+  float4 rq[4 * G::W];
+  float4 TA[NV + 1][G::NO], TB[NV + 1][G::NO], BA[NV + 1][G::NO], BB[NV + 1][G::NO];
+  uint64_t bar;
+};
+
+template <int N, int HALO, int NV>
+struct OState {
+  using G = OBand<N, HALO, NV>;
+  float2 A0[G::H], A1[G::H], B0[G::H], B1[G::H];
+};
+
+__device__ __forceinline__ float4 pk4(float2 a, float2 b) { return make_float4(a.x, a.y, b.x, b.y); }
+__device__ __forceinline__ float2 lo2(float4 a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ float2 hi2(float4 a) { return make_float2(a.z, a.w); }
+
+// row coefficients and sources (as the four-column kernels, rq rows of 64 B)
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void o_begin(OShared<N, HALO, NV>& X, float* Fs, const float* __restrict__ Fb, int gi0,
+                                        const float* __restrict__ coef, const float* __restrict__ invd,
+                                        const float* __restrict__ diag, uint32_t extra) {
+  using G = OBand<N, HALO, NV>;
+  const int fa = max(gi0, 0), fb = min(gi0 + G::W, N);
+  if (threadIdx.x == 0) {
+    umma::mbar_init(&X.bar, 1);
+    umma::fence_mbar_init();
+    const uint32_t bytes = (uint32_t)((fb - fa) * G::NH * sizeof(float));
+    umma::mbar_arrive_expect_tx(&X.bar, 2 * bytes + extra);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+      umma::bulk_g2s(Fs + (c * G::W + fa - gi0) * G::NH, Fb + ((size_t)c * N + fa) * G::NH, bytes, &X.bar);
+  }
+  for (int r = threadIdx.x; r < G::W; r += blockDim.x) {
+    const int gi = gi0 + r;
+    float4 z = make_float4(0.f, 0.f, 0.f, 0.f), p0 = z, p1 = z, p2 = z, p3 = z;
+    if (gi >= 0 && gi < N) {
+      const size_t row = (size_t)gi * N;
+      const float aS = coef[gi], aN = coef[N + gi], bh = coef[2 * N + gi], id = invd[row + 1], ide = invd[row];
+      p0 = make_float4(aS, aS, aN, aN);
+      p1 = make_float4(bh, bh, id, id);
+      p2 = make_float4(ide, id, id, ide);
+      p3 = make_float4(diag[row + 1], diag[row], coef[3 * N + gi], 0.f);
+    }
+    X.rq[4 * r] = p0;
+    X.rq[4 * r + 1] = p1;
+    X.rq[4 * r + 2] = p2;
+    X.rq[4 * r + 3] = p3;
+  }
+  const int nlo = fa - gi0, nhi = gi0 + G::W - fb;
+  for (int e = threadIdx.x; e < (nlo + nhi) * G::NH; e += blockDim.x) {
+    const int rr = e / G::NH, k = e - rr * G::NH;
+    const int r = rr < nlo ? rr : fb - gi0 + (rr - nlo);
+    Fs[r * G::NH + k] = 0.f;
+    Fs[(G::W + r) * G::NH + k] = 0.f;
+  }
+}
+
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void o_load(OState<N, HALO, NV>& S, const float* __restrict__ Ub, int g0, int o) {
+  using G = OBand<N, HALO, NV>;
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const int gi = g0 + r;
+    if (Ub) {
+      const float* ev = Ub + uidx(N, gi, 8 * o);       // even columns 8o, 8o + 2, 8o + 4, 8o + 6
+      const float* od = Ub + uidx(N, gi, 8 * o + 1);   // odd columns
+      S.A0[r] = f2(ev[0], ev[1]);
+      S.A1[r] = f2(ev[2], ev[3]);
+      S.B0[r] = f2(od[0], od[1]);
+      S.B1[r] = f2(od[2], od[3]);
+    } else {
+      S.A0[r] = S.A1[r] = S.B0[r] = S.B1[r] = f2(0.f, 0.f);
+    }
+  }
+}
+
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void o_store(const OState<N, HALO, NV>& S, float* __restrict__ Ub, int gi0, int v, int o) {
+  using G = OBand<N, HALO, NV>;
+  const int rb = v * G::H;
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const int rg = rb + r;
+    if (rg < HALO || rg >= HALO + G::BR) continue;
+    float* ev = Ub + uidx(N, gi0 + rg, 8 * o);
+    float* od = Ub + uidx(N, gi0 + rg, 8 * o + 1);
+    ev[0] = S.A0[r].x; ev[1] = S.A0[r].y; ev[2] = S.A1[r].x; ev[3] = S.A1[r].y;
+    od[0] = S.B0[r].x; od[1] = S.B0[r].y; od[2] = S.B1[r].x; od[3] = S.B1[r].y;
+  }
+}
+
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void o_publish_all(const OState<N, HALO, NV>& S, OShared<N, HALO, NV>& X, int v, int o) {
+  using G = OBand<N, HALO, NV>;
+  X.TA[v][o] = pk4(S.A0[0], S.A1[0]);
+  X.TB[v][o] = pk4(S.B0[0], S.B1[0]);
+  X.BA[v + 1][o] = pk4(S.A0[G::H - 1], S.A1[G::H - 1]);
+  X.BB[v + 1][o] = pk4(S.B0[G::H - 1], S.B1[G::H - 1]);
+  if (v == 0) {
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    X.TA[NV][o] = X.TB[NV][o] = X.BA[0][o] = X.BB[0][o] = z;
+  }
+}
+
+// one half-sweep of colour C over the thread's rows (rb = v H even)
+template <int N, int HALO, int NV, int C>
+__device__ __forceinline__ void o_half_sweep(OState<N, HALO, NV>& S, OShared<N, HALO, NV>& X,
+                                             const float* __restrict__ Fs, int v, int o) {
+  using G = OBand<N, HALO, NV>;
+  const int rb = v * G::H;
+  const bool first = o == 0, last = o == G::NO - 1;
+  const float* Fr = Fs + (C * G::W + rb) * G::NH + 4 * o;
+  const float4* R = X.rq + 4 * rb;
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const float4 p0 = R[4 * r], p1 = R[4 * r + 1];
+    const float2 idi = f2(p1.z, p1.w);
+    const float4 F = *reinterpret_cast<const float4*>(Fr + r * G::NH);
+    const float2 qS = f2(p0.x, p0.y), qN = f2(p0.z, p0.w), qB = f2(p1.x, p1.y);
+    if (((r + HALO) & 1) == C) {
+      // A0 = (8o, 8o + 2): west 8o - 1 (lane o - 1's B1.y) and B0.x, east B0.x and B0.y;
+      // A1 = (8o + 4, 8o + 6): west B0.y and B1.x, east B1.x and B1.y
+      float w = __shfl_up_sync(0xffffffffu, S.B1[r].y, 1, G::WID);
+      if (first) w = 0.f;
+      const float4 nN = r > 0 ? pk4(S.A0[r - 1], S.A1[r - 1]) : X.BA[v][o];
+      const float4 nS = r + 1 < G::H ? pk4(S.A0[r + 1], S.A1[r + 1]) : X.TA[v + 1][o];
+      const float2 id0 = first ? f2(R[4 * r + 2].x, R[4 * r + 2].y) : idi;
+      const float2 s0 = __fadd2_rn(S.B0[r], f2(w, S.B0[r].x));
+      const float2 s1 = __fadd2_rn(S.B1[r], f2(S.B0[r].y, S.B1[r].x));
+      const float2 t0 = __ffma2_rn(qB, s0, __ffma2_rn(qN, lo2(nN), __ffma2_rn(qS, lo2(nS), neg2(lo2(F)))));
+      const float2 t1 = __ffma2_rn(qB, s1, __ffma2_rn(qN, hi2(nN), __ffma2_rn(qS, hi2(nS), neg2(hi2(F)))));
+      S.A0[r] = __fmul2_rn(t0, id0);
+      S.A1[r] = __fmul2_rn(t1, idi);
+      if (r == 0) X.TA[v][o] = pk4(S.A0[r], S.A1[r]);
+      if (r == G::H - 1) X.BA[v + 1][o] = pk4(S.A0[r], S.A1[r]);
+    } else {
+      // B0 = (8o + 1, 8o + 3): west A0.x and A0.y, east A0.y and A1.x;
+      // B1 = (8o + 5, 8o + 7): west A1.x and A1.y, east A1.y and 8o + 8 (lane o + 1's A0.x)
+      float e = __shfl_down_sync(0xffffffffu, S.A0[r].x, 1, G::WID);
+      if (last) e = 0.f;
+      const float4 nN = r > 0 ? pk4(S.B0[r - 1], S.B1[r - 1]) : X.BB[v][o];
+      const float4 nS = r + 1 < G::H ? pk4(S.B0[r + 1], S.B1[r + 1]) : X.TB[v + 1][o];
+      const float2 id1 = last ? f2(R[4 * r + 2].z, R[4 * r + 2].w) : idi;
+      const float2 s0 = __fadd2_rn(S.A0[r], f2(S.A0[r].y, S.A1[r].x));
+      const float2 s1 = __fadd2_rn(S.A1[r], f2(S.A1[r].y, e));
+      const float2 t0 = __ffma2_rn(qB, s0, __ffma2_rn(qN, lo2(nN), __ffma2_rn(qS, lo2(nS), neg2(lo2(F)))));
+      const float2 t1 = __ffma2_rn(qB, s1, __ffma2_rn(qN, hi2(nN), __ffma2_rn(qS, hi2(nS), neg2(hi2(F)))));
+      S.B0[r] = __fmul2_rn(t0, idi);
+      S.B1[r] = __fmul2_rn(t1, id1);
+      if (r == 0) X.TB[v][o] = pk4(S.B0[r], S.B1[r]);
+      if (r == G::H - 1) X.BB[v + 1][o] = pk4(S.B0[r], S.B1[r]);
+    }
+  }
+}
+
+template <int N, int HALO, int NV>
+__device__ __forceinline__ void o_sweeps(OState<N, HALO, NV>& S, OShared<N, HALO, NV>& X, const float* __restrict__ Fs,
+                                         int v, int o) {
+#pragma unroll 1
+  for (int it = 0; it < 2; ++it) {
+    o_half_sweep<N, HALO, NV, 0>(S, X, Fs, v, o);
+    __syncthreads();
+    o_half_sweep<N, HALO, NV, 1>(S, X, Fs, v, o);
+    __syncthreads();
+  }
+}
+
+template <int N, int NV>
+__global__ void __launch_bounds__(OBand<N, kSRHalo, NV>::NT) k_oct_smooth_restrict(
+    const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
+    const float* __restrict__ coef, const float* __restrict__ invd, const float* __restrict__ diag,
+    const float* __restrict__ rden, float* __restrict__ fc, int* d_err) {
+  constexpr int HALO = kSRHalo;
+  using G = OBand<N, HALO, NV>;
+  extern __shared__ __align__(128) unsigned char smem_osr[];
+  float* Fs = reinterpret_cast<float*>(smem_osr);
+  __shared__ OShared<N, HALO, NV> X;
+  const size_t b = blockIdx.z;
+  const int gi0 = blockIdx.x * G::BR - HALO;
+  const int v = threadIdx.x / G::NO, o = threadIdx.x % G::NO;
+  const int rb = v * G::H;
+  const bool first = o == 0, last = o == G::NO - 1;
+  o_begin<N, HALO, NV>(X, Fs, f + b * N * N, gi0, coef, invd, diag, 0);
+  OState<N, HALO, NV> S;
+  o_load<N, HALO, NV>(S, u_in ? u_in + b * upatch(N) : nullptr, gi0 + rb, o);
+  o_publish_all<N, HALO, NV>(S, X, v, o);
+  if (!band_wait(&X.bar, d_err)) return;
+  o_sweeps<N, HALO, NV>(S, X, Fs, v, o);
+  o_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, o);
+  // red residuals of the band rows, written over their sources
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const int rg = rb + r;
+    if (rg < HALO || rg >= HALO + G::BR) continue;
+    const float4 p0 = X.rq[4 * rg], p1 = X.rq[4 * rg + 1], p3 = X.rq[4 * rg + 3];
+    const float2 qS = f2(p0.x, p0.y), qN = f2(p0.z, p0.w), qB = f2(p1.x, p1.y), dgi = f2(p3.x, p3.x);
+    float4* Fr = reinterpret_cast<float4*>(Fs + rg * G::NH + 4 * o);
+    float2 nb0, nb1;
+    if (((r + HALO) & 1) == 0) {   // red pairs A0, A1
+      float w = __shfl_up_sync(0xffffffffu, S.B1[r].y, 1, G::WID);
+      if (first) w = 0.f;
+      const float4 nN = r > 0 ? pk4(S.A0[r - 1], S.A1[r - 1]) : X.BA[v][o];
+      const float4 nS = r + 1 < G::H ? pk4(S.A0[r + 1], S.A1[r + 1]) : X.TA[v + 1][o];
+      const float2 d0 = f2(first ? p3.y : p3.x, p3.x);
+      nb0 = __ffma2_rn(qB, __fadd2_rn(S.B0[r], f2(w, S.B0[r].x)),
+                       __ffma2_rn(qN, lo2(nN), __ffma2_rn(qS, lo2(nS), __fmul2_rn(neg2(d0), S.A0[r]))));
+      nb1 = __ffma2_rn(qB, __fadd2_rn(S.B1[r], f2(S.B0[r].y, S.B1[r].x)),
+                       __ffma2_rn(qN, hi2(nN), __ffma2_rn(qS, hi2(nS), __fmul2_rn(neg2(dgi), S.A1[r]))));
+    } else {                        // red pairs B0, B1
+      float e = __shfl_down_sync(0xffffffffu, S.A0[r].x, 1, G::WID);
+      if (last) e = 0.f;
+      const float4 nN = r > 0 ? pk4(S.B0[r - 1], S.B1[r - 1]) : X.BB[v][o];
+      const float4 nS = r + 1 < G::H ? pk4(S.B0[r + 1], S.B1[r + 1]) : X.TB[v + 1][o];
+      const float2 d1 = f2(p3.x, last ? p3.y : p3.x);
+      nb0 = __ffma2_rn(qB, __fadd2_rn(S.A0[r], f2(S.A0[r].y, S.A1[r].x)),
+                       __ffma2_rn(qN, lo2(nN), __ffma2_rn(qS, lo2(nS), __fmul2_rn(neg2(dgi), S.B0[r]))));
+      nb1 = __ffma2_rn(qB, __fadd2_rn(S.A1[r], f2(S.A1[r].y, e)),
+                       __ffma2_rn(qN, hi2(nN), __ffma2_rn(qS, hi2(nS), __fmul2_rn(neg2(d1), S.B1[r]))));
+    }
+    const float4 Fv = *Fr;
+    const float2 z = f2(0.f, 0.f);
+    *Fr = pk4(__fadd2_rn(z, __fadd2_rn(lo2(Fv), neg2(nb0))), __fadd2_rn(z, __fadd2_rn(hi2(Fv), neg2(nb1))));
+  }
+  __syncthreads();
+  // restriction: coarse cells (I, 4o .. 4o + 3)
+  constexpr int NC = G::NC;
+  float* fcb = fc + b * NC * NC;
+  for (int Il = v; Il < G::BR / 2; Il += NV) {
+    const int rg = HALO + 2 * Il, I = (gi0 + rg) >> 1;
+    const float a0 = X.rq[4 * rg + 3].z, a1 = X.rq[4 * rg + 7].z;
+    const float4 rs0 = *reinterpret_cast<const float4*>(Fs + rg * G::NH + 4 * o);
+    const float4 rs1 = *reinterpret_cast<const float4*>(Fs + (rg + 1) * G::NH + 4 * o);
+    const float2 z = f2(0.f, 0.f), A0v = f2(a0, a0), A1v = f2(a1, a1);
+    const float rd = rden[I];
+    const float2 outl = __fmul2_rn(__ffma2_rn(A1v, lo2(rs1), __ffma2_rn(A0v, lo2(rs0), z)), f2(rd, rd));
+    const float2 outh = __fmul2_rn(__ffma2_rn(A1v, hi2(rs1), __ffma2_rn(A0v, hi2(rs0), z)), f2(rd, rd));
+    // coarse columns 4o, 4o + 2 in colour plane I & 1, 4o + 1, 4o + 3 in the other (entries 2o, 2o + 1)
+    *reinterpret_cast<float2*>(fcb + fidx(NC, I, 4 * o)) = f2(outl.x, outh.x);
+    *reinterpret_cast<float2*>(fcb + fidx(NC, I, 4 * o + 1)) = f2(outl.y, outh.y);
+  }
+}
+
+template <int N, int NV>
+__global__ void __launch_bounds__(OBand<N, 4, NV>::NT) k_oct_prolong_smooth(
+    const float* __restrict__ u_in, float* __restrict__ u_out, const float* __restrict__ f,
+    const float* __restrict__ coef, const float* __restrict__ invd, const float* __restrict__ diag,
+    const float* __restrict__ uc, int* d_err) {
+  constexpr int HALO = 4;
+  using G = OBand<N, HALO, NV>;
+  constexpr int NC = G::NC, Wc = G::Wc, Pc = G::Pc;
+  extern __shared__ __align__(128) unsigned char smem_ops[];
+  float* Fs = reinterpret_cast<float*>(smem_ops);
+  float* E = Fs + 2 * G::W * G::NH;
+  __shared__ OShared<N, HALO, NV> X;
+  const size_t b = blockIdx.z;
+  const int gi0 = blockIdx.x * G::BR - HALO;
+  const int v = threadIdx.x / G::NO, o = threadIdx.x % G::NO;
+  const int rb = v * G::H;
+  const uint32_t cbytes = (uint32_t)(Wc * Pc * sizeof(float));
+  o_begin<N, HALO, NV>(X, Fs, f + b * N * N, gi0, coef, invd, diag, 2 * cbytes);
+  if (threadIdx.x == 0) {
+    const float* Cc = uc + b * upatch(NC) + (size_t)((gi0 >> 1) - 1 + 1 + kUHalo) * Pc;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) umma::bulk_g2s(E + c * Wc * Pc, Cc + c * uplane_of(NC), cbytes, &X.bar);
+  }
+  OState<N, HALO, NV> S;
+  o_load<N, HALO, NV>(S, u_in + b * upatch(N), gi0 + rb, o);
+  if (!band_wait(&X.bar, d_err)) return;
+  // black cells += P(e_c): the A pairs of odd rows (coarse columns 4o .. 4o + 3, outer
+  // neighbours 4o - 1 .. 4o + 2), the B pairs of even rows (outer neighbours 4o + 1 .. 4o + 4)
+  const float2 nine = f2(9.f, 9.f), three = f2(3.f, 3.f), sixteenth = f2(0.0625f, 0.0625f);
+#pragma unroll
+  for (int r = 0; r < G::H; ++r) {
+    const int rg = rb + r, gi = gi0 + rg;
+    if ((unsigned)gi >= (unsigned)N) continue;
+    const bool rowedge = gi == 0 || gi == N - 1;
+    const int a = (rg >> 1) + 1, da = (r & 1) ? a + 1 : a - 1;
+    const int pa = (a + (gi0 >> 1) + 1) & 1, pd = pa ^ 1;
+    // entry 2o + j of the row's even / odd coarse columns: columns 4o - 2 + 2j / 4o - 1 + 2j
+    const float* Ea0 = E + (pa * Wc + a) * Pc + 2 * o;
+    const float* Ea1 = E + ((pa ^ 1) * Wc + a) * Pc + 2 * o;
+    const float* Ed0 = E + (pd * Wc + da) * Pc + 2 * o;
+    const float* Ed1 = E + ((pd ^ 1) * Wc + da) * Pc + 2 * o;
+    // coarse columns 4o, 4o + 1 (pair 0) and 4o + 2, 4o + 3 (pair 1)
+    const float2 e0 = f2(Ea0[1], Ea1[1]), e1 = f2(Ea0[2], Ea1[2]);
+    const float2 d0 = f2(Ed0[1], Ed1[1]), d1 = f2(Ed0[2], Ed1[2]);
+    if (r & 1) {   // odd row: A0 (4o, 4o + 1), A1 (4o + 2, 4o + 3); neighbours J - 1
+      const float2 c0 = __fmul2_rn(__ffma2_rn(nine, e0, __ffma2_rn(three, __fadd2_rn(d0, f2(Ea1[0], Ea0[1])), f2(Ed1[0], Ed0[1]))), sixteenth);
+      const float2 c1 = __fmul2_rn(__ffma2_rn(nine, e1, __ffma2_rn(three, __fadd2_rn(d1, f2(Ea1[1], Ea0[2])), f2(Ed1[1], Ed0[2]))), sixteenth);
+      S.A0[r] = __fadd2_rn(S.A0[r], f2((rowedge || o == 0) ? e0.x : c0.x, rowedge ? e0.y : c0.y));
+      S.A1[r] = __fadd2_rn(S.A1[r], f2(rowedge ? e1.x : c1.x, rowedge ? e1.y : c1.y));
+    } else {       // even row: B0, B1; neighbours J + 1
+      const float2 c0 = __fmul2_rn(__ffma2_rn(nine, e0, __ffma2_rn(three, __fadd2_rn(d0, f2(Ea1[1], Ea0[2])), f2(Ed1[1], Ed0[2]))), sixteenth);
+      const float2 c1 = __fmul2_rn(__ffma2_rn(nine, e1, __ffma2_rn(three, __fadd2_rn(d1, f2(Ea1[2], Ea0[3])), f2(Ed1[2], Ed0[3]))), sixteenth);
+      S.B0[r] = __fadd2_rn(S.B0[r], f2(rowedge ? e0.x : c0.x, rowedge ? e0.y : c0.y));
+      S.B1[r] = __fadd2_rn(S.B1[r], f2(rowedge ? e1.x : c1.x, (rowedge || o == G::NO - 1) ? e1.y : c1.y));
+    }
+  }
+  o_publish_all<N, HALO, NV>(S, X, v, o);
+  __syncthreads();
+  o_sweeps<N, HALO, NV>(S, X, Fs, v, o);
+  o_store<N, HALO, NV>(S, u_out + b * upatch(N), gi0, v, o);
 }
 
 // ---------------------------------------------------------------------------
@@ -2004,13 +2338,40 @@ struct MG {
                dim3(QB::NT), smb, (const float*)U2(l), (float*)U(l), (const float*)F(l), (const float*)C(l),
                (const float*)D(l), (const float*)G(l), (const float*)U(l + 1), ctx->d_err);
   }
+  // eight columns per thread (k_oct_*, 256-cell patches) or four (k_reg_*) in
+  // the register band kernels; row parts 3 and 4 measured fastest at Nside 2048
+  static constexpr bool kOctSR = true, kOctPS = true;
+  static constexpr int kOctPartsSR = 3, kOctPartsPS = 4;
+  template <int N>
+  void oct_smooth_restrict(int l, bool zero) {
+    using OB = OBand<N, kSRHalo, kOctPartsSR>;
+    cudaFuncSetAttribute(k_oct_smooth_restrict<N, kOctPartsSR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)OB::f_bytes);
+    CLC_LAUNCH(ctx, "k_smooth_restrict", (k_oct_smooth_restrict<N, kOctPartsSR>), dim3(N / OB::BR, 1, s->npatch),
+               dim3(OB::NT), (OB::f_bytes), zero ? nullptr : (const float*)U(l), (float*)U2(l), (const float*)F(l),
+               (const float*)C(l), (const float*)D(l), (const float*)G(l), (const float*)RD(l), (float*)F(l + 1),
+               ctx->d_err);
+  }
+  template <int N>
+  void oct_prolong_smooth(int l) {
+    using OB = OBand<N, 4, kOctPartsPS>;
+    constexpr size_t smb = OB::f_bytes + OB::e_bytes;
+    cudaFuncSetAttribute(k_oct_prolong_smooth<N, kOctPartsPS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+    CLC_LAUNCH(ctx, "k_prolong_smooth", (k_oct_prolong_smooth<N, kOctPartsPS>), dim3(N / OB::BR, 1, s->npatch),
+               dim3(OB::NT), smb, (const float*)U2(l), (float*)U(l), (const float*)F(l), (const float*)C(l),
+               (const float*)D(l), (const float*)G(l), (const float*)U(l + 1), ctx->d_err);
+  }
   bool use_reg(int n, int nu) const { return kF32 && nu == 2 && (n == 128 || n == 256); }
 
   void smooth_restrict(int l, bool zero) {
     const int n = s->sizes[l], nu = s->p.nu1;
     if (use_reg(n, nu)) {
-      if (n == 128) reg_smooth_restrict<128>(l, zero);
-      else reg_smooth_restrict<256>(l, zero);
+      if (kOctSR && n == 256) {
+        oct_smooth_restrict<256>(l, zero);
+      } else {
+        if (n == 128) reg_smooth_restrict<128>(l, zero);
+        else reg_smooth_restrict<256>(l, zero);
+      }
       return;
     }
     const size_t smb = band_smem<T>(n, 2 * nu + 1);
@@ -2035,8 +2396,12 @@ struct MG {
   void prolong_smooth(int l) {
     const int n = s->sizes[l], nu = s->p.nu2;
     if (use_reg(n, nu)) {
-      if (n == 128) reg_prolong_smooth<128>(l);
-      else reg_prolong_smooth<256>(l);
+      if (kOctPS && n == 256) {
+        oct_prolong_smooth<256>(l);
+      } else {
+        if (n == 128) reg_prolong_smooth<128>(l);
+        else reg_prolong_smooth<256>(l);
+      }
       return;
     }
     const int wcb = ((n < kBandRows ? n : kBandRows) + 4 * nu) / 2 + 2;
