@@ -240,7 +240,7 @@ def band_floor(cfg):
 # first V-cycle).  Traffic grows with the number of patches, so a launch at
 # another patch count moves (this x patches / 3) bytes on average.
 BAND_DRAM_PER_PATCH_CYCLE = {
-    "k_prolong_smooth": (0.0329 + 0.1283 + 0.0182 + 0.4880 + 0.1711) * 1e9 / 768,
+    "k_prolong_smooth": (0.0329 + 0.1283 + 0.0182 + 0.4107 + 0.1685) * 1e9 / 768,
 }
 
 
