@@ -1932,7 +1932,7 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
 // pair: every e + d is formed once, kept for the rows above and below in
 // registers, and handed to the horizontal neighbours by warp shuffles; the
 // sums use ff_add_lite.  Every load and store of a warp is contiguous.
-constexpr int kWalk = 16;
+constexpr int kWalk = 32;
 
 __global__ void __launch_bounds__(kBX * kBY) k_resid_ff_walk(const float2* __restrict__ e_old,
                                                               const float* __restrict__ d,
