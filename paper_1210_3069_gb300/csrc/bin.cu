@@ -17,11 +17,29 @@ __global__ void k_bin(const double* __restrict__ z, const double* __restrict__ p
 }
 
 // kappa = scale * (counts / nbar - 1), each operation rounded separately
+// kappa of a pixel with c particles: scale (c / nbar - 1), each operation
+// correctly rounded
+__device__ __forceinline__ double kappa_of(uint32_t c, double nbar, double scale) {
+  return __dmul_rn(scale, __dsub_rn(__ddiv_rn((double)c, nbar), 1.0));
+}
+
+// Counts are small integers, so kappa takes few distinct values: a table of
+// the first kKappaTable (the same correctly rounded operations, once per
+// count) replaces the FP64 division per pixel, which would make this pass
+// FP64-bound; larger counts divide.
+constexpr int kKappaTable = 4096;
+
+__global__ void k_kappa_table(double nbar, double scale, double* __restrict__ tab) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < kKappaTable) tab[c] = kappa_of((uint32_t)c, nbar, scale);
+}
+
 __global__ void k_counts_to_kappa(const uint32_t* __restrict__ counts, int64_t npix, double nbar,
-                                  double scale, double* __restrict__ kappa) {
+                                  double scale, const double* __restrict__ tab, double* __restrict__ kappa) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < npix; i += stride) {
-    kappa[i] = __dmul_rn(scale, __dsub_rn(__ddiv_rn((double)counts[i], nbar), 1.0));
+    const uint32_t c = counts[i];
+    kappa[i] = c < (uint32_t)kKappaTable ? tab[c] : kappa_of(c, nbar, scale);
   }
 }
 
@@ -230,7 +248,11 @@ extern "C" int clc_counts_to_kappa(clc_ctx* ctx, const uint32_t* counts, int nsi
   if (!counts || !kappa) return set_err(ctx, CLC_EINVAL, "clc_counts_to_kappa: null pointer");
   cudaSetDevice(ctx->device);
   const int64_t npix = 12ll * nside * nside;
-  CLC_LAUNCH(ctx, "k_counts_to_kappa", k_counts_to_kappa, grid_for(ctx, npix, 256), 256, 0, counts, npix, nbar, scale, kappa);
+  double* tab = (double*)scratch(ctx, 7, sizeof(double) * kKappaTable);
+  if (!tab) return CLC_ENOMEM;
+  CLC_LAUNCH(ctx, "k_counts_to_kappa", k_kappa_table, kKappaTable / 256, 256, 0, nbar, scale, tab);
+  CLC_LAUNCH(ctx, "k_counts_to_kappa", k_counts_to_kappa, grid_for(ctx, npix, 256), 256, 0, counts, npix, nbar, scale,
+             (const double*)tab, kappa);
   return launch_check(ctx, "k_counts_to_kappa");
 }
 
