@@ -1904,13 +1904,9 @@ __global__ void k_resnorm(const T* __restrict__ u, const T* __restrict__ f, cons
   if (threadIdx.x == 0 && rr != 0.0) atomicAdd(norms + b, rr);
 }
 
-__global__ void k_max_ratio(const double* __restrict__ rr, const double* __restrict__ ff, int npatch,
-                            double* __restrict__ out) {
-  double mx = 0.0;
-  for (int b = threadIdx.x; b < npatch; b += blockDim.x) {
-    const double fn = sqrt(ff[b]);
-    mx = fmax(mx, sqrt(rr[b]) / (fn > 0 ? fn : 1.0));
-  }
+// Block maximum of non-negative doubles (NaN ignored, as fmax does) folded
+// into *out, which starts at 0: non-negative doubles order like their bits.
+__device__ __forceinline__ void block_max_into(double mx, double* out) {
   __shared__ double s[32];
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
@@ -1918,8 +1914,21 @@ __global__ void k_max_ratio(const double* __restrict__ rr, const double* __restr
   if (threadIdx.x < 32) {
     mx = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) out[0] = mx;
+    if (threadIdx.x == 0 && mx > 0.0)
+      atomicMax(reinterpret_cast<unsigned long long*>(out), (unsigned long long)__double_as_longlong(mx));
   }
+}
+
+// max over patches of ||r|| / ||f|| (one patch per thread, *out zeroed first)
+__global__ void k_max_ratio(const double* __restrict__ rr, const double* __restrict__ ff, int npatch,
+                            double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (b < npatch) {
+    const double fn = sqrt(ff[b]);
+    mx = fmax(mx, sqrt(rr[b]) / (fn > 0 ? fn : 1.0));
+  }
+  block_max_into(mx, out);
 }
 
 // Mixed refinement step, fused: e_new = e_old + d (d = the last FP32
@@ -2258,21 +2267,14 @@ __global__ void k_tau_norm(int n, const double* __restrict__ base, const E* __re
 // cells against (n/2)^2 coarse ones)
 __global__ void k_max_ratio_tau(const double* __restrict__ rr, const double* __restrict__ t2, int npatch,
                                 double* __restrict__ out) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
   double mx = 0.0;
-  for (int b = threadIdx.x; b < npatch; b += blockDim.x) {
+  if (b < npatch) {
     const double r = rr[b], t = t2[b];
     const double q = t > 0.0 ? 0.5 * sqrt(r / t) : (r > 0.0 ? HUGE_VAL : 0.0);
     mx = fmax(mx, q);
   }
-  __shared__ double s[32];
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    mx = threadIdx.x < (blockDim.x >> 5) ? s[threadIdx.x] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (threadIdx.x == 0) out[0] = mx;
-  }
+  block_max_into(mx, out);
 }
 
 template <typename T>
@@ -2482,7 +2484,9 @@ struct MG {
   void stop_ratio(const E* e, bool tau) {
     const int n = s->sizes[0];
     if (!tau) {
-      CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->fnorm.p,
+      cudaMemsetAsync(s->ratio.p, 0, sizeof(double), ctx->stream);
+      CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio, (s->npatch + 255) / 256, 256, 0, (const double*)s->norms.p,
+                 (const double*)s->fnorm.p,
                  s->npatch, (double*)s->ratio.p);
       return;
     }
@@ -2490,7 +2494,9 @@ struct MG {
     CLC_LAUNCH(ctx, "k_tau_norm", k_tau_norm<E>, grid3(n / 2, n / 2, s->npatch), dim3(kBX, kBY), 0, n,
                (const double*)s->base.p, e, C64(0), G64(0), C64(1), G64(1), (const double*)s->rden[0].p,
                (const double*)s->gc.p, (double*)s->tau2.p);
-    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio_tau, 1, 1024, 0, (const double*)s->norms.p, (const double*)s->tau2.p,
+    cudaMemsetAsync(s->ratio.p, 0, sizeof(double), ctx->stream);
+    CLC_LAUNCH(ctx, "k_max_ratio", k_max_ratio_tau, (s->npatch + 255) / 256, 256, 0, (const double*)s->norms.p,
+               (const double*)s->tau2.p,
                s->npatch, (double*)s->ratio.p);
   }
 
